@@ -1,0 +1,152 @@
+"""Element and node orderings (integer results, bit-exact).
+
+Test infrastructure only (see the package docstring).
+
+Permutations are returned as `order` arrays: order[new] = old id. The library
+exports the inverse maps (new id of each old id); ``inverse`` converts.
+
+* ``hilbert_element_order`` -- Section 4.3, reordering steps 1-4: element
+  centroids are mapped to the cells of a W x H grid laid over the mesh's
+  bounding box, the cells are walked along the generalized Hilbert curve and
+  the elements of each visited cell are appended to the list L. Readings of
+  the garbled/open points: the "subrectangle width w_s = w_b / w_m" is a scale
+  (cells per unit length), W = ceil(sqrt(n_e)) as an integer, H = max(1,
+  ceil(W / r)) with r = w_m / h_m; centroid = ((x0 + x1) + (x2 + x3)) * 0.25;
+  cell ix = min(W - 1, floor(((xc - x_min) * W) / w_m)) (iy likewise with H,
+  h_m), all in FP64 without fused multiply-add; elements sharing a cell keep
+  ascending input id; empty cells are skipped.
+* ``renumber_nodes`` -- Section 4.3, node procedure: walk the elements in their
+  new order, collect each element's not-yet-seen nodes N^(e) (in local index
+  order), sort N^(e) by ascending degree (stable, so ties keep local index
+  order) and append. Reading: the degree of a node is the number of distinct
+  other nodes that share at least one element with it.
+* ``random_order`` -- Fisher-Yates driven by splitmix64: for i = n-1 down to 1,
+  j = next() mod (i + 1), swap a[i], a[j]; elements use stream seed+2 and
+  nodes stream seed+3 (independently).
+* ``orderings(kind)`` -- NONE: identity for both; ROWMAJOR: input element
+  order with nodes renumbered as above; RANDOM: random elements and random
+  nodes; HILBERT: the curve order with nodes renumbered as above.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import hilbert as _hilbert
+
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int):
+    """Generator of splitmix64 outputs (Steele, Lea & Flood 2014)."""
+    s = seed & MASK64
+    while True:
+        s = (s + 0x9E3779B97F4A7C15) & MASK64
+        z = s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        yield z ^ (z >> 31)
+
+
+def random_order(n: int, seed: int) -> np.ndarray:
+    a = list(range(n))
+    g = splitmix64(seed)
+    for i in range(n - 1, 0, -1):
+        j = next(g) % (i + 1)
+        a[i], a[j] = a[j], a[i]
+    return np.array(a, dtype=np.int64)
+
+
+def inverse(order: np.ndarray) -> np.ndarray:
+    inv = np.empty_like(order)
+    inv[order] = np.arange(order.size, dtype=order.dtype)
+    return inv
+
+
+def isqrt_ceil(n: int) -> int:
+    r = math.isqrt(n)
+    return r if r * r == n else r + 1
+
+
+def hilbert_grid(coords: np.ndarray, quads: np.ndarray):
+    """Return (W, H, ix[E], iy[E]): the curve grid and each element's cell."""
+    coords = np.asarray(coords, dtype=np.float64)
+    quads = np.asarray(quads, dtype=np.int64)
+    E = quads.shape[0]
+    xmin, ymin = coords[:, 0].min(), coords[:, 1].min()
+    wm = coords[:, 0].max() - xmin
+    hm = coords[:, 1].max() - ymin
+    W = isqrt_ceil(E)
+    r = wm / hm
+    H = max(1, math.ceil(W / r))
+    c = coords[quads]                                     # (E, 4, 2)
+    xc = ((c[:, 0, 0] + c[:, 1, 0]) + (c[:, 2, 0] + c[:, 3, 0])) * 0.25
+    yc = ((c[:, 0, 1] + c[:, 1, 1]) + (c[:, 2, 1] + c[:, 3, 1])) * 0.25
+    ix = np.minimum(W - 1, np.floor(((xc - xmin) * float(W)) / wm).astype(np.int64))
+    iy = np.minimum(H - 1, np.floor(((yc - ymin) * float(H)) / hm).astype(np.int64))
+    return W, H, np.maximum(ix, 0), np.maximum(iy, 0)
+
+
+def hilbert_element_order(coords, quads) -> np.ndarray:
+    """The list L of Section 4.3 as order[new] = old element id."""
+    W, H, ix, iy = hilbert_grid(coords, quads)
+    rank = _hilbert.rank_grid(W, H)
+    key = rank[ix, iy]
+    return np.argsort(key, kind="stable").astype(np.int64)   # ties: ascending input id
+
+
+def node_degrees(conn: np.ndarray, n_nodes: int) -> np.ndarray:
+    """Number of distinct other nodes sharing an element with each node."""
+    E, P = conn.shape
+    A = sp.csr_matrix((np.ones(E * P, dtype=np.int8), (np.repeat(np.arange(E), P), conn.ravel())),
+                      shape=(E, n_nodes))
+    C = (A.T.astype(np.int32) @ A.astype(np.int32)).tocsr()
+    return np.diff(C.indptr).astype(np.int64) - 1
+
+
+def renumber_nodes_loop(conn, elem_order, degree) -> np.ndarray:
+    """The node procedure of Section 4.3 as a plain loop (small meshes)."""
+    seen = np.zeros(int(conn.max()) + 1, dtype=bool)
+    out = []
+    for e in elem_order:
+        group = []
+        for v in conn[e]:
+            if not seen[v]:
+                seen[v] = True
+                group.append(int(v))
+        group.sort(key=lambda v: degree[v])               # stable
+        out.extend(group)
+    return np.array(out, dtype=np.int64)
+
+
+def renumber_nodes(conn, elem_order, degree) -> np.ndarray:
+    """Same result as `renumber_nodes_loop`, by sorting on (first-touching
+    element position, degree, local index of the first touch)."""
+    P = conn.shape[1]
+    seq = conn[elem_order].ravel()
+    nodes, first = np.unique(seq, return_index=True)
+    group = first // P
+    local = first % P
+    idx = np.lexsort((local, degree[nodes], group))
+    return nodes[idx].astype(np.int64)
+
+
+def orderings(kind: str, coords, quads, conn, n_nodes, seed: int = 2104084160, degree=None):
+    """(elem_order, node_order) for kind in none/rowmajor/random/hilbert."""
+    E = conn.shape[0]
+    kind = kind.lower()
+    if kind == "none":
+        return np.arange(E, dtype=np.int64), np.arange(n_nodes, dtype=np.int64)
+    if kind == "random":
+        return random_order(E, seed + 2), random_order(n_nodes, seed + 3)
+    if kind == "rowmajor":
+        eo = np.arange(E, dtype=np.int64)
+    elif kind == "hilbert":
+        eo = hilbert_element_order(coords, quads)
+    else:
+        raise ValueError(kind)
+    if degree is None:
+        degree = node_degrees(conn, n_nodes)
+    return eo, renumber_nodes(conn, eo, degree)
