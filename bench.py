@@ -1,0 +1,365 @@
+"""Throughput of the spectral-element time step on GB300.
+
+One "step" is one leapfrog time step of the whole hot path over the mesh:
+gather, GLL gradient, metric, transposed contraction, deterministic
+assembly, inverse mass, source, Kahan-compensated update and receiver traces.
+Workload (default): the graded heterogeneous mesh, 512 x 512 quads on the
+unit square, widths graded 8x toward (0,0), interior vertices perturbed by up
+to 20% of the local width, order 4 (4,198,401 GLL nodes), c ~ U[1,3] per
+element, Ricker f0 = 10 at the centre, dt = 0.3 CFL, 2000 steps, Hilbert
+ordering, FP32 bulk with the Kahan leapfrog and FP64 precompute/traces.
+
+Metric: GLL node-updates/s = nodes x steps / time (higher is better).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (its own shot; weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "GLL node-updates/s (order 4)"
+UNIT = "node-updates/s"
+WORKLOAD = "graded_512x512_p4"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32_kahan", choices=["fp32_kahan", "fp64", "fp32"])
+    ap.add_argument("--ordering", default="hilbert", choices=["hilbert", "rowmajor", "random", "none"])
+    ap.add_argument("--n", type=int, default=512, help="quads per side of the graded mesh")
+    ap.add_argument("--no-compare", action="store_true", help="skip the per-ordering comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eb", type=int, default=0, help="elements per block (0 = library default)")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(n, rank=0):
+    m = gen.graded(n)
+    # replicas: each rank shoots from its own source position
+    if rank:
+        g = gen.SplitMix64(gen.DEFAULT_SEED + 100 + rank)
+        m["src_xy"] = (0.25 + 0.5 * g.uniform(), 0.25 + 0.5 * g.uniform())
+    return m
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        try:
+            with open(self.f.name) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        return rows
+
+    @staticmethod
+    def summarize(rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_handle(P, m, precision, ordering, nsteps_cap, eb=0):
+    h = P.SEM(m["coords"], m["quads"], 4, precision)
+    h.sem_reorder(ordering)
+    h.sem_set_model(m["vel"], m["rho"])
+    if eb:
+        h.sem_set_tuning(eb)
+    h.sem_set_source(m["f0"], m["t0"], m["amp"], *m["src_xy"])
+    h.sem_set_receivers(m["receivers"], nsteps_cap)
+    h.sem_set_dt(0.3 * h.sem_cfl_dt())
+    return h
+
+
+def time_steps(torch, h, k):
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    h.sem_step(k)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def cpu_baseline(n, budget_s=12.0):
+    """Oracle (FP64 NumPy, as it stands) on the same graded mesh: a bounded
+    number of leapfrog steps after its set-up."""
+    from oracle import sem as osem
+    m = gen.graded(n)
+    S = osem.SEM(m["coords"], m["quads"], 4, m["vel"], m["rho"], validate=False)
+    _ = S.Ke
+    dt = 0.3 * S.cfl_dt()
+    src = (m["src_xy"][0], m["src_xy"][1], m["f0"], m["t0"], m["amp"])
+    S.run(1, dt, src=src)
+    k = 1
+    while True:
+        t = time.perf_counter()
+        S.run(k, dt, src=src, receivers=m["receivers"])
+        el = time.perf_counter() - t
+        if el > budget_s / 4 or k >= 64:
+            break
+        k *= 2
+    return S.n_nodes * k / el, k, S.n_nodes
+
+
+def threads_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 CPU oracle timed on the host cores; each of
+    the K steps is one leapfrog step of the oracle on a graded mesh of the
+    same family sized so that the whole run ends within a few minutes."""
+    if rank != 0:
+        return
+    from oracle import sem as osem
+    budget = 120.0
+    per_step = budget / max(1, args.steps + args.warmup)
+    # oracle speed on this host is roughly 6e6 node-updates/s; pick the side
+    nodes = max(2000.0, per_step * 6e6)
+    n = int(max(8, min(args.n, (nodes ** 0.5 - 1) / 4)))
+    m = gen.graded(n)
+    S = osem.SEM(m["coords"], m["quads"], 4, m["vel"], m["rho"], validate=False)
+    _ = S.Ke
+    dt = 0.3 * S.cfl_dt()
+    src = (m["src_xy"][0], m["src_xy"][1], m["f0"], m["t0"], m["amp"])
+    S.run(args.warmup, dt, src=src)
+    t = time.perf_counter()
+    S.run(args.steps, dt, src=src, receivers=m["receivers"])
+    el = time.perf_counter() - t
+    v = S.n_nodes * args.steps / el
+    sample = f"graded_{n}x{n}_p4 ({S.n_nodes} nodes), {args.steps} leapfrog steps of the FP64 NumPy oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2104_08416_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2104_08416_gb300 as P
+    P.load()
+    P.sem_set_allocator_torch()
+
+    K, W = args.steps, args.warmup
+    m = workload(args.n, rank)
+    cap = W + 2 * K + 8
+    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb)
+    N = h.n_nodes
+    # warm-up (the first call builds the device data)
+    h.sem_step(W)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.2)
+    # timed region: K steps, barrier + sync on both sides
+    if world > 1:
+        dist.barrier()
+    el = time_steps(torch, h, K)
+    if world > 1:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    # second pass with per-kernel events for the roofline
+    h.sem_profile_enable(True)
+    prof_el = time_steps(torch, h, K)
+    bms, bl, oms, ol = h.sem_profile_read()
+    h.sem_profile_enable(False)
+    block_bytes, open_bytes = h.sem_traffic_model()
+    launches, nopen = h.sem_launch_info()
+    time.sleep(0.2)
+    clocks = ClockSampler.summarize(sampler.stop()) if sampler else None
+    u = h.sem_read_wavefield()
+    finite = bool(np.isfinite(u).all())
+    h.sem_destroy()
+
+    # end to end through the public API with host buffers: set-up, K steps,
+    # traces and wavefield back to the host, all inside the timed region
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb)
+    h2.sem_step(K)
+    tr = h2.sem_read_traces()
+    u2 = h2.sem_read_wavefield()
+    torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - t0
+    h2d, d2h = h2.sem_transfer_bytes()
+    h2.sem_destroy()
+    if world > 1:
+        t = torch.tensor([e2e_el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_el = float(t.item())
+
+    # ordering comparison (the paper's locality claim, restated on the GPU)
+    orderings = None
+    if rank == 0 and not args.no_compare:
+        orderings = {}
+        kk = min(K, 500)
+        for kind in ("hilbert", "rowmajor", "random", "none"):
+            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb)
+            hh.sem_step(W)
+            t_ord = time_steps(torch, hh, kk)
+            hh.sem_profile_enable(True)
+            time_steps(torch, hh, kk)
+            b_ms, b_l, o_ms, o_l = hh.sem_profile_read()
+            bb, ob = hh.sem_traffic_model()
+            _, no = hh.sem_launch_info()
+            hh.sem_destroy()
+            orderings[kind] = {"node_updates_per_s": N * kk / t_ord, "ms_per_step": 1e3 * t_ord / kk,
+                               "block_kernel_us": 1e3 * b_ms / max(b_l, 1), "open_kernel_us": 1e3 * o_ms / max(o_l, 1),
+                               "open_nodes": no, "block_bytes": bb, "open_bytes": ob}
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, k, nn = cpu_baseline(args.n)
+        cpu = {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+               "sample": f"{k} leapfrog steps of the FP64 NumPy oracle on the full {WORKLOAD} mesh ({nn} nodes), "
+                         "set-up excluded"}
+
+    peak, peak_kind = read_peaks()
+    blk_us = 1e3 * bms / max(bl, 1)
+    achieved = block_bytes / (blk_us * 1e-6) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "block_kernel_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            if tj.get("workload") == WORKLOAD and tj.get("precision") == args.precision:
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    value = world * N * K / el
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32_kahan": "f32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "elements": m["quads"].shape[0], "order": 4,
+                   "precision": args.precision, "ordering": args.ordering,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
+                   "finite": finite},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "sem_block_kernel", "peak_kind": peak_kind,
+                     "block_kernel_us": blk_us, "open_kernel_us": 1e3 * oms / max(ol, 1),
+                     "block_bytes_per_launch": block_bytes, "open_bytes_per_launch": open_bytes,
+                     "open_nodes": nopen, "profiled_ms_per_step": 1e3 * prof_el / K},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * N * K / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+                "d2h_bytes_per_step": d2h / K, "includes": "mesh set-up, reordering, precompute, K steps, read-back"},
+        "gpu_launches": int(launches * K),
+        "clocks": clocks,
+        "orderings": orderings,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

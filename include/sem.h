@@ -1,0 +1,256 @@
+/*
+ * sem.h -- C ABI of the GB300 spectral-element wave stepper.
+ *
+ * The library advances the 2D acoustic wave equation (Section 4.1,
+ * Eqs. def_v_1 and def_u_1, eliminated to the scalar second-order form
+ * (1/K) u_tt = div((1/rho) grad u) + f with K = rho c^2 and natural Neumann
+ * boundaries from the weak form, Eq. def_weak_u) on an unstructured mesh of
+ * quadrilaterals with a tensor-product Gauss-Lobatto-Legendre (GLL) nodal
+ * basis whose nodes double as quadrature points (Section 4.2,
+ * Eq. numerical_integ). One time step is:
+ *   gather U_mu(q,e) per element (Section 4.2, the U_2 gather of Algorithm 1),
+ *   reference gradient and per-point metric G_q = w_q |J_q| rho_e^-1 J_q^-1 J_q^-T
+ *   (Eq. deriv_u with K^(e) = J^-1), transposed derivative contraction and
+ *   assembly into global nodes (Eq. u_change_r_effic), the lumped inverse mass
+ *   (Eq. Abar with M = 1/K) and point source (Algorithm 3), then an explicit
+ *   leapfrog update, u^{n+1} = 2u^n - u^{n-1} + dt^2 M^-1 (f(t_n) e_s - K u^n).
+ * Elements and nodes are stored in an order chosen by sem_reorder; the
+ * Hilbert ordering is the memory reordering of Section 4.3.
+ *
+ * Conventions for every call:
+ *  - All calls return sem_status and never throw. NULL handle or pointer
+ *    arguments return SEM_ERR_INVALID_ARG. sem_last_error() gives a
+ *    human-readable message for the last failing call on a handle.
+ *  - Arrays passed by the caller are HOST arrays (plain C memory) unless the
+ *    argument name says "dev_". They are copied; the caller keeps ownership.
+ *  - User-facing arrays use the ORIGINAL numbering: vertex/element ids as
+ *    passed to sem_mesh_create, and the canonical global node numbering
+ *    defined below. Permutations are applied and undone inside the library.
+ *  - The library owns all device memory of a handle (allocated through
+ *    sem_set_allocator's callbacks when set, else cudaMalloc) and frees it
+ *    in sem_destroy. A handle is not thread-safe; use one per thread.
+ *  - Device work is enqueued on the stream given to sem_mesh_create
+ *    (NULL = legacy default stream). Calls that return data to the host
+ *    synchronise that stream.
+ *
+ * Canonical global node numbering (the paper adds SEM nodes to its meshes in
+ * memory without fixing their labels; this library fixes one). Local point
+ * (i, j), i, j in 0..p, has local index j*(p+1) + i; xi runs from corner 0 to
+ * corner 1 and eta from corner 0 to corner 3 (corners counter-clockwise).
+ * Global ids: first the mesh vertices in input order; then the p-1 interior
+ * nodes of each edge, edges in order of first appearance when scanning
+ * elements 0..E-1 over local edges (c0c1, c1c2, c2c3, c3c0), each edge's
+ * nodes ordered from its lower vertex id to its higher one; then the (p-1)^2
+ * interior nodes of each element, elements ascending, i fastest.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SEM_OK = 0,
+    SEM_ERR_INVALID_ARG = 1,  /* bad pointer, size, index, mesh or value      */
+    SEM_ERR_STATE = 2,        /* call out of order (e.g. reorder after a step) */
+    SEM_ERR_CUDA = 3,         /* a CUDA runtime call failed                    */
+    SEM_ERR_OOM = 4,          /* device or host allocation failed              */
+    SEM_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                 */
+    SEM_ERR_UNSUPPORTED = 6   /* order or option not built into this library   */
+} sem_status;
+
+typedef enum {
+    SEM_FP64 = 0,        /* FP64 storage and arithmetic, three-level leapfrog    */
+    SEM_FP32_KAHAN = 1,  /* FP32 bulk; increment-form leapfrog with a Kahan-
+                            compensated accumulation of u; FP64 precompute      */
+    SEM_FP32 = 2         /* FP32 bulk, plain three-level leapfrog (no Kahan)    */
+} sem_precision;
+
+typedef enum {
+    SEM_ORDER_NONE = 0,     /* input order for elements and nodes ("No Strategy",
+                               Section 6.1)                                      */
+    SEM_ORDER_ROWMAJOR = 1, /* input element order; nodes renumbered by the
+                               node procedure of Section 4.3                     */
+    SEM_ORDER_RANDOM = 2,   /* Fisher-Yates shuffles of elements (splitmix64
+                               stream seed+2) and of nodes (stream seed+3)       */
+    SEM_ORDER_HILBERT = 3   /* Section 4.3: elements along a generalized Hilbert
+                               curve over the centroid grid, nodes renumbered by
+                               first touch, ascending degree                     */
+} sem_ordering;
+
+typedef enum { SEM_SRC_RICKER = 0 } sem_source_kind;
+
+typedef struct sem_mesh sem_mesh;
+
+/* Optional device allocator (e.g. a framework's caching allocator). alloc
+ * returns a device pointer of at least `bytes` bytes usable on `stream`, or
+ * NULL on failure; free releases it. Applies to handles created afterwards
+ * in this process. Pass NULLs to restore cudaMalloc/cudaFree. */
+typedef void* (*sem_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*sem_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+sem_status sem_set_allocator(sem_alloc_fn alloc, sem_free_fn free_fn, void* ctx);
+
+/* Create a mesh handle (Section 4.2: unstructured mesh of non-overlapping
+ * elements, each mapped from the reference element; here bilinear quads).
+ *   coords [nv][2]  vertex coordinates (x, y), FP64.
+ *   quads  [ne][4]  vertex ids of each quad, counter-clockwise.
+ *   order           polynomial order p, 1..8 (p+1 GLL points per direction).
+ *   prec            arithmetic of the time loop (see sem_precision).
+ *   cuda_stream     cudaStream_t to enqueue work on (NULL = default stream).
+ * Validation (SEM_ERR_INVALID_ARG): nv, ne > 0; indices in [0, nv); every
+ * vertex referenced; no edge shared by more than two quads; the Jacobian
+ * determinant positive at every GLL point (clockwise or degenerate quads are
+ * rejected). The ordering starts as SEM_ORDER_NONE. */
+sem_status sem_mesh_create(const double* coords, int64_t nv, const int32_t* quads, int64_t ne,
+                           int order, sem_precision prec, void* cuda_stream, sem_mesh** out);
+
+/* Choose the memory ordering of elements and nodes (Section 4.3 for HILBERT).
+ * Must precede the first sem_step / sem_set_state / sem_apply_stiffness
+ * (else SEM_ERR_STATE). `seed` is used by SEM_ORDER_RANDOM only. */
+sem_status sem_reorder(sem_mesh* m, sem_ordering kind, uint64_t seed);
+
+/* Per-element material (Section 4.1: rho and K = rho c^2, constant per
+ * element as assumed before Eq. u_change). vel[ne] > 0 (wave speed c);
+ * rho[ne] > 0, or NULL for rho = 1. Original element order. Before the first
+ * step only. */
+sem_status sem_set_model(sem_mesh* m, const double* vel, const double* rho);
+
+/* Point source (Eq. def_u_2 source term; Algorithm 3): a Ricker wavelet
+ * amp (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2) at t_n = n dt,
+ * added to the global node nearest to (x, y) (Euclidean distance; ties to the
+ * lowest original node id), scaled by the inverse lumped mass. f0 > 0.
+ * Before the first step only. */
+sem_status sem_set_source(sem_mesh* m, int kind, double f0, double t0, double amp, double x,
+                          double y);
+
+/* Receivers: xy[nrec][2] positions, each snapped like the source. Traces of
+ * u at those nodes are recorded in FP64 after every step, for up to
+ * max_steps steps (sem_step returns SEM_ERR_INVALID_ARG beyond that).
+ * nrec = 0 removes them. Before the first step only. */
+sem_status sem_set_receivers(sem_mesh* m, const double* xy, int32_t nrec, int64_t max_steps);
+
+/* dt_cfl = min over elements of (the shortest distance between GLL points
+ * adjacent along a local grid line) / c_e. The paper only says its step
+ * meets the CFL condition (Section 6.2); this is the definition used here.
+ * Needs the model. */
+sem_status sem_cfl_dt(const sem_mesh* m, double* dt_cfl);
+
+/* Time step dt > 0 (values above sem_cfl_dt are accepted; stability is the
+ * caller's business). Before the first step only. */
+sem_status sem_set_dt(sem_mesh* m, double dt);
+
+/* Advance nsteps >= 0 leapfrog steps from the current state (u^0 = u^-1 = 0
+ * unless sem_set_state was called; Eq. initial_cond). Asynchronous on the
+ * handle's stream. The first call builds the device data (allocation and
+ * host-to-device copies). Needs the model and dt. */
+sem_status sem_step(sem_mesh* m, int64_t nsteps);
+
+/* Number of steps taken so far. */
+sem_status sem_get_step(const sem_mesh* m, int64_t* step);
+
+/* Copy traces to out[nrec][cap]: out[r*cap + k] = u at receiver r after step
+ * k+1, for k < min(cap, steps taken). Synchronises the stream. */
+sem_status sem_read_traces(sem_mesh* m, double* out, int64_t cap);
+
+/* u^n at every global node, original node order, as FP64. Synchronises. */
+sem_status sem_read_wavefield(sem_mesh* m, double* u);
+
+/* Set (u^n, u^{n-1}) in original node order and the step counter n (which
+ * sets t_n = n dt for the source). In FP32 modes the values are rounded to
+ * FP32 once (SEM_FP32_KAHAN stores u and delta = u^n - u^{n-1}, computed in
+ * FP64). Builds the device data if needed. Needs the model and dt. */
+sem_status sem_set_state(sem_mesh* m, const double* u, const double* u_prev, int64_t step);
+
+/* Read (u^n, u^{n-1}) back in original node order (either pointer may be
+ * NULL). Synchronises. */
+sem_status sem_get_state(sem_mesh* m, double* u, double* u_prev, int64_t* step);
+
+/* Matrix-free stiffness application Ku = K u (Eq. u_change_r_effic in the
+ * second-order form) with the handle's precision, on host arrays in original
+ * node order (u[N] in, Ku[N] out). Does not change the time-stepping state.
+ * Synchronises. Needs the model. */
+sem_status sem_apply_stiffness(sem_mesh* m, const double* u, double* Ku);
+
+/* Lumped diagonal mass M_nu = sum over (e, q) with mu(q, e) = nu of
+ * w_q |J_q| / (rho_e c_e^2) (Eq. Abar with M = 1/K), computed in FP64 on the
+ * device, original node order. Synchronises. Needs the model. */
+sem_status sem_read_mass(sem_mesh* m, double* mass);
+
+/* Permutations chosen by sem_reorder: elem_new_of_old[ne] and
+ * node_new_of_old[N] (either may be NULL). */
+sem_status sem_get_permutation(const sem_mesh* m, int64_t* elem_new_of_old,
+                               int64_t* node_new_of_old);
+
+/* Global node count N and element count E. */
+sem_status sem_get_sizes(const sem_mesh* m, int64_t* n_nodes, int64_t* n_elems);
+
+/* Positions of the global nodes, original order, out[N][2]. */
+sem_status sem_node_coordinates(const sem_mesh* m, double* xy);
+
+/* Indices (original numbering) of the source node and receiver nodes
+ * (either pointer may be NULL; rec must hold nrec entries). */
+sem_status sem_get_snapped(const sem_mesh* m, int64_t* src_node, int64_t* rec_nodes);
+
+/* Host-only ordering computation, no device needed: the element and node
+ * orderings sem_reorder would choose for this mesh, as order arrays
+ * (elem_order[new] = old element id, node_order[new] = old node id). Same
+ * validation as sem_mesh_create. n_nodes_out receives N (may be NULL);
+ * node_order must hold N entries, computable as sem_count_nodes. */
+sem_status sem_compute_ordering(const double* coords, int64_t nv, const int32_t* quads, int64_t ne,
+                                int order, sem_ordering kind, uint64_t seed, int64_t* elem_order,
+                                int64_t* node_order);
+
+/* Global node count of a mesh at polynomial order `order`, host only. */
+sem_status sem_count_nodes(const int32_t* quads, int64_t nv, int64_t ne, int order,
+                           int64_t* n_nodes);
+
+/* Generalized Hilbert curve over a W x H cell grid (Section 3, after
+ * Cerveny 2020; equals Listing 1's curve when W = H = 2^a): cells[k] =
+ * (x, y) of the k-th visited cell, out cells[W*H][2]. Host only. */
+sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells);
+
+/* Launch accounting of the time loop: kernel launches per step (the block
+ * kernel and the open-node kernel) and the number of open nodes, i.e. nodes
+ * whose elements span more than one element block and are finished by the
+ * open-node kernel (-1 before the device data is built). Either pointer may
+ * be NULL. */
+sem_status sem_launch_info(const sem_mesh* m, int64_t* launches_per_step, int64_t* open_nodes);
+
+/* Elements per block of the block kernel (0 = default, about 1600 element
+ * points per block). Before the device data is built. elems_per_block *
+ * (order+1)^2 must not exceed 65535. */
+sem_status sem_set_tuning(sem_mesh* m, int elems_per_block);
+
+/* Per-kernel device timing for measurement. While enabled, sem_step records
+ * CUDA events on the handle's stream around every block-kernel and
+ * open-kernel launch. sem_profile_read synchronises the stream and returns
+ * the summed durations (milliseconds) and launch counts since the last read,
+ * then resets them. Any output pointer may be NULL. */
+sem_status sem_profile_enable(sem_mesh* m, int enable);
+sem_status sem_profile_read(sem_mesh* m, double* block_ms, int64_t* block_launches, double* open_ms,
+                            int64_t* open_launches);
+
+/* Compulsory DRAM bytes of one launch of each time-loop kernel under the
+ * current plan and precision: every array the launch touches counted once
+ * (per-slot entry indices and local node lists, per-element geometry, per-node
+ * state read and written, partial sums). Needs the device data (after the
+ * first sem_step). Either pointer may be NULL. */
+sem_status sem_traffic_model(const sem_mesh* m, double* block_bytes, double* open_bytes);
+
+/* Host<->device bytes this handle's calls have copied so far. */
+sem_status sem_transfer_bytes(const sem_mesh* m, int64_t* h2d, int64_t* d2h);
+
+/* Message of the last failing call on this handle ("" if none). Never NULL. */
+const char* sem_last_error(const sem_mesh* m);
+
+/* Free the handle and all its device memory. NULL is a no-op. */
+void sem_destroy(sem_mesh* m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_H */

@@ -1,0 +1,348 @@
+"""Python binding of the GB300 spectral-element wave stepper (libsem.so).
+
+Argument marshalling only: every step of the time loop runs in the CUDA
+kernels behind the C ABI declared in include/sem.h, and the functions here
+carry the same names as the C calls. PyTorch provides the device memory
+(through its caching allocator, installed with ``sem_set_allocator``) and the
+CUDA stream the library enqueues on.
+
+The library is built in-tree (``paper_2104_08416_gb300/libsem.so``) by
+``paper_2104_08416_gb300.build.build()``. If it is missing, ``load()`` raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsem.so")
+
+SEM_OK, SEM_ERR_INVALID_ARG, SEM_ERR_STATE, SEM_ERR_CUDA, SEM_ERR_OOM, SEM_ERR_TIMEOUT, SEM_ERR_UNSUPPORTED = range(7)
+SEM_FP64, SEM_FP32_KAHAN, SEM_FP32 = 0, 1, 2
+SEM_ORDER_NONE, SEM_ORDER_ROWMAJOR, SEM_ORDER_RANDOM, SEM_ORDER_HILBERT = 0, 1, 2, 3
+SEM_SRC_RICKER = 0
+PRECISIONS = {"fp64": SEM_FP64, "fp32_kahan": SEM_FP32_KAHAN, "fp32": SEM_FP32}
+ORDERINGS = {"none": SEM_ORDER_NONE, "rowmajor": SEM_ORDER_ROWMAJOR, "random": SEM_ORDER_RANDOM,
+             "hilbert": SEM_ORDER_HILBERT}
+DEFAULT_SEED = 2104084160
+
+# every symbol include/sem.h declares
+EXPORTS = (
+    "sem_set_allocator", "sem_mesh_create", "sem_reorder", "sem_set_model", "sem_set_source",
+    "sem_set_receivers", "sem_cfl_dt", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
+    "sem_read_wavefield", "sem_set_state", "sem_get_state", "sem_apply_stiffness", "sem_read_mass",
+    "sem_get_permutation", "sem_get_sizes", "sem_node_coordinates", "sem_get_snapped",
+    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_launch_info", "sem_set_tuning",
+    "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
+    "sem_last_error", "sem_destroy",
+)
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I64 = C.POINTER(C.c_int64)
+_I32 = C.POINTER(C.c_int32)
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class SemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sem status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libsem.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: run paper_2104_08416_gb300.build.build() first")
+    lib = C.CDLL(path)
+    sig = {
+        "sem_set_allocator": (_ALLOC, _FREE, _P),
+        "sem_mesh_create": (_D, C.c_int64, _I32, C.c_int64, C.c_int, C.c_int, _P, C.POINTER(_P)),
+        "sem_reorder": (_P, C.c_int, C.c_uint64),
+        "sem_set_model": (_P, _D, _D),
+        "sem_set_source": (_P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double),
+        "sem_set_receivers": (_P, _D, C.c_int32, C.c_int64),
+        "sem_cfl_dt": (_P, _D),
+        "sem_set_dt": (_P, C.c_double),
+        "sem_step": (_P, C.c_int64),
+        "sem_get_step": (_P, _I64),
+        "sem_read_traces": (_P, _D, C.c_int64),
+        "sem_read_wavefield": (_P, _D),
+        "sem_set_state": (_P, _D, _D, C.c_int64),
+        "sem_get_state": (_P, _D, _D, _I64),
+        "sem_apply_stiffness": (_P, _D, _D),
+        "sem_read_mass": (_P, _D),
+        "sem_get_permutation": (_P, _I64, _I64),
+        "sem_get_sizes": (_P, _I64, _I64),
+        "sem_node_coordinates": (_P, _D),
+        "sem_get_snapped": (_P, _I64, _I64),
+        "sem_compute_ordering": (_D, C.c_int64, _I32, C.c_int64, C.c_int, C.c_int, C.c_uint64, _I64, _I64),
+        "sem_count_nodes": (_I32, C.c_int64, C.c_int64, C.c_int, _I64),
+        "sem_hilbert_cells": (C.c_int32, C.c_int32, _I32),
+        "sem_launch_info": (_P, _I64, _I64),
+        "sem_set_tuning": (_P, C.c_int),
+        "sem_profile_enable": (_P, C.c_int),
+        "sem_profile_read": (_P, _D, _I64, _D, _I64),
+        "sem_traffic_model": (_P, _D, _D),
+        "sem_transfer_bytes": (_P, _I64, _I64),
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = list(args)
+        f.restype = C.c_int
+    lib.sem_last_error.argtypes = [_P]
+    lib.sem_last_error.restype = C.c_char_p
+    lib.sem_destroy.argtypes = [_P]
+    lib.sem_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _check(st: int, handle=None):
+    if st != SEM_OK:
+        msg = ""
+        if handle is not None and _lib is not None:
+            msg = (_lib.sem_last_error(handle) or b"").decode()
+        raise SemError(st, msg)
+
+
+# ---------------------------------------------------------------- allocator
+_torch_alloc_refs = None
+
+
+def sem_set_allocator_torch():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_alloc_refs
+    import torch
+
+    lib = load()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          stream if stream else 0))
+        except Exception:  # out of memory -> NULL, the library reports SEM_ERR_OOM
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC(_alloc), _FREE(_free)
+    _check(lib.sem_set_allocator(a, f, None))
+    _torch_alloc_refs = (a, f)
+
+
+def sem_set_allocator_default():
+    global _torch_alloc_refs
+    lib = load()
+    _check(lib.sem_set_allocator(_ALLOC(), _FREE(), None))
+    _torch_alloc_refs = None
+
+
+# ------------------------------------------------------------- host-only calls
+def sem_count_nodes(quads, nv: int, order: int) -> int:
+    lib = load()
+    q = np.ascontiguousarray(quads, dtype=np.int32)
+    n = C.c_int64()
+    _check(lib.sem_count_nodes(_ptr(q, C.c_int32), int(nv), q.shape[0], int(order), C.byref(n)))
+    return n.value
+
+
+def sem_compute_ordering(coords, quads, order: int, kind, seed: int = DEFAULT_SEED):
+    """(elem_order, node_order) with order[new] = old id; no device needed."""
+    lib = load()
+    kind = ORDERINGS[kind] if isinstance(kind, str) else int(kind)
+    c = np.ascontiguousarray(coords, dtype=np.float64)
+    q = np.ascontiguousarray(quads, dtype=np.int32)
+    nn = sem_count_nodes(q, c.shape[0], order)
+    eo = np.zeros(q.shape[0], dtype=np.int64)
+    no = np.zeros(nn, dtype=np.int64)
+    _check(lib.sem_compute_ordering(_ptr(c, C.c_double), c.shape[0], _ptr(q, C.c_int32), q.shape[0], int(order),
+                                    kind, C.c_uint64(seed & (2 ** 64 - 1)), _ptr(eo, C.c_int64),
+                                    _ptr(no, C.c_int64)))
+    return eo, no
+
+
+def sem_hilbert_cells(W: int, H: int) -> np.ndarray:
+    lib = load()
+    out = np.zeros((W * H, 2), dtype=np.int32)
+    _check(lib.sem_hilbert_cells(int(W), int(H), _ptr(out, C.c_int32)))
+    return out
+
+
+# ------------------------------------------------------------------ handle
+class SEM:
+    """One mesh handle (sem_mesh*). Methods mirror the C calls."""
+
+    def __init__(self, coords, quads, order: int, precision="fp32_kahan", stream=None):
+        lib = load()
+        self._lib = lib
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        c = np.ascontiguousarray(coords, dtype=np.float64)
+        q = np.ascontiguousarray(quads, dtype=np.int32)
+        h = _P()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        st = lib.sem_mesh_create(_ptr(c, C.c_double), c.shape[0], _ptr(q, C.c_int32), q.shape[0], int(order),
+                                 prec, _P(stream or None), C.byref(h))
+        _check(st)
+        self.h = h
+        self.order = order
+        self.precision = prec
+        nn, ne = C.c_int64(), C.c_int64()
+        _check(lib.sem_get_sizes(h, C.byref(nn), C.byref(ne)), h)
+        self.n_nodes, self.n_elems = nn.value, ne.value
+        self.nrec = 0
+        self.max_steps = 0
+
+    def _c(self, st):
+        _check(st, self.h)
+
+    def sem_reorder(self, kind, seed: int = DEFAULT_SEED):
+        kind = ORDERINGS[kind] if isinstance(kind, str) else int(kind)
+        self._c(self._lib.sem_reorder(self.h, kind, C.c_uint64(seed & (2 ** 64 - 1))))
+
+    def sem_set_model(self, vel, rho=None):
+        v = np.ascontiguousarray(np.broadcast_to(np.asarray(vel, dtype=np.float64), (self.n_elems,)))
+        r = None if rho is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(rho, dtype=np.float64), (self.n_elems,)))
+        self._c(self._lib.sem_set_model(self.h, _ptr(v, C.c_double), None if r is None else _ptr(r, C.c_double)))
+
+    def sem_set_source(self, f0, t0, amp, x, y, kind=SEM_SRC_RICKER):
+        self._c(self._lib.sem_set_source(self.h, kind, f0, t0, amp, x, y))
+
+    def sem_set_receivers(self, xy, max_steps: int):
+        a = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        self._c(self._lib.sem_set_receivers(self.h, _ptr(a, C.c_double), a.shape[0], int(max_steps)))
+        self.nrec = a.shape[0]
+        self.max_steps = int(max_steps)
+
+    def sem_cfl_dt(self) -> float:
+        d = C.c_double()
+        self._c(self._lib.sem_cfl_dt(self.h, C.byref(d)))
+        return d.value
+
+    def sem_set_dt(self, dt: float):
+        self._c(self._lib.sem_set_dt(self.h, float(dt)))
+
+    def sem_set_tuning(self, elems_per_block: int):
+        self._c(self._lib.sem_set_tuning(self.h, int(elems_per_block)))
+
+    def sem_step(self, nsteps: int):
+        self._c(self._lib.sem_step(self.h, int(nsteps)))
+
+    def sem_get_step(self) -> int:
+        s = C.c_int64()
+        self._c(self._lib.sem_get_step(self.h, C.byref(s)))
+        return s.value
+
+    def sem_read_traces(self, cap: int | None = None) -> np.ndarray:
+        cap = self.max_steps if cap is None else cap
+        out = np.zeros((self.nrec, cap), dtype=np.float64)
+        self._c(self._lib.sem_read_traces(self.h, _ptr(out, C.c_double), int(cap)))
+        return out
+
+    def sem_read_wavefield(self) -> np.ndarray:
+        u = np.zeros(self.n_nodes, dtype=np.float64)
+        self._c(self._lib.sem_read_wavefield(self.h, _ptr(u, C.c_double)))
+        return u
+
+    def sem_set_state(self, u, u_prev, step: int = 0):
+        a = np.ascontiguousarray(u, dtype=np.float64)
+        b = np.ascontiguousarray(u_prev, dtype=np.float64)
+        self._c(self._lib.sem_set_state(self.h, _ptr(a, C.c_double), _ptr(b, C.c_double), int(step)))
+
+    def sem_get_state(self):
+        a = np.zeros(self.n_nodes)
+        b = np.zeros(self.n_nodes)
+        s = C.c_int64()
+        self._c(self._lib.sem_get_state(self.h, _ptr(a, C.c_double), _ptr(b, C.c_double), C.byref(s)))
+        return a, b, s.value
+
+    def sem_apply_stiffness(self, u) -> np.ndarray:
+        a = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros(self.n_nodes)
+        self._c(self._lib.sem_apply_stiffness(self.h, _ptr(a, C.c_double), _ptr(out, C.c_double)))
+        return out
+
+    def sem_read_mass(self) -> np.ndarray:
+        out = np.zeros(self.n_nodes)
+        self._c(self._lib.sem_read_mass(self.h, _ptr(out, C.c_double)))
+        return out
+
+    def sem_get_permutation(self):
+        e = np.zeros(self.n_elems, dtype=np.int64)
+        n = np.zeros(self.n_nodes, dtype=np.int64)
+        self._c(self._lib.sem_get_permutation(self.h, _ptr(e, C.c_int64), _ptr(n, C.c_int64)))
+        return e, n
+
+    def sem_node_coordinates(self) -> np.ndarray:
+        out = np.zeros((self.n_nodes, 2))
+        self._c(self._lib.sem_node_coordinates(self.h, _ptr(out, C.c_double)))
+        return out
+
+    def sem_get_snapped(self):
+        s = C.c_int64()
+        r = np.zeros(max(self.nrec, 1), dtype=np.int64)
+        self._c(self._lib.sem_get_snapped(self.h, C.byref(s), _ptr(r, C.c_int64)))
+        return s.value, r[: self.nrec]
+
+    def sem_launch_info(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._c(self._lib.sem_launch_info(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def sem_profile_enable(self, enable: bool = True):
+        self._c(self._lib.sem_profile_enable(self.h, 1 if enable else 0))
+
+    def sem_profile_read(self):
+        """(block_ms, block_launches, open_ms, open_launches) since the last read."""
+        bm, om = C.c_double(), C.c_double()
+        bl, ol = C.c_int64(), C.c_int64()
+        self._c(self._lib.sem_profile_read(self.h, C.byref(bm), C.byref(bl), C.byref(om), C.byref(ol)))
+        return bm.value, bl.value, om.value, ol.value
+
+    def sem_traffic_model(self):
+        a, b = C.c_double(), C.c_double()
+        self._c(self._lib.sem_traffic_model(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def sem_transfer_bytes(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._c(self._lib.sem_transfer_bytes(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def sem_destroy(self):
+        if getattr(self, "h", None):
+            self._lib.sem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.sem_destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.sem_destroy()
+
+
+def sem_mesh_create(coords, quads, order: int, precision="fp32_kahan", stream=None) -> SEM:
+    return SEM(coords, quads, order, precision, stream)

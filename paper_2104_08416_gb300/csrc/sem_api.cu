@@ -1,0 +1,907 @@
+// C ABI of the spectral-element stepper (declarations and contracts in
+// include/sem.h). Host orchestration: validation, orderings and the block
+// plan come from sem_host.cpp; all per-step arithmetic runs in the kernels of
+// sem_kernels.cu on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sem.h"
+#include "sem_host.h"
+#include "sem_kernels.cuh"
+
+namespace {
+
+std::mutex g_alloc_mu;
+sem_alloc_fn g_alloc = nullptr;
+sem_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct sem_mesh {
+    semhost::Mesh mesh;
+    sem_precision prec = SEM_FP64;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // allocator captured at creation
+    sem_alloc_fn alloc = nullptr;
+    sem_free_fn free_fn = nullptr;
+    void* alloc_ctx = nullptr;
+    std::vector<DevBuf> bufs;
+
+    int ordering = SEM_ORDER_NONE;
+    uint64_t seed = 0;
+    std::vector<int64_t> elem_order, node_order;  // order[new] = old
+    std::vector<int64_t> elem_new, node_new;      // new id of each old id
+    std::vector<double> node_xy;                  // original order
+
+    bool have_model = false;
+    std::vector<double> vel, rho;
+    bool have_src = false;
+    double f0 = 0, t0 = 0, amp = 0, sx = 0, sy = 0;
+    int64_t src_node = -1;  // original id
+    int32_t nrec = 0;
+    int64_t trace_cap = 0;
+    std::vector<int64_t> rec_nodes;  // original ids
+    std::vector<int32_t> rec_row;    // -1, or the earlier receiver on the same node
+    bool have_dt = false;
+    double dt = 0;
+    int eb_request = 0;
+
+    // device state
+    bool built = false;
+    int64_t step = 0;
+    int64_t stepped_calls = 0;
+    semhost::BlockPlan plan;
+    semdev::Plan dplan{};
+    int smem = 0;
+    semdev::Basis<double> basis64{};
+    semdev::Basis<float> basis32{};
+    double* d_coords = nullptr;
+    int32_t* d_quads = nullptr;
+    double* d_rho = nullptr;
+    double* d_vel = nullptr;
+    float4* d_coef = nullptr;
+    double* d_G64 = nullptr;
+    double* d_mloc = nullptr;
+    double* d_M = nullptr;
+    void* d_s = nullptr;
+    void* d_u[2] = {nullptr, nullptr};
+    void* d_delta = nullptr;
+    void* d_comp = nullptr;
+    void* d_partial = nullptr;
+    void* d_apply_in = nullptr;
+    void* d_apply_out = nullptr;
+    double* d_src = nullptr;
+    int64_t src_cap = 0;
+    int32_t* d_rec_gid = nullptr;
+    uint8_t* d_rec_closed = nullptr;
+    int32_t* d_open_rec = nullptr;
+    double* d_trace = nullptr;
+    // measurement
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_block, ev_open;
+    int64_t h2d = 0, d2h = 0;
+};
+
+namespace {
+
+sem_status fail(sem_mesh* m, sem_status st, const std::string& msg) {
+    if (m) m->err = msg;
+    return st;
+}
+
+sem_status cuda_fail(sem_mesh* m, cudaError_t e, const char* where) {
+    return fail(m, SEM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SEM_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return cuda_fail(m, _e, #call);  \
+    } while (0)
+
+void* dev_alloc(sem_mesh* m, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (m->alloc) {
+        p = m->alloc(bytes, (void*)m->stream, m->alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) m->bufs.push_back({p, bytes});
+    return p;
+}
+
+void dev_free_all(sem_mesh* m) {
+    if (!m->bufs.empty()) cudaStreamSynchronize(m->stream);
+    for (auto& b : m->bufs) {
+        if (m->free_fn) m->free_fn(b.ptr, b.bytes, (void*)m->stream, m->alloc_ctx);
+        else cudaFree(b.ptr);
+    }
+    m->bufs.clear();
+}
+
+template <typename T>
+sem_status upload(sem_mesh* m, T** dst, const T* src, size_t n) {
+    *dst = static_cast<T*>(dev_alloc(m, n * sizeof(T)));
+    if (!*dst) return fail(m, SEM_ERR_OOM, "device allocation failed");
+    if (n) {
+        cudaError_t e = cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, m->stream);
+        m->h2d += (int64_t)(n * sizeof(T));
+        if (e != cudaSuccess) return cuda_fail(m, e, "cudaMemcpyAsync H2D");
+        // host vectors may die right after this call returns
+        e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) return cuda_fail(m, e, "cudaStreamSynchronize");
+    }
+    return SEM_OK;
+}
+
+sem_status zeros(sem_mesh* m, void** dst, size_t bytes) {
+    *dst = dev_alloc(m, bytes);
+    if (!*dst) return fail(m, SEM_ERR_OOM, "device allocation failed");
+    cudaError_t e = cudaMemsetAsync(*dst, 0, bytes, m->stream);
+    if (e != cudaSuccess) return cuda_fail(m, e, "cudaMemsetAsync");
+    return SEM_OK;
+}
+
+bool fp64(const sem_mesh* m) { return m->prec == SEM_FP64; }
+size_t tsize(const sem_mesh* m) { return fp64(m) ? 8 : 4; }
+int mode_of(const sem_mesh* m) {
+    return m->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
+}
+
+template <typename T>
+void fill_basis(semdev::Basis<T>& b, int p) {
+    std::vector<double> x, w, D;
+    semhost::gll_rule(p, x, w);
+    semhost::gll_derivative(x, D);
+    std::memset(&b, 0, sizeof(b));
+    const int n = p + 1;
+    for (int i = 0; i < n; ++i) {
+        b.x[i] = (T)x[i];
+        b.w[i] = (T)w[i];
+        for (int k = 0; k < n; ++k) b.D[i * n + k] = (T)D[(size_t)i * n + k];
+    }
+}
+
+void compute_orderings(sem_mesh* m) {
+    semhost::orderings(m->mesh, m->ordering, m->seed, m->elem_order, m->node_order);
+    m->elem_new.assign(m->elem_order.size(), 0);
+    m->node_new.assign(m->node_order.size(), 0);
+    for (size_t k = 0; k < m->elem_order.size(); ++k) m->elem_new[(size_t)m->elem_order[k]] = (int64_t)k;
+    for (size_t k = 0; k < m->node_order.size(); ++k) m->node_new[(size_t)m->node_order[k]] = (int64_t)k;
+}
+
+sem_status fill_source(sem_mesh* m, int64_t upto) {
+    // Ricker values f(t_n), t_n = n dt, tabulated in FP64 on the host.
+    if (upto <= m->src_cap) return SEM_OK;
+    int64_t cap = std::max<int64_t>(upto, std::max<int64_t>(1024, m->src_cap * 2));
+    std::vector<double> f((size_t)cap, 0.0);
+    if (m->have_src) {
+        for (int64_t n = 0; n < cap; ++n) {
+            double a = M_PI * m->f0 * ((double)n * m->dt - m->t0);
+            a = a * a;
+            f[(size_t)n] = m->amp * (1.0 - 2.0 * a) * std::exp(-a);
+        }
+    }
+    double* d = nullptr;
+    sem_status st = upload(m, &d, f.data(), f.size());
+    if (st != SEM_OK) return st;
+    m->d_src = d;  // the old table stays allocated until sem_destroy
+    m->src_cap = cap;
+    return SEM_OK;
+}
+
+int default_eb(int P) {
+    int eb = 1600 / P;
+    return eb < 1 ? 1 : eb;
+}
+
+sem_status build(sem_mesh* m) {
+    if (m->built) return SEM_OK;
+    if (!m->have_model) return fail(m, SEM_ERR_STATE, "sem_set_model must come first");
+    const auto& M = m->mesh;
+    const int P = M.P;
+    if (m->elem_order.empty()) compute_orderings(m);
+    // permuted connectivity and element data
+    std::vector<int32_t> conn_new((size_t)(M.ne * P));
+    std::vector<int32_t> quads_new((size_t)M.ne * 4);
+    std::vector<double> rho_new((size_t)M.ne), vel_new((size_t)M.ne);
+    for (int64_t en = 0; en < M.ne; ++en) {
+        int64_t eo = m->elem_order[(size_t)en];
+        for (int q = 0; q < P; ++q)
+            conn_new[(size_t)(en * P + q)] = (int32_t)m->node_new[(size_t)M.conn[(size_t)(eo * P + q)]];
+        for (int c = 0; c < 4; ++c) quads_new[(size_t)en * 4 + c] = M.quads[(size_t)eo * 4 + c];
+        rho_new[(size_t)en] = m->rho[(size_t)eo];
+        vel_new[(size_t)en] = m->vel[(size_t)eo];
+    }
+    int eb = m->eb_request > 0 ? m->eb_request : default_eb(P);
+    if ((int64_t)eb * P > 65535) eb = 65535 / P;
+    semhost::build_block_plan(conn_new, M.ne, P, M.nn, eb, m->plan);
+    conn_new.clear();
+    conn_new.shrink_to_fit();
+    const auto& pl = m->plan;
+    m->smem = semdev::smem_bytes_for(P, pl.eb, pl.max_entries, fp64(m));
+    if (m->smem > 227 * 1024) return fail(m, SEM_ERR_UNSUPPORTED, "block plan does not fit in shared memory");
+
+    sem_status st;
+    uint16_t *lidx, *lrow, *lsl;
+    int32_t *ent_ptr, *ent_gid, *ent_pslot, *open_gid, *open_ptr;
+    if ((st = upload(m, &lidx, pl.lidx.data(), pl.lidx.size())) != SEM_OK) return st;
+    if ((st = upload(m, &lrow, pl.lrow.data(), pl.lrow.size())) != SEM_OK) return st;
+    if ((st = upload(m, &lsl, pl.lsl.data(), pl.lsl.size())) != SEM_OK) return st;
+    if ((st = upload(m, &ent_ptr, pl.ent_ptr.data(), pl.ent_ptr.size())) != SEM_OK) return st;
+    if ((st = upload(m, &ent_gid, pl.ent_gid.data(), pl.ent_gid.size())) != SEM_OK) return st;
+    if ((st = upload(m, &ent_pslot, pl.ent_pslot.data(), pl.ent_pslot.size())) != SEM_OK) return st;
+    if ((st = upload(m, &open_gid, pl.open_gid.data(), pl.open_gid.size())) != SEM_OK) return st;
+    if ((st = upload(m, &open_ptr, pl.open_ptr.data(), pl.open_ptr.size())) != SEM_OK) return st;
+    semdev::Plan& dp = m->dplan;
+    dp.lidx = lidx;
+    dp.lrow = lrow;
+    dp.lsl = lsl;
+    dp.ent_ptr = ent_ptr;
+    dp.ent_gid = ent_gid;
+    dp.ent_pslot = ent_pslot;
+    dp.open_gid = open_gid;
+    dp.open_ptr = open_ptr;
+    dp.open_rec = nullptr;
+    dp.ne = M.ne;
+    dp.eb = pl.eb;
+    dp.nblocks = (int)pl.nblocks;
+    dp.nopen = (int)pl.open_gid.size();
+    dp.max_entries = pl.max_entries;
+
+    fill_basis(m->basis64, M.p);
+    fill_basis(m->basis32, M.p);
+
+    // FP64 geometry and mass on the device
+    if ((st = upload(m, &m->d_coords, M.coords.data(), M.coords.size())) != SEM_OK) return st;
+    if ((st = upload(m, &m->d_quads, quads_new.data(), quads_new.size())) != SEM_OK) return st;
+    if ((st = upload(m, &m->d_rho, rho_new.data(), rho_new.size())) != SEM_OK) return st;
+    if ((st = upload(m, &m->d_vel, vel_new.data(), vel_new.size())) != SEM_OK) return st;
+    const size_t nslot = (size_t)(M.ne * P);
+    m->d_mloc = (double*)dev_alloc(m, nslot * 8);
+    m->d_M = (double*)dev_alloc(m, (size_t)M.nn * 8);
+    m->d_partial = dev_alloc(m, (size_t)std::max<int64_t>(pl.npartial, 1) * 8);
+    if (!m->d_mloc || !m->d_M || !m->d_partial) return fail(m, SEM_ERR_OOM, "device allocation failed");
+    if (fp64(m)) {
+        m->d_G64 = (double*)dev_alloc(m, nslot * 3 * 8);
+        if (!m->d_G64) return fail(m, SEM_ERR_OOM, "device allocation failed");
+    } else {
+        m->d_coef = (float4*)dev_alloc(m, (size_t)M.ne * 2 * sizeof(float4));
+        if (!m->d_coef) return fail(m, SEM_ERR_OOM, "device allocation failed");
+    }
+    SEM_CUDA(semdev::launch_geometry(M.np, m->d_coords, m->d_quads, m->d_rho, m->d_vel, M.ne, m->basis64, m->d_coef,
+                                     m->d_G64, nullptr, m->d_mloc, m->stream));
+    SEM_CUDA(semdev::launch_mass(dp, P, m->d_mloc, (double*)m->d_partial, m->d_M, m->stream));
+
+    // time-stepping state
+    const size_t nb = (size_t)M.nn * tsize(m);
+    if ((st = zeros(m, &m->d_u[0], nb)) != SEM_OK) return st;
+    if ((st = zeros(m, &m->d_u[1], nb)) != SEM_OK) return st;
+    if ((st = zeros(m, &m->d_s, nb)) != SEM_OK) return st;
+    if (m->prec == SEM_FP32_KAHAN) {
+        if ((st = zeros(m, &m->d_delta, nb)) != SEM_OK) return st;
+        if ((st = zeros(m, &m->d_comp, nb)) != SEM_OK) return st;
+    }
+    if (m->have_dt) {
+        SEM_CUDA(semdev::launch_scale(m->d_M, M.nn, m->dt, fp64(m) ? (double*)m->d_s : nullptr,
+                                      fp64(m) ? nullptr : (float*)m->d_s, m->stream));
+    }
+    // receivers
+    if (m->nrec > 0) {
+        std::vector<int32_t> rg((size_t)m->nrec);
+        std::vector<uint8_t> rc((size_t)m->nrec, 1);
+        std::vector<int32_t> orec(pl.open_gid.size(), -1);
+        m->rec_row.assign((size_t)m->nrec, -1);
+        for (int32_t r = 0; r < m->nrec; ++r) {
+            int32_t g = (int32_t)m->node_new[(size_t)m->rec_nodes[(size_t)r]];
+            rg[(size_t)r] = g;
+            // a second receiver on the same node copies the first one's trace
+            for (int32_t q = 0; q < r; ++q)
+                if (rg[(size_t)q] == g) {
+                    m->rec_row[(size_t)r] = q;
+                    break;
+                }
+            if (m->rec_row[(size_t)r] >= 0) {
+                rc[(size_t)r] = 0;
+                continue;
+            }
+            auto it = std::lower_bound(pl.open_gid.begin(), pl.open_gid.end(), g);
+            if (it != pl.open_gid.end() && *it == g) {
+                rc[(size_t)r] = 0;
+                orec[(size_t)(it - pl.open_gid.begin())] = r;
+            }
+        }
+        if ((st = upload(m, &m->d_rec_gid, rg.data(), rg.size())) != SEM_OK) return st;
+        if ((st = upload(m, &m->d_rec_closed, rc.data(), rc.size())) != SEM_OK) return st;
+        if ((st = upload(m, &m->d_open_rec, orec.data(), orec.size())) != SEM_OK) return st;
+        dp.open_rec = m->d_open_rec;
+        void* tr = nullptr;
+        if ((st = zeros(m, &tr, (size_t)m->nrec * (size_t)m->trace_cap * 8)) != SEM_OK) return st;
+        m->d_trace = (double*)tr;
+    }
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(m, e, "build");
+    m->built = true;
+    return SEM_OK;
+}
+
+template <typename T>
+semdev::StepArgs<T> step_args(sem_mesh* m) {
+    semdev::StepArgs<T> a{};
+    const int cur = (int)(m->step & 1);
+    a.u_cur = (const T*)m->d_u[cur];
+    a.u_out = (T*)m->d_u[cur ^ 1];
+    a.u_prev = (const T*)m->d_u[cur ^ 1];
+    a.delta = (T*)m->d_delta;
+    a.comp = (T*)m->d_comp;
+    a.s = (const T*)m->d_s;
+    a.partial = (T*)m->d_partial;
+    a.G = (const T*)m->d_G64;
+    a.gstride = m->mesh.ne * m->mesh.P;
+    a.coef = m->d_coef;
+    a.apply_out = nullptr;
+    a.src_f = m->d_src;
+    a.step = m->step;
+    a.src_gid = m->have_src ? (int32_t)m->node_new[(size_t)m->src_node] : -1;
+    a.rec_gid = m->d_rec_gid;
+    a.rec_closed = m->d_rec_closed;
+    a.nrec = m->nrec;
+    a.trace = m->d_trace;
+    a.trace_cap = m->trace_cap;
+    return a;
+}
+
+cudaEvent_t take_event(sem_mesh* m) {
+    if (!m->ev_pool.empty()) {
+        cudaEvent_t e = m->ev_pool.back();
+        m->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+sem_status launch_one_step(sem_mesh* m) {
+    const bool f64 = fp64(m);
+    const int mode = mode_of(m);
+    const void* basis = f64 ? (const void*)&m->basis64 : (const void*)&m->basis32;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+    if (m->profiling) {
+        e0 = take_event(m);
+        e1 = take_event(m);
+        e2 = take_event(m);
+        e3 = take_event(m);
+        if (!e0 || !e1 || !e2 || !e3) return fail(m, SEM_ERR_CUDA, "cudaEventCreate failed");
+    }
+    auto rec = [&](cudaEvent_t ev) { return ev ? cudaEventRecord(ev, m->stream) : cudaSuccess; };
+    cudaError_t e = rec(e0);
+    if (f64) {
+        auto a = step_args<double>(m);
+        if (e == cudaSuccess) e = semdev::launch_step(m->mesh.np, true, mode, false, m->dplan, &a, basis, m->smem, m->stream);
+        if (e == cudaSuccess) e = rec(e1);
+        if (e == cudaSuccess) e = rec(e2);
+        if (e == cudaSuccess) e = semdev::launch_open(true, mode, m->dplan, &a, m->stream);
+    } else {
+        auto a = step_args<float>(m);
+        if (e == cudaSuccess) e = semdev::launch_step(m->mesh.np, false, mode, true, m->dplan, &a, basis, m->smem, m->stream);
+        if (e == cudaSuccess) e = rec(e1);
+        if (e == cudaSuccess) e = rec(e2);
+        if (e == cudaSuccess) e = semdev::launch_open(false, mode, m->dplan, &a, m->stream);
+    }
+    if (e == cudaSuccess) e = rec(e3);
+    if (e != cudaSuccess) return cuda_fail(m, e, "step launch");
+    if (m->profiling) {
+        m->ev_block.push_back({e0, e1});
+        m->ev_open.push_back({e2, e3});
+    }
+    m->step++;
+    return SEM_OK;
+}
+
+template <typename T>
+void to_new_order(const sem_mesh* m, const double* src, std::vector<T>& dst) {
+    dst.resize(m->node_order.size());
+    for (size_t k = 0; k < dst.size(); ++k) dst[k] = (T)src[(size_t)m->node_order[k]];
+}
+
+sem_status read_nodes(sem_mesh* m, const void* dptr, bool as_f64, std::vector<double>& out_new) {
+    const size_t nn = (size_t)m->mesh.nn;
+    out_new.assign(nn, 0.0);
+    if (as_f64) {
+        SEM_CUDA(cudaMemcpyAsync(out_new.data(), dptr, nn * 8, cudaMemcpyDeviceToHost, m->stream));
+        m->d2h += (int64_t)(nn * 8);
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+    } else {
+        std::vector<float> tmp(nn);
+        SEM_CUDA(cudaMemcpyAsync(tmp.data(), dptr, nn * 4, cudaMemcpyDeviceToHost, m->stream));
+        m->d2h += (int64_t)(nn * 4);
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+        for (size_t k = 0; k < nn; ++k) out_new[k] = (double)tmp[k];
+    }
+    return SEM_OK;
+}
+
+void to_original(const sem_mesh* m, const std::vector<double>& v_new, double* out) {
+    for (size_t k = 0; k < v_new.size(); ++k) out[(size_t)m->node_order[k]] = v_new[k];
+}
+
+sem_status write_nodes(sem_mesh* m, void* dptr, const double* src_orig) {
+    if (fp64(m)) {
+        std::vector<double> v;
+        to_new_order(m, src_orig, v);
+        SEM_CUDA(cudaMemcpyAsync(dptr, v.data(), v.size() * 8, cudaMemcpyHostToDevice, m->stream));
+        m->h2d += (int64_t)(v.size() * 8);
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+    } else {
+        std::vector<float> v;
+        to_new_order(m, src_orig, v);
+        SEM_CUDA(cudaMemcpyAsync(dptr, v.data(), v.size() * 4, cudaMemcpyHostToDevice, m->stream));
+        m->h2d += (int64_t)(v.size() * 4);
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+    }
+    return SEM_OK;
+}
+
+bool before_first_step(sem_mesh* m) { return !m->built; }
+
+}  // namespace
+
+extern "C" {
+
+sem_status sem_set_allocator(sem_alloc_fn alloc, sem_free_fn free_fn, void* ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return SEM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+    return SEM_OK;
+}
+
+sem_status sem_mesh_create(const double* coords, int64_t nv, const int32_t* quads, int64_t ne, int order,
+                           sem_precision prec, void* cuda_stream, sem_mesh** out) {
+    if (!out) return SEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!coords || !quads) return SEM_ERR_INVALID_ARG;
+    if (prec != SEM_FP64 && prec != SEM_FP32_KAHAN && prec != SEM_FP32) return SEM_ERR_INVALID_ARG;
+    if (ne > 0 && (ne * (int64_t)(order + 1) * (order + 1) >= (int64_t)1 << 31)) return SEM_ERR_UNSUPPORTED;
+    std::string why = semhost::validate(coords, nv, quads, ne, order);
+    if (!why.empty()) return SEM_ERR_INVALID_ARG;
+    sem_mesh* m = new (std::nothrow) sem_mesh();
+    if (!m) return SEM_ERR_OOM;
+    try {
+        m->mesh.p = order;
+        m->mesh.nv = nv;
+        m->mesh.ne = ne;
+        m->mesh.coords.assign(coords, coords + nv * 2);
+        m->mesh.quads.assign(quads, quads + ne * 4);
+        semhost::number_nodes(m->mesh);
+    } catch (const std::bad_alloc&) {
+        delete m;
+        return SEM_ERR_OOM;
+    }
+    if (m->mesh.nn >= ((int64_t)1 << 31)) {
+        delete m;
+        return SEM_ERR_UNSUPPORTED;
+    }
+    m->prec = prec;
+    m->stream = (cudaStream_t)cuda_stream;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        m->alloc = g_alloc;
+        m->free_fn = g_free;
+        m->alloc_ctx = g_alloc_ctx;
+    }
+    *out = m;
+    return SEM_OK;
+}
+
+sem_status sem_reorder(sem_mesh* m, sem_ordering kind, uint64_t seed) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if ((int)kind < 0 || (int)kind > 3) return fail(m, SEM_ERR_INVALID_ARG, "unknown ordering");
+    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_reorder after the device data was built");
+    m->ordering = (int)kind;
+    m->seed = seed;
+    try {
+        compute_orderings(m);
+    } catch (const std::bad_alloc&) {
+        return fail(m, SEM_ERR_OOM, "host allocation failed");
+    }
+    return SEM_OK;
+}
+
+sem_status sem_set_model(sem_mesh* m, const double* vel, const double* rho) {
+    if (!m || !vel) return m ? fail(m, SEM_ERR_INVALID_ARG, "vel is NULL") : SEM_ERR_INVALID_ARG;
+    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_model after the device data was built");
+    const int64_t ne = m->mesh.ne;
+    for (int64_t e = 0; e < ne; ++e) {
+        if (!(vel[e] > 0.0) || !std::isfinite(vel[e])) return fail(m, SEM_ERR_INVALID_ARG, "vel must be > 0");
+        if (rho && (!(rho[e] > 0.0) || !std::isfinite(rho[e]))) return fail(m, SEM_ERR_INVALID_ARG, "rho must be > 0");
+    }
+    m->vel.assign(vel, vel + ne);
+    if (rho) m->rho.assign(rho, rho + ne);
+    else m->rho.assign((size_t)ne, 1.0);
+    m->have_model = true;
+    return SEM_OK;
+}
+
+static void ensure_node_xy(sem_mesh* m) {
+    if (m->node_xy.empty()) semhost::node_coordinates(m->mesh, m->node_xy);
+}
+
+sem_status sem_set_source(sem_mesh* m, int kind, double f0, double t0, double amp, double x, double y) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (kind != SEM_SRC_RICKER) return fail(m, SEM_ERR_INVALID_ARG, "unknown source kind");
+    if (!(f0 > 0.0) || !std::isfinite(t0) || !std::isfinite(amp) || !std::isfinite(x) || !std::isfinite(y))
+        return fail(m, SEM_ERR_INVALID_ARG, "bad source parameters");
+    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_source after the first step");
+    ensure_node_xy(m);
+    m->f0 = f0;
+    m->t0 = t0;
+    m->amp = amp;
+    m->sx = x;
+    m->sy = y;
+    m->src_node = semhost::snap(m->node_xy, x, y);
+    m->have_src = true;
+    return SEM_OK;
+}
+
+sem_status sem_set_receivers(sem_mesh* m, const double* xy, int32_t nrec, int64_t max_steps) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (nrec < 0 || (nrec > 0 && (!xy || max_steps < 1))) return fail(m, SEM_ERR_INVALID_ARG, "bad receivers");
+    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_receivers after the first step");
+    ensure_node_xy(m);
+    m->rec_nodes.assign((size_t)nrec, 0);
+    for (int32_t r = 0; r < nrec; ++r) m->rec_nodes[(size_t)r] = semhost::snap(m->node_xy, xy[2 * r], xy[2 * r + 1]);
+    m->nrec = nrec;
+    m->trace_cap = nrec > 0 ? max_steps : 0;
+    return SEM_OK;
+}
+
+sem_status sem_cfl_dt(const sem_mesh* m, double* dt_cfl) {
+    if (!m || !dt_cfl) return SEM_ERR_INVALID_ARG;
+    if (!m->have_model) return SEM_ERR_STATE;
+    *dt_cfl = semhost::cfl_dt(m->mesh, m->vel.data());
+    return SEM_OK;
+}
+
+sem_status sem_set_dt(sem_mesh* m, double dt) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(m, SEM_ERR_INVALID_ARG, "dt must be > 0");
+    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_dt after the device data was built");
+    m->dt = dt;
+    m->have_dt = true;
+    return SEM_OK;
+}
+
+sem_status sem_set_tuning(sem_mesh* m, int elems_per_block) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (elems_per_block < 0 || (int64_t)elems_per_block * m->mesh.P > 65535)
+        return fail(m, SEM_ERR_INVALID_ARG, "elems_per_block out of range");
+    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_tuning after the device data was built");
+    m->eb_request = elems_per_block;
+    return SEM_OK;
+}
+
+sem_status sem_step(sem_mesh* m, int64_t nsteps) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (nsteps < 0) return fail(m, SEM_ERR_INVALID_ARG, "nsteps < 0");
+    if (!m->have_model || !m->have_dt) return fail(m, SEM_ERR_STATE, "model and dt must be set before sem_step");
+    sem_status st = build(m);
+    if (st != SEM_OK) return st;
+    if (m->nrec > 0 && m->step + nsteps > m->trace_cap)
+        return fail(m, SEM_ERR_INVALID_ARG, "steps beyond the receivers' max_steps");
+    if ((st = fill_source(m, m->step + nsteps)) != SEM_OK) return st;
+    for (int64_t k = 0; k < nsteps; ++k)
+        if ((st = launch_one_step(m)) != SEM_OK) return st;
+    m->stepped_calls++;
+    return SEM_OK;
+}
+
+sem_status sem_get_step(const sem_mesh* m, int64_t* step) {
+    if (!m || !step) return SEM_ERR_INVALID_ARG;
+    *step = m->step;
+    return SEM_OK;
+}
+
+sem_status sem_read_traces(sem_mesh* m, double* out, int64_t cap) {
+    if (!m || !out || cap < 0) return SEM_ERR_INVALID_ARG;
+    if (m->nrec == 0 || cap == 0) return SEM_OK;
+    if (!m->built) {
+        std::fill(out, out + (size_t)m->nrec * (size_t)cap, 0.0);
+        return SEM_OK;
+    }
+    const int64_t n = std::min(cap, m->step);
+    std::fill(out, out + (size_t)m->nrec * (size_t)cap, 0.0);
+    if (n > 0) {
+        SEM_CUDA(cudaMemcpy2DAsync(out, (size_t)cap * 8, m->d_trace, (size_t)m->trace_cap * 8, (size_t)n * 8,
+                                   (size_t)m->nrec, cudaMemcpyDeviceToHost, m->stream));
+        m->d2h += (int64_t)n * 8 * m->nrec;
+    }
+    SEM_CUDA(cudaStreamSynchronize(m->stream));
+    for (int32_t r = 0; r < m->nrec; ++r) {
+        const int32_t q = m->rec_row[(size_t)r];
+        if (q >= 0) std::copy(out + (size_t)q * cap, out + (size_t)(q + 1) * cap, out + (size_t)r * cap);
+    }
+    return SEM_OK;
+}
+
+sem_status sem_read_wavefield(sem_mesh* m, double* u) { return sem_get_state(m, u, nullptr, nullptr); }
+
+sem_status sem_set_state(sem_mesh* m, const double* u, const double* u_prev, int64_t step) {
+    if (!m || !u || !u_prev || step < 0) return SEM_ERR_INVALID_ARG;
+    if (!m->have_model || !m->have_dt) return fail(m, SEM_ERR_STATE, "model and dt must be set first");
+    sem_status st = build(m);
+    if (st != SEM_OK) return st;
+    if (m->nrec > 0 && step > m->trace_cap) return fail(m, SEM_ERR_INVALID_ARG, "step beyond max_steps");
+    m->step = step;
+    const int cur = (int)(step & 1);
+    if ((st = write_nodes(m, m->d_u[cur], u)) != SEM_OK) return st;
+    if (m->prec == SEM_FP32_KAHAN) {
+        std::vector<double> d((size_t)m->mesh.nn);
+        for (size_t k = 0; k < d.size(); ++k) d[k] = u[k] - u_prev[k];
+        if ((st = write_nodes(m, m->d_delta, d.data())) != SEM_OK) return st;
+        SEM_CUDA(cudaMemsetAsync(m->d_comp, 0, (size_t)m->mesh.nn * 4, m->stream));
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+    } else {
+        if ((st = write_nodes(m, m->d_u[cur ^ 1], u_prev)) != SEM_OK) return st;
+    }
+    return SEM_OK;
+}
+
+sem_status sem_get_state(sem_mesh* m, double* u, double* u_prev, int64_t* step) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (step) *step = m->step;
+    const size_t nn = (size_t)m->mesh.nn;
+    if (!m->built) {
+        if (u) std::fill(u, u + nn, 0.0);
+        if (u_prev) std::fill(u_prev, u_prev + nn, 0.0);
+        return SEM_OK;
+    }
+    const int cur = (int)(m->step & 1);
+    std::vector<double> un, tmp;
+    sem_status st = read_nodes(m, m->d_u[cur], fp64(m), un);
+    if (st != SEM_OK) return st;
+    if (m->prec == SEM_FP32_KAHAN) {
+        // compensated value u - c; u^{n-1} = u^n - delta^{n-1/2}
+        if ((st = read_nodes(m, m->d_comp, false, tmp)) != SEM_OK) return st;
+        for (size_t k = 0; k < nn; ++k) un[k] -= tmp[k];
+        if (u_prev) {
+            if ((st = read_nodes(m, m->d_delta, false, tmp)) != SEM_OK) return st;
+            for (size_t k = 0; k < nn; ++k) tmp[k] = un[k] - tmp[k];
+            to_original(m, tmp, u_prev);
+        }
+    } else if (u_prev) {
+        if ((st = read_nodes(m, m->d_u[cur ^ 1], fp64(m), tmp)) != SEM_OK) return st;
+        to_original(m, tmp, u_prev);
+    }
+    if (u) to_original(m, un, u);
+    return SEM_OK;
+}
+
+sem_status sem_apply_stiffness(sem_mesh* m, const double* u, double* Ku) {
+    if (!m || !u || !Ku) return SEM_ERR_INVALID_ARG;
+    if (!m->have_model) return fail(m, SEM_ERR_STATE, "sem_set_model must come first");
+    sem_status st = build(m);
+    if (st != SEM_OK) return st;
+    const size_t nb = (size_t)m->mesh.nn * tsize(m);
+    if (!m->d_apply_in) {
+        m->d_apply_in = dev_alloc(m, nb);
+        m->d_apply_out = dev_alloc(m, nb);
+        if (!m->d_apply_in || !m->d_apply_out) return fail(m, SEM_ERR_OOM, "device allocation failed");
+    }
+    if ((st = write_nodes(m, m->d_apply_in, u)) != SEM_OK) return st;
+    const bool f64 = fp64(m);
+    const void* basis = f64 ? (const void*)&m->basis64 : (const void*)&m->basis32;
+    cudaError_t e;
+    if (f64) {
+        auto a = step_args<double>(m);
+        a.u_cur = (const double*)m->d_apply_in;
+        a.apply_out = (double*)m->d_apply_out;
+        e = semdev::launch_step(m->mesh.np, true, semdev::MODE_APPLY, false, m->dplan, &a, basis, m->smem, m->stream);
+        if (e == cudaSuccess) e = semdev::launch_open(true, semdev::MODE_APPLY, m->dplan, &a, m->stream);
+    } else {
+        auto a = step_args<float>(m);
+        a.u_cur = (const float*)m->d_apply_in;
+        a.apply_out = (float*)m->d_apply_out;
+        e = semdev::launch_step(m->mesh.np, false, semdev::MODE_APPLY, true, m->dplan, &a, basis, m->smem,
+                                m->stream);
+        if (e == cudaSuccess) e = semdev::launch_open(false, semdev::MODE_APPLY, m->dplan, &a, m->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(m, e, "apply launch");
+    std::vector<double> out;
+    if ((st = read_nodes(m, m->d_apply_out, f64, out)) != SEM_OK) return st;
+    to_original(m, out, Ku);
+    return SEM_OK;
+}
+
+sem_status sem_read_mass(sem_mesh* m, double* mass) {
+    if (!m || !mass) return SEM_ERR_INVALID_ARG;
+    if (!m->have_model) return fail(m, SEM_ERR_STATE, "sem_set_model must come first");
+    sem_status st = build(m);
+    if (st != SEM_OK) return st;
+    std::vector<double> v;
+    if ((st = read_nodes(m, m->d_M, true, v)) != SEM_OK) return st;
+    to_original(m, v, mass);
+    return SEM_OK;
+}
+
+sem_status sem_get_permutation(const sem_mesh* mc, int64_t* elem_new_of_old, int64_t* node_new_of_old) {
+    sem_mesh* m = const_cast<sem_mesh*>(mc);
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (m->elem_order.empty()) compute_orderings(m);
+    if (elem_new_of_old) std::copy(m->elem_new.begin(), m->elem_new.end(), elem_new_of_old);
+    if (node_new_of_old) std::copy(m->node_new.begin(), m->node_new.end(), node_new_of_old);
+    return SEM_OK;
+}
+
+sem_status sem_get_sizes(const sem_mesh* m, int64_t* n_nodes, int64_t* n_elems) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (n_nodes) *n_nodes = m->mesh.nn;
+    if (n_elems) *n_elems = m->mesh.ne;
+    return SEM_OK;
+}
+
+sem_status sem_node_coordinates(const sem_mesh* mc, double* xy) {
+    sem_mesh* m = const_cast<sem_mesh*>(mc);
+    if (!m || !xy) return SEM_ERR_INVALID_ARG;
+    ensure_node_xy(m);
+    std::copy(m->node_xy.begin(), m->node_xy.end(), xy);
+    return SEM_OK;
+}
+
+sem_status sem_get_snapped(const sem_mesh* m, int64_t* src_node, int64_t* rec_nodes) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (src_node) *src_node = m->have_src ? m->src_node : -1;
+    if (rec_nodes) std::copy(m->rec_nodes.begin(), m->rec_nodes.end(), rec_nodes);
+    return SEM_OK;
+}
+
+sem_status sem_count_nodes(const int32_t* quads, int64_t nv, int64_t ne, int order, int64_t* n_nodes) {
+    if (!quads || !n_nodes || nv <= 0 || ne <= 0 || order < 1 || order > 8) return SEM_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < ne * 4; ++i)
+        if (quads[i] < 0 || quads[i] >= nv) return SEM_ERR_INVALID_ARG;
+    semhost::Mesh mm;
+    mm.p = order;
+    mm.nv = nv;
+    mm.ne = ne;
+    mm.quads.assign(quads, quads + ne * 4);
+    semhost::number_nodes(mm);
+    *n_nodes = mm.nn;
+    return SEM_OK;
+}
+
+sem_status sem_compute_ordering(const double* coords, int64_t nv, const int32_t* quads, int64_t ne, int order,
+                                sem_ordering kind, uint64_t seed, int64_t* elem_order, int64_t* node_order) {
+    if (!coords || !quads || !elem_order || !node_order) return SEM_ERR_INVALID_ARG;
+    if ((int)kind < 0 || (int)kind > 3) return SEM_ERR_INVALID_ARG;
+    if (!semhost::validate(coords, nv, quads, ne, order).empty()) return SEM_ERR_INVALID_ARG;
+    semhost::Mesh mm;
+    mm.p = order;
+    mm.nv = nv;
+    mm.ne = ne;
+    mm.coords.assign(coords, coords + nv * 2);
+    mm.quads.assign(quads, quads + ne * 4);
+    semhost::number_nodes(mm);
+    std::vector<int64_t> eo, no;
+    semhost::orderings(mm, (int)kind, seed, eo, no);
+    std::copy(eo.begin(), eo.end(), elem_order);
+    std::copy(no.begin(), no.end(), node_order);
+    return SEM_OK;
+}
+
+sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells) {
+    if (!cells || W < 1 || H < 1) return SEM_ERR_INVALID_ARG;
+    std::vector<int32_t> c;
+    semhost::hilbert_cells(W, H, c);
+    std::copy(c.begin(), c.end(), cells);
+    return SEM_OK;
+}
+
+sem_status sem_launch_info(const sem_mesh* m, int64_t* launches_per_step, int64_t* open_nodes) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (launches_per_step) *launches_per_step = 2;
+    if (open_nodes) *open_nodes = m->built ? (int64_t)m->plan.open_gid.size() : -1;
+    return SEM_OK;
+}
+
+sem_status sem_profile_enable(sem_mesh* m, int enable) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    m->profiling = enable != 0;
+    return SEM_OK;
+}
+
+sem_status sem_profile_read(sem_mesh* m, double* block_ms, int64_t* block_launches, double* open_ms,
+                            int64_t* open_launches) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    SEM_CUDA(cudaStreamSynchronize(m->stream));
+    double tb = 0.0, to = 0.0;
+    for (auto& pr : m->ev_block) {
+        float ms = 0.f;
+        SEM_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tb += ms;
+    }
+    for (auto& pr : m->ev_open) {
+        float ms = 0.f;
+        SEM_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        to += ms;
+    }
+    if (block_ms) *block_ms = tb;
+    if (open_ms) *open_ms = to;
+    if (block_launches) *block_launches = (int64_t)m->ev_block.size();
+    if (open_launches) *open_launches = (int64_t)m->ev_open.size();
+    for (auto& pr : m->ev_block) m->ev_pool.push_back(pr.first), m->ev_pool.push_back(pr.second);
+    for (auto& pr : m->ev_open) m->ev_pool.push_back(pr.first), m->ev_pool.push_back(pr.second);
+    m->ev_block.clear();
+    m->ev_open.clear();
+    return SEM_OK;
+}
+
+sem_status sem_traffic_model(const sem_mesh* m, double* block_bytes, double* open_bytes) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (!m->built) return SEM_ERR_STATE;
+    const auto& pl = m->plan;
+    const double ts = (double)tsize(m);
+    const double slots = (double)m->mesh.ne * m->mesh.P;
+    const double nent = (double)pl.ent_gid.size();
+    const double nb = (double)pl.nblocks;
+    const double nopen = (double)pl.open_gid.size();
+    const double nn = (double)m->mesh.nn;
+    const double nclosed = nn - nopen;
+    // node state touched by the update: Kahan: u in, u out, s, delta r/w,
+    // comp r/w; three-level: u in, u out, s, u^{n-1}
+    const double upd = m->prec == SEM_FP32_KAHAN ? 7.0 * ts : 4.0 * ts;
+    double geo = fp64(m) ? slots * 3.0 * ts : (double)m->mesh.ne * 32.0;
+    double blk = slots * 2.0 * 2.0                 // lidx + lsl
+                 + (nent + nb) * 2.0               // lrow
+                 + nent * 8.0 + (nb + 1) * 4.0      // ent_gid, ent_pslot, ent_ptr
+                 + geo                              // geometry
+                 + nopen * ts                       // u at open nodes (gather)
+                 + nclosed * upd                    // closed nodes: gather + update
+                 + (double)pl.npartial * ts;        // partial sums written
+    double opn = nopen * (8.0 + upd) + (double)pl.npartial * ts + (m->nrec > 0 ? nopen * 4.0 : 0.0);
+    if (block_bytes) *block_bytes = blk;
+    if (open_bytes) *open_bytes = opn;
+    return SEM_OK;
+}
+
+sem_status sem_transfer_bytes(const sem_mesh* m, int64_t* h2d, int64_t* d2h) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (h2d) *h2d = m->h2d;
+    if (d2h) *d2h = m->d2h;
+    return SEM_OK;
+}
+
+const char* sem_last_error(const sem_mesh* m) {
+    if (!m) return "NULL handle";
+    return m->err.c_str();
+}
+
+void sem_destroy(sem_mesh* m) {
+    if (!m) return;
+    dev_free_all(m);
+    for (auto& pr : m->ev_block) m->ev_pool.push_back(pr.first), m->ev_pool.push_back(pr.second);
+    for (auto& pr : m->ev_open) m->ev_pool.push_back(pr.first), m->ev_pool.push_back(pr.second);
+    for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+    delete m;
+}
+
+}  // extern "C"

@@ -1,0 +1,592 @@
+// Host-side preprocessing (see sem_host.h). Built with -ffp-contract=off so
+// that the floating-point steps that decide integers (Hilbert cells) round
+// exactly as written.
+#include "sem_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <unordered_map>
+
+namespace semhost {
+
+// ---------------------------------------------------------------- GLL rule
+static void legendre_eval(int p, double x, double& Pp, double& Pm1) {
+    double a = 1.0, b = x;  // P_0, P_1
+    if (p == 0) { Pp = 1.0; Pm1 = 0.0; return; }
+    for (int k = 1; k < p; ++k) {
+        double c = ((2.0 * k + 1.0) * x * b - k * a) / (k + 1.0);
+        a = b;
+        b = c;
+    }
+    Pp = b;
+    Pm1 = a;
+}
+
+void gll_rule(int p, std::vector<double>& x, std::vector<double>& w) {
+    const int n = p + 1;
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    x[0] = -1.0;
+    x[p] = 1.0;
+    // interior nodes: roots of P_p', Newton from the Chebyshev-Lobatto points
+    for (int k = 1; k < p; ++k) {
+        double t = -std::cos(M_PI * k / p);
+        for (int it = 0; it < 100; ++it) {
+            double Pp, Pm1;
+            legendre_eval(p, t, Pp, Pm1);
+            double d1 = p * (t * Pp - Pm1) / (t * t - 1.0);                 // P_p'
+            double d2 = (2.0 * t * d1 - p * (p + 1.0) * Pp) / (1.0 - t * t);  // P_p''
+            double dt = d1 / d2;
+            t -= dt;
+            if (std::fabs(dt) < 1e-17) break;
+        }
+        x[k] = t;
+    }
+    std::vector<double> s(x);
+    for (int k = 0; k < n; ++k) x[k] = 0.5 * (s[k] - s[p - k]);
+    for (int k = 0; k < n; ++k) {
+        double Pp, Pm1;
+        legendre_eval(p, x[k], Pp, Pm1);
+        w[k] = 2.0 / (p * (p + 1.0) * Pp * Pp);
+    }
+}
+
+void gll_derivative(const std::vector<double>& x, std::vector<double>& D) {
+    // Closed form for the GLL collocation derivative (e.g. Canuto, Hussaini,
+    // Quarteroni & Zang, Spectral Methods, eq. 2.4.34):
+    // D_ij = P_p(x_i) / (P_p(x_j) (x_i - x_j)) for i != j, D_00 = -p(p+1)/4,
+    // D_pp = p(p+1)/4, other diagonal entries 0.
+    const int n = (int)x.size();
+    const int p = n - 1;
+    std::vector<double> L(n);
+    for (int i = 0; i < n; ++i) {
+        double Pp, Pm1;
+        legendre_eval(p, x[i], Pp, Pm1);
+        L[i] = Pp;
+    }
+    D.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (i != j) D[(size_t)i * n + j] = L[i] / (L[j] * (x[i] - x[j]));
+    if (p >= 1) {
+        D[0] = -p * (p + 1.0) / 4.0;
+        D[(size_t)p * n + p] = p * (p + 1.0) / 4.0;
+    }
+}
+
+// --------------------------------------------------------------- geometry
+// Bilinear map X(xi, eta) = a + b xi + c eta + d xi eta of a quad with
+// counter-clockwise corners X0..X3 at (-1,-1), (1,-1), (1,1), (-1,1).
+static inline void jac_at(const double* X, double xi, double eta, double J[4]) {
+    // columns: dX/dxi, dX/deta
+    for (int a = 0; a < 2; ++a) {
+        double x0 = X[0 * 2 + a], x1 = X[1 * 2 + a], x2 = X[2 * 2 + a], x3 = X[3 * 2 + a];
+        J[a * 2 + 0] = 0.25 * ((x1 - x0) * (1.0 - eta) + (x2 - x3) * (1.0 + eta));
+        J[a * 2 + 1] = 0.25 * ((x3 - x0) * (1.0 - xi) + (x2 - x1) * (1.0 + xi));
+    }
+}
+
+std::string validate(const double* coords, int64_t nv, const int32_t* quads, int64_t ne, int p) {
+    if (nv <= 0 || ne <= 0) return "empty mesh";
+    if (p < 1 || p > 8) return "order must be in 1..8";
+    std::vector<uint8_t> used((size_t)nv, 0);
+    for (int64_t i = 0; i < ne * 4; ++i) {
+        int32_t v = quads[i];
+        if (v < 0 || v >= nv) return "quad vertex index out of range";
+        used[(size_t)v] = 1;
+    }
+    for (int64_t v = 0; v < nv; ++v)
+        if (!used[(size_t)v]) return "unreferenced vertex " + std::to_string(v);
+    for (int64_t i = 0; i < nv * 2; ++i)
+        if (!std::isfinite(coords[i])) return "non-finite coordinate";
+    std::unordered_map<uint64_t, int> ecount;
+    ecount.reserve((size_t)ne * 3);
+    for (int64_t e = 0; e < ne; ++e) {
+        const int32_t* q = quads + e * 4;
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (q[a] == q[b]) return "quad " + std::to_string(e) + " repeats a vertex";
+        for (int le = 0; le < 4; ++le) {
+            uint64_t lo = (uint64_t)std::min(q[le], q[(le + 1) & 3]);
+            uint64_t hi = (uint64_t)std::max(q[le], q[(le + 1) & 3]);
+            if (++ecount[lo * (uint64_t)nv + hi] > 2) return "edge shared by more than two quads";
+        }
+    }
+    std::vector<double> x, w;
+    gll_rule(p, x, w);
+    for (int64_t e = 0; e < ne; ++e) {
+        double X[8];
+        for (int c = 0; c < 4; ++c) {
+            X[c * 2 + 0] = coords[(size_t)quads[e * 4 + c] * 2 + 0];
+            X[c * 2 + 1] = coords[(size_t)quads[e * 4 + c] * 2 + 1];
+        }
+        for (int j = 0; j <= p; ++j)
+            for (int i = 0; i <= p; ++i) {
+                double J[4];
+                jac_at(X, x[i], x[j], J);
+                double det = J[0] * J[3] - J[1] * J[2];
+                if (!(det > 0.0))
+                    return "non-positive Jacobian in quad " + std::to_string(e) +
+                           " (clockwise or degenerate)";
+            }
+    }
+    return "";
+}
+
+// ------------------------------------------------------- canonical numbering
+void number_nodes(Mesh& m) {
+    const int p = m.p, n = p + 1, P = n * n;
+    m.np = n;
+    m.P = P;
+    m.conn.assign((size_t)m.ne * P, -1);
+    m.edge_lo.clear();
+    m.edge_hi.clear();
+    m.edge_first.clear();
+    std::unordered_map<uint64_t, int64_t> edge_id;
+    edge_id.reserve((size_t)m.ne * 3);
+    const int corner[4] = {0, p, p * n + p, p * n};
+    int64_t next = m.nv;
+    // pass 1: edges in order of first appearance
+    std::vector<int64_t> eid((size_t)m.ne * 4);
+    for (int64_t e = 0; e < m.ne; ++e) {
+        const int32_t* q = &m.quads[(size_t)e * 4];
+        for (int le = 0; le < 4; ++le) {
+            int64_t va = q[le], vb = q[(le + 1) & 3];
+            int64_t lo = std::min(va, vb), hi = std::max(va, vb);
+            uint64_t key = (uint64_t)lo * (uint64_t)m.nv + (uint64_t)hi;
+            auto it = edge_id.find(key);
+            int64_t id;
+            if (it == edge_id.end()) {
+                id = (int64_t)m.edge_lo.size();
+                edge_id.emplace(key, id);
+                m.edge_lo.push_back(lo);
+                m.edge_hi.push_back(hi);
+                m.edge_first.push_back(next);
+                next += p - 1;
+            } else {
+                id = it->second;
+            }
+            eid[(size_t)e * 4 + le] = id;
+        }
+    }
+    for (int64_t e = 0; e < m.ne; ++e) {
+        const int32_t* q = &m.quads[(size_t)e * 4];
+        int32_t* c = &m.conn[(size_t)e * P];
+        for (int k = 0; k < 4; ++k) c[corner[k]] = q[k];
+        for (int le = 0; le < 4; ++le) {
+            int64_t id = eid[(size_t)e * 4 + le];
+            bool forward = q[le] < q[(le + 1) & 3];  // walking from lower to higher id
+            for (int t = 1; t < p; ++t) {
+                // t-th interior point from the edge's first corner
+                int li;
+                if (le == 0) li = t;
+                else if (le == 1) li = t * n + p;
+                else if (le == 2) li = p * n + (p - t);
+                else li = (p - t) * n;
+                int k = forward ? t : p - t;  // position counted from the lower vertex
+                c[li] = (int32_t)(m.edge_first[(size_t)id] + (k - 1));
+            }
+        }
+    }
+    for (int64_t e = 0; e < m.ne; ++e) {
+        int32_t* c = &m.conn[(size_t)e * P];
+        for (int j = 1; j < p; ++j)
+            for (int i = 1; i < p; ++i) c[j * n + i] = (int32_t)(next++);
+    }
+    m.nn = next;
+}
+
+void node_coordinates(const Mesh& m, std::vector<double>& xy) {
+    std::vector<double> x, w;
+    gll_rule(m.p, x, w);
+    const int p = m.p, n = p + 1;
+    xy.assign((size_t)m.nn * 2, 0.0);
+    for (size_t i = 0; i < (size_t)m.nv * 2; ++i) xy[i] = m.coords[i];
+    for (size_t ed = 0; ed < m.edge_lo.size(); ++ed) {
+        const double* A = &m.coords[(size_t)m.edge_lo[ed] * 2];
+        const double* B = &m.coords[(size_t)m.edge_hi[ed] * 2];
+        for (int k = 1; k < p; ++k) {
+            double s = x[k];
+            int64_t id = m.edge_first[ed] + k - 1;
+            xy[(size_t)id * 2 + 0] = 0.5 * ((1.0 - s) * A[0] + (1.0 + s) * B[0]);
+            xy[(size_t)id * 2 + 1] = 0.5 * ((1.0 - s) * A[1] + (1.0 + s) * B[1]);
+        }
+    }
+    for (int64_t e = 0; e < m.ne; ++e) {
+        const int32_t* q = &m.quads[(size_t)e * 4];
+        const int32_t* c = &m.conn[(size_t)e * m.P];
+        for (int j = 1; j < p; ++j)
+            for (int i = 1; i < p; ++i) {
+                double xi = x[i], eta = x[j];
+                double f0 = 0.25 * (1 - xi) * (1 - eta), f1 = 0.25 * (1 + xi) * (1 - eta);
+                double f2 = 0.25 * (1 + xi) * (1 + eta), f3 = 0.25 * (1 - xi) * (1 + eta);
+                for (int a = 0; a < 2; ++a) {
+                    double v = ((f0 * m.coords[(size_t)q[0] * 2 + a] + f1 * m.coords[(size_t)q[1] * 2 + a]) +
+                                f2 * m.coords[(size_t)q[2] * 2 + a]) +
+                               f3 * m.coords[(size_t)q[3] * 2 + a];
+                    xy[(size_t)c[j * n + i] * 2 + a] = v;
+                }
+            }
+    }
+}
+
+// ------------------------------------------------ generalized Hilbert curve
+// Recursive split of a w x h block spanned by the integer vectors A (length w
+// along the curve's main direction) and B (length h), starting at origin O
+// and ending at O + (w-1) a. Long blocks (2w > 3h) are cut in two along A
+// (first part even when h is even); otherwise the block is cut into a
+// transposed lower-left part, the full-width upper part and a reversed
+// lower-right part, with the cut height made even so that every part admits a
+// path between the required corners.
+namespace {
+struct Frame {
+    int64_t ox, oy, ax, ay, bx, by;
+};
+inline int64_t sgn(int64_t v) { return (v > 0) - (v < 0); }
+}  // namespace
+
+void hilbert_cells(int64_t W, int64_t H, std::vector<int32_t>& cells) {
+    cells.clear();
+    cells.reserve((size_t)(W * H * 2));
+    std::vector<Frame> st;
+    if ((W & 1) && !(H & 1)) st.push_back({0, 0, 0, H, W, 0});
+    else st.push_back({0, 0, W, 0, 0, H});
+    while (!st.empty()) {
+        Frame f = st.back();
+        st.pop_back();
+        int64_t w = std::llabs(f.ax) + std::llabs(f.ay), h = std::llabs(f.bx) + std::llabs(f.by);
+        int64_t dax = sgn(f.ax), day = sgn(f.ay), dbx = sgn(f.bx), dby = sgn(f.by);
+        if (h == 1) {
+            for (int64_t i = 0; i < w; ++i) {
+                cells.push_back((int32_t)(f.ox + i * dax));
+                cells.push_back((int32_t)(f.oy + i * day));
+            }
+            continue;
+        }
+        if (w == 1) {
+            for (int64_t j = 0; j < h; ++j) {
+                cells.push_back((int32_t)(f.ox + j * dbx));
+                cells.push_back((int32_t)(f.oy + j * dby));
+            }
+            continue;
+        }
+        if (2 * w > 3 * h) {
+            int64_t w1 = w / 2;
+            if ((h % 2 == 0) && (w1 % 2 == 1) && w1 > 1) w1 -= 1;
+            Frame second{f.ox + w1 * dax, f.oy + w1 * day, (w - w1) * dax, (w - w1) * day, f.bx, f.by};
+            Frame first{f.ox, f.oy, w1 * dax, w1 * day, f.bx, f.by};
+            st.push_back(second);
+            st.push_back(first);
+        } else {
+            int64_t h1 = h / 2;
+            if ((h1 % 2 == 1) && h > 2) h1 += 1;
+            int64_t w1 = w / 2;
+            Frame lowleft{f.ox, f.oy, h1 * dbx, h1 * dby, w1 * dax, w1 * day};
+            Frame upper{f.ox + h1 * dbx, f.oy + h1 * dby, f.ax, f.ay, (h - h1) * dbx, (h - h1) * dby};
+            Frame lowright{f.ox + (w - 1) * dax + (h1 - 1) * dbx, f.oy + (w - 1) * day + (h1 - 1) * dby,
+                           -h1 * dbx, -h1 * dby, -(w - w1) * dax, -(w - w1) * day};
+            st.push_back(lowright);
+            st.push_back(upper);
+            st.push_back(lowleft);
+        }
+    }
+}
+
+// ------------------------------------------------------------- orderings
+static int64_t ceil_sqrt(int64_t n) {
+    int64_t r = (int64_t)std::sqrt((double)n);
+    while (r * r > n) --r;
+    while ((r + 1) * (r + 1) <= n) ++r;
+    return r * r == n ? r : r + 1;
+}
+
+void element_order_hilbert(const Mesh& m, std::vector<int64_t>& order) {
+    // Section 4.3: element centroids on a W x H grid over the bounding box,
+    // cells walked along the curve, elements of a cell appended in input order.
+    double xmin = std::numeric_limits<double>::infinity(), ymin = xmin;
+    double xmax = -xmin, ymax = -xmin;
+    for (int64_t v = 0; v < m.nv; ++v) {
+        xmin = std::min(xmin, m.coords[(size_t)v * 2]);
+        xmax = std::max(xmax, m.coords[(size_t)v * 2]);
+        ymin = std::min(ymin, m.coords[(size_t)v * 2 + 1]);
+        ymax = std::max(ymax, m.coords[(size_t)v * 2 + 1]);
+    }
+    const double wm = xmax - xmin, hm = ymax - ymin;
+    const int64_t W = ceil_sqrt(m.ne);
+    const double r = wm / hm;
+    int64_t H = (int64_t)std::ceil((double)W / r);
+    if (H < 1) H = 1;
+    std::vector<int32_t> cells;
+    hilbert_cells(W, H, cells);
+    std::vector<int64_t> rank((size_t)(W * H));
+    for (int64_t k = 0; k < W * H; ++k) rank[(size_t)(cells[k * 2] * H + cells[k * 2 + 1])] = k;
+    std::vector<int64_t> key((size_t)m.ne);
+    for (int64_t e = 0; e < m.ne; ++e) {
+        const int32_t* q = &m.quads[(size_t)e * 4];
+        double xs = (m.coords[(size_t)q[0] * 2] + m.coords[(size_t)q[1] * 2]) +
+                    (m.coords[(size_t)q[2] * 2] + m.coords[(size_t)q[3] * 2]);
+        double ys = (m.coords[(size_t)q[0] * 2 + 1] + m.coords[(size_t)q[1] * 2 + 1]) +
+                    (m.coords[(size_t)q[2] * 2 + 1] + m.coords[(size_t)q[3] * 2 + 1]);
+        double xc = xs * 0.25, yc = ys * 0.25;
+        double fx = std::floor(((xc - xmin) * (double)W) / wm);
+        double fy = std::floor(((yc - ymin) * (double)H) / hm);
+        int64_t ix = std::max<int64_t>(0, std::min<int64_t>(W - 1, (int64_t)fx));
+        int64_t iy = std::max<int64_t>(0, std::min<int64_t>(H - 1, (int64_t)fy));
+        key[(size_t)e] = rank[(size_t)(ix * H + iy)];
+    }
+    // stable counting sort by curve position
+    std::vector<int64_t> cnt((size_t)(W * H + 1), 0);
+    for (int64_t e = 0; e < m.ne; ++e) cnt[(size_t)key[(size_t)e] + 1]++;
+    for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+    order.assign((size_t)m.ne, 0);
+    for (int64_t e = 0; e < m.ne; ++e) order[(size_t)cnt[(size_t)key[(size_t)e]]++] = e;
+}
+
+void node_degrees(const Mesh& m, std::vector<int32_t>& deg) {
+    // degree = number of distinct other nodes sharing an element. Nodes of one
+    // element only have P-1; all interior nodes of an edge share one element
+    // set, so one evaluation per edge and per vertex suffices.
+    const int P = m.P, p = m.p;
+    deg.assign((size_t)m.nn, P - 1);
+    // vertex -> elements, edge -> elements
+    std::vector<int64_t> vptr((size_t)m.nv + 1, 0);
+    for (int64_t i = 0; i < m.ne * 4; ++i) vptr[(size_t)m.quads[(size_t)i] + 1]++;
+    for (size_t k = 1; k < vptr.size(); ++k) vptr[k] += vptr[k - 1];
+    std::vector<int64_t> vel((size_t)(m.ne * 4));
+    {
+        std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
+        for (int64_t e = 0; e < m.ne; ++e)
+            for (int c = 0; c < 4; ++c) vel[(size_t)fill[(size_t)m.quads[(size_t)e * 4 + c]]++] = e;
+    }
+    std::vector<int64_t> stamp((size_t)m.nn, -1);
+    int64_t tag = 0;
+    auto count_union = [&](const int64_t* els, int k) {
+        ++tag;
+        int32_t c = 0;
+        for (int t = 0; t < k; ++t) {
+            const int32_t* cc = &m.conn[(size_t)els[t] * P];
+            for (int q = 0; q < P; ++q)
+                if (stamp[(size_t)cc[q]] != tag) {
+                    stamp[(size_t)cc[q]] = tag;
+                    ++c;
+                }
+        }
+        return c - 1;
+    };
+    for (int64_t v = 0; v < m.nv; ++v)
+        deg[(size_t)v] = count_union(&vel[(size_t)vptr[(size_t)v]], (int)(vptr[(size_t)v + 1] - vptr[(size_t)v]));
+    if (p >= 2) {
+        // elements of an edge = elements holding both of its vertices
+        for (size_t ed = 0; ed < m.edge_lo.size(); ++ed) {
+            int64_t a = m.edge_lo[ed], b = m.edge_hi[ed];
+            int64_t els[8];
+            int k = 0;
+            for (int64_t t = vptr[(size_t)a]; t < vptr[(size_t)a + 1]; ++t) {
+                int64_t e = vel[(size_t)t];
+                const int32_t* q = &m.quads[(size_t)e * 4];
+                for (int c = 0; c < 4; ++c) {
+                    if (q[c] == b && (q[(c + 1) & 3] == a || q[(c + 3) & 3] == a)) {
+                        if (k < 8) els[k++] = e;
+                        break;
+                    }
+                }
+            }
+            int32_t d = count_union(els, k);
+            for (int t = 1; t < p; ++t) deg[(size_t)(m.edge_first[ed] + t - 1)] = d;
+        }
+    }
+}
+
+void renumber_nodes(const Mesh& m, const std::vector<int64_t>& elem_order, const std::vector<int32_t>& deg,
+                    std::vector<int64_t>& node_order) {
+    // Section 4.3 node procedure: first touch along the element order, each
+    // element's new nodes sorted by ascending degree (stable).
+    const int P = m.P;
+    std::vector<uint8_t> seen((size_t)m.nn, 0);
+    node_order.clear();
+    node_order.reserve((size_t)m.nn);
+    std::vector<int64_t> group;
+    group.reserve((size_t)P);
+    for (int64_t e : elem_order) {
+        group.clear();
+        const int32_t* c = &m.conn[(size_t)e * P];
+        for (int q = 0; q < P; ++q)
+            if (!seen[(size_t)c[q]]) {
+                seen[(size_t)c[q]] = 1;
+                group.push_back(c[q]);
+            }
+        std::stable_sort(group.begin(), group.end(),
+                         [&](int64_t a, int64_t b) { return deg[(size_t)a] < deg[(size_t)b]; });
+        node_order.insert(node_order.end(), group.begin(), group.end());
+    }
+}
+
+static inline uint64_t splitmix_next(uint64_t& s) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void random_order(int64_t n, uint64_t seed, std::vector<int64_t>& order) {
+    order.resize((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    uint64_t s = seed;
+    for (int64_t i = n - 1; i >= 1; --i) {
+        uint64_t j = splitmix_next(s) % (uint64_t)(i + 1);
+        std::swap(order[(size_t)i], order[(size_t)j]);
+    }
+}
+
+void orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_t>& eo, std::vector<int64_t>& no) {
+    if (kind == 0) {
+        eo.resize((size_t)m.ne);
+        std::iota(eo.begin(), eo.end(), 0);
+        no.resize((size_t)m.nn);
+        std::iota(no.begin(), no.end(), 0);
+        return;
+    }
+    if (kind == 2) {
+        random_order(m.ne, seed + 2, eo);
+        random_order(m.nn, seed + 3, no);
+        return;
+    }
+    if (kind == 1) {
+        eo.resize((size_t)m.ne);
+        std::iota(eo.begin(), eo.end(), 0);
+    } else {
+        element_order_hilbert(m, eo);
+    }
+    std::vector<int32_t> deg;
+    node_degrees(m, deg);
+    renumber_nodes(m, eo, deg, no);
+}
+
+int64_t snap(const std::vector<double>& xy, double x, double y) {
+    int64_t best = 0;
+    double bd = std::numeric_limits<double>::infinity();
+    const int64_t n = (int64_t)(xy.size() / 2);
+    for (int64_t i = 0; i < n; ++i) {
+        double dx = xy[(size_t)i * 2] - x, dy = xy[(size_t)i * 2 + 1] - y;
+        double d = dx * dx + dy * dy;
+        if (d < bd) {
+            bd = d;
+            best = i;
+        }
+    }
+    return best;
+}
+
+double cfl_dt(const Mesh& m, const double* vel) {
+    std::vector<double> x, w;
+    gll_rule(m.p, x, w);
+    const int n = m.p + 1;
+    double best = std::numeric_limits<double>::infinity();
+    std::vector<double> pts((size_t)n * n * 2);
+    for (int64_t e = 0; e < m.ne; ++e) {
+        const int32_t* q = &m.quads[(size_t)e * 4];
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double xi = x[i], eta = x[j];
+                double f0 = 0.25 * (1 - xi) * (1 - eta), f1 = 0.25 * (1 + xi) * (1 - eta);
+                double f2 = 0.25 * (1 + xi) * (1 + eta), f3 = 0.25 * (1 - xi) * (1 + eta);
+                for (int a = 0; a < 2; ++a)
+                    pts[((size_t)j * n + i) * 2 + a] =
+                        ((f0 * m.coords[(size_t)q[0] * 2 + a] + f1 * m.coords[(size_t)q[1] * 2 + a]) +
+                         f2 * m.coords[(size_t)q[2] * 2 + a]) +
+                        f3 * m.coords[(size_t)q[3] * 2 + a];
+            }
+        double dmin = std::numeric_limits<double>::infinity();
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i + 1 < n; ++i) {
+                const double* A = &pts[((size_t)j * n + i) * 2];
+                const double* B = &pts[((size_t)j * n + i + 1) * 2];
+                dmin = std::min(dmin, std::hypot(B[0] - A[0], B[1] - A[1]));
+            }
+        for (int j = 0; j + 1 < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                const double* A = &pts[((size_t)j * n + i) * 2];
+                const double* B = &pts[((size_t)(j + 1) * n + i) * 2];
+                dmin = std::min(dmin, std::hypot(B[0] - A[0], B[1] - A[1]));
+            }
+        best = std::min(best, dmin / vel[e]);
+    }
+    return best;
+}
+
+// ------------------------------------------------------------ block plan
+void build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P, int64_t nn, int eb, BlockPlan& pl) {
+    pl.eb = eb;
+    pl.nblocks = (ne + eb - 1) / eb;
+    const int64_t nb = pl.nblocks;
+    std::vector<int32_t> valence((size_t)nn, 0);
+    for (int64_t s = 0; s < ne * P; ++s) valence[(size_t)conn[(size_t)s]]++;
+    pl.lidx.assign((size_t)(ne * P), 0);
+    pl.lsl.assign((size_t)(ne * P), 0);
+    pl.ent_ptr.assign((size_t)nb + 1, 0);
+    pl.ent_gid.clear();
+    pl.ent_pslot.clear();
+    pl.lrow.clear();
+    pl.max_entries = 0;
+    std::vector<int32_t> local((size_t)nn, -1);     // entry id of a node in the current block
+    std::vector<int64_t> owner_block((size_t)nn, -1);
+    std::vector<int32_t> opencount((size_t)nn, 0);
+    std::vector<int32_t> cnt;
+    // pass 1: entries, local CSR, closedness
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t e0 = b * eb, e1 = std::min(ne, e0 + eb);
+        int64_t s0 = e0 * P, s1 = e1 * P;
+        int32_t nent = 0;
+        int64_t ebase = (int64_t)pl.ent_gid.size();
+        cnt.clear();
+        for (int64_t s = s0; s < s1; ++s) {
+            int32_t g = conn[(size_t)s];
+            if (owner_block[(size_t)g] != b) {
+                owner_block[(size_t)g] = b;
+                local[(size_t)g] = nent++;
+                pl.ent_gid.push_back(g);
+                cnt.push_back(0);
+            }
+            int32_t l = local[(size_t)g];
+            pl.lidx[(size_t)s] = (uint16_t)l;
+            cnt[(size_t)l]++;
+        }
+        pl.max_entries = std::max(pl.max_entries, (int)nent);
+        // local CSR (offsets relative to the block's first slot)
+        size_t rbase = pl.lrow.size();
+        pl.lrow.resize(rbase + (size_t)nent + 1);
+        pl.lrow[rbase] = 0;
+        for (int32_t l = 0; l < nent; ++l) pl.lrow[rbase + l + 1] = (uint16_t)(pl.lrow[rbase + l] + cnt[(size_t)l]);
+        std::vector<uint16_t> fill(pl.lrow.begin() + rbase, pl.lrow.begin() + rbase + nent);
+        for (int64_t s = s0; s < s1; ++s) {
+            int32_t l = pl.lidx[(size_t)s];
+            pl.lsl[(size_t)(s0 + fill[(size_t)l]++)] = (uint16_t)(s - s0);
+        }
+        for (int32_t l = 0; l < nent; ++l) {
+            int32_t g = pl.ent_gid[(size_t)(ebase + l)];
+            bool closed = cnt[(size_t)l] == valence[(size_t)g];
+            pl.ent_pslot.push_back(closed ? -1 : 0);
+            if (!closed) opencount[(size_t)g]++;
+        }
+        pl.ent_ptr[(size_t)b + 1] = (int32_t)pl.ent_gid.size();
+    }
+    // open nodes ascending, partial slots grouped per node in block order
+    pl.open_gid.clear();
+    pl.open_ptr.assign(1, 0);
+    std::vector<int32_t> first((size_t)nn, -1);
+    for (int64_t g = 0; g < nn; ++g)
+        if (opencount[(size_t)g] > 0) {
+            first[(size_t)g] = pl.open_ptr.back();
+            pl.open_gid.push_back((int32_t)g);
+            pl.open_ptr.push_back(pl.open_ptr.back() + opencount[(size_t)g]);
+        }
+    pl.npartial = pl.open_ptr.back();
+    for (size_t k = 0; k < pl.ent_gid.size(); ++k)
+        if (pl.ent_pslot[k] >= 0) pl.ent_pslot[k] = first[(size_t)pl.ent_gid[k]]++;
+}
+
+}  // namespace semhost

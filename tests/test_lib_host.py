@@ -1,0 +1,136 @@
+"""Host-side parts of the C ABI, checked against the oracle on the CPU:
+exported symbols, canonical numbering, Hilbert curve, orderings (bit-exact),
+snapping, CFL step and input validation. No device is touched."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gen
+from oracle import hilbert, mesh, ordering, sem as osem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_08416_gb300 import build
+    build.build()
+    import paper_2104_08416_gb300 as P
+    return P
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "sem.h")).read()
+    declared = set(re.findall(r"^\s*(?:sem_status|void|const char\*)\s+(sem_\w+)\(", hdr, re.M))
+    assert len(declared) >= 25
+    assert declared == set(lib.EXPORTS)
+    so = lib.load()
+    for name in declared:
+        assert hasattr(so, name), name
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (2, 2), (4, 4), (32, 32), (3, 5), (5, 4), (7, 7), (64, 16), (2048, 8),
+                                 (13, 29), (1, 9), (9, 1), (100, 37)])
+def test_hilbert_cells_bit_exact(lib, W, H):
+    np.testing.assert_array_equal(lib.sem_hilbert_cells(W, H), hilbert.generalized_cells(W, H))
+
+
+def test_hilbert_cells_listing1_order5(lib):
+    np.testing.assert_array_equal(lib.sem_hilbert_cells(32, 32), hilbert.listing1_cells(5))
+
+
+def _meshes():
+    yield "unit32", gen.unit_square(32)
+    yield "graded24", gen.graded(24, seed=7)
+    yield "graded_relab", gen.relabel(gen.graded(12, seed=3), seed=5)
+    yield "layered", gen.layered(64, 16)
+    yield "unit_relab", gen.relabel(gen.unit_square(10), seed=1)
+
+
+@pytest.mark.parametrize("kind", ["none", "rowmajor", "random", "hilbert"])
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_orderings_bit_exact(lib, kind, p):
+    for name, m in _meshes():
+        conn, n, _ = mesh.canonical_numbering(m["quads"], m["coords"].shape[0], p)
+        eo_ref, no_ref = ordering.orderings(kind, m["coords"], m["quads"], conn, n, seed=12345)
+        eo, no = lib.sem_compute_ordering(m["coords"], m["quads"], p, kind, seed=12345)
+        np.testing.assert_array_equal(eo, eo_ref, err_msg=name)
+        np.testing.assert_array_equal(no, no_ref, err_msg=name)
+
+
+def test_node_count(lib):
+    for name, m in _meshes():
+        for p in (1, 3, 8):
+            _, n, _ = mesh.canonical_numbering(m["quads"], m["coords"].shape[0], p)
+            assert lib.sem_count_nodes(m["quads"], m["coords"].shape[0], p) == n
+
+
+@pytest.mark.parametrize("p", [1, 2, 4, 7])
+def test_node_coordinates_and_snapping(lib, p):
+    m = gen.relabel(gen.graded(8, seed=2), seed=4)
+    h = lib.SEM(m["coords"], m["quads"], p, "fp64", stream=0)
+    S = osem.SEM(m["coords"], m["quads"], p, m["vel"], m["rho"])
+    assert h.n_nodes == S.n_nodes
+    np.testing.assert_allclose(h.sem_node_coordinates(), S.node_xy, rtol=0, atol=1e-15)
+    h.sem_set_model(m["vel"], m["rho"])
+    assert abs(h.sem_cfl_dt() - S.cfl_dt()) <= 1e-14 * S.cfl_dt()
+    h.sem_set_source(10.0, 0.12, 1.0, 0.37, 0.61)
+    rec = np.array([[0.0, 0.0], [0.5, 1.0], [0.93, 0.12]])
+    h.sem_set_receivers(rec, 10)
+    s, r = h.sem_get_snapped()
+    assert s == osem.snap(S.node_xy, 0.37, 0.61)
+    assert r.tolist() == [osem.snap(S.node_xy, x, y) for x, y in rec]
+    h.sem_reorder("hilbert")
+    e_new, n_new = h.sem_get_permutation()
+    conn, n, _ = mesh.canonical_numbering(m["quads"], m["coords"].shape[0], p)
+    eo, no = ordering.orderings("hilbert", m["coords"], m["quads"], conn, n)
+    np.testing.assert_array_equal(e_new, ordering.inverse(eo))
+    np.testing.assert_array_equal(n_new, ordering.inverse(no))
+    h.sem_destroy()
+
+
+def test_gll_rule_through_cfl(lib):
+    """The CFL step of one affine square element of side 1 is the smallest GLL
+    spacing / 2 (nodes on [-1, 1] scaled to [0, 1]); p = 4: (1 - sqrt(3/7)) / 2."""
+    coords = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    quads = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    h = lib.SEM(coords, quads, 4, "fp64", stream=0)
+    h.sem_set_model([2.0])
+    assert abs(h.sem_cfl_dt() - (1 - np.sqrt(3 / 7)) / 2 / 2.0) < 1e-15
+
+
+def _expect_invalid(lib, coords, quads, p=2):
+    with pytest.raises(lib.SemError) as ei:
+        lib.SEM(coords, quads, p, "fp64", stream=0)
+    assert ei.value.status == lib.SEM_ERR_INVALID_ARG
+
+
+def test_invalid_meshes_rejected(lib):
+    sq = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    _expect_invalid(lib, sq, np.array([[0, 3, 2, 1]], dtype=np.int32))          # clockwise
+    _expect_invalid(lib, sq, np.array([[0, 1, 2, 4]], dtype=np.int32))          # index out of range
+    _expect_invalid(lib, np.vstack([sq, [[5.0, 5.0]]]), np.array([[0, 1, 2, 3]], dtype=np.int32))  # unused vertex
+    _expect_invalid(lib, sq, np.array([[0, 1, 1, 3]], dtype=np.int32))          # repeated vertex
+    bow = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])          # self-intersecting
+    _expect_invalid(lib, bow, np.array([[0, 1, 2, 3]], dtype=np.int32))
+    _expect_invalid(lib, sq, np.array([[0, 1, 2, 3]], dtype=np.int32), p=9)    # order too high
+    _expect_invalid(lib, sq, np.zeros((0, 4), dtype=np.int32))                  # empty
+
+
+def test_state_errors_before_device(lib):
+    m = gen.unit_square(2)
+    h = lib.SEM(m["coords"], m["quads"], 2, "fp32_kahan", stream=0)
+    with pytest.raises(lib.SemError) as ei:
+        h.sem_step(1)                      # no model, no dt
+    assert ei.value.status == lib.SEM_ERR_STATE
+    with pytest.raises(lib.SemError):
+        h.sem_set_model(np.full(4, -1.0))
+    with pytest.raises(lib.SemError):
+        h.sem_set_dt(0.0)
+    with pytest.raises(lib.SemError):
+        h.sem_reorder(7)
+    with pytest.raises(lib.SemError):
+        h.sem_set_source(-1.0, 0.0, 1.0, 0.5, 0.5)
+    h.sem_destroy()
