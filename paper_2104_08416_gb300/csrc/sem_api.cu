@@ -73,7 +73,7 @@ struct sem_mesh {
     int32_t* d_quads = nullptr;
     double* d_rho = nullptr;
     double* d_vel = nullptr;
-    float4* d_coef = nullptr;
+    uint8_t* d_packet = nullptr;
     double* d_G64 = nullptr;
     double* d_mloc = nullptr;
     double* d_M = nullptr;
@@ -208,9 +208,13 @@ sem_status fill_source(sem_mesh* m, int64_t upto) {
     return SEM_OK;
 }
 
-int default_eb(int P) {
-    int eb = 1600 / P;
-    return eb < 1 ? 1 : eb;
+int default_eb(int np) {
+    // a multiple of the kernel's element lanes, about 1500 points per block
+    const int P = np * np;
+    const int lanes = semdev::lanes_for(np);
+    int rounds = (1536 + lanes * P / 2) / (lanes * P);
+    if (rounds < 1) rounds = 1;
+    return lanes * rounds;
 }
 
 sem_status build(sem_mesh* m) {
@@ -231,41 +235,37 @@ sem_status build(sem_mesh* m) {
         rho_new[(size_t)en] = m->rho[(size_t)eo];
         vel_new[(size_t)en] = m->vel[(size_t)eo];
     }
-    int eb = m->eb_request > 0 ? m->eb_request : default_eb(P);
+    int eb = m->eb_request > 0 ? m->eb_request : default_eb(M.np);
     if ((int64_t)eb * P > 65535) eb = 65535 / P;
     semhost::build_block_plan(conn_new, M.ne, P, M.nn, eb, m->plan);
     conn_new.clear();
     conn_new.shrink_to_fit();
     const auto& pl = m->plan;
-    m->smem = semdev::smem_bytes_for(P, pl.eb, pl.max_entries, fp64(m));
+    m->smem = semdev::smem_bytes_for(P, pl.eb, pl.max_entries, (int)pl.max_packet, fp64(m), mode_of(m));
     if (m->smem > 227 * 1024) return fail(m, SEM_ERR_UNSUPPORTED, "block plan does not fit in shared memory");
 
     sem_status st;
-    uint16_t *lidx, *lrow, *lsl;
-    int32_t *ent_ptr, *ent_gid, *ent_pslot, *open_gid, *open_ptr;
-    if ((st = upload(m, &lidx, pl.lidx.data(), pl.lidx.size())) != SEM_OK) return st;
-    if ((st = upload(m, &lrow, pl.lrow.data(), pl.lrow.size())) != SEM_OK) return st;
-    if ((st = upload(m, &lsl, pl.lsl.data(), pl.lsl.size())) != SEM_OK) return st;
-    if ((st = upload(m, &ent_ptr, pl.ent_ptr.data(), pl.ent_ptr.size())) != SEM_OK) return st;
-    if ((st = upload(m, &ent_gid, pl.ent_gid.data(), pl.ent_gid.size())) != SEM_OK) return st;
-    if ((st = upload(m, &ent_pslot, pl.ent_pslot.data(), pl.ent_pslot.size())) != SEM_OK) return st;
+    uint8_t* packet;
+    int32_t *hdr, *open_gid, *open_ptr, *open_src;
+    if ((st = upload(m, &packet, pl.packet.data(), pl.packet.size())) != SEM_OK) return st;
+    if ((st = upload(m, &hdr, pl.hdr.data(), pl.hdr.size())) != SEM_OK) return st;
     if ((st = upload(m, &open_gid, pl.open_gid.data(), pl.open_gid.size())) != SEM_OK) return st;
     if ((st = upload(m, &open_ptr, pl.open_ptr.data(), pl.open_ptr.size())) != SEM_OK) return st;
+    if ((st = upload(m, &open_src, pl.open_src.data(), pl.open_src.size())) != SEM_OK) return st;
+    m->d_packet = packet;
     semdev::Plan& dp = m->dplan;
-    dp.lidx = lidx;
-    dp.lrow = lrow;
-    dp.lsl = lsl;
-    dp.ent_ptr = ent_ptr;
-    dp.ent_gid = ent_gid;
-    dp.ent_pslot = ent_pslot;
+    dp.packet = packet;
+    dp.hdr = reinterpret_cast<const int4*>(hdr);
     dp.open_gid = open_gid;
     dp.open_ptr = open_ptr;
+    dp.open_src = open_src;
     dp.open_rec = nullptr;
     dp.ne = M.ne;
     dp.eb = pl.eb;
     dp.nblocks = (int)pl.nblocks;
     dp.nopen = (int)pl.open_gid.size();
     dp.max_entries = pl.max_entries;
+    dp.max_packet = (int)pl.max_packet;
 
     fill_basis(m->basis64, M.p);
     fill_basis(m->basis32, M.p);
@@ -283,12 +283,9 @@ sem_status build(sem_mesh* m) {
     if (fp64(m)) {
         m->d_G64 = (double*)dev_alloc(m, nslot * 3 * 8);
         if (!m->d_G64) return fail(m, SEM_ERR_OOM, "device allocation failed");
-    } else {
-        m->d_coef = (float4*)dev_alloc(m, (size_t)M.ne * 2 * sizeof(float4));
-        if (!m->d_coef) return fail(m, SEM_ERR_OOM, "device allocation failed");
     }
-    SEM_CUDA(semdev::launch_geometry(M.np, m->d_coords, m->d_quads, m->d_rho, m->d_vel, M.ne, m->basis64, m->d_coef,
-                                     m->d_G64, nullptr, m->d_mloc, m->stream));
+    SEM_CUDA(semdev::launch_geometry(M.np, m->d_coords, m->d_quads, m->d_rho, m->d_vel, dp, m->basis64, m->d_packet,
+                                     m->d_G64, m->d_mloc, m->stream));
     SEM_CUDA(semdev::launch_mass(dp, P, m->d_mloc, (double*)m->d_partial, m->d_M, m->stream));
 
     // time-stepping state
@@ -356,7 +353,6 @@ semdev::StepArgs<T> step_args(sem_mesh* m) {
     a.partial = (T*)m->d_partial;
     a.G = (const T*)m->d_G64;
     a.gstride = m->mesh.ne * m->mesh.P;
-    a.coef = m->d_coef;
     a.apply_out = nullptr;
     a.src_f = m->d_src;
     a.step = m->step;
@@ -861,23 +857,19 @@ sem_status sem_traffic_model(const sem_mesh* m, double* block_bytes, double* ope
     const auto& pl = m->plan;
     const double ts = (double)tsize(m);
     const double slots = (double)m->mesh.ne * m->mesh.P;
-    const double nent = (double)pl.ent_gid.size();
-    const double nb = (double)pl.nblocks;
     const double nopen = (double)pl.open_gid.size();
-    const double nn = (double)m->mesh.nn;
-    const double nclosed = nn - nopen;
-    // node state touched by the update: Kahan: u in, u out, s, delta r/w,
-    // comp r/w; three-level: u in, u out, s, u^{n-1}
+    const double nclosed_nodes = (double)pl.nclosed_total;
+    const double nopen_entries = (double)(pl.nent_total - pl.nclosed_total);
+    // node state read and written by an update: Kahan: u in, u out, s, delta
+    // in/out, comp in/out; three-level: u in, u out, s, u^{n-1}
     const double upd = m->prec == SEM_FP32_KAHAN ? 7.0 * ts : 4.0 * ts;
-    double geo = fp64(m) ? slots * 3.0 * ts : (double)m->mesh.ne * 32.0;
-    double blk = slots * 2.0 * 2.0                 // lidx + lsl
-                 + (nent + nb) * 2.0               // lrow
-                 + nent * 8.0 + (nb + 1) * 4.0      // ent_gid, ent_pslot, ent_ptr
-                 + geo                              // geometry
-                 + nopen * ts                       // u at open nodes (gather)
-                 + nclosed * upd                    // closed nodes: gather + update
-                 + (double)pl.npartial * ts;        // partial sums written
-    double opn = nopen * (8.0 + upd) + (double)pl.npartial * ts + (m->nrec > 0 ? nopen * 4.0 : 0.0);
+    const double geo = fp64(m) ? slots * 3.0 * ts : 0.0;   // FP32: geometry is in the packet
+    const double blk = (double)pl.packet.size() + (double)pl.nblocks * 16.0  // packets + headers
+                       + geo                                                // stored metric (FP64)
+                       + nopen * ts                                         // u at open nodes
+                       + nclosed_nodes * upd                                // closed nodes: u + update
+                       + nopen_entries * ts;                                // partial sums written
+    const double opn = nopen * (8.0 + upd) + nopen_entries * (4.0 + ts) + (m->nrec > 0 ? nopen * 4.0 : 0.0);
     if (block_bytes) *block_bytes = blk;
     if (open_bytes) *open_bytes = opn;
     return SEM_OK;

@@ -519,62 +519,108 @@ double cfl_dt(const Mesh& m, const double* vel) {
 }
 
 // ------------------------------------------------------------ block plan
+static inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+PacketLayout packet_layout(int64_t nslot, int64_t nent, int64_t neb) {
+    PacketLayout L;
+    L.lidx = 0;
+    L.lsl = 2 * nslot;
+    L.lrow = 4 * nslot;
+    L.gid = align_up(L.lrow + 2 * (nent + 1), 4);
+    L.coef = align_up(L.gid + 4 * nent, 16);
+    L.bytes = align_up(L.coef + 32 * neb, 16);
+    return L;
+}
+
 void build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P, int64_t nn, int eb, BlockPlan& pl) {
     pl.eb = eb;
     pl.nblocks = (ne + eb - 1) / eb;
     const int64_t nb = pl.nblocks;
     std::vector<int32_t> valence((size_t)nn, 0);
     for (int64_t s = 0; s < ne * P; ++s) valence[(size_t)conn[(size_t)s]]++;
-    pl.lidx.assign((size_t)(ne * P), 0);
-    pl.lsl.assign((size_t)(ne * P), 0);
-    pl.ent_ptr.assign((size_t)nb + 1, 0);
-    pl.ent_gid.clear();
-    pl.ent_pslot.clear();
-    pl.lrow.clear();
+    pl.hdr.assign((size_t)nb * 4, 0);
+    pl.packet.clear();
     pl.max_entries = 0;
-    std::vector<int32_t> local((size_t)nn, -1);     // entry id of a node in the current block
-    std::vector<int64_t> owner_block((size_t)nn, -1);
+    pl.max_packet = 0;
+    pl.nent_total = pl.nclosed_total = 0;
+    std::vector<int32_t> local((size_t)nn, -1);
+    std::vector<int64_t> seen_block((size_t)nn, -1);
     std::vector<int32_t> opencount((size_t)nn, 0);
-    std::vector<int32_t> cnt;
-    // pass 1: entries, local CSR, closedness
+    std::vector<int32_t> first_ent, cnt, order, rank;
+    std::vector<uint16_t> lidx, lsl, lrow;
+    std::vector<int32_t> gid;
+    // open entries of each block, in entry order, as node ids (for pass 2)
+    std::vector<int32_t> open_nodes_flat;
+    std::vector<int64_t> open_nodes_ptr(1, 0);
+    int64_t pbase = 0;
     for (int64_t b = 0; b < nb; ++b) {
-        int64_t e0 = b * eb, e1 = std::min(ne, e0 + eb);
-        int64_t s0 = e0 * P, s1 = e1 * P;
-        int32_t nent = 0;
-        int64_t ebase = (int64_t)pl.ent_gid.size();
+        const int64_t e0 = b * eb, e1 = std::min(ne, e0 + eb);
+        const int64_t s0 = e0 * P, nslot = (e1 - e0) * P;
+        // entries by first appearance
+        first_ent.clear();
         cnt.clear();
-        for (int64_t s = s0; s < s1; ++s) {
-            int32_t g = conn[(size_t)s];
-            if (owner_block[(size_t)g] != b) {
-                owner_block[(size_t)g] = b;
-                local[(size_t)g] = nent++;
-                pl.ent_gid.push_back(g);
+        std::vector<int32_t> raw((size_t)nslot);
+        for (int64_t t = 0; t < nslot; ++t) {
+            int32_t g = conn[(size_t)(s0 + t)];
+            if (seen_block[(size_t)g] != b) {
+                seen_block[(size_t)g] = b;
+                local[(size_t)g] = (int32_t)first_ent.size();
+                first_ent.push_back(g);
                 cnt.push_back(0);
             }
-            int32_t l = local[(size_t)g];
-            pl.lidx[(size_t)s] = (uint16_t)l;
-            cnt[(size_t)l]++;
+            raw[(size_t)t] = local[(size_t)g];
+            cnt[(size_t)local[(size_t)g]]++;
         }
-        pl.max_entries = std::max(pl.max_entries, (int)nent);
-        // local CSR (offsets relative to the block's first slot)
-        size_t rbase = pl.lrow.size();
-        pl.lrow.resize(rbase + (size_t)nent + 1);
-        pl.lrow[rbase] = 0;
-        for (int32_t l = 0; l < nent; ++l) pl.lrow[rbase + l + 1] = (uint16_t)(pl.lrow[rbase + l] + cnt[(size_t)l]);
-        std::vector<uint16_t> fill(pl.lrow.begin() + rbase, pl.lrow.begin() + rbase + nent);
-        for (int64_t s = s0; s < s1; ++s) {
-            int32_t l = pl.lidx[(size_t)s];
-            pl.lsl[(size_t)(s0 + fill[(size_t)l]++)] = (uint16_t)(s - s0);
-        }
+        const int32_t nent = (int32_t)first_ent.size();
+        // closed entries first, then open, each in first-appearance order
+        rank.assign((size_t)nent, 0);
+        int32_t nclosed = 0;
+        for (int32_t l = 0; l < nent; ++l)
+            if (cnt[(size_t)l] == valence[(size_t)first_ent[(size_t)l]]) nclosed++;
+        int32_t ic = 0, io = nclosed;
+        gid.assign((size_t)nent, 0);
+        std::vector<int32_t> c2((size_t)nent);
         for (int32_t l = 0; l < nent; ++l) {
-            int32_t g = pl.ent_gid[(size_t)(ebase + l)];
-            bool closed = cnt[(size_t)l] == valence[(size_t)g];
-            pl.ent_pslot.push_back(closed ? -1 : 0);
-            if (!closed) opencount[(size_t)g]++;
+            bool closed = cnt[(size_t)l] == valence[(size_t)first_ent[(size_t)l]];
+            int32_t r = closed ? ic++ : io++;
+            rank[(size_t)l] = r;
+            gid[(size_t)r] = first_ent[(size_t)l];
+            c2[(size_t)r] = cnt[(size_t)l];
         }
-        pl.ent_ptr[(size_t)b + 1] = (int32_t)pl.ent_gid.size();
+        for (int32_t r = nclosed; r < nent; ++r) {
+            open_nodes_flat.push_back(gid[(size_t)r]);
+            opencount[(size_t)gid[(size_t)r]]++;
+        }
+        open_nodes_ptr.push_back((int64_t)open_nodes_flat.size());
+        lidx.assign((size_t)nslot, 0);
+        for (int64_t t = 0; t < nslot; ++t) lidx[(size_t)t] = (uint16_t)rank[(size_t)raw[(size_t)t]];
+        lrow.assign((size_t)nent + 1, 0);
+        for (int32_t r = 0; r < nent; ++r) lrow[(size_t)r + 1] = (uint16_t)(lrow[(size_t)r] + c2[(size_t)r]);
+        std::vector<uint16_t> fill(lrow.begin(), lrow.end() - 1);
+        lsl.assign((size_t)nslot, 0);
+        for (int64_t t = 0; t < nslot; ++t) lsl[(size_t)fill[(size_t)lidx[(size_t)t]]++] = (uint16_t)t;
+        // packet
+        PacketLayout L = packet_layout(nslot, nent, e1 - e0);
+        const int64_t start = (int64_t)pl.packet.size();
+        pl.packet.resize((size_t)(start + L.bytes), 0);
+        uint8_t* pk = pl.packet.data() + start;
+        std::memcpy(pk + L.lidx, lidx.data(), (size_t)nslot * 2);
+        std::memcpy(pk + L.lsl, lsl.data(), (size_t)nslot * 2);
+        std::memcpy(pk + L.lrow, lrow.data(), (size_t)(nent + 1) * 2);
+        std::memcpy(pk + L.gid, gid.data(), (size_t)nent * 4);
+        int32_t* h = &pl.hdr[(size_t)b * 4];
+        h[0] = (int32_t)(start / 16);
+        h[1] = nent;
+        h[2] = nclosed;
+        h[3] = (int32_t)pbase;
+        pbase += nent - nclosed;
+        pl.max_entries = std::max(pl.max_entries, (int)nent);
+        pl.max_packet = std::max(pl.max_packet, L.bytes);
+        pl.nent_total += nent;
+        pl.nclosed_total += nclosed;
     }
-    // open nodes ascending, partial slots grouped per node in block order
+    pl.npartial = pbase;
+    // open nodes ascending; their partial indices in ascending block order
     pl.open_gid.clear();
     pl.open_ptr.assign(1, 0);
     std::vector<int32_t> first((size_t)nn, -1);
@@ -584,9 +630,14 @@ void build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P, int64
             pl.open_gid.push_back((int32_t)g);
             pl.open_ptr.push_back(pl.open_ptr.back() + opencount[(size_t)g]);
         }
-    pl.npartial = pl.open_ptr.back();
-    for (size_t k = 0; k < pl.ent_gid.size(); ++k)
-        if (pl.ent_pslot[k] >= 0) pl.ent_pslot[k] = first[(size_t)pl.ent_gid[k]]++;
+    pl.open_src.assign((size_t)pl.npartial, 0);
+    for (int64_t b = 0; b < nb; ++b) {
+        const int32_t base = pl.hdr[(size_t)b * 4 + 3];
+        for (int64_t k = open_nodes_ptr[(size_t)b]; k < open_nodes_ptr[(size_t)b + 1]; ++k) {
+            int32_t g = open_nodes_flat[(size_t)k];
+            pl.open_src[(size_t)first[(size_t)g]++] = base + (int32_t)(k - open_nodes_ptr[(size_t)b]);
+        }
+    }
 }
 
 }  // namespace semhost

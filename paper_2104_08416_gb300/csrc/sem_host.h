@@ -60,21 +60,37 @@ double cfl_dt(const Mesh& m, const double* vel);
 // global node is an "entry"; element slots point at their entry (lidx) and
 // each entry lists its slots (a local CSR, slots ascending). An entry is
 // closed when every slot of its node lies in this block: the block finishes
-// that node by itself. Other entries write a partial sum; the open-node pass
-// adds the partials of each open node in ascending block order.
+// that node by itself. Closed entries come first (in order of first
+// appearance), then open ones; open entry k of block b writes its partial sum
+// to partial[pbase_b + k], and the open-node pass adds the partials of each
+// open node in ascending block order.
+//
+// Everything a block reads besides node values is one contiguous, 16-byte
+// aligned "packet" (copied to shared memory in one go):
+//   lidx  u16[nslot]      entry of each slot
+//   lsl   u16[nslot]      slots of each entry (local CSR)
+//   lrow  u16[nent + 1]   local CSR offsets
+//   gid   i32[nent]       node id of each entry (4-byte aligned)
+//   coef  f32[neb][8]     bilinear-map coefficients (16-byte aligned; filled
+//                         on the device)
+// with the offsets given by packet_layout().
+struct PacketLayout {
+    int64_t lidx, lsl, lrow, gid, coef, bytes;
+};
+PacketLayout packet_layout(int64_t nslot, int64_t nent, int64_t neb);
+
 struct BlockPlan {
     int eb = 0;
     int64_t nblocks = 0;
     int max_entries = 0;                 // largest entry count of a block
-    std::vector<uint16_t> lidx;          // [ne*P] entry of each slot (block-local)
-    std::vector<int32_t> ent_ptr;        // [nblocks+1]
-    std::vector<int32_t> ent_gid;        // [nent] node id (new numbering)
-    std::vector<int32_t> ent_pslot;      // [nent] partial slot, -1 when closed
-    std::vector<uint16_t> lrow;          // [nent + nblocks] per block: count+1 offsets
-    std::vector<uint16_t> lsl;           // [ne*P] slots of each entry (block-local)
+    int64_t max_packet = 0;              // largest packet (bytes)
+    std::vector<uint8_t> packet;         // all packets, block after block
+    std::vector<int32_t> hdr;            // [nblocks][4]: packet start / 16, nent, nclosed, pbase
     std::vector<int32_t> open_gid;       // [nopen] ascending
-    std::vector<int32_t> open_ptr;       // [nopen+1] into the partial array
+    std::vector<int32_t> open_ptr;       // [nopen+1] into open_src
+    std::vector<int32_t> open_src;       // [npartial] partial index of each contribution
     int64_t npartial = 0;
+    int64_t nent_total = 0, nclosed_total = 0;
 };
 // conn_new: [ne][P] new node ids, elements in the new order.
 void build_block_plan(const std::vector<int32_t>& conn_new, int64_t ne, int P, int64_t nn, int eb,

@@ -27,10 +27,11 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 // Finish node g whose assembled stiffness is ku and whose current value is
-// un. Returns the new value in FP64 (for a receiver trace); in Kahan mode that
-// is the compensated sum u - c.
+// un; st0/st1/st2 are its staged state (s, then u^{n-1} or delta, comp).
+// Returns the new value in FP64 (for a receiver trace); in Kahan mode that is
+// the compensated sum u - c.
 template <typename T, int MODE>
-__device__ __forceinline__ double finish_node(const StepArgs<T>& a, int32_t g, T ku, T un) {
+__device__ __forceinline__ double finish_node(const StepArgs<T>& a, int32_t g, T ku, T un, T st0, T st1, T st2) {
     if (MODE == MODE_APPLY) {
         a.apply_out[g] = ku;
         return (double)ku;
@@ -39,15 +40,14 @@ __device__ __forceinline__ double finish_node(const StepArgs<T>& a, int32_t g, T
     if (g == a.src_gid) f = (T)a.src_f[a.step];
     const T acc = f - ku;
     if (MODE == MODE_THREE_LEVEL) {
-        const T up = a.u_prev[g];
-        const T un1 = (T(2) * un - up) + a.s[g] * acc;
+        const T un1 = (T(2) * un - st1) + st0 * acc;
         a.u_out[g] = un1;
         return (double)un1;
     } else {
         // increment form: delta^{n+1/2} = delta^{n-1/2} + s (f - K u^n),
         // u^{n+1} = u^n + delta^{n+1/2} with a Kahan-compensated sum.
-        const T d = a.delta[g] + a.s[g] * acc;
-        const T y = sub_rn(d, a.comp[g]);
+        const T d = st1 + st0 * acc;
+        const T y = sub_rn(d, st2);
         const T t = un + y;
         const T c = sub_rn(sub_rn(t, un), y);
         a.delta[g] = d;
@@ -57,95 +57,194 @@ __device__ __forceinline__ double finish_node(const StepArgs<T>& a, int32_t g, T
     }
 }
 
-// Metric G = w |J| / rho * J^-1 J^-T at local point (i, j) of element e.
-template <typename T, bool BIL>
-__device__ __forceinline__ void metric(const StepArgs<T>& a, const Basis<T>& bs, int64_t e, int64_t slot, int i,
-                                       int j, T& gxx, T& gxy, T& gyy) {
-    if constexpr (BIL) {
-        // X(xi, eta) = a0 + b xi + c eta + d xi eta, so J = [b + d eta | c + d xi];
-        // w |J| / rho * J^-1 J^-T = w / (rho |J|) * adj(J) adj(J)^T.
-        const float4 c0 = __ldg(&a.coef[e * 2 + 0]);  // bx, by, cx, cy
-        const float4 c1 = __ldg(&a.coef[e * 2 + 1]);  // dx, dy, 1/rho, unused
-        const float xi = (float)bs.x[i], eta = (float)bs.x[j];
-        const float j00 = c0.x + c1.x * eta, j10 = c0.y + c1.y * eta;
-        const float j01 = c0.z + c1.x * xi, j11 = c0.w + c1.y * xi;
-        const float det = j00 * j11 - j01 * j10;
-        const float k = ((float)bs.w[i] * (float)bs.w[j]) * c1.z / det;
-        gxx = (T)(k * (j11 * j11 + j01 * j01));
-        gxy = (T)(-k * (j10 * j11 + j00 * j01));
-        gyy = (T)(k * (j10 * j10 + j00 * j00));
-    } else {
-        gxx = a.G[slot];
-        gxy = a.G[slot + a.gstride];
-        gyy = a.G[slot + 2 * a.gstride];
-    }
+// Same, loading the node state from global memory.
+template <typename T, int MODE>
+__device__ __forceinline__ double finish_node_global(const StepArgs<T>& a, int32_t g, T ku, T un) {
+    if (MODE == MODE_APPLY) return finish_node<T, MODE>(a, g, ku, un, T(0), T(0), T(0));
+    if (MODE == MODE_THREE_LEVEL) return finish_node<T, MODE>(a, g, ku, un, a.s[g], a.u_prev[g], T(0));
+    return finish_node<T, MODE>(a, g, ku, un, a.s[g], a.delta[g], a.comp[g]);
 }
 
+// Keeps a value in a register: the compiler cannot re-derive it from memory.
+__device__ __forceinline__ float pin(float v) {
+    asm volatile("" : "+f"(v));
+    return v;
+}
+__device__ __forceinline__ double pin(double v) {
+    asm volatile("" : "+d"(v));
+    return v;
+}
+
+// ---------------------------------------------------------- async copies
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Metric G = w |J| / rho * J^-1 J^-T at a point (xi, eta) of weight wq,
+// from the element's bilinear-map coefficients (b, c, d, 1/rho):
+// X(xi, eta) = a0 + b xi + c eta + d xi eta, so J = [b + d eta | c + d xi], and
+// w |J| / rho * J^-1 J^-T = w / (rho |J|) * adj(J) adj(J)^T.
+template <typename T>
+__device__ __forceinline__ void metric_bilinear(const float4 c0, const float4 c1, float xi, float eta, float wq,
+                                                T& gxx, T& gxy, T& gyy) {
+    const float j00 = c0.x + c1.x * eta, j10 = c0.y + c1.y * eta;
+    const float j01 = c0.z + c1.x * xi, j11 = c0.w + c1.y * xi;
+    const float det = j00 * j11 - j01 * j10;
+    const float k = wq * c1.z / det;
+    gxx = (T)(k * (j11 * j11 + j01 * j01));
+    gxy = (T)(-k * (j10 * j11 + j00 * j01));
+    gyy = (T)(k * (j10 * j10 + j00 * j00));
+}
+
+// Elements processed side by side by one CTA: each thread keeps one GLL point
+// (i, j) of one element lane for the whole kernel, so its rows and columns of
+// the derivative matrix live in registers.
+template <int NP>
+struct Lanes {
+    static constexpr int P = NP * NP;
+    static constexpr int EBW = (kThreads / P) > 0 ? (kThreads / P) : 1;
+    static constexpr int THREADS = EBW * P;
+};
+
 template <int NP, typename T, int MODE, bool BIL>
-__global__ void __launch_bounds__(kThreads) sem_block_kernel(const Plan pl, const StepArgs<T> a,
-                                                              const Basis<T> bs) {
+__global__ void __launch_bounds__(Lanes<NP>::THREADS) sem_block_kernel(const Plan pl, const StepArgs<T> a,
+                                                                       const Basis<T> bs) {
     constexpr int P = NP * NP;
+    constexpr int EBW = Lanes<NP>::EBW;
+    constexpr int NT = Lanes<NP>::THREADS;
+    constexpr bool STAGE = MODE != MODE_APPLY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* su = reinterpret_cast<T*>(smem_raw);        // [max_entries] u at the block's nodes
-    T* sue = su + pl.max_entries;                  // [eb*P] element values, then residuals
-    T* sf1 = sue + (int64_t)pl.eb * P;             // [eb*P] flux, xi component
-    T* sf2 = sf1 + (int64_t)pl.eb * P;             // [eb*P] flux, eta component
+    uint8_t* spk = smem_raw;                                          // packet
+    T* su = reinterpret_cast<T*>(smem_raw + pl.max_packet);           // [max_entries] u at the entries
+    T* st0 = su + pl.max_entries;                                     // staged node state
+    T* st1 = st0 + (STAGE ? pl.max_entries : 0);
+    T* st2 = st1 + (STAGE ? pl.max_entries : 0);
+    T* sue = st2 + (MODE == MODE_KAHAN ? pl.max_entries : 0);         // [eb*P] element values, then residuals
+    T* sf1 = sue + pl.eb * P;                                         // [eb*P] flux, xi component
+    T* sf2 = sf1 + pl.eb * P;                                         // [eb*P] flux, eta component
 
     const int b = blockIdx.x;
+    const int4 hd = pl.hdr[b];
+    const int nent = hd.y, nclosed = hd.z, pbase = hd.w;
     const int64_t e0 = (int64_t)b * pl.eb;
     const int neb = (int)min((int64_t)pl.eb, pl.ne - e0);
     const int nslot = neb * P;
-    const int64_t s0 = e0 * P;
-    const int ent0 = pl.ent_ptr[b];
-    const int nent = pl.ent_ptr[b + 1] - ent0;
+    const PacketOffsets L = packet_offsets(nslot, nent, neb);
     const int tid = threadIdx.x;
+    const int q = tid % P, lane_el = tid / P;
+    const int j = q / NP, i = q - j * NP;
 
-    // 1. gather u at the block's nodes
-    for (int l = tid; l < nent; l += kThreads) su[l] = a.u_cur[pl.ent_gid[ent0 + l]];
+    // 0. stage the block's packet (indices, local lists, geometry) with
+    //    16-byte asynchronous copies
+    {
+        const uint8_t* gpk = pl.packet + (int64_t)hd.x * 16;
+        for (int off = tid * 16; off < L.bytes; off += NT * 16) cp_async16(spk + off, gpk + off);
+        cp_async_commit();
+    }
+    // GLL tables to shared memory (kernel parameters indexed per thread would
+    // serialise in the constant cache), then this thread's derivative rows and
+    // columns into registers, pinned there
+    __shared__ T sD[P];
+    __shared__ float sxw[2 * NP];
+    for (int t = tid; t < P; t += NT) sD[t] = bs.D[t];
+    for (int t = tid; t < NP; t += NT) {
+        sxw[t] = (float)bs.x[t];
+        sxw[NP + t] = (float)bs.w[t];
+    }
+    __syncthreads();
+    T Di[NP], Dj[NP], DTi[NP], DTj[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        Di[k] = pin(sD[i * NP + k]);
+        Dj[k] = pin(sD[j * NP + k]);
+        DTi[k] = pin(sD[k * NP + i]);
+        DTj[k] = pin(sD[k * NP + j]);
+    }
+    const float xi = pin(sxw[i]), eta = pin(sxw[j]);
+    const float wq = pin(sxw[NP + i] * sxw[NP + j]);
+    cp_async_wait<0>();
+    __syncthreads();
+    const uint16_t* lidx = reinterpret_cast<const uint16_t*>(spk + L.lidx);
+    const uint16_t* lsl = reinterpret_cast<const uint16_t*>(spk + L.lsl);
+    const uint16_t* lrow = reinterpret_cast<const uint16_t*>(spk + L.lrow);
+    const int32_t* gid = reinterpret_cast<const int32_t*>(spk + L.gid);
+    const float4* coef = reinterpret_cast<const float4*>(spk + L.coef);
+
+    // 1. gather u at the entries (group 1), then the closed nodes' state (group 2)
+    for (int l = tid; l < nent; l += NT) cp_async_small<sizeof(T)>(su + l, a.u_cur + gid[l]);
+    cp_async_commit();
+    if (STAGE) {
+        for (int l = tid; l < nclosed; l += NT) {
+            const int32_t g = gid[l];
+            cp_async_small<sizeof(T)>(st0 + l, a.s + g);
+            if (MODE == MODE_THREE_LEVEL) {
+                cp_async_small<sizeof(T)>(st1 + l, a.u_prev + g);
+            } else {
+                cp_async_small<sizeof(T)>(st1 + l, a.delta + g);
+                cp_async_small<sizeof(T)>(st2 + l, a.comp + g);
+            }
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
     __syncthreads();
     // 2. element-local copies U_mu(q,e)
-    for (int s = tid; s < nslot; s += kThreads) sue[s] = su[pl.lidx[s0 + s]];
+    for (int el = lane_el; el < neb; el += EBW) sue[el * P + q] = su[lidx[el * P + q]];
     __syncthreads();
     // 3. reference gradient, metric, fluxes
-    for (int s = tid; s < nslot; s += kThreads) {
-        const int el = s / P, q = s - el * P;
-        const int j = q / NP, i = q - j * NP;
+    for (int el = lane_el; el < neb; el += EBW) {
         const T* ue = sue + el * P;
         T dxi = T(0), deta = T(0);
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            dxi += bs.D[i * NP + k] * ue[j * NP + k];
-            deta += bs.D[j * NP + k] * ue[k * NP + i];
+            dxi += Di[k] * ue[j * NP + k];
+            deta += Dj[k] * ue[k * NP + i];
         }
         T gxx, gxy, gyy;
-        metric<T, BIL>(a, bs, e0 + el, s0 + s, i, j, gxx, gxy, gyy);
-        sf1[s] = gxx * dxi + gxy * deta;
-        sf2[s] = gxy * dxi + gyy * deta;
+        if constexpr (BIL) {
+            metric_bilinear<T>(coef[el * 2], coef[el * 2 + 1], xi, eta, wq, gxx, gxy, gyy);
+        } else {
+            const int64_t sl = (e0 + el) * P + q;
+            gxx = a.G[sl];
+            gxy = a.G[sl + a.gstride];
+            gyy = a.G[sl + 2 * a.gstride];
+        }
+        sf1[el * P + q] = gxx * dxi + gxy * deta;
+        sf2[el * P + q] = gxy * dxi + gyy * deta;
     }
     __syncthreads();
     // 4. transposed derivative: element residuals (stored over sue)
-    for (int s = tid; s < nslot; s += kThreads) {
-        const int el = s / P, q = s - el * P;
-        const int j = q / NP, i = q - j * NP;
+    for (int el = lane_el; el < neb; el += EBW) {
         const T* f1 = sf1 + el * P;
         const T* f2 = sf2 + el * P;
         T r = T(0);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) r += bs.D[k * NP + i] * f1[j * NP + k] + bs.D[k * NP + j] * f2[k * NP + i];
-        sue[s] = r;
+        for (int k = 0; k < NP; ++k) r += DTi[k] * f1[j * NP + k] + DTj[k] * f2[k * NP + i];
+        sue[el * P + q] = r;
     }
+    cp_async_wait<0>();
     __syncthreads();
-    // 5. assembly in fixed (slot-ascending) order; finish closed nodes
-    const uint16_t* lrow = pl.lrow + ent0 + b;
-    for (int l = tid; l < nent; l += kThreads) {
+    // 5. assembly in fixed (slot-ascending) order; closed nodes are finished
+    //    here, open ones leave a partial sum
+    for (int l = tid; l < nent; l += NT) {
         const int r0 = lrow[l], r1 = lrow[l + 1];
         T acc = T(0);
-        for (int t = r0; t < r1; ++t) acc += sue[pl.lsl[s0 + t]];
-        const int32_t ps = pl.ent_pslot[ent0 + l];
-        if (ps >= 0) {
-            a.partial[ps] = acc;
+        for (int t = r0; t < r1; ++t) acc += sue[lsl[t]];
+        if (l >= nclosed) {
+            a.partial[pbase + (l - nclosed)] = acc;
+        } else if (STAGE) {
+            finish_node<T, MODE>(a, gid[l], acc, su[l], st0[l], st1[l], MODE == MODE_KAHAN ? st2[l] : T(0));
         } else {
-            finish_node<T, MODE>(a, pl.ent_gid[ent0 + l], acc, su[l]);
+            finish_node<T, MODE>(a, gid[l], acc, su[l], T(0), T(0), T(0));
         }
     }
 }
@@ -165,10 +264,10 @@ __global__ void __launch_bounds__(kThreads) sem_open_kernel(const Plan pl, const
     for (int k = blockIdx.x * kThreads + threadIdx.x; k < pl.nopen; k += gridDim.x * kThreads) {
         const int p0 = pl.open_ptr[k], p1 = pl.open_ptr[k + 1];
         T acc = T(0);
-        for (int t = p0; t < p1; ++t) acc += a.partial[t];
+        for (int t = p0; t < p1; ++t) acc += a.partial[pl.open_src[t]];
         const int32_t g = pl.open_gid[k];
         const T un = (MODE == MODE_APPLY) ? T(0) : a.u_cur[g];
-        const double v = finish_node<T, MODE>(a, g, acc, un);
+        const double v = finish_node_global<T, MODE>(a, g, acc, un);
         if (MODE != MODE_APPLY && pl.open_rec != nullptr) {
             const int r = pl.open_rec[k];
             if (r >= 0) a.trace[(int64_t)r * a.trace_cap + a.step] = v;
@@ -178,10 +277,10 @@ __global__ void __launch_bounds__(kThreads) sem_open_kernel(const Plan pl, const
 
 // ------------------------------------------------------------ precompute
 __global__ void geometry_kernel(int np, const double* __restrict__ coords, const int32_t* __restrict__ quads,
-                                const double* __restrict__ rho, const double* __restrict__ vel, int64_t ne,
-                                const Basis<double> bs, float4* coef, double* G64, float* G32,
-                                double* mloc) {
+                                const double* __restrict__ rho, const double* __restrict__ vel, const Plan pl,
+                                const Basis<double> bs, uint8_t* packet, double* G64, double* mloc) {
     const int P = np * np;
+    const int64_t ne = pl.ne;
     const int64_t total = ne * P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -202,9 +301,15 @@ __global__ void geometry_kernel(int np, const double* __restrict__ coords, const
         const double dx = 0.25 * ((X[0] - X[1]) + (X[2] - X[3]));
         const double dy = 0.25 * ((Y[0] - Y[1]) + (Y[2] - Y[3]));
         const double rinv = 1.0 / rho[e];
-        if (q == 0 && coef != nullptr) {
-            coef[e * 2 + 0] = make_float4((float)bx, (float)by, (float)cx, (float)cy);
-            coef[e * 2 + 1] = make_float4((float)dx, (float)dy, (float)rinv, 0.0f);
+        if (q == 0 && packet != nullptr) {
+            const int b = (int)(e / pl.eb);
+            const int el = (int)(e - (int64_t)b * pl.eb);
+            const int neb = (int)min((int64_t)pl.eb, ne - (int64_t)b * pl.eb);
+            const int4 hd = pl.hdr[b];
+            const PacketOffsets L = packet_offsets(neb * P, hd.y, neb);
+            float4* cf = reinterpret_cast<float4*>(packet + (int64_t)hd.x * 16 + L.coef) + el * 2;
+            cf[0] = make_float4((float)bx, (float)by, (float)cx, (float)cy);
+            cf[1] = make_float4((float)dx, (float)dy, (float)rinv, 0.0f);
         }
         const double xi = bs.x[i], eta = bs.x[j];
         const double j00 = bx + dx * eta, j10 = by + dy * eta;
@@ -212,18 +317,10 @@ __global__ void geometry_kernel(int np, const double* __restrict__ coords, const
         const double det = j00 * j11 - j01 * j10;
         const double wq = bs.w[i] * bs.w[j];
         const double k = wq * rinv / det;
-        const double gxx = k * (j11 * j11 + j01 * j01);
-        const double gxy = -k * (j10 * j11 + j00 * j01);
-        const double gyy = k * (j10 * j10 + j00 * j00);
         if (G64 != nullptr) {
-            G64[t] = gxx;
-            G64[t + total] = gxy;
-            G64[t + 2 * total] = gyy;
-        }
-        if (G32 != nullptr) {
-            G32[t] = (float)gxx;
-            G32[t + total] = (float)gxy;
-            G32[t + 2 * total] = (float)gyy;
+            G64[t] = k * (j11 * j11 + j01 * j01);
+            G64[t + total] = -k * (j10 * j11 + j00 * j01);
+            G64[t + 2 * total] = k * (j10 * j10 + j00 * j00);
         }
         if (mloc != nullptr) mloc[t] = wq * det * rinv / (vel[e] * vel[e]);
     }
@@ -232,23 +329,27 @@ __global__ void geometry_kernel(int np, const double* __restrict__ coords, const
 __global__ void __launch_bounds__(kThreads) mass_block_kernel(const Plan pl, int P, const double* __restrict__ mloc,
                                                              double* partial, double* M) {
     const int b = blockIdx.x;
-    const int64_t s0 = (int64_t)b * pl.eb * P;
-    const int ent0 = pl.ent_ptr[b];
-    const int nent = pl.ent_ptr[b + 1] - ent0;
-    const uint16_t* lrow = pl.lrow + ent0 + b;
-    for (int l = threadIdx.x; l < nent; l += kThreads) {
+    const int4 hd = pl.hdr[b];
+    const int64_t e0 = (int64_t)b * pl.eb;
+    const int neb = (int)min((int64_t)pl.eb, pl.ne - e0);
+    const PacketOffsets L = packet_offsets(neb * P, hd.y, neb);
+    const uint8_t* pk = pl.packet + (int64_t)hd.x * 16;
+    const uint16_t* lsl = reinterpret_cast<const uint16_t*>(pk + L.lsl);
+    const uint16_t* lrow = reinterpret_cast<const uint16_t*>(pk + L.lrow);
+    const int32_t* gid = reinterpret_cast<const int32_t*>(pk + L.gid);
+    const int64_t s0 = e0 * P;
+    for (int l = threadIdx.x; l < hd.y; l += kThreads) {
         double acc = 0.0;
-        for (int t = lrow[l]; t < lrow[l + 1]; ++t) acc += mloc[s0 + pl.lsl[s0 + t]];
-        const int32_t ps = pl.ent_pslot[ent0 + l];
-        if (ps >= 0) partial[ps] = acc;
-        else M[pl.ent_gid[ent0 + l]] = acc;
+        for (int t = lrow[l]; t < lrow[l + 1]; ++t) acc += mloc[s0 + lsl[t]];
+        if (l >= hd.z) partial[hd.w + (l - hd.z)] = acc;
+        else M[gid[l]] = acc;
     }
 }
 
 __global__ void mass_open_kernel(const Plan pl, const double* __restrict__ partial, double* M) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pl.nopen; k += gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int t = pl.open_ptr[k]; t < pl.open_ptr[k + 1]; ++t) acc += partial[t];
+        for (int t = pl.open_ptr[k]; t < pl.open_ptr[k + 1]; ++t) acc += partial[pl.open_src[t]];
         M[pl.open_gid[k]] = acc;
     }
 }
@@ -277,7 +378,7 @@ cudaError_t launch_block_t(const Plan& pl, const void* args, const void* basis, 
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    kern<<<pl.nblocks, kThreads, smem, st>>>(pl, *static_cast<const StepArgs<T>*>(args),
+    kern<<<pl.nblocks, Lanes<NP>::THREADS, smem, st>>>(pl, *static_cast<const StepArgs<T>*>(args),
                                              *static_cast<const Basis<T>*>(basis));
     return cudaGetLastError();
 }
@@ -299,9 +400,24 @@ cudaError_t dispatch_np(int np, const Plan& pl, const void* args, const void* ba
 
 }  // namespace
 
-int smem_bytes_for(int P, int eb, int max_entries, bool fp64) {
+int lanes_for(int np) {
+    switch (np) {
+        case 2: return Lanes<2>::EBW;
+        case 3: return Lanes<3>::EBW;
+        case 4: return Lanes<4>::EBW;
+        case 5: return Lanes<5>::EBW;
+        case 6: return Lanes<6>::EBW;
+        case 7: return Lanes<7>::EBW;
+        case 8: return Lanes<8>::EBW;
+        case 9: return Lanes<9>::EBW;
+        default: return 1;
+    }
+}
+
+int smem_bytes_for(int P, int eb, int max_entries, int max_packet, bool fp64, int mode) {
     const int sz = fp64 ? 8 : 4;
-    return (max_entries + 3 * eb * P) * sz;
+    const int staged = mode == MODE_KAHAN ? 3 : (mode == MODE_THREE_LEVEL ? 2 : 0);
+    return max_packet + (max_entries * (1 + staged) + 3 * eb * P) * sz;
 }
 
 cudaError_t launch_step(int np, bool fp64, int mode, bool bilinear, const Plan& pl, const void* args,
@@ -346,10 +462,10 @@ cudaError_t launch_open(bool fp64, int mode, const Plan& pl, const void* args, c
 }
 
 cudaError_t launch_geometry(int np, const double* coords, const int32_t* quads_new, const double* rho,
-                            const double* vel, int64_t ne, const Basis<double>& basis, float4* coef, double* G64,
-                            float* G32, double* mloc, cudaStream_t st) {
-    geometry_kernel<<<grid_for(ne * np * np, kThreads), kThreads, 0, st>>>(np, coords, quads_new, rho, vel, ne, basis,
-                                                                          coef, G64, G32, mloc);
+                            const double* vel, const Plan& plan, const Basis<double>& basis, uint8_t* packet,
+                            double* G64, double* mloc, cudaStream_t st) {
+    geometry_kernel<<<grid_for(plan.ne * np * np, kThreads), kThreads, 0, st>>>(np, coords, quads_new, rho, vel, plan,
+                                                                               basis, packet, G64, mloc);
     return cudaGetLastError();
 }
 

@@ -16,23 +16,38 @@ struct Basis {
     T x[MAX_NP];           // GLL nodes
 };
 
-// Block plan on the device (see semhost::BlockPlan).
+// Block plan on the device (see semhost::BlockPlan): per-block packets and
+// headers (packet start / 16, entries, closed entries, first partial slot),
+// and the open-node lists.
 struct Plan {
-    const uint16_t* lidx;
-    const int32_t* ent_ptr;
-    const int32_t* ent_gid;
-    const int32_t* ent_pslot;
-    const uint16_t* lrow;
-    const uint16_t* lsl;
+    const uint8_t* packet;
+    const int4* hdr;
     const int32_t* open_gid;
     const int32_t* open_ptr;
+    const int32_t* open_src;
     const int32_t* open_rec;   // receiver index of an open node, or -1 (may be null)
     int64_t ne;
     int eb;
     int nblocks;
     int nopen;
     int max_entries;
+    int max_packet;
 };
+
+// Packet layout, identical to semhost::packet_layout.
+struct PacketOffsets {
+    int lidx, lsl, lrow, gid, coef, bytes;
+};
+__host__ __device__ inline PacketOffsets packet_offsets(int nslot, int nent, int neb) {
+    PacketOffsets L;
+    L.lidx = 0;
+    L.lsl = 2 * nslot;
+    L.lrow = 4 * nslot;
+    L.gid = (L.lrow + 2 * (nent + 1) + 3) / 4 * 4;
+    L.coef = (L.gid + 4 * nent + 15) / 16 * 16;
+    L.bytes = (L.coef + 32 * neb + 15) / 16 * 16;
+    return L;
+}
 
 enum Mode : int {
     MODE_THREE_LEVEL = 0,  // u^{n+1} = 2u^n - u^{n-1} + s (f e_src - K u^n)
@@ -55,7 +70,6 @@ struct StepArgs {
     T* partial;            // partial sums of open nodes
     const T* G;            // stored metric [3][gstride] or null
     int64_t gstride;       // ne * P
-    const float4* coef;    // bilinear coefficients [ne][2] or null
     T* apply_out;          // MODE_APPLY output
     const double* src_f;   // Ricker table f(t_n)
     int64_t step;          // n
@@ -76,14 +90,17 @@ cudaError_t launch_open(bool fp64, int mode, const Plan& plan, const void* args,
 // coordinates: the bilinear coefficients (FP32), the stored metric (FP64 or
 // FP32, when G_out is non-null), and w_q |J_q| / (rho c^2) per slot.
 cudaError_t launch_geometry(int np, const double* coords, const int32_t* quads_new, const double* rho,
-                            const double* vel, int64_t ne, const Basis<double>& basis, float4* coef,
-                            double* G64, float* G32, double* mloc, cudaStream_t st);
+                            const double* vel, const Plan& plan, const Basis<double>& basis, uint8_t* packet,
+                            double* G64, double* mloc, cudaStream_t st);
 // Lumped mass through the block plan (deterministic), M[nn] in FP64.
 cudaError_t launch_mass(const Plan& plan, int P, const double* mloc, double* partial, double* M,
                         cudaStream_t st);
 // s = dt^2 / M (FP64 arithmetic, rounded once to the storage type).
 cudaError_t launch_scale(const double* M, int64_t nn, double dt, double* s64, float* s32, cudaStream_t st);
 
-int smem_bytes_for(int P, int eb, int max_entries, bool fp64);
+int smem_bytes_for(int P, int eb, int max_entries, int max_packet, bool fp64, int mode);
+// Element lanes of the block kernel: elements processed side by side, one
+// thread per GLL point of each (blockDim = lanes * (p+1)^2).
+int lanes_for(int np);
 
 }  // namespace semdev
