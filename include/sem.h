@@ -244,6 +244,31 @@ sem_status sem_traffic_model(const sem_mesh* m, double* block_bytes, double* ope
 /* Host<->device bytes this handle's calls have copied so far. */
 sem_status sem_transfer_bytes(const sem_mesh* m, int64_t* h2d, int64_t* d2h);
 
+/* Stiffness application that allocates nothing, for callers that cannot
+ * call cudaMalloc themselves or let a library do it: code running while a
+ * CUDA graph is being captured, a real-time loop that must not hit the
+ * allocator, or a host process whose memory budget was fixed up front. The
+ * paper has no counterpart; it is a deployment aid.
+ *   dev_u   [N] device array, input; dev_Ku [N] device array, output. Both hold
+ *           the handle's storage type (double for SEM_FP64, float otherwise)
+ *           indexed by the library's storage order of the nodes
+ *           (node_new_of_old from sem_get_permutation).
+ * Computes dev_Ku = K dev_u like sem_apply_stiffness, enqueued on the
+ * handle's stream without synchronising. The per-block partial sums go to a
+ * scratch array that is a file-scope device variable of the library:
+ * SEM_NOALLOC_SCRATCH_BYTES bytes, held on every GPU that loads the library
+ * until the process exits. A mesh whose partial sums need more
+ * (open entries x element size) gets SEM_ERR_INVALID_ARG. The handle's device
+ * data must exist already (after sem_step, sem_set_state or
+ * sem_apply_stiffness), else SEM_ERR_STATE. The first call on a device looks
+ * up the scratch array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture. All calls share the one scratch
+ * array: calls that may overlap on the GPU (different streams, handles or
+ * threads) race on it. Every scratch value a call reads was written earlier
+ * in the same call, so nothing needs clearing between calls. */
+#define SEM_NOALLOC_SCRATCH_BYTES (16u << 20)
+sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void* dev_Ku);
+
 /* Message of the last failing call on this handle ("" if none). Never NULL. */
 const char* sem_last_error(const sem_mesh* m);
 

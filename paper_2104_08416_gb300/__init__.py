@@ -37,7 +37,7 @@ EXPORTS = (
     "sem_get_permutation", "sem_get_sizes", "sem_node_coordinates", "sem_get_snapped",
     "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_launch_info", "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
-    "sem_last_error", "sem_destroy",
+    "sem_apply_stiffness_dev_noalloc", "sem_last_error", "sem_destroy",
 )
 
 _lib = None
@@ -94,6 +94,7 @@ def load(path: str | None = None):
         "sem_profile_read": (_P, _D, _I64, _D, _I64),
         "sem_traffic_model": (_P, _D, _D),
         "sem_transfer_bytes": (_P, _I64, _I64),
+        "sem_apply_stiffness_dev_noalloc": (_P, _P, _P),
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -325,6 +326,11 @@ class SEM:
         a, b = C.c_int64(), C.c_int64()
         self._c(self._lib.sem_transfer_bytes(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def sem_apply_stiffness_dev_noalloc(self, dev_u_ptr: int, dev_Ku_ptr: int):
+        """K u on device arrays (storage order, handle's storage type) without
+        any allocation; enqueued on the handle's stream, not synchronised."""
+        self._c(self._lib.sem_apply_stiffness_dev_noalloc(self.h, _P(dev_u_ptr), _P(dev_Ku_ptr)))
 
     def sem_destroy(self):
         if getattr(self, "h", None):

@@ -896,4 +896,69 @@ void sem_destroy(sem_mesh* m) {
     delete m;
 }
 
+// ------------------------------------------------ allocation-free variant
+}  // extern "C"
+
+namespace {
+// Scratch of sem_apply_stiffness_dev_noalloc: partial sums of open entries.
+// A file-scope device array, so the call needs no allocation. In host code
+// the name is only a host-side stand-in; its device address comes from
+// cudaGetSymbolAddress, looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SEM_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};
+
+cudaError_t noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void* dev_Ku) {
+    if (!m || !dev_u || !dev_Ku) return SEM_ERR_INVALID_ARG;
+    if (!m->built)
+        return fail(m, SEM_ERR_STATE, "device data not built: call sem_step, sem_set_state or sem_apply_stiffness once");
+    const int64_t open_entries = m->plan.nent_total - m->plan.nclosed_total;
+    if ((double)open_entries * (double)tsize(m) > (double)SEM_NOALLOC_SCRATCH_BYTES)
+        return fail(m, SEM_ERR_INVALID_ARG,
+                    "mesh needs " + std::to_string(open_entries * (int64_t)tsize(m)) +
+                        " bytes of partial sums, above the allocation-free limit of " +
+                        std::to_string((unsigned)SEM_NOALLOC_SCRATCH_BYTES) + " bytes");
+    void* scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(m, e, "cudaGetSymbolAddress");
+    const bool f64 = fp64(m);
+    const void* basis = f64 ? (const void*)&m->basis64 : (const void*)&m->basis32;
+    if (f64) {
+        auto a = step_args<double>(m);
+        a.u_cur = (const double*)dev_u;
+        a.apply_out = (double*)dev_Ku;
+        a.partial = (double*)scratch;
+        e = semdev::launch_step(m->mesh.np, true, semdev::MODE_APPLY, false, m->dplan, &a, basis, m->smem, m->stream);
+        if (e == cudaSuccess) e = semdev::launch_open(true, semdev::MODE_APPLY, m->dplan, &a, m->stream);
+    } else {
+        auto a = step_args<float>(m);
+        a.u_cur = (const float*)dev_u;
+        a.apply_out = (float*)dev_Ku;
+        a.partial = (float*)scratch;
+        e = semdev::launch_step(m->mesh.np, false, semdev::MODE_APPLY, true, m->dplan, &a, basis, m->smem, m->stream);
+        if (e == cudaSuccess) e = semdev::launch_open(false, semdev::MODE_APPLY, m->dplan, &a, m->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(m, e, "noalloc apply launch");
+    return SEM_OK;
+}
+
 }  // extern "C"
