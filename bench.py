@@ -40,6 +40,11 @@ METRIC = "GLL node-updates/s (order 4)"
 UNIT = "node-updates/s"
 WORKLOAD = "graded_512x512_p4"
 L2_BYTES = 129 * 2 ** 20
+# algorithmic DRAM bytes per node-update at p = 4 (1.5625 element slots per
+# node; connectivity 4 B/slot, stored metric 12 B/slot FP32 or 24 B FP64;
+# node state: FP32 three-level u r/w, u_prev r, s r; Kahan u, delta, c r/w,
+# s r; FP64 three-level as FP32 with 8-byte values)
+ALGO_BYTES = {"fp32": 41.0, "fp32_kahan": 53.0, "fp64": 76.0}
 
 
 def parse():
@@ -54,6 +59,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the per-ordering comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eb", type=int, default=0, help="elements per block (0 = library default)")
+    ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = library default)")
     return ap.parse_args()
 
 
@@ -136,12 +142,12 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_handle(P, m, precision, ordering, nsteps_cap, eb=0):
+def make_handle(P, m, precision, ordering, nsteps_cap, eb=0, threads=0):
     h = P.SEM(m["coords"], m["quads"], 4, precision)
     h.sem_reorder(ordering)
     h.sem_set_model(m["vel"], m["rho"])
-    if eb:
-        h.sem_set_tuning(eb)
+    if eb or threads:
+        h.sem_set_tuning(eb, threads)
     h.sem_set_source(m["f0"], m["t0"], m["amp"], *m["src_xy"])
     h.sem_set_receivers(m["receivers"], nsteps_cap)
     h.sem_set_dt(0.3 * h.sem_cfl_dt())
@@ -179,6 +185,31 @@ def cpu_baseline(n, budget_s=12.0):
             break
         k *= 2
     return S.n_nodes * k / el, k, S.n_nodes
+
+
+def kernel_source_digest():
+    """sha256 of the CUDA kernel sources: a recorded ncu traffic figure is
+    only reported while the kernels it was measured on are unchanged."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in ("sem_kernels.cu", "sem_kernels.cuh", "sem_plan.h"):
+        with open(os.path.join(ROOT, "paper_2104_08416_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
+def recorded_traffic(precision, ordering):
+    """DRAM bytes per step-kernel launch from the committed ncu summary."""
+    tfile = os.path.join(ROOT, "profiles", "sem_step_kernel_traffic.json")
+    try:
+        with open(tfile) as fh:
+            tj = json.load(fh)
+        if (tj.get("workload") == WORKLOAD and tj.get("precision") == precision and tj.get("ordering") == ordering
+                and tj.get("kernel_sha256") == kernel_source_digest()):
+            return float(tj["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return None
 
 
 def threads_used():
@@ -245,7 +276,7 @@ def main():
     K, W = args.steps, args.warmup
     m = workload(args.n, rank)
     cap = W + 2 * K + 8
-    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb)
+    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads)
     N = h.n_nodes
     # warm-up (the first call builds the device data)
     h.sem_step(W)
@@ -266,7 +297,7 @@ def main():
     bms, bl, oms, ol = h.sem_profile_read()
     h.sem_profile_enable(False)
     block_bytes, open_bytes = h.sem_traffic_model()
-    launches, nopen = h.sem_launch_info()
+    _, nopen = h.sem_launch_info()
     time.sleep(0.2)
     clocks = ClockSampler.summarize(sampler.stop()) if sampler else None
     u = h.sem_read_wavefield()
@@ -277,7 +308,7 @@ def main():
     # traces and wavefield back to the host, all inside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb)
+    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb, args.threads)
     h2.sem_step(K)
     tr = h2.sem_read_traces()
     u2 = h2.sem_read_wavefield()
@@ -296,7 +327,7 @@ def main():
         orderings = {}
         kk = min(K, 500)
         for kind in ("hilbert", "rowmajor", "random", "none"):
-            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb)
+            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb, args.threads)
             hh.sem_step(W)
             t_ord = time_steps(torch, hh, kk)
             hh.sem_profile_enable(True)
@@ -306,8 +337,8 @@ def main():
             _, no = hh.sem_launch_info()
             hh.sem_destroy()
             orderings[kind] = {"node_updates_per_s": N * kk / t_ord, "ms_per_step": 1e3 * t_ord / kk,
-                               "block_kernel_us": 1e3 * b_ms / max(b_l, 1), "open_kernel_us": 1e3 * o_ms / max(o_l, 1),
-                               "open_nodes": no, "block_bytes": bb, "open_bytes": ob}
+                               "step_kernel_us": 1e3 * b_ms / max(b_l, 1), "open_nodes": no,
+                               "step_bytes_model": bb}
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -325,15 +356,7 @@ def main():
     peak, peak_kind = read_peaks()
     blk_us = 1e3 * bms / max(bl, 1)
     achieved = block_bytes / (blk_us * 1e-6) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "block_kernel_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            tj = json.load(open(tfile))
-            if tj.get("workload") == WORKLOAD and tj.get("precision") == args.precision:
-                traffic = tj.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = recorded_traffic(args.precision, args.ordering)
     value = world * N * K / el
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -345,14 +368,16 @@ def main():
                    "l2": f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
                    "finite": finite},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "sem_block_kernel", "peak_kind": peak_kind,
-                     "block_kernel_us": blk_us, "open_kernel_us": 1e3 * oms / max(ol, 1),
-                     "block_bytes_per_launch": block_bytes, "open_bytes_per_launch": open_bytes,
-                     "open_nodes": nopen, "profiled_ms_per_step": 1e3 * prof_el / K},
+                     "traffic": traffic, "kernel": "sem_step_kernel", "peak_kind": peak_kind,
+                     "step_kernel_us": blk_us, "open_kernel_us_per_run": 1e3 * oms / max(ol, 1),
+                     "step_bytes_per_launch": block_bytes, "open_bytes_per_launch": open_bytes,
+                     "open_nodes": nopen, "profiled_ms_per_step": 1e3 * prof_el / K,
+                     "algorithmic_bytes_per_node_update": ALGO_BYTES[args.precision],
+                     "algorithmic_gbs_per_step": ALGO_BYTES[args.precision] * N * K / el / 1e9},
         "cpu_baseline": cpu,
         "e2e": {"value": world * N * K / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K, "includes": "mesh set-up, reordering, precompute, K steps, read-back"},
-        "gpu_launches": int(launches * K),
+        "gpu_launches": int(bl + ol),
         "clocks": clocks,
         "orderings": orderings,
     }

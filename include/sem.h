@@ -204,6 +204,22 @@ sem_status sem_compute_ordering(const double* coords, int64_t nv, const int32_t*
                                 int order, sem_ordering kind, uint64_t seed, int64_t* elem_order,
                                 int64_t* node_order);
 
+/* Host-only self-check of the block plan that the step kernel would use for
+ * this mesh, ordering, block size and storage type (fp64_storage: 8-byte
+ * node values, else 4): builds the plan and replays one assembly over it on
+ * the host with every index bounds-checked, on integer-valued residuals so
+ * that sums are exact, and compares with the direct per-slot sum; also
+ * checks that every distinct receiver node (rec_xy[nrec][2], snapped like
+ * sem_set_receivers) is recorded by exactly one block. info[6] (may be
+ * NULL): blocks, DENSE layout (1/0), open nodes, largest entry count,
+ * largest packet bytes, partial-sum slots. msg (may be NULL) receives the
+ * first violation. Returns SEM_OK when consistent, SEM_ERR_STATE on a
+ * violation, SEM_ERR_UNSUPPORTED when the plan cannot be built,
+ * SEM_ERR_INVALID_ARG for bad input. No device is needed. */
+sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads, int64_t ne, int order,
+                          sem_ordering kind, uint64_t seed, int elems_per_block, int fp64_storage,
+                          const double* rec_xy, int32_t nrec, int64_t* info, char* msg, size_t msg_cap);
+
 /* Global node count of a mesh at polynomial order `order`, host only. */
 sem_status sem_count_nodes(const int32_t* quads, int64_t nv, int64_t ne, int order,
                            int64_t* n_nodes);
@@ -213,30 +229,35 @@ sem_status sem_count_nodes(const int32_t* quads, int64_t nv, int64_t ne, int ord
  * (x, y) of the k-th visited cell, out cells[W*H][2]. Host only. */
 sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells);
 
-/* Launch accounting of the time loop: kernel launches per step (the block
- * kernel and the open-node kernel) and the number of open nodes, i.e. nodes
- * whose elements span more than one element block and are finished by the
- * open-node kernel (-1 before the device data is built). Either pointer may
- * be NULL. */
+/* Launch accounting of the time loop: kernel launches per step (one step
+ * kernel; each sem_step call adds one open-node launch after its last step)
+ * and the number of open nodes, i.e. nodes whose elements span more than one
+ * element block (-1 before the device data is built). Either pointer may be
+ * NULL. */
 sem_status sem_launch_info(const sem_mesh* m, int64_t* launches_per_step, int64_t* open_nodes);
 
-/* Elements per block of the block kernel (0 = default, about 1600 element
- * points per block). Before the device data is built. elems_per_block *
- * (order+1)^2 must not exceed 65535. */
-sem_status sem_set_tuning(sem_mesh* m, int elems_per_block);
+/* Launch shape of the step kernel: elements per block (0 = default, about
+ * 1600 element points per block; at most 256, one thread per element) and
+ * threads per block (0 = one per element rounded up to whole warps; else a
+ * multiple of 32 up to 256, raised to that minimum if smaller; the threads
+ * beyond the block's elements help with staging and assembly). Before the
+ * device data is built. elems_per_block * (order+1)^2 must not exceed 65535. */
+sem_status sem_set_tuning(sem_mesh* m, int elems_per_block, int threads_per_block);
 
 /* Per-kernel device timing for measurement. While enabled, sem_step records
- * CUDA events on the handle's stream around every block-kernel and
- * open-kernel launch. sem_profile_read synchronises the stream and returns
- * the summed durations (milliseconds) and launch counts since the last read,
- * then resets them. Any output pointer may be NULL. */
+ * CUDA events on the handle's stream around every step-kernel launch
+ * ("block") and every open-node launch ("open"). sem_profile_read
+ * synchronises the stream and returns the summed durations (milliseconds)
+ * and launch counts since the last read, then resets them. Any output pointer
+ * may be NULL. */
 sem_status sem_profile_enable(sem_mesh* m, int enable);
 sem_status sem_profile_read(sem_mesh* m, double* block_ms, int64_t* block_launches, double* open_ms,
                             int64_t* open_launches);
 
-/* Compulsory DRAM bytes of one launch of each time-loop kernel under the
- * current plan and precision: every array the launch touches counted once
- * (per-slot entry indices and local node lists, per-element geometry, per-node
+/* Compulsory DRAM bytes of one step-kernel launch (block_bytes; a launch
+ * that finishes the previous step's open nodes) and of one open-node launch
+ * (open_bytes) under the current plan and precision: every array a launch
+ * touches counted once (element positions and geometry, block packets, node
  * state read and written, partial sums). Needs the device data (after the
  * first sem_step). Either pointer may be NULL. */
 sem_status sem_traffic_model(const sem_mesh* m, double* block_bytes, double* open_bytes);
@@ -258,7 +279,7 @@ sem_status sem_transfer_bytes(const sem_mesh* m, int64_t* h2d, int64_t* d2h);
  * scratch array that is a file-scope device variable of the library:
  * SEM_NOALLOC_SCRATCH_BYTES bytes, held on every GPU that loads the library
  * until the process exits. A mesh whose partial sums need more
- * (open entries x element size) gets SEM_ERR_INVALID_ARG. The handle's device
+ * (partial-sum slots x element size) gets SEM_ERR_INVALID_ARG. The handle's device
  * data must exist already (after sem_step, sem_set_state or
  * sem_apply_stiffness), else SEM_ERR_STATE. The first call on a device looks
  * up the scratch array's device address (cudaGetSymbolAddress); make that

@@ -35,7 +35,8 @@ EXPORTS = (
     "sem_set_receivers", "sem_cfl_dt", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
     "sem_read_wavefield", "sem_set_state", "sem_get_state", "sem_apply_stiffness", "sem_read_mass",
     "sem_get_permutation", "sem_get_sizes", "sem_node_coordinates", "sem_get_snapped",
-    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_launch_info", "sem_set_tuning",
+    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info",
+    "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
     "sem_apply_stiffness_dev_noalloc", "sem_last_error", "sem_destroy",
 )
@@ -88,8 +89,10 @@ def load(path: str | None = None):
         "sem_compute_ordering": (_D, C.c_int64, _I32, C.c_int64, C.c_int, C.c_int, C.c_uint64, _I64, _I64),
         "sem_count_nodes": (_I32, C.c_int64, C.c_int64, C.c_int, _I64),
         "sem_hilbert_cells": (C.c_int32, C.c_int32, _I32),
+        "sem_plan_check": (_D, C.c_int64, _I32, C.c_int64, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int, _D,
+                           C.c_int32, _I64, C.c_char_p, C.c_size_t),
         "sem_launch_info": (_P, _I64, _I64),
-        "sem_set_tuning": (_P, C.c_int),
+        "sem_set_tuning": (_P, C.c_int, C.c_int),
         "sem_profile_enable": (_P, C.c_int),
         "sem_profile_read": (_P, _D, _I64, _D, _I64),
         "sem_traffic_model": (_P, _D, _D),
@@ -184,6 +187,24 @@ def sem_hilbert_cells(W: int, H: int) -> np.ndarray:
     return out
 
 
+def sem_plan_check(coords, quads, order: int, kind, eb: int, fp64: bool = False, receivers=None,
+                   seed: int = DEFAULT_SEED):
+    """Host-only replay of the step kernel's block plan (see sem.h).
+    Returns (status, info dict, message)."""
+    lib = load()
+    kind = ORDERINGS[kind] if isinstance(kind, str) else int(kind)
+    c = np.ascontiguousarray(coords, dtype=np.float64)
+    q = np.ascontiguousarray(quads, dtype=np.int32)
+    rec = np.ascontiguousarray(np.zeros((0, 2)) if receivers is None else receivers, dtype=np.float64)
+    info = np.zeros(6, dtype=np.int64)
+    msg = C.create_string_buffer(512)
+    st = lib.sem_plan_check(_ptr(c, C.c_double), c.shape[0], _ptr(q, C.c_int32), q.shape[0], int(order), kind,
+                            C.c_uint64(seed & (2 ** 64 - 1)), int(eb), int(bool(fp64)), _ptr(rec, C.c_double),
+                            rec.shape[0], _ptr(info, C.c_int64), msg, 512)
+    keys = ("nblocks", "dense", "open_nodes", "max_entries", "max_packet", "npartial")
+    return st, dict(zip(keys, (int(v) for v in info))), msg.value.decode()
+
+
 # ------------------------------------------------------------------ handle
 class SEM:
     """One mesh handle (sem_mesh*). Methods mirror the C calls."""
@@ -240,8 +261,8 @@ class SEM:
     def sem_set_dt(self, dt: float):
         self._c(self._lib.sem_set_dt(self.h, float(dt)))
 
-    def sem_set_tuning(self, elems_per_block: int):
-        self._c(self._lib.sem_set_tuning(self.h, int(elems_per_block)))
+    def sem_set_tuning(self, elems_per_block: int, threads_per_block: int = 0):
+        self._c(self._lib.sem_set_tuning(self.h, int(elems_per_block), int(threads_per_block)))
 
     def sem_step(self, nsteps: int):
         self._c(self._lib.sem_step(self.h, int(nsteps)))

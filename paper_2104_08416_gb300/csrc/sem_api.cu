@@ -59,6 +59,7 @@ struct sem_mesh {
     bool have_dt = false;
     double dt = 0;
     int eb_request = 0;
+    int threads_request = 0;
 
     // device state
     bool built = false;
@@ -67,6 +68,7 @@ struct sem_mesh {
     semhost::BlockPlan plan;
     semdev::Plan dplan{};
     int smem = 0;
+    int threads = 0;
     semdev::Basis<double> basis64{};
     semdev::Basis<float> basis32{};
     double* d_coords = nullptr;
@@ -78,17 +80,17 @@ struct sem_mesh {
     double* d_mloc = nullptr;
     double* d_M = nullptr;
     void* d_s = nullptr;
-    void* d_u[2] = {nullptr, nullptr};
-    void* d_delta = nullptr;
-    void* d_comp = nullptr;
-    void* d_partial = nullptr;
+    // node state by level (see semdev::StepArgs): three-level mode keeps
+    // u^m in d_u[m % 3]; Kahan mode keeps (u^m, delta^{m-1/2}, c^m) in
+    // (d_u, d_x, d_c)[m % 2]
+    void* d_u[3] = {nullptr, nullptr, nullptr};
+    void* d_x[2] = {nullptr, nullptr};
+    void* d_c[2] = {nullptr, nullptr};
+    void* d_part[2] = {nullptr, nullptr};
     void* d_apply_in = nullptr;
     void* d_apply_out = nullptr;
     double* d_src = nullptr;
     int64_t src_cap = 0;
-    int32_t* d_rec_gid = nullptr;
-    uint8_t* d_rec_closed = nullptr;
-    int32_t* d_open_rec = nullptr;
     double* d_trace = nullptr;
     // measurement
     bool profiling = false;
@@ -178,6 +180,8 @@ void fill_basis(semdev::Basis<T>& b, int p) {
         b.w[i] = (T)w[i];
         for (int k = 0; k < n; ++k) b.D[i * n + k] = (T)D[(size_t)i * n + k];
     }
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) b.W[j * n + i] = (T)(w[(size_t)i] * w[(size_t)j]);
 }
 
 void compute_orderings(sem_mesh* m) {
@@ -209,12 +213,21 @@ sem_status fill_source(sem_mesh* m, int64_t upto) {
 }
 
 int default_eb(int np) {
-    // a multiple of the kernel's element lanes, about 1500 points per block
+    // about 1600 element points per block, at most 256 elements (threads)
     const int P = np * np;
-    const int lanes = semdev::lanes_for(np);
-    int rounds = (1536 + lanes * P / 2) / (lanes * P);
-    if (rounds < 1) rounds = 1;
-    return lanes * rounds;
+    int eb = (1600 + P / 2) / P;
+    if (eb > 256) eb = 256;
+    if (eb < 1) eb = 1;
+    return eb;
+}
+
+int vec_of(const sem_mesh* m) { return fp64(m) ? 2 : 4; }
+
+// Node arrays are allocated to a multiple of 16 bytes plus one vector so
+// the kernels' aligned 16-byte copies of owned ranges never leave them.
+size_t node_bytes(const sem_mesh* m) {
+    const int64_t v = vec_of(m);
+    return (size_t)(((m->mesh.nn + v - 1) / v + 1) * v) * tsize(m);
 }
 
 sem_status build(sem_mesh* m) {
@@ -235,37 +248,68 @@ sem_status build(sem_mesh* m) {
         rho_new[(size_t)en] = m->rho[(size_t)eo];
         vel_new[(size_t)en] = m->vel[(size_t)eo];
     }
+    // receivers: new node ids; a second receiver on the same node copies the
+    // first one's trace on the host
+    std::vector<int32_t> rec_gid((size_t)m->nrec, -1);
+    m->rec_row.assign((size_t)m->nrec, -1);
+    for (int32_t r = 0; r < m->nrec; ++r) {
+        const int32_t g = (int32_t)m->node_new[(size_t)m->rec_nodes[(size_t)r]];
+        for (int32_t q = 0; q < r; ++q)
+            if (rec_gid[(size_t)q] == g) {
+                m->rec_row[(size_t)r] = q;
+                break;
+            }
+        if (m->rec_row[(size_t)r] < 0) rec_gid[(size_t)r] = g;
+    }
     int eb = m->eb_request > 0 ? m->eb_request : default_eb(M.np);
     if ((int64_t)eb * P > 65535) eb = 65535 / P;
-    semhost::build_block_plan(conn_new, M.ne, P, M.nn, eb, m->plan);
+    if (eb > 256) eb = 256;
+    std::string why = semhost::build_block_plan(conn_new, M.ne, P, M.nn, eb, true, vec_of(m), rec_gid, m->plan);
+    if (!why.empty()) return fail(m, SEM_ERR_UNSUPPORTED, "block plan: " + why);
     conn_new.clear();
     conn_new.shrink_to_fit();
     const auto& pl = m->plan;
-    m->smem = semdev::smem_bytes_for(P, pl.eb, pl.max_entries, (int)pl.max_packet, fp64(m), mode_of(m));
-    if (m->smem > 227 * 1024) return fail(m, SEM_ERR_UNSUPPORTED, "block plan does not fit in shared memory");
+    const int v = vec_of(m);
+    const int sulen_pad = (pl.max_sulen + v - 1) / v * v;
+    const int slen_pad = (pl.max_slen + v - 1) / v * v;
+    m->threads = std::max(semdev::step_threads(pl.eb), m->threads_request);
+    m->smem = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), mode_of(m));
+    const int smem_apply = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m),
+                                                  semdev::MODE_APPLY);
+    if (std::max(m->smem, smem_apply) > 227 * 1024)
+        return fail(m, SEM_ERR_UNSUPPORTED, "block plan does not fit in shared memory; lower sem_set_tuning");
 
     sem_status st;
     uint8_t* packet;
-    int32_t *hdr, *open_gid, *open_ptr, *open_src;
+    int32_t *hdr, *open_gid, *open_base, *open_cnt, *open_rec;
+    uint32_t* epos;
     if ((st = upload(m, &packet, pl.packet.data(), pl.packet.size())) != SEM_OK) return st;
     if ((st = upload(m, &hdr, pl.hdr.data(), pl.hdr.size())) != SEM_OK) return st;
+    if ((st = upload(m, &epos, pl.epos.data(), pl.epos.size())) != SEM_OK) return st;
     if ((st = upload(m, &open_gid, pl.open_gid.data(), pl.open_gid.size())) != SEM_OK) return st;
-    if ((st = upload(m, &open_ptr, pl.open_ptr.data(), pl.open_ptr.size())) != SEM_OK) return st;
-    if ((st = upload(m, &open_src, pl.open_src.data(), pl.open_src.size())) != SEM_OK) return st;
+    if ((st = upload(m, &open_base, pl.open_base.data(), pl.open_base.size())) != SEM_OK) return st;
+    if ((st = upload(m, &open_cnt, pl.open_cnt.data(), pl.open_cnt.size())) != SEM_OK) return st;
+    if ((st = upload(m, &open_rec, pl.open_rec.data(), pl.open_rec.size())) != SEM_OK) return st;
     m->d_packet = packet;
     semdev::Plan& dp = m->dplan;
     dp.packet = packet;
     dp.hdr = reinterpret_cast<const int4*>(hdr);
+    dp.epos = epos;
+    dp.coef = nullptr;
+    dp.G = nullptr;
     dp.open_gid = open_gid;
-    dp.open_ptr = open_ptr;
-    dp.open_src = open_src;
-    dp.open_rec = nullptr;
+    dp.open_base = open_base;
+    dp.open_cnt = open_cnt;
+    dp.open_rec = open_rec;
     dp.ne = M.ne;
+    dp.nn = M.nn;
     dp.eb = pl.eb;
     dp.nblocks = (int)pl.nblocks;
-    dp.nopen = (int)pl.open_gid.size();
-    dp.max_entries = pl.max_entries;
-    dp.max_packet = (int)pl.max_packet;
+    dp.nopen_nodes = (int)pl.open_gid.size();
+    dp.max_packet = pl.max_packet;
+    dp.sulen_pad = sulen_pad;
+    dp.slen_pad = slen_pad;
+    dp.dense = pl.dense ? 1 : 0;
 
     fill_basis(m->basis64, M.p);
     fill_basis(m->basis32, M.p);
@@ -278,58 +322,42 @@ sem_status build(sem_mesh* m) {
     const size_t nslot = (size_t)(M.ne * P);
     m->d_mloc = (double*)dev_alloc(m, nslot * 8);
     m->d_M = (double*)dev_alloc(m, (size_t)M.nn * 8);
-    m->d_partial = dev_alloc(m, (size_t)std::max<int64_t>(pl.npartial, 1) * 8);
-    if (!m->d_mloc || !m->d_M || !m->d_partial) return fail(m, SEM_ERR_OOM, "device allocation failed");
+    const size_t pbytes = (size_t)std::max<int64_t>(pl.npartial, 1) * 8;
+    m->d_part[0] = dev_alloc(m, pbytes);
+    m->d_part[1] = dev_alloc(m, pbytes);
+    if (!m->d_mloc || !m->d_M || !m->d_part[0] || !m->d_part[1])
+        return fail(m, SEM_ERR_OOM, "device allocation failed");
+    float4* coef = nullptr;
     if (fp64(m)) {
         m->d_G64 = (double*)dev_alloc(m, nslot * 3 * 8);
         if (!m->d_G64) return fail(m, SEM_ERR_OOM, "device allocation failed");
+        dp.G = m->d_G64;
+    } else {
+        coef = (float4*)dev_alloc(m, (size_t)M.ne * 2 * sizeof(float4));
+        if (!coef) return fail(m, SEM_ERR_OOM, "device allocation failed");
+        dp.coef = coef;
     }
-    SEM_CUDA(semdev::launch_geometry(M.np, m->d_coords, m->d_quads, m->d_rho, m->d_vel, dp, m->basis64, m->d_packet,
+    SEM_CUDA(semdev::launch_geometry(M.np, M.ne, m->d_coords, m->d_quads, m->d_rho, m->d_vel, m->basis64, coef,
                                      m->d_G64, m->d_mloc, m->stream));
-    SEM_CUDA(semdev::launch_mass(dp, P, m->d_mloc, (double*)m->d_partial, m->d_M, m->stream));
+    SEM_CUDA(semdev::launch_mass(dp, P, m->d_mloc, (double*)m->d_part[0], m->d_M, m->stream));
 
     // time-stepping state
-    const size_t nb = (size_t)M.nn * tsize(m);
-    if ((st = zeros(m, &m->d_u[0], nb)) != SEM_OK) return st;
-    if ((st = zeros(m, &m->d_u[1], nb)) != SEM_OK) return st;
+    const size_t nb = node_bytes(m);
+    const int nu = m->prec == SEM_FP32_KAHAN ? 2 : 3;
+    for (int k = 0; k < nu; ++k)
+        if ((st = zeros(m, &m->d_u[k], nb)) != SEM_OK) return st;
     if ((st = zeros(m, &m->d_s, nb)) != SEM_OK) return st;
     if (m->prec == SEM_FP32_KAHAN) {
-        if ((st = zeros(m, &m->d_delta, nb)) != SEM_OK) return st;
-        if ((st = zeros(m, &m->d_comp, nb)) != SEM_OK) return st;
+        for (int k = 0; k < 2; ++k) {
+            if ((st = zeros(m, &m->d_x[k], nb)) != SEM_OK) return st;
+            if ((st = zeros(m, &m->d_c[k], nb)) != SEM_OK) return st;
+        }
     }
     if (m->have_dt) {
         SEM_CUDA(semdev::launch_scale(m->d_M, M.nn, m->dt, fp64(m) ? (double*)m->d_s : nullptr,
                                       fp64(m) ? nullptr : (float*)m->d_s, m->stream));
     }
-    // receivers
     if (m->nrec > 0) {
-        std::vector<int32_t> rg((size_t)m->nrec);
-        std::vector<uint8_t> rc((size_t)m->nrec, 1);
-        std::vector<int32_t> orec(pl.open_gid.size(), -1);
-        m->rec_row.assign((size_t)m->nrec, -1);
-        for (int32_t r = 0; r < m->nrec; ++r) {
-            int32_t g = (int32_t)m->node_new[(size_t)m->rec_nodes[(size_t)r]];
-            rg[(size_t)r] = g;
-            // a second receiver on the same node copies the first one's trace
-            for (int32_t q = 0; q < r; ++q)
-                if (rg[(size_t)q] == g) {
-                    m->rec_row[(size_t)r] = q;
-                    break;
-                }
-            if (m->rec_row[(size_t)r] >= 0) {
-                rc[(size_t)r] = 0;
-                continue;
-            }
-            auto it = std::lower_bound(pl.open_gid.begin(), pl.open_gid.end(), g);
-            if (it != pl.open_gid.end() && *it == g) {
-                rc[(size_t)r] = 0;
-                orec[(size_t)(it - pl.open_gid.begin())] = r;
-            }
-        }
-        if ((st = upload(m, &m->d_rec_gid, rg.data(), rg.size())) != SEM_OK) return st;
-        if ((st = upload(m, &m->d_rec_closed, rc.data(), rc.size())) != SEM_OK) return st;
-        if ((st = upload(m, &m->d_open_rec, orec.data(), orec.size())) != SEM_OK) return st;
-        dp.open_rec = m->d_open_rec;
         void* tr = nullptr;
         if ((st = zeros(m, &tr, (size_t)m->nrec * (size_t)m->trace_cap * 8)) != SEM_OK) return st;
         m->d_trace = (double*)tr;
@@ -340,28 +368,42 @@ sem_status build(sem_mesh* m) {
     return SEM_OK;
 }
 
+// Buffers of level m.
+void* level_u(const sem_mesh* m, int64_t lv) {
+    return m->prec == SEM_FP32_KAHAN ? m->d_u[lv & 1] : m->d_u[((lv % 3) + 3) % 3];
+}
+void* level_x(const sem_mesh* m, int64_t lv) {
+    return m->prec == SEM_FP32_KAHAN ? m->d_x[lv & 1] : m->d_u[(((lv - 1) % 3) + 3) % 3];
+}
+void* level_c(const sem_mesh* m, int64_t lv) { return m->prec == SEM_FP32_KAHAN ? m->d_c[lv & 1] : nullptr; }
+
+// Arguments of launch k (reads level k, writes level k+1 at closed nodes).
 template <typename T>
-semdev::StepArgs<T> step_args(sem_mesh* m) {
+semdev::StepArgs<T> step_args(sem_mesh* m, int64_t k, bool pending) {
     semdev::StepArgs<T> a{};
-    const int cur = (int)(m->step & 1);
-    a.u_cur = (const T*)m->d_u[cur];
-    a.u_out = (T*)m->d_u[cur ^ 1];
-    a.u_prev = (const T*)m->d_u[cur ^ 1];
-    a.delta = (T*)m->d_delta;
-    a.comp = (T*)m->d_comp;
+    a.u_k = (const T*)level_u(m, k);
+    a.x_k = (const T*)level_x(m, k);
+    a.c_k = (const T*)level_c(m, k);
+    a.u_km1 = (const T*)level_u(m, k - 1);
+    a.x_km1 = (const T*)level_x(m, k - 1);
+    a.c_km1 = (const T*)level_c(m, k - 1);
+    a.u_kp1 = (T*)level_u(m, k + 1);
+    a.x_kp1 = m->prec == SEM_FP32_KAHAN ? (T*)level_x(m, k + 1) : nullptr;
+    a.c_kp1 = (T*)level_c(m, k + 1);
+    a.u_kw = (T*)level_u(m, k);
+    a.x_kw = m->prec == SEM_FP32_KAHAN ? (T*)level_x(m, k) : nullptr;
+    a.c_kw = (T*)level_c(m, k);
     a.s = (const T*)m->d_s;
-    a.partial = (T*)m->d_partial;
-    a.G = (const T*)m->d_G64;
-    a.gstride = m->mesh.ne * m->mesh.P;
+    a.part_rd = (const T*)m->d_part[(k + 1) & 1];
+    a.part_wr = (T*)m->d_part[k & 1];
     a.apply_out = nullptr;
     a.src_f = m->d_src;
-    a.step = m->step;
+    a.step = k;
     a.src_gid = m->have_src ? (int32_t)m->node_new[(size_t)m->src_node] : -1;
-    a.rec_gid = m->d_rec_gid;
-    a.rec_closed = m->d_rec_closed;
-    a.nrec = m->nrec;
     a.trace = m->d_trace;
     a.trace_cap = m->trace_cap;
+    a.pending = pending ? 1 : 0;
+    a.vec_ok = 1;
     return a;
 }
 
@@ -376,40 +418,97 @@ cudaEvent_t take_event(sem_mesh* m) {
     return e;
 }
 
-sem_status launch_one_step(sem_mesh* m) {
+const void* basis_of(const sem_mesh* m) {
+    return fp64(m) ? (const void*)&m->basis64 : (const void*)&m->basis32;
+}
+
+// Launch k of a run: the step kernel (pending = not the first launch of the
+// run), recorded with events when profiling.
+sem_status launch_one_step(sem_mesh* m, bool pending) {
     const bool f64 = fp64(m);
     const int mode = mode_of(m);
-    const void* basis = f64 ? (const void*)&m->basis64 : (const void*)&m->basis32;
-    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (m->profiling) {
         e0 = take_event(m);
         e1 = take_event(m);
-        e2 = take_event(m);
-        e3 = take_event(m);
-        if (!e0 || !e1 || !e2 || !e3) return fail(m, SEM_ERR_CUDA, "cudaEventCreate failed");
+        if (!e0 || !e1) return fail(m, SEM_ERR_CUDA, "cudaEventCreate failed");
     }
-    auto rec = [&](cudaEvent_t ev) { return ev ? cudaEventRecord(ev, m->stream) : cudaSuccess; };
-    cudaError_t e = rec(e0);
-    if (f64) {
-        auto a = step_args<double>(m);
-        if (e == cudaSuccess) e = semdev::launch_step(m->mesh.np, true, mode, false, m->dplan, &a, basis, m->smem, m->stream);
-        if (e == cudaSuccess) e = rec(e1);
-        if (e == cudaSuccess) e = rec(e2);
-        if (e == cudaSuccess) e = semdev::launch_open(true, mode, m->dplan, &a, m->stream);
-    } else {
-        auto a = step_args<float>(m);
-        if (e == cudaSuccess) e = semdev::launch_step(m->mesh.np, false, mode, true, m->dplan, &a, basis, m->smem, m->stream);
-        if (e == cudaSuccess) e = rec(e1);
-        if (e == cudaSuccess) e = rec(e2);
-        if (e == cudaSuccess) e = semdev::launch_open(false, mode, m->dplan, &a, m->stream);
+    cudaError_t e = e0 ? cudaEventRecord(e0, m->stream) : cudaSuccess;
+    if (e == cudaSuccess) {
+        if (f64) {
+            auto a = step_args<double>(m, m->step, pending);
+            e = semdev::launch_step(m->mesh.np, true, mode, m->dplan, &a, basis_of(m), m->threads, m->smem, m->stream);
+        } else {
+            auto a = step_args<float>(m, m->step, pending);
+            e = semdev::launch_step(m->mesh.np, false, mode, m->dplan, &a, basis_of(m), m->threads, m->smem, m->stream);
+        }
     }
-    if (e == cudaSuccess) e = rec(e3);
+    if (e == cudaSuccess && e1) e = cudaEventRecord(e1, m->stream);
     if (e != cudaSuccess) return cuda_fail(m, e, "step launch");
-    if (m->profiling) {
-        m->ev_block.push_back({e0, e1});
-        m->ev_open.push_back({e2, e3});
-    }
+    if (m->profiling) m->ev_block.push_back({e0, e1});
     m->step++;
+    return SEM_OK;
+}
+
+// After the last launch k of a run: finish the open nodes to level k+1.
+sem_status launch_flush(sem_mesh* m) {
+    const bool f64 = fp64(m);
+    const int mode = mode_of(m);
+    const int64_t k = m->step - 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (m->profiling) {
+        e0 = take_event(m);
+        e1 = take_event(m);
+        if (!e0 || !e1) return fail(m, SEM_ERR_CUDA, "cudaEventCreate failed");
+    }
+    cudaError_t e = e0 ? cudaEventRecord(e0, m->stream) : cudaSuccess;
+    if (e == cudaSuccess) {
+        if (f64) {
+            auto a = step_args<double>(m, k, false);
+            a.part_rd = (const double*)m->d_part[k & 1];
+            e = semdev::launch_open_finish(true, mode, m->dplan, &a, m->stream);
+        } else {
+            auto a = step_args<float>(m, k, false);
+            a.part_rd = (const float*)m->d_part[k & 1];
+            e = semdev::launch_open_finish(false, mode, m->dplan, &a, m->stream);
+        }
+    }
+    if (e == cudaSuccess && e1) e = cudaEventRecord(e1, m->stream);
+    if (e != cudaSuccess) return cuda_fail(m, e, "open-node launch");
+    if (m->profiling) m->ev_open.push_back({e0, e1});
+    return SEM_OK;
+}
+
+// K u for u in the library's storage type and order (dev_in), into dev_out,
+// with `partial` as scratch for the open entries' partial sums.
+sem_status launch_apply(sem_mesh* m, const void* dev_in, void* dev_out, void* partial) {
+    const bool f64 = fp64(m);
+    const bool vok = ((uintptr_t)dev_in % 16) == 0;
+    cudaError_t e;
+    if (f64) {
+        semdev::StepArgs<double> a{};
+        a.u_k = (const double*)dev_in;
+        a.apply_out = (double*)dev_out;
+        a.part_wr = (double*)partial;
+        a.part_rd = (const double*)partial;
+        a.vec_ok = vok;
+        a.src_gid = -1;
+        e = semdev::launch_step(m->mesh.np, true, semdev::MODE_APPLY, m->dplan, &a, basis_of(m), m->threads, m->smem,
+                                m->stream);
+        if (e == cudaSuccess) e = semdev::launch_open_finish(true, semdev::MODE_APPLY, m->dplan, &a, m->stream);
+    } else {
+        semdev::StepArgs<float> a{};
+        a.u_k = (const float*)dev_in;
+        a.apply_out = (float*)dev_out;
+        a.part_wr = (float*)partial;
+        a.part_rd = (const float*)partial;
+        a.vec_ok = vok;
+        a.src_gid = -1;
+        e = semdev::launch_step(m->mesh.np, false, semdev::MODE_APPLY, m->dplan, &a, basis_of(m), m->threads,
+                                m->smem, m->stream);
+        if (e == cudaSuccess) e = semdev::launch_open_finish(false, semdev::MODE_APPLY, m->dplan, &a, m->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(m, e, "apply launch");
     return SEM_OK;
 }
 
@@ -588,12 +687,15 @@ sem_status sem_set_dt(sem_mesh* m, double dt) {
     return SEM_OK;
 }
 
-sem_status sem_set_tuning(sem_mesh* m, int elems_per_block) {
+sem_status sem_set_tuning(sem_mesh* m, int elems_per_block, int threads_per_block) {
     if (!m) return SEM_ERR_INVALID_ARG;
-    if (elems_per_block < 0 || (int64_t)elems_per_block * m->mesh.P > 65535)
+    if (elems_per_block < 0 || elems_per_block > 256 || (int64_t)elems_per_block * m->mesh.P > 65535)
         return fail(m, SEM_ERR_INVALID_ARG, "elems_per_block out of range");
+    if (threads_per_block < 0 || threads_per_block > 256 || threads_per_block % 32 != 0)
+        return fail(m, SEM_ERR_INVALID_ARG, "threads_per_block must be 0 or a multiple of 32 up to 256");
     if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_tuning after the device data was built");
     m->eb_request = elems_per_block;
+    m->threads_request = threads_per_block;
     return SEM_OK;
 }
 
@@ -605,9 +707,14 @@ sem_status sem_step(sem_mesh* m, int64_t nsteps) {
     if (st != SEM_OK) return st;
     if (m->nrec > 0 && m->step + nsteps > m->trace_cap)
         return fail(m, SEM_ERR_INVALID_ARG, "steps beyond the receivers' max_steps");
+    if (nsteps == 0) return SEM_OK;
     if ((st = fill_source(m, m->step + nsteps)) != SEM_OK) return st;
+    // the first launch reads a fully stored level; later ones finish the
+    // open nodes of the previous launch themselves; the flush completes the
+    // open nodes after the last launch
     for (int64_t k = 0; k < nsteps; ++k)
-        if ((st = launch_one_step(m)) != SEM_OK) return st;
+        if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+    if ((st = launch_flush(m)) != SEM_OK) return st;
     m->stepped_calls++;
     return SEM_OK;
 }
@@ -649,16 +756,15 @@ sem_status sem_set_state(sem_mesh* m, const double* u, const double* u_prev, int
     if (st != SEM_OK) return st;
     if (m->nrec > 0 && step > m->trace_cap) return fail(m, SEM_ERR_INVALID_ARG, "step beyond max_steps");
     m->step = step;
-    const int cur = (int)(step & 1);
-    if ((st = write_nodes(m, m->d_u[cur], u)) != SEM_OK) return st;
+    if ((st = write_nodes(m, level_u(m, step), u)) != SEM_OK) return st;
     if (m->prec == SEM_FP32_KAHAN) {
         std::vector<double> d((size_t)m->mesh.nn);
         for (size_t k = 0; k < d.size(); ++k) d[k] = u[k] - u_prev[k];
-        if ((st = write_nodes(m, m->d_delta, d.data())) != SEM_OK) return st;
-        SEM_CUDA(cudaMemsetAsync(m->d_comp, 0, (size_t)m->mesh.nn * 4, m->stream));
+        if ((st = write_nodes(m, level_x(m, step), d.data())) != SEM_OK) return st;
+        SEM_CUDA(cudaMemsetAsync(level_c(m, step), 0, (size_t)m->mesh.nn * 4, m->stream));
         SEM_CUDA(cudaStreamSynchronize(m->stream));
     } else {
-        if ((st = write_nodes(m, m->d_u[cur ^ 1], u_prev)) != SEM_OK) return st;
+        if ((st = write_nodes(m, level_x(m, step), u_prev)) != SEM_OK) return st;
     }
     return SEM_OK;
 }
@@ -672,21 +778,20 @@ sem_status sem_get_state(sem_mesh* m, double* u, double* u_prev, int64_t* step) 
         if (u_prev) std::fill(u_prev, u_prev + nn, 0.0);
         return SEM_OK;
     }
-    const int cur = (int)(m->step & 1);
     std::vector<double> un, tmp;
-    sem_status st = read_nodes(m, m->d_u[cur], fp64(m), un);
+    sem_status st = read_nodes(m, level_u(m, m->step), fp64(m), un);
     if (st != SEM_OK) return st;
     if (m->prec == SEM_FP32_KAHAN) {
         // compensated value u - c; u^{n-1} = u^n - delta^{n-1/2}
-        if ((st = read_nodes(m, m->d_comp, false, tmp)) != SEM_OK) return st;
+        if ((st = read_nodes(m, level_c(m, m->step), false, tmp)) != SEM_OK) return st;
         for (size_t k = 0; k < nn; ++k) un[k] -= tmp[k];
         if (u_prev) {
-            if ((st = read_nodes(m, m->d_delta, false, tmp)) != SEM_OK) return st;
+            if ((st = read_nodes(m, level_x(m, m->step), false, tmp)) != SEM_OK) return st;
             for (size_t k = 0; k < nn; ++k) tmp[k] = un[k] - tmp[k];
             to_original(m, tmp, u_prev);
         }
     } else if (u_prev) {
-        if ((st = read_nodes(m, m->d_u[cur ^ 1], fp64(m), tmp)) != SEM_OK) return st;
+        if ((st = read_nodes(m, level_x(m, m->step), fp64(m), tmp)) != SEM_OK) return st;
         to_original(m, tmp, u_prev);
     }
     if (u) to_original(m, un, u);
@@ -698,33 +803,18 @@ sem_status sem_apply_stiffness(sem_mesh* m, const double* u, double* Ku) {
     if (!m->have_model) return fail(m, SEM_ERR_STATE, "sem_set_model must come first");
     sem_status st = build(m);
     if (st != SEM_OK) return st;
-    const size_t nb = (size_t)m->mesh.nn * tsize(m);
+    const size_t nb = node_bytes(m);
     if (!m->d_apply_in) {
         m->d_apply_in = dev_alloc(m, nb);
         m->d_apply_out = dev_alloc(m, nb);
         if (!m->d_apply_in || !m->d_apply_out) return fail(m, SEM_ERR_OOM, "device allocation failed");
     }
     if ((st = write_nodes(m, m->d_apply_in, u)) != SEM_OK) return st;
-    const bool f64 = fp64(m);
-    const void* basis = f64 ? (const void*)&m->basis64 : (const void*)&m->basis32;
-    cudaError_t e;
-    if (f64) {
-        auto a = step_args<double>(m);
-        a.u_cur = (const double*)m->d_apply_in;
-        a.apply_out = (double*)m->d_apply_out;
-        e = semdev::launch_step(m->mesh.np, true, semdev::MODE_APPLY, false, m->dplan, &a, basis, m->smem, m->stream);
-        if (e == cudaSuccess) e = semdev::launch_open(true, semdev::MODE_APPLY, m->dplan, &a, m->stream);
-    } else {
-        auto a = step_args<float>(m);
-        a.u_cur = (const float*)m->d_apply_in;
-        a.apply_out = (float*)m->d_apply_out;
-        e = semdev::launch_step(m->mesh.np, false, semdev::MODE_APPLY, true, m->dplan, &a, basis, m->smem,
-                                m->stream);
-        if (e == cudaSuccess) e = semdev::launch_open(false, semdev::MODE_APPLY, m->dplan, &a, m->stream);
-    }
-    if (e != cudaSuccess) return cuda_fail(m, e, "apply launch");
+    // the partial-sum buffer of the step that comes next is free: every
+    // launch that reads partials first has them written by its predecessor
+    if ((st = launch_apply(m, m->d_apply_in, m->d_apply_out, m->d_part[m->step & 1])) != SEM_OK) return st;
     std::vector<double> out;
-    if ((st = read_nodes(m, m->d_apply_out, f64, out)) != SEM_OK) return st;
+    if ((st = read_nodes(m, m->d_apply_out, fp64(m), out)) != SEM_OK) return st;
     to_original(m, out, Ku);
     return SEM_OK;
 }
@@ -771,6 +861,102 @@ sem_status sem_get_snapped(const sem_mesh* m, int64_t* src_node, int64_t* rec_no
     return SEM_OK;
 }
 
+sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads, int64_t ne, int order,
+                          sem_ordering kind, uint64_t seed, int elems_per_block, int fp64_storage,
+                          const double* rec_xy, int32_t nrec, int64_t* info, char* msg, size_t msg_cap) {
+    auto say = [&](const std::string& t) {
+        if (msg && msg_cap > 0) {
+            const size_t n = std::min(msg_cap - 1, t.size());
+            std::memcpy(msg, t.data(), n);
+            msg[n] = 0;
+        }
+    };
+    say("");
+    if (!coords || !quads || (nrec > 0 && !rec_xy) || nrec < 0) return SEM_ERR_INVALID_ARG;
+    if ((int)kind < 0 || (int)kind > 3 || elems_per_block < 1 || elems_per_block > 256) return SEM_ERR_INVALID_ARG;
+    const std::string bad = semhost::validate(coords, nv, quads, ne, order);
+    if (!bad.empty()) {
+        say(bad);
+        return SEM_ERR_INVALID_ARG;
+    }
+    semhost::Mesh mm;
+    mm.p = order;
+    mm.nv = nv;
+    mm.ne = ne;
+    mm.coords.assign(coords, coords + nv * 2);
+    mm.quads.assign(quads, quads + ne * 4);
+    semhost::number_nodes(mm);
+    std::vector<int64_t> eo, no;
+    semhost::orderings(mm, (int)kind, seed, eo, no);
+    std::vector<int64_t> nnew(no.size());
+    for (size_t k = 0; k < no.size(); ++k) nnew[(size_t)no[k]] = (int64_t)k;
+    const int P = mm.P;
+    std::vector<int32_t> conn_new((size_t)(ne * P));
+    for (int64_t en = 0; en < ne; ++en)
+        for (int q = 0; q < P; ++q)
+            conn_new[(size_t)(en * P + q)] = (int32_t)nnew[(size_t)mm.conn[(size_t)(eo[(size_t)en] * P + q)]];
+    std::vector<double> xy;
+    semhost::node_coordinates(mm, xy);
+    std::vector<int32_t> rec_gid((size_t)nrec, -1);
+    for (int32_t r = 0; r < nrec; ++r) {
+        const int32_t g = (int32_t)nnew[(size_t)semhost::snap(xy, rec_xy[2 * r], rec_xy[2 * r + 1])];
+        bool dup = false;
+        for (int32_t q = 0; q < r; ++q) dup = dup || rec_gid[(size_t)q] == g;
+        if (!dup) rec_gid[(size_t)r] = g;
+    }
+    const int vec = fp64_storage ? 2 : 4;
+    semhost::BlockPlan pl;
+    std::string why = semhost::build_block_plan(conn_new, ne, P, mm.nn, elems_per_block, true, vec, rec_gid, pl);
+    if (!why.empty()) {
+        say(why);
+        return SEM_ERR_UNSUPPORTED;
+    }
+    if (info) {
+        info[0] = pl.nblocks;
+        info[1] = pl.dense ? 1 : 0;
+        info[2] = (int64_t)pl.open_gid.size();
+        info[3] = pl.max_entries;
+        info[4] = pl.max_packet;
+        info[5] = pl.npartial;
+    }
+    why = semhost::check_block_plan(pl, conn_new, vec);
+    if (!why.empty()) {
+        say(why);
+        return SEM_ERR_STATE;
+    }
+    // receivers: every distinct receiver node is recorded exactly once
+    std::vector<int> seen((size_t)nrec, 0);
+    for (int64_t b = 0; b < pl.nblocks; ++b) {
+        const int32_t* h = &pl.hdr[(size_t)b * semplan::HDR_INTS];
+        const int nrc = h[semplan::H_NREC] >> 16, nro = h[semplan::H_NREC] & 0xFFFF;
+        const int neb = (int)std::min<int64_t>(elems_per_block, ne - b * elems_per_block);
+        const semplan::Offsets L =
+            semplan::offsets(neb * P, h[semplan::H_NENT], h[semplan::H_NOWN], h[semplan::H_NOPEN], nrc + nro);
+        const int32_t* recs = reinterpret_cast<const int32_t*>(pl.packet.data() + (size_t)h[0] * 16 + L.recs);
+        for (int k = 0; k < nrc + nro; ++k) {
+            const int r = recs[2 * k + 1];
+            if (r < 0 || r >= nrec) {
+                say("receiver record out of range");
+                return SEM_ERR_STATE;
+            }
+            seen[(size_t)r]++;
+        }
+    }
+    for (size_t k = 0; k < pl.open_rec.size(); ++k)
+        if (pl.open_rec[k] >= 0) seen[(size_t)pl.open_rec[k]] += 1000;  // finished again by the open-node pass
+    for (int32_t r = 0; r < nrec; ++r) {
+        const int want = rec_gid[(size_t)r] < 0 ? 0 : 1;
+        const int got = seen[(size_t)r] % 1000;
+        const bool open_node = seen[(size_t)r] >= 1000;
+        if ((want == 0 && seen[(size_t)r] != 0) || (want == 1 && !(got == 1))) {
+            say("receiver " + std::to_string(r) + " recorded " + std::to_string(got) + " times in blocks");
+            return SEM_ERR_STATE;
+        }
+        (void)open_node;
+    }
+    return SEM_OK;
+}
+
 sem_status sem_count_nodes(const int32_t* quads, int64_t nv, int64_t ne, int order, int64_t* n_nodes) {
     if (!quads || !n_nodes || nv <= 0 || ne <= 0 || order < 1 || order > 8) return SEM_ERR_INVALID_ARG;
     for (int64_t i = 0; i < ne * 4; ++i)
@@ -814,7 +1000,7 @@ sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells) {
 
 sem_status sem_launch_info(const sem_mesh* m, int64_t* launches_per_step, int64_t* open_nodes) {
     if (!m) return SEM_ERR_INVALID_ARG;
-    if (launches_per_step) *launches_per_step = 2;
+    if (launches_per_step) *launches_per_step = 1;
     if (open_nodes) *open_nodes = m->built ? (int64_t)m->plan.open_gid.size() : -1;
     return SEM_OK;
 }
@@ -856,22 +1042,29 @@ sem_status sem_traffic_model(const sem_mesh* m, double* block_bytes, double* ope
     if (!m->built) return SEM_ERR_STATE;
     const auto& pl = m->plan;
     const double ts = (double)tsize(m);
-    const double slots = (double)m->mesh.ne * m->mesh.P;
-    const double nopen = (double)pl.open_gid.size();
-    const double nclosed_nodes = (double)pl.nclosed_total;
-    const double nopen_entries = (double)(pl.nent_total - pl.nclosed_total);
-    // node state read and written by an update: Kahan: u in, u out, s, delta
-    // in/out, comp in/out; three-level: u in, u out, s, u^{n-1}
-    const double upd = m->prec == SEM_FP32_KAHAN ? 7.0 * ts : 4.0 * ts;
-    const double geo = fp64(m) ? slots * 3.0 * ts : 0.0;   // FP32: geometry is in the packet
-    const double blk = (double)pl.packet.size() + (double)pl.nblocks * 16.0  // packets + headers
-                       + geo                                                // stored metric (FP64)
-                       + nopen * ts                                         // u at open nodes
-                       + nclosed_nodes * upd                                // closed nodes: u + update
-                       + nopen_entries * ts;                                // partial sums written
-    const double opn = nopen * (8.0 + upd) + nopen_entries * (4.0 + ts) + (m->nrec > 0 ? nopen * 4.0 : 0.0);
-    if (block_bytes) *block_bytes = blk;
-    if (open_bytes) *open_bytes = opn;
+    const double ne = (double)m->mesh.ne, nn = (double)m->mesh.nn;
+    const double slots = ne * m->mesh.P;
+    const bool kahan = m->prec == SEM_FP32_KAHAN;
+    const double nopen_nodes = (double)pl.open_gid.size();
+    const double nclosed = (double)pl.nclosed_total;
+    const double nopen_entries = (double)pl.nopen_entries;
+    // element side: packed positions, geometry (FP32 bilinear map or FP64 metric)
+    const double elem = (double)pl.epos.size() * 4.0 + (fp64(m) ? slots * 3.0 * ts : ne * 32.0);
+    const double plan = (double)pl.packet.size() + (double)pl.nblocks * 32.0;
+    // closed nodes: read u, s and the update state, write u and the state
+    const double state_words = kahan ? 3.0 : 2.0;          // u, delta, c  |  u, u_prev
+    const double closed_rw = nclosed * ts * ((1.0 + state_words) + (kahan ? 3.0 : 1.0));
+    // open entries of a pending launch: partials of the node, level k-1
+    // state and s; the owner stores level k; every open entry writes a partial
+    double part_per_node = 0.0;
+    for (int32_t c : pl.open_cnt) part_per_node += c;
+    const double avg_cnt = nopen_nodes > 0 ? part_per_node / nopen_nodes : 0.0;
+    const double open_rw = nopen_entries * ts * (avg_cnt + 1.0 + state_words + 1.0) + nopen_nodes * ts * state_words;
+    (void)nn;
+    if (block_bytes) *block_bytes = elem + plan + closed_rw + open_rw;
+    // open-node pass after the last launch: lists, partials, state in and out
+    if (open_bytes)
+        *open_bytes = nopen_nodes * (16.0 + ts * (avg_cnt + 1.0 + 2.0 * state_words + (kahan ? 1.0 : 0.0)));
     return SEM_OK;
 }
 
@@ -931,34 +1124,15 @@ sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void*
     if (!m || !dev_u || !dev_Ku) return SEM_ERR_INVALID_ARG;
     if (!m->built)
         return fail(m, SEM_ERR_STATE, "device data not built: call sem_step, sem_set_state or sem_apply_stiffness once");
-    const int64_t open_entries = m->plan.nent_total - m->plan.nclosed_total;
-    if ((double)open_entries * (double)tsize(m) > (double)SEM_NOALLOC_SCRATCH_BYTES)
+    const int64_t need = m->plan.npartial * (int64_t)tsize(m);
+    if ((double)need > (double)SEM_NOALLOC_SCRATCH_BYTES)
         return fail(m, SEM_ERR_INVALID_ARG,
-                    "mesh needs " + std::to_string(open_entries * (int64_t)tsize(m)) +
-                        " bytes of partial sums, above the allocation-free limit of " +
+                    "mesh needs " + std::to_string(need) + " bytes of partial sums, above the allocation-free limit of " +
                         std::to_string((unsigned)SEM_NOALLOC_SCRATCH_BYTES) + " bytes");
     void* scratch = nullptr;
     cudaError_t e = noalloc_scratch(&scratch);
     if (e != cudaSuccess) return cuda_fail(m, e, "cudaGetSymbolAddress");
-    const bool f64 = fp64(m);
-    const void* basis = f64 ? (const void*)&m->basis64 : (const void*)&m->basis32;
-    if (f64) {
-        auto a = step_args<double>(m);
-        a.u_cur = (const double*)dev_u;
-        a.apply_out = (double*)dev_Ku;
-        a.partial = (double*)scratch;
-        e = semdev::launch_step(m->mesh.np, true, semdev::MODE_APPLY, false, m->dplan, &a, basis, m->smem, m->stream);
-        if (e == cudaSuccess) e = semdev::launch_open(true, semdev::MODE_APPLY, m->dplan, &a, m->stream);
-    } else {
-        auto a = step_args<float>(m);
-        a.u_cur = (const float*)dev_u;
-        a.apply_out = (float*)dev_Ku;
-        a.partial = (float*)scratch;
-        e = semdev::launch_step(m->mesh.np, false, semdev::MODE_APPLY, true, m->dplan, &a, basis, m->smem, m->stream);
-        if (e == cudaSuccess) e = semdev::launch_open(false, semdev::MODE_APPLY, m->dplan, &a, m->stream);
-    }
-    if (e != cudaSuccess) return cuda_fail(m, e, "noalloc apply launch");
-    return SEM_OK;
+    return launch_apply(m, dev_u, dev_Ku, scratch);
 }
 
 }  // extern "C"

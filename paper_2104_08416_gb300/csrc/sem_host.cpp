@@ -521,123 +521,321 @@ double cfl_dt(const Mesh& m, const double* vel) {
 // ------------------------------------------------------------ block plan
 static inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-PacketLayout packet_layout(int64_t nslot, int64_t nent, int64_t neb) {
-    PacketLayout L;
-    L.lidx = 0;
-    L.lsl = 2 * nslot;
-    L.lrow = 4 * nslot;
-    L.gid = align_up(L.lrow + 2 * (nent + 1), 4);
-    L.coef = align_up(L.gid + 4 * nent, 16);
-    L.bytes = align_up(L.coef + 32 * neb, 16);
-    return L;
-}
-
-void build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P, int64_t nn, int eb, BlockPlan& pl) {
+std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P, int64_t nn, int eb,
+                             bool allow_dense, int vec, const std::vector<int32_t>& rec_gid, BlockPlan& pl) {
+    using namespace semplan;
+    pl = BlockPlan();
     pl.eb = eb;
+    pl.P = P;
+    pl.ne = ne;
+    pl.nn = nn;
     pl.nblocks = (ne + eb - 1) / eb;
     const int64_t nb = pl.nblocks;
-    std::vector<int32_t> valence((size_t)nn, 0);
-    for (int64_t s = 0; s < ne * P; ++s) valence[(size_t)conn[(size_t)s]]++;
-    pl.hdr.assign((size_t)nb * 4, 0);
-    pl.packet.clear();
-    pl.max_entries = 0;
-    pl.max_packet = 0;
-    pl.nent_total = pl.nclosed_total = 0;
+    if ((int64_t)eb * P > 65535) return "elements per block x points per element above 65535";
+    // blocks touching each node (blocks are visited in ascending order)
+    std::vector<int32_t> nblk((size_t)nn, 0);
+    std::vector<int64_t> last((size_t)nn, -1);
+    for (int64_t s = 0; s < ne * P; ++s) {
+        const int32_t g = conn[(size_t)s];
+        const int64_t b = s / P / eb;
+        if (last[(size_t)g] != b) {
+            last[(size_t)g] = b;
+            nblk[(size_t)g]++;
+        }
+    }
+    // DENSE when the nodes first touched by each block are the next id range
+    bool dense = allow_dense;
+    if (dense) {
+        std::vector<uint8_t> seen((size_t)nn, 0);
+        int64_t next = 0;
+        for (int64_t b = 0; b < nb && dense; ++b) {
+            const int64_t s0 = b * eb * P, s1 = std::min(ne, (b + 1) * eb) * P;
+            int64_t cnt = 0;
+            for (int64_t t = s0; t < s1 && dense; ++t) {
+                const int32_t g = conn[(size_t)t];
+                if (!seen[(size_t)g]) {
+                    seen[(size_t)g] = 1;
+                    if (g < next || g >= next + (s1 - s0)) dense = false;
+                    cnt++;
+                }
+            }
+            for (int64_t g = next; g < next + cnt && dense; ++g)
+                if (g >= nn || !seen[(size_t)g]) dense = false;
+            next += cnt;
+        }
+    }
+    pl.dense = dense;
+    // partial-sum slots: a contiguous run per open node, ascending node id
+    std::vector<int64_t> base((size_t)nn, -1);
+    for (int64_t g = 0; g < nn; ++g) {
+        if (nblk[(size_t)g] > MAX_BLOCKS_PER_NODE) return "a node is touched by more than 255 element blocks";
+        if (nblk[(size_t)g] > 1) {
+            base[(size_t)g] = pl.npartial;
+            pl.open_gid.push_back((int32_t)g);
+            pl.open_base.push_back((int32_t)pl.npartial);
+            pl.open_cnt.push_back(nblk[(size_t)g]);
+            pl.npartial += nblk[(size_t)g];
+        }
+    }
+    if (pl.npartial > INT32_MAX) return "too many partial sums";
+    std::vector<int32_t> rec_of((size_t)nn, -1);
+    for (size_t r = 0; r < rec_gid.size(); ++r)
+        if (rec_gid[r] >= 0 && rec_of[(size_t)rec_gid[r]] < 0) rec_of[(size_t)rec_gid[r]] = (int32_t)r;
+    pl.open_rec.resize(pl.open_gid.size());
+    for (size_t k = 0; k < pl.open_gid.size(); ++k) pl.open_rec[k] = rec_of[(size_t)pl.open_gid[k]];
+
+    const int UPH = (P + 1) / 2;
+    pl.epos.assign((size_t)UPH * (size_t)ne, 0u);
+    pl.hdr.assign((size_t)nb * HDR_INTS, 0);
+    std::vector<int32_t> seen_rank((size_t)nn, 0);   // blocks that touched the node so far
+    std::vector<int64_t> in_block((size_t)nn, -1);
     std::vector<int32_t> local((size_t)nn, -1);
-    std::vector<int64_t> seen_block((size_t)nn, -1);
-    std::vector<int32_t> opencount((size_t)nn, 0);
-    std::vector<int32_t> first_ent, cnt, order, rank;
-    std::vector<uint16_t> lidx, lsl, lrow;
-    std::vector<int32_t> gid;
-    // open entries of each block, in entry order, as node ids (for pass 2)
-    std::vector<int32_t> open_nodes_flat;
-    std::vector<int64_t> open_nodes_ptr(1, 0);
-    int64_t pbase = 0;
+    std::vector<uint8_t> touched((size_t)nn, 0);
+    std::vector<int32_t> ent_gid, cnt, slot_ent;
+    std::vector<int32_t> recs;
+    int64_t own_next = 0;
     for (int64_t b = 0; b < nb; ++b) {
         const int64_t e0 = b * eb, e1 = std::min(ne, e0 + eb);
         const int64_t s0 = e0 * P, nslot = (e1 - e0) * P;
-        // entries by first appearance
-        first_ent.clear();
+        ent_gid.clear();
         cnt.clear();
-        std::vector<int32_t> raw((size_t)nslot);
-        for (int64_t t = 0; t < nslot; ++t) {
-            int32_t g = conn[(size_t)(s0 + t)];
-            if (seen_block[(size_t)g] != b) {
-                seen_block[(size_t)g] = b;
-                local[(size_t)g] = (int32_t)first_ent.size();
-                first_ent.push_back(g);
+        int64_t own_start = 0, nown = 0;
+        if (dense) {
+            own_start = own_next;
+            for (int64_t t = s0; t < s0 + nslot; ++t) {
+                const int32_t g = conn[(size_t)t];
+                if (!touched[(size_t)g]) {
+                    touched[(size_t)g] = 1;
+                    nown++;
+                }
+            }
+            for (int64_t l = 0; l < nown; ++l) {
+                const int32_t g = (int32_t)(own_start + l);
+                in_block[(size_t)g] = b;
+                local[(size_t)g] = (int32_t)l;
+                ent_gid.push_back(g);
                 cnt.push_back(0);
             }
-            raw[(size_t)t] = local[(size_t)g];
+            own_next = own_start + nown;
+        }
+        slot_ent.assign((size_t)nslot, 0);
+        for (int64_t t = 0; t < nslot; ++t) {
+            const int32_t g = conn[(size_t)(s0 + t)];
+            if (in_block[(size_t)g] != b) {
+                in_block[(size_t)g] = b;
+                local[(size_t)g] = (int32_t)ent_gid.size();
+                ent_gid.push_back(g);
+                cnt.push_back(0);
+            }
+            slot_ent[(size_t)t] = local[(size_t)g];
             cnt[(size_t)local[(size_t)g]]++;
         }
-        const int32_t nent = (int32_t)first_ent.size();
-        // closed entries first, then open, each in first-appearance order
-        rank.assign((size_t)nent, 0);
-        int32_t nclosed = 0;
-        for (int32_t l = 0; l < nent; ++l)
-            if (cnt[(size_t)l] == valence[(size_t)first_ent[(size_t)l]]) nclosed++;
-        int32_t ic = 0, io = nclosed;
-        gid.assign((size_t)nent, 0);
-        std::vector<int32_t> c2((size_t)nent);
-        for (int32_t l = 0; l < nent; ++l) {
-            bool closed = cnt[(size_t)l] == valence[(size_t)first_ent[(size_t)l]];
-            int32_t r = closed ? ic++ : io++;
-            rank[(size_t)l] = r;
-            gid[(size_t)r] = first_ent[(size_t)l];
-            c2[(size_t)r] = cnt[(size_t)l];
+        const int64_t nent = (int64_t)ent_gid.size();
+        const int64_t off = dense ? own_start % vec : 0;
+        const int64_t ulen = dense ? align_up(off + nown, vec) : 0;
+        const int64_t sulen = ulen + (nent - nown);
+        const int64_t slen = dense ? ulen : nent;
+        if (nent > 65535 || sulen > 65535) return "too many nodes in one element block";
+        // open ranks in entry order
+        std::vector<int32_t> orank_of((size_t)nent, -1);
+        int64_t nopen = 0;
+        for (int64_t l = 0; l < nent; ++l)
+            if (nblk[(size_t)ent_gid[(size_t)l]] > 1) orank_of[(size_t)l] = (int32_t)nopen++;
+        if (nopen >= 65535) return "too many open nodes in one element block";
+        recs.clear();
+        int64_t nrc = 0, nro = 0;
+        for (int64_t l = 0; l < nent; ++l) {
+            const int32_t g = ent_gid[(size_t)l];
+            if (rec_of[(size_t)g] >= 0 && orank_of[(size_t)l] < 0) {
+                recs.push_back((int32_t)l);
+                recs.push_back(rec_of[(size_t)g]);
+                nrc++;
+            }
         }
-        for (int32_t r = nclosed; r < nent; ++r) {
-            open_nodes_flat.push_back(gid[(size_t)r]);
-            opencount[(size_t)gid[(size_t)r]]++;
+        for (int64_t l = 0; l < nent; ++l) {
+            const int32_t g = ent_gid[(size_t)l];
+            if (rec_of[(size_t)g] >= 0 && orank_of[(size_t)l] >= 0 && seen_rank[(size_t)g] == 0) {
+                recs.push_back(orank_of[(size_t)l]);
+                recs.push_back(rec_of[(size_t)g]);
+                nro++;
+            }
         }
-        open_nodes_ptr.push_back((int64_t)open_nodes_flat.size());
-        lidx.assign((size_t)nslot, 0);
-        for (int64_t t = 0; t < nslot; ++t) lidx[(size_t)t] = (uint16_t)rank[(size_t)raw[(size_t)t]];
-        lrow.assign((size_t)nent + 1, 0);
-        for (int32_t r = 0; r < nent; ++r) lrow[(size_t)r + 1] = (uint16_t)(lrow[(size_t)r] + c2[(size_t)r]);
-        std::vector<uint16_t> fill(lrow.begin(), lrow.end() - 1);
-        lsl.assign((size_t)nslot, 0);
-        for (int64_t t = 0; t < nslot; ++t) lsl[(size_t)fill[(size_t)lidx[(size_t)t]]++] = (uint16_t)t;
-        // packet
-        PacketLayout L = packet_layout(nslot, nent, e1 - e0);
+        if (nrc > 65535 || nro > 65535) return "too many receivers in one element block";
+        const Offsets L = offsets((int)nslot, (int)nent, (int)nown, (int)nopen, (int)(nrc + nro));
         const int64_t start = (int64_t)pl.packet.size();
         pl.packet.resize((size_t)(start + L.bytes), 0);
         uint8_t* pk = pl.packet.data() + start;
-        std::memcpy(pk + L.lidx, lidx.data(), (size_t)nslot * 2);
-        std::memcpy(pk + L.lsl, lsl.data(), (size_t)nslot * 2);
-        std::memcpy(pk + L.lrow, lrow.data(), (size_t)(nent + 1) * 2);
-        std::memcpy(pk + L.gid, gid.data(), (size_t)nent * 4);
-        int32_t* h = &pl.hdr[(size_t)b * 4];
-        h[0] = (int32_t)(start / 16);
-        h[1] = nent;
-        h[2] = nclosed;
-        h[3] = (int32_t)pbase;
-        pbase += nent - nclosed;
-        pl.max_entries = std::max(pl.max_entries, (int)nent);
-        pl.max_packet = std::max(pl.max_packet, L.bytes);
+        uint16_t* lsl = reinterpret_cast<uint16_t*>(pk + L.lsl);
+        uint16_t* lrow = reinterpret_cast<uint16_t*>(pk + L.lrow);
+        uint16_t* aux = reinterpret_cast<uint16_t*>(pk + L.aux);
+        int32_t* egid = reinterpret_cast<int32_t*>(pk + L.egid);
+        int32_t* obase = reinterpret_cast<int32_t*>(pk + L.obase);
+        uint16_t* oent = reinterpret_cast<uint16_t*>(pk + L.oent);
+        uint8_t* ocnt = pk + L.ocnt;
+        uint8_t* orank = pk + L.orank;
+        int32_t* prec = reinterpret_cast<int32_t*>(pk + L.recs);
+        lrow[0] = 0;
+        for (int64_t l = 0; l < nent; ++l) lrow[l + 1] = (uint16_t)(lrow[l] + cnt[(size_t)l]);
+        {
+            std::vector<uint16_t> fill(lrow, lrow + nent);
+            for (int64_t t = 0; t < nslot; ++t) lsl[fill[(size_t)slot_ent[(size_t)t]]++] = (uint16_t)t;
+        }
+        for (int64_t l = 0; l < nent; ++l) {
+            const int32_t g = ent_gid[(size_t)l];
+            const int32_t o = orank_of[(size_t)l];
+            if (o < 0) {
+                aux[l] = CLOSED;
+                pl.nclosed_total++;
+            } else {
+                aux[l] = (uint16_t)o;
+                obase[o] = (int32_t)base[(size_t)g];
+                oent[o] = (uint16_t)l;
+                ocnt[o] = (uint8_t)nblk[(size_t)g];
+                orank[o] = (uint8_t)seen_rank[(size_t)g];
+            }
+            seen_rank[(size_t)g]++;
+            if (l >= nown) egid[l - nown] = g;
+        }
+        std::copy(recs.begin(), recs.end(), prec);
+        for (int64_t t = 0; t < nslot; ++t) {
+            const int64_t e = e0 + t / P;
+            const int q = (int)(t % P);
+            const uint32_t pos = (uint32_t)entry_pos(slot_ent[(size_t)t], (int)nown, (int)off, (int)ulen);
+            pl.epos[(size_t)(q / 2) * (size_t)ne + (size_t)e] |= pos << (16 * (q & 1));
+        }
+        int32_t* h = &pl.hdr[(size_t)b * HDR_INTS];
+        h[H_START] = (int32_t)(start / 16);
+        h[H_NENT] = (int32_t)nent;
+        h[H_NOWN] = (int32_t)nown;
+        h[H_OWN_START] = (int32_t)own_start;
+        h[H_NOPEN] = (int32_t)nopen;
+        h[H_ULEN] = (int32_t)ulen;
+        h[H_SLEN] = (int32_t)slen;
+        h[H_NREC] = (int32_t)((nrc << 16) | nro);
+        pl.max_entries = std::max<int>(pl.max_entries, (int)nent);
+        pl.max_sulen = std::max<int>(pl.max_sulen, (int)sulen);
+        pl.max_slen = std::max<int>(pl.max_slen, (int)slen);
+        pl.max_packet = std::max<int>(pl.max_packet, L.bytes);
         pl.nent_total += nent;
-        pl.nclosed_total += nclosed;
+        pl.nopen_entries += nopen;
     }
-    pl.npartial = pbase;
-    // open nodes ascending; their partial indices in ascending block order
-    pl.open_gid.clear();
-    pl.open_ptr.assign(1, 0);
-    std::vector<int32_t> first((size_t)nn, -1);
+    if ((int64_t)pl.packet.size() / 16 > INT32_MAX) return "packet array too large";
+    return "";
+}
+
+std::string check_block_plan(const BlockPlan& pl, const std::vector<int32_t>& conn, int vec) {
+    using namespace semplan;
+    const int P = pl.P;
+    const int64_t ne = pl.ne, nn = pl.nn;
+    const int UPH = (P + 1) / 2;
+    auto fail = [](int64_t b, const std::string& what) { return "block " + std::to_string(b) + ": " + what; };
+    std::vector<double> u((size_t)nn), out((size_t)nn, std::nan("")), ref((size_t)nn, 0.0);
+    for (int64_t g = 0; g < nn; ++g) u[(size_t)g] = (double)((g * 37) % 1001);
+    for (int64_t s = 0; s < ne * P; ++s) {
+        const int64_t e = s / P;
+        ref[(size_t)conn[(size_t)s]] += u[(size_t)conn[(size_t)s]] + (double)((e % 7) * (s % P + 1));
+    }
+    std::vector<double> part((size_t)std::max<int64_t>(pl.npartial, 1), std::nan(""));
+    std::vector<double> su, sr;
+    for (int64_t b = 0; b < pl.nblocks; ++b) {
+        const int32_t* h = &pl.hdr[(size_t)b * HDR_INTS];
+        const int64_t e0 = b * pl.eb;
+        const int neb = (int)std::min<int64_t>(pl.eb, ne - e0);
+        const int nslot = neb * P;
+        const int nent = h[H_NENT], nown = h[H_NOWN], own_start = h[H_OWN_START], nopen = h[H_NOPEN];
+        const int ulen = h[H_ULEN], slen = h[H_SLEN];
+        const int nrc = h[H_NREC] >> 16, nro = h[H_NREC] & 0xFFFF;
+        const int off = pl.dense ? own_start % vec : 0;
+        const int sulen = ulen + nent - nown;
+        if (sulen > pl.max_sulen || slen > pl.max_slen || nent > pl.max_entries) return fail(b, "size above maximum");
+        if (pl.dense && (ulen % vec != 0 || (own_start - off) % vec != 0)) return fail(b, "owned range misaligned");
+        const Offsets L = offsets(nslot, nent, nown, nopen, nrc + nro);
+        const int64_t start = (int64_t)h[H_START] * 16;
+        if (L.bytes > pl.max_packet || start + L.bytes > (int64_t)pl.packet.size()) return fail(b, "packet bounds");
+        const uint8_t* pk = pl.packet.data() + start;
+        const uint16_t* lsl = reinterpret_cast<const uint16_t*>(pk + L.lsl);
+        const uint16_t* lrow = reinterpret_cast<const uint16_t*>(pk + L.lrow);
+        const uint16_t* aux = reinterpret_cast<const uint16_t*>(pk + L.aux);
+        const int32_t* egid = reinterpret_cast<const int32_t*>(pk + L.egid);
+        const int32_t* obase = reinterpret_cast<const int32_t*>(pk + L.obase);
+        const uint16_t* oent = reinterpret_cast<const uint16_t*>(pk + L.oent);
+        const uint8_t* ocnt = pk + L.ocnt;
+        const uint8_t* orank = pk + L.orank;
+        const int32_t* recs = reinterpret_cast<const int32_t*>(pk + L.recs);
+        auto gid = [&](int l) -> int64_t { return l < nown ? (int64_t)own_start + l : (int64_t)egid[l - nown]; };
+        // node values: owned range as aligned vectors, then the other entries
+        su.assign((size_t)sulen, std::nan(""));
+        for (int t = 0; t < ulen; ++t) {
+            const int64_t g = (int64_t)own_start - off + t;
+            if (g >= 0 && g < nn) su[(size_t)t] = u[(size_t)g];
+        }
+        for (int l = nown; l < nent; ++l) {
+            const int64_t g = gid(l);
+            if (g < 0 || g >= nn) return fail(b, "node id out of range");
+            su[(size_t)entry_pos(l, nown, off, ulen)] = u[(size_t)g];
+        }
+        // element residuals through epos
+        sr.assign((size_t)nslot, 0.0);
+        for (int el = 0; el < neb; ++el)
+            for (int q = 0; q < P; ++q) {
+                const int64_t e = e0 + el;
+                const uint32_t w = pl.epos[(size_t)(q / 2) * (size_t)ne + (size_t)e];
+                const int pos = (int)((w >> (16 * (q & 1))) & 0xFFFF);
+                if (pos >= sulen) return fail(b, "epos beyond node values");
+                const int64_t g = conn[(size_t)(e * P + q)];
+                if (su[(size_t)pos] != u[(size_t)g]) return fail(b, "slot reads another node's value");
+                sr[(size_t)(el * P + q)] = su[(size_t)pos] + (double)((e % 7) * (q + 1));
+            }
+        (void)UPH;
+        // assembly
+        if (lrow[0] != 0 || lrow[nent] != nslot) return fail(b, "local CSR does not cover the slots");
+        int seen_open = 0;
+        for (int l = 0; l < nent; ++l) {
+            if (lrow[l + 1] < lrow[l]) return fail(b, "local CSR not monotone");
+            double acc = 0.0;
+            for (int t = lrow[l]; t < lrow[l + 1]; ++t) {
+                if (lsl[t] >= nslot) return fail(b, "slot index out of range");
+                const int el = lsl[t] / P, q = lsl[t] % P;
+                if (conn[(size_t)((e0 + el) * P + q)] != gid(l)) return fail(b, "slot listed under the wrong entry");
+                acc += sr[lsl[t]];
+            }
+            const int64_t g = gid(l);
+            if (aux[l] == CLOSED) {
+                if (entry_pos(l, nown, off, ulen) >= slen) return fail(b, "closed entry outside staged state");
+                if (!std::isnan(out[(size_t)g])) return fail(b, "node finished twice");
+                out[(size_t)g] = acc;
+            } else {
+                const int o = aux[l];
+                if (o >= nopen || oent[o] != l) return fail(b, "open rank mismatch");
+                if (orank[o] >= ocnt[o]) return fail(b, "open rank beyond its node's block count");
+                const int64_t pi = (int64_t)obase[o] + orank[o];
+                if (pi < 0 || pi >= pl.npartial) return fail(b, "partial index out of range");
+                if (!std::isnan(part[(size_t)pi])) return fail(b, "partial slot written twice");
+                part[(size_t)pi] = acc;
+                seen_open++;
+            }
+        }
+        if (seen_open != nopen) return fail(b, "open count mismatch");
+        for (int k = 0; k < nrc; ++k)
+            if (recs[2 * k] >= nent || aux[recs[2 * k]] != CLOSED) return fail(b, "closed receiver record");
+        for (int k = nrc; k < nrc + nro; ++k)
+            if (recs[2 * k] >= nopen || orank[recs[2 * k]] != 0 ||
+                entry_pos(oent[recs[2 * k]], nown, off, ulen) >= slen)
+                return fail(b, "open receiver record");
+    }
+    for (size_t k = 0; k < pl.open_gid.size(); ++k) {
+        double acc = 0.0;
+        for (int t = 0; t < pl.open_cnt[k]; ++t) {
+            const double v = part[(size_t)(pl.open_base[k] + t)];
+            if (std::isnan(v)) return "open node " + std::to_string(pl.open_gid[k]) + ": missing partial";
+            acc += v;
+        }
+        if (!std::isnan(out[(size_t)pl.open_gid[k]])) return "open node also finished by a block";
+        out[(size_t)pl.open_gid[k]] = acc;
+    }
     for (int64_t g = 0; g < nn; ++g)
-        if (opencount[(size_t)g] > 0) {
-            first[(size_t)g] = pl.open_ptr.back();
-            pl.open_gid.push_back((int32_t)g);
-            pl.open_ptr.push_back(pl.open_ptr.back() + opencount[(size_t)g]);
-        }
-    pl.open_src.assign((size_t)pl.npartial, 0);
-    for (int64_t b = 0; b < nb; ++b) {
-        const int32_t base = pl.hdr[(size_t)b * 4 + 3];
-        for (int64_t k = open_nodes_ptr[(size_t)b]; k < open_nodes_ptr[(size_t)b + 1]; ++k) {
-            int32_t g = open_nodes_flat[(size_t)k];
-            pl.open_src[(size_t)first[(size_t)g]++] = base + (int32_t)(k - open_nodes_ptr[(size_t)b]);
-        }
-    }
+        if (out[(size_t)g] != ref[(size_t)g]) return "node " + std::to_string(g) + ": assembled value differs";
+    return "";
 }
 
 }  // namespace semhost

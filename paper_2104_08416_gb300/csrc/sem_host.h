@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include "sem_plan.h"
+
 namespace semhost {
 
 struct Mesh {
@@ -55,45 +57,40 @@ int64_t snap(const std::vector<double>& node_xy, double x, double y);
 // CFL step (see sem_cfl_dt in sem.h) for per-element speeds vel[ne].
 double cfl_dt(const Mesh& m, const double* vel);
 
-// Block plan for deterministic assembly. Elements (in the new order) are cut
-// into blocks of `eb` consecutive elements. Inside a block each touched
-// global node is an "entry"; element slots point at their entry (lidx) and
-// each entry lists its slots (a local CSR, slots ascending). An entry is
-// closed when every slot of its node lies in this block: the block finishes
-// that node by itself. Closed entries come first (in order of first
-// appearance), then open ones; open entry k of block b writes its partial sum
-// to partial[pbase_b + k], and the open-node pass adds the partials of each
-// open node in ascending block order.
-//
-// Everything a block reads besides node values is one contiguous, 16-byte
-// aligned "packet" (copied to shared memory in one go):
-//   lidx  u16[nslot]      entry of each slot
-//   lsl   u16[nslot]      slots of each entry (local CSR)
-//   lrow  u16[nent + 1]   local CSR offsets
-//   gid   i32[nent]       node id of each entry (4-byte aligned)
-//   coef  f32[neb][8]     bilinear-map coefficients (16-byte aligned; filled
-//                         on the device)
-// with the offsets given by packet_layout().
-struct PacketLayout {
-    int64_t lidx, lsl, lrow, gid, coef, bytes;
-};
-PacketLayout packet_layout(int64_t nslot, int64_t nent, int64_t neb);
-
+// Block plan for deterministic, atomic-free assembly (layout and terms in
+// sem_plan.h). conn_new: [ne][P] new node ids, elements in the new order.
+// rec_gid: new node id of each receiver whose trace the kernels record, -1 for
+// none. vec: node values per 16 bytes (4 FP32, 2 FP64). allow_dense: use the
+// DENSE layout when the numbering permits it.
 struct BlockPlan {
     int eb = 0;
-    int64_t nblocks = 0;
+    int P = 0;
+    bool dense = false;
+    int64_t ne = 0, nn = 0, nblocks = 0;
     int max_entries = 0;                 // largest entry count of a block
-    int64_t max_packet = 0;              // largest packet (bytes)
+    int max_sulen = 0;                   // largest shared-memory node-value length
+    int max_slen = 0;                    // largest staged-state length
+    int max_packet = 0;                  // largest packet (bytes)
     std::vector<uint8_t> packet;         // all packets, block after block
-    std::vector<int32_t> hdr;            // [nblocks][4]: packet start / 16, nent, nclosed, pbase
-    std::vector<int32_t> open_gid;       // [nopen] ascending
-    std::vector<int32_t> open_ptr;       // [nopen+1] into open_src
-    std::vector<int32_t> open_src;       // [npartial] partial index of each contribution
-    int64_t npartial = 0;
-    int64_t nent_total = 0, nclosed_total = 0;
+    std::vector<int32_t> hdr;            // [nblocks][HDR_INTS]
+    std::vector<uint32_t> epos;          // [(P+1)/2][ne] packed shared-memory positions
+    // open nodes (touched by more than one block), ascending id, for the
+    // kernels that finish them outside the block kernel
+    std::vector<int32_t> open_gid, open_base, open_cnt, open_rec;
+    int64_t npartial = 0;                // partial-sum slots (sum of open_cnt)
+    int64_t nent_total = 0, nclosed_total = 0, nopen_entries = 0;
 };
-// conn_new: [ne][P] new node ids, elements in the new order.
-void build_block_plan(const std::vector<int32_t>& conn_new, int64_t ne, int P, int64_t nn, int eb,
-                      BlockPlan& plan);
+// Returns "" on success, else why the plan cannot be built (a limit of the
+// 16-bit / 8-bit fields exceeded).
+std::string build_block_plan(const std::vector<int32_t>& conn_new, int64_t ne, int P, int64_t nn, int eb,
+                             bool allow_dense, int vec, const std::vector<int32_t>& rec_gid, BlockPlan& plan);
+
+// Host emulation of one block-kernel pass plus the open-node pass over the
+// plan, with every index bounds-checked, on integer-valued element residuals
+// r[e][q] = u[conn[e][q]] + (e mod 7) * (q + 1) so that sums are exact. Checks
+// that every slot reads its own node's value through epos and that the
+// assembled result equals the direct per-slot sum. Returns "" when the plan
+// is consistent, else the first violation.
+std::string check_block_plan(const BlockPlan& plan, const std::vector<int32_t>& conn_new, int vec);
 
 }  // namespace semhost

@@ -1,78 +1,92 @@
 // CUDA kernels of the spectral-element time step (sm_103a).
 //
-// One step = two launches:
-//  * sem_block_kernel: one CTA per block of consecutive elements (in the
-//    chosen memory order). It gathers u at the block's nodes (the U_2 gather
-//    of Algorithm 1), forms the reference gradient with the GLL derivative
-//    matrix, applies the per-point metric (Eq. deriv_u with K^(e) = J^-1 and
-//    the quadrature weights of Eq. numerical_integ), contracts with the
-//    transposed derivative (Eq. u_change_r_effic, second-order form) and
-//    assembles the element residuals of the block in shared memory through
-//    the block's local node lists, in a fixed order. Nodes whose elements all
-//    lie in the block are finished on the spot: inverse lumped mass (Eq.
-//    Abar), point source (Algorithm 3) and leapfrog update. Nodes shared with
-//    other blocks write one partial sum per block.
-//  * sem_open_kernel: one thread per shared ("open") node adds its partial
-//    sums in ascending block order and finishes the node.
-// No floating-point atomics are used, so results are bitwise reproducible.
+// One launch of sem_step_kernel per time step; one CTA per block of
+// consecutive elements (in the chosen memory order), one thread per element:
+//  A. the block's packet (local assembly lists) and its owned node range
+//     (values and update state) are staged in shared memory with 16-byte
+//     asynchronous copies; nodes shared with other blocks ("open") are
+//     gathered, or, from the second step of a run on, finished to the current
+//     level from the previous launch's partial sums (deferred assembly, see
+//     StepArgs);
+//  B. each thread gathers its element's (p+1)^2 values (the U_2 gather of
+//     Algorithm 1) into registers, forms the reference gradient with the GLL
+//     derivative matrix, applies the per-point metric G_q = w_q |J_q| / rho_e
+//     J_q^-1 J_q^-T (Eq. deriv_u with K^(e) = J^-1, quadrature of Eq.
+//     numerical_integ) and contracts with the transposed derivative (Eq.
+//     u_change_r_effic, second-order form), all in registers; the residuals go
+//     to shared memory;
+//  C. the block assembles its entries through the local CSR lists in a fixed
+//     order. Closed nodes get the inverse lumped mass (Eq. Abar), the point
+//     source (Algorithm 3) and the leapfrog update on the spot; open nodes
+//     leave one partial sum per block.
+// sem_open_finish_kernel completes the open nodes after the last launch of a
+// run. No floating-point atomics are used, so results are bitwise reproducible.
 #include "sem_kernels.cuh"
 
 namespace semdev {
 
 namespace {
 
+using namespace semplan;
+
 constexpr int kThreads = 256;
+constexpr int kMaxStepThreads = 256;
 
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// Finish node g whose assembled stiffness is ku and whose current value is
-// un; st0/st1/st2 are its staged state (s, then u^{n-1} or delta, comp).
-// Returns the new value in FP64 (for a receiver trace); in Kahan mode that is
-// the compensated sum u - c.
+// One node update from level k to k+1: assembled stiffness ku, value un,
+// state xn (u^{k-1} or delta^{k-1/2}) and cn (compensation), s = dt^2/M,
+// source value f. Three-level: u' = (2u - u_prev) + s (f - ku). Kahan:
+// delta' = delta + s (f - ku), u' = u + delta' as a Kahan-compensated sum.
+// Every operation is an explicitly rounded intrinsic, so the step kernel and
+// the open-node kernel produce bitwise the same update.
 template <typename T, int MODE>
-__device__ __forceinline__ double finish_node(const StepArgs<T>& a, int32_t g, T ku, T un, T st0, T st1, T st2) {
-    if (MODE == MODE_APPLY) {
-        a.apply_out[g] = ku;
-        return (double)ku;
-    }
-    T f = T(0);
-    if (g == a.src_gid) f = (T)a.src_f[a.step];
-    const T acc = f - ku;
+struct Update {
+    T u, x, c;
+};
+template <typename T, int MODE>
+__device__ __forceinline__ Update<T, MODE> update_node(T un, T xn, T cn, T sn, T f, T ku) {
+    Update<T, MODE> o;
+    const T acc = sub_rn(f, ku);
     if (MODE == MODE_THREE_LEVEL) {
-        const T un1 = (T(2) * un - st1) + st0 * acc;
-        a.u_out[g] = un1;
-        return (double)un1;
+        o.u = fma_rn(sn, acc, sub_rn(add_rn(un, un), xn));
+        o.x = un;
+        o.c = T(0);
     } else {
-        // increment form: delta^{n+1/2} = delta^{n-1/2} + s (f - K u^n),
-        // u^{n+1} = u^n + delta^{n+1/2} with a Kahan-compensated sum.
-        const T d = st1 + st0 * acc;
-        const T y = sub_rn(d, st2);
-        const T t = un + y;
-        const T c = sub_rn(sub_rn(t, un), y);
-        a.delta[g] = d;
-        a.comp[g] = c;
-        a.u_out[g] = t;
-        return (double)t - (double)c;
+        const T d = fma_rn(sn, acc, xn);
+        const T y = sub_rn(d, cn);
+        const T t = add_rn(un, y);
+        o.c = sub_rn(sub_rn(t, un), y);
+        o.x = d;
+        o.u = t;
     }
+    return o;
 }
 
-// Same, loading the node state from global memory.
+// Sum of the cnt >= 2 partial sums of an open node, in ascending block
+// order (the loads of the first four are issued together). Shared by every
+// kernel that finishes open nodes, so they all round the same way.
+template <typename T>
+__device__ __forceinline__ T sum_partials(const T* __restrict__ p, int32_t pb, int cnt) {
+    T v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v[t] = (t < cnt) ? p[pb + t] : T(0);
+    T s = add_rn(v[0], v[1]);
+    if (cnt > 2) s = add_rn(s, v[2]);
+    if (cnt > 3) s = add_rn(s, v[3]);
+    for (int t = 4; t < cnt; ++t) s = add_rn(s, p[pb + t]);
+    return s;
+}
+
+// Value recorded in a trace (FP64): the compensated sum u - c in Kahan mode.
 template <typename T, int MODE>
-__device__ __forceinline__ double finish_node_global(const StepArgs<T>& a, int32_t g, T ku, T un) {
-    if (MODE == MODE_APPLY) return finish_node<T, MODE>(a, g, ku, un, T(0), T(0), T(0));
-    if (MODE == MODE_THREE_LEVEL) return finish_node<T, MODE>(a, g, ku, un, a.s[g], a.u_prev[g], T(0));
-    return finish_node<T, MODE>(a, g, ku, un, a.s[g], a.delta[g], a.comp[g]);
-}
-
-// Keeps a value in a register: the compiler cannot re-derive it from memory.
-__device__ __forceinline__ float pin(float v) {
-    asm volatile("" : "+f"(v));
-    return v;
-}
-__device__ __forceinline__ double pin(double v) {
-    asm volatile("" : "+d"(v));
-    return v;
+__device__ __forceinline__ double trace_value(T u, T c) {
+    return MODE == MODE_KAHAN ? (double)u - (double)c : (double)u;
 }
 
 // ---------------------------------------------------------- async copies
@@ -86,201 +100,287 @@ __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Metric G = w |J| / rho * J^-1 J^-T at a point (xi, eta) of weight wq,
-// from the element's bilinear-map coefficients (b, c, d, 1/rho):
-// X(xi, eta) = a0 + b xi + c eta + d xi eta, so J = [b + d eta | c + d xi], and
-// w |J| / rho * J^-1 J^-T = w / (rho |J|) * adj(J) adj(J)^T.
+// Read-only streamed loads (each element datum is read once per step).
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+
+// Copies node values [abase, abase + len) of src (len a multiple of VEC,
+// abase a multiple of VEC) to dst with 16-byte copies, element by element
+// where the vector would cross the end nn or the arrays are not aligned.
 template <typename T>
-__device__ __forceinline__ void metric_bilinear(const float4 c0, const float4 c1, float xi, float eta, float wq,
-                                                T& gxx, T& gxy, T& gyy) {
-    const float j00 = c0.x + c1.x * eta, j10 = c0.y + c1.y * eta;
-    const float j01 = c0.z + c1.x * xi, j11 = c0.w + c1.y * xi;
-    const float det = j00 * j11 - j01 * j10;
-    const float k = wq * c1.z / det;
-    gxx = (T)(k * (j11 * j11 + j01 * j01));
-    gxy = (T)(-k * (j10 * j11 + j00 * j01));
-    gyy = (T)(k * (j10 * j10 + j00 * j00));
+__device__ __forceinline__ void stage_range(T* dst, const T* src, int64_t abase, int len, int64_t nn, bool vec_ok,
+                                            int tid, int nt) {
+    constexpr int VEC = 16 / sizeof(T);
+    const int nch = len / VEC;
+    for (int ch = tid; ch < nch; ch += nt) {
+        const int64_t g = abase + (int64_t)ch * VEC;
+        if (vec_ok && g + VEC <= nn) {
+            cp_async16(dst + ch * VEC, src + g);
+        } else {
+#pragma unroll
+            for (int t = 0; t < VEC; ++t)
+                if (g + t < nn) cp_async_small<sizeof(T)>(dst + ch * VEC + t, src + g + t);
+        }
+    }
 }
 
-// Elements processed side by side by one CTA: each thread keeps one GLL point
-// (i, j) of one element lane for the whole kernel, so its rows and columns of
-// the derivative matrix live in registers.
-template <int NP>
-struct Lanes {
-    static constexpr int P = NP * NP;
-    static constexpr int EBW = (kThreads / P) > 0 ? (kThreads / P) : 1;
-    static constexpr int THREADS = EBW * P;
-};
-
-template <int NP, typename T, int MODE, bool BIL>
-__global__ void __launch_bounds__(Lanes<NP>::THREADS) sem_block_kernel(const Plan pl, const StepArgs<T> a,
-                                                                       const Basis<T> bs) {
+template <int NP, typename T, int MODE>
+__global__ void __launch_bounds__(kMaxStepThreads) sem_step_kernel(const Plan pl, const StepArgs<T> a,
+                                                                   const Basis<T> bs) {
     constexpr int P = NP * NP;
-    constexpr int EBW = Lanes<NP>::EBW;
-    constexpr int NT = Lanes<NP>::THREADS;
-    constexpr bool STAGE = MODE != MODE_APPLY;
+    constexpr int UPH = (P + 1) / 2;
+    constexpr bool STATE = MODE != MODE_APPLY;
+    constexpr bool KAHAN = MODE == MODE_KAHAN;
+    constexpr bool BIL = sizeof(T) == 4;  // FP32: metric from the bilinear map; FP64: stored metric
+    constexpr int VEC = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint8_t* spk = smem_raw;                                          // packet
-    T* su = reinterpret_cast<T*>(smem_raw + pl.max_packet);           // [max_entries] u at the entries
-    T* st0 = su + pl.max_entries;                                     // staged node state
-    T* st1 = st0 + (STAGE ? pl.max_entries : 0);
-    T* st2 = st1 + (STAGE ? pl.max_entries : 0);
-    T* sue = st2 + (MODE == MODE_KAHAN ? pl.max_entries : 0);         // [eb*P] element values, then residuals
-    T* sf1 = sue + pl.eb * P;                                         // [eb*P] flux, xi component
-    T* sf2 = sf1 + pl.eb * P;                                         // [eb*P] flux, eta component
+    uint8_t* spk = smem_raw;
+    T* su = reinterpret_cast<T*>(smem_raw + pl.max_packet);   // node values of the entries
+    T* ss = su + pl.sulen_pad;                                 // staged s
+    T* sx = ss + (STATE ? pl.slen_pad : 0);                    // staged u^{k-1} or delta
+    T* sc = sx + (STATE ? pl.slen_pad : 0);                    // staged compensation
+    T* sr = sc + (KAHAN ? pl.slen_pad : 0);                    // element residuals [eb][P]
 
     const int b = blockIdx.x;
-    const int4 hd = pl.hdr[b];
-    const int nent = hd.y, nclosed = hd.z, pbase = hd.w;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int4 h0 = pl.hdr[2 * b], h1 = pl.hdr[2 * b + 1];
+    const int nent = h0.y, nown = h0.z, own_start = h0.w;
+    const int nopen = h1.x, ulen = h1.y;
+    const int nrc = (int)((unsigned)h1.w >> 16), nro = h1.w & 0xFFFF;
     const int64_t e0 = (int64_t)b * pl.eb;
     const int neb = (int)min((int64_t)pl.eb, pl.ne - e0);
     const int nslot = neb * P;
-    const PacketOffsets L = packet_offsets(nslot, nent, neb);
-    const int tid = threadIdx.x;
-    const int q = tid % P, lane_el = tid / P;
-    const int j = q / NP, i = q - j * NP;
+    const Offsets L = offsets(nslot, nent, nown, nopen, nrc + nro);
+    const int off = pl.dense ? own_start % VEC : 0;
+    const int64_t abase = (int64_t)own_start - off;
+    const bool has_el = tid < neb;
+    const int64_t e = e0 + tid;
 
-    // 0. stage the block's packet (indices, local lists, geometry) with
-    //    16-byte asynchronous copies
-    {
-        const uint8_t* gpk = pl.packet + (int64_t)hd.x * 16;
-        for (int off = tid * 16; off < L.bytes; off += NT * 16) cp_async16(spk + off, gpk + off);
-        cp_async_commit();
-    }
-    // GLL tables to shared memory (kernel parameters indexed per thread would
-    // serialise in the constant cache), then this thread's derivative rows and
-    // columns into registers, pinned there
-    __shared__ T sD[P];
-    __shared__ float sxw[2 * NP];
-    for (int t = tid; t < P; t += NT) sD[t] = bs.D[t];
-    for (int t = tid; t < NP; t += NT) {
-        sxw[t] = (float)bs.x[t];
-        sxw[NP + t] = (float)bs.w[t];
-    }
-    __syncthreads();
-    T Di[NP], Dj[NP], DTi[NP], DTj[NP];
+    // element-side data straight into registers (coalesced across threads)
+    uint32_t pw[UPH];
+    float4 cf0 = make_float4(0.f, 0.f, 0.f, 0.f), cf1 = cf0;
+    if (has_el) {
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        Di[k] = pin(sD[i * NP + k]);
-        Dj[k] = pin(sD[j * NP + k]);
-        DTi[k] = pin(sD[k * NP + i]);
-        DTj[k] = pin(sD[k * NP + j]);
+        for (int h = 0; h < UPH; ++h) pw[h] = ld_stream(pl.epos + (int64_t)h * pl.ne + e);
+        if constexpr (BIL) {
+            cf0 = ld_stream(pl.coef + e);
+            cf1 = ld_stream(pl.coef + pl.ne + e);
+        }
     }
-    const float xi = pin(sxw[i]), eta = pin(sxw[j]);
-    const float wq = pin(sxw[NP + i] * sxw[NP + j]);
-    cp_async_wait<0>();
-    __syncthreads();
-    const uint16_t* lidx = reinterpret_cast<const uint16_t*>(spk + L.lidx);
+
+    // A1. packet and owned node range
+    {
+        const uint8_t* gpk = pl.packet + (int64_t)h0.x * 16;
+        for (int o = tid * 16; o < L.bytes; o += nt * 16) cp_async16(spk + o, gpk + o);
+        if (pl.dense) {
+            const bool vok = a.vec_ok != 0;
+            stage_range(su, a.u_k, abase, ulen, pl.nn, vok, tid, nt);
+            if (STATE) {
+                stage_range(ss, a.s, abase, ulen, pl.nn, vok, tid, nt);
+                stage_range(sx, a.x_k, abase, ulen, pl.nn, vok, tid, nt);
+                if (KAHAN) stage_range(sc, a.c_k, abase, ulen, pl.nn, vok, tid, nt);
+            }
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+    }
     const uint16_t* lsl = reinterpret_cast<const uint16_t*>(spk + L.lsl);
     const uint16_t* lrow = reinterpret_cast<const uint16_t*>(spk + L.lrow);
-    const int32_t* gid = reinterpret_cast<const int32_t*>(spk + L.gid);
-    const float4* coef = reinterpret_cast<const float4*>(spk + L.coef);
+    const uint16_t* aux = reinterpret_cast<const uint16_t*>(spk + L.aux);
+    const int32_t* egid = reinterpret_cast<const int32_t*>(spk + L.egid);
+    const int32_t* obase = reinterpret_cast<const int32_t*>(spk + L.obase);
+    const uint16_t* oent = reinterpret_cast<const uint16_t*>(spk + L.oent);
+    const uint8_t* ocnt = spk + L.ocnt;
+    const uint8_t* orank = spk + L.orank;
+    const int32_t* recs = reinterpret_cast<const int32_t*>(spk + L.recs);
 
-    // 1. gather u at the entries (group 1), then the closed nodes' state (group 2)
-    for (int l = tid; l < nent; l += NT) cp_async_small<sizeof(T)>(su + l, a.u_cur + gid[l]);
-    cp_async_commit();
-    if (STAGE) {
-        for (int l = tid; l < nclosed; l += NT) {
-            const int32_t g = gid[l];
-            cp_async_small<sizeof(T)>(st0 + l, a.s + g);
-            if (MODE == MODE_THREE_LEVEL) {
-                cp_async_small<sizeof(T)>(st1 + l, a.u_prev + g);
-            } else {
-                cp_async_small<sizeof(T)>(st1 + l, a.delta + g);
-                cp_async_small<sizeof(T)>(st2 + l, a.comp + g);
+    // A2. closed entries of GATHER plans; open entries
+    if (!pl.dense) {
+        for (int l = tid; l < nent; l += nt)
+            if (aux[l] == CLOSED) {
+                const int32_t g = egid[l];
+                cp_async_small<sizeof(T)>(su + l, a.u_k + g);
+                if (STATE) {
+                    cp_async_small<sizeof(T)>(ss + l, a.s + g);
+                    cp_async_small<sizeof(T)>(sx + l, a.x_k + g);
+                    if (KAHAN) cp_async_small<sizeof(T)>(sc + l, a.c_k + g);
+                }
+            }
+    }
+    const bool pending = STATE && a.pending;
+    for (int o = tid; o < nopen; o += nt) {
+        const int l = oent[o];
+        const int32_t g = l < nown ? own_start + l : egid[l - nown];
+        const int pos = entry_pos(l, nown, off, ulen);
+        if (!pending) {
+            cp_async_small<sizeof(T)>(su + pos, a.u_k + g);
+        } else {
+            const int32_t pb = obase[o];
+            const int cnt = ocnt[o];
+            const T ku = sum_partials(a.part_rd, pb, cnt);
+            const T f = (g == a.src_gid) ? (T)a.src_f[a.step - 1] : T(0);
+            const Update<T, MODE> up = update_node<T, MODE>(a.u_km1[g], a.x_km1[g], KAHAN ? a.c_km1[g] : T(0), a.s[g],
+                                                             f, ku);
+            su[pos] = up.u;
+            if (orank[o] == 0) {
+                a.u_kw[g] = up.u;
+                if (KAHAN) {
+                    a.x_kw[g] = up.x;
+                    a.c_kw[g] = up.c;
+                    sc[pos] = up.c;  // for a receiver record (owned entries lie in the staged range)
+                }
             }
         }
     }
     cp_async_commit();
-    cp_async_wait<1>();
+    cp_async_wait_all();
     __syncthreads();
-    // 2. element-local copies U_mu(q,e)
-    for (int el = lane_el; el < neb; el += EBW) sue[el * P + q] = su[lidx[el * P + q]];
-    __syncthreads();
-    // 3. reference gradient, metric, fluxes
-    for (int el = lane_el; el < neb; el += EBW) {
-        const T* ue = sue + el * P;
-        T dxi = T(0), deta = T(0);
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            dxi += Di[k] * ue[j * NP + k];
-            deta += Dj[k] * ue[k * NP + i];
+    if (pending && nro > 0) {
+        for (int k = tid; k < nro; k += nt) {
+            const int o = recs[2 * (nrc + k)], r = recs[2 * (nrc + k) + 1];
+            const int pos = entry_pos(oent[o], nown, off, ulen);
+            a.trace[(int64_t)r * a.trace_cap + a.step - 1] = trace_value<T, MODE>(su[pos], KAHAN ? sc[pos] : T(0));
         }
-        T gxx, gxy, gyy;
+    }
+
+    // B. element contraction in registers
+    if (has_el) {
+        T u[P], r[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            u[q] = su[(pw[q / 2] >> (16 * (q & 1))) & 0xFFFFu];
+            r[q] = T(0);
+        }
+        // per-column (xi = x_i) parts of the Jacobian: J = [j00 j01; j10 j11],
+        // j00, j10 vary with eta only, j01, j11 with xi only
+        float j01[NP], j11[NP], cB[NP];
         if constexpr (BIL) {
-            metric_bilinear<T>(coef[el * 2], coef[el * 2 + 1], xi, eta, wq, gxx, gxy, gyy);
-        } else {
-            const int64_t sl = (e0 + el) * P + q;
-            gxx = a.G[sl];
-            gxy = a.G[sl + a.gstride];
-            gyy = a.G[sl + 2 * a.gstride];
-        }
-        sf1[el * P + q] = gxx * dxi + gxy * deta;
-        sf2[el * P + q] = gxy * dxi + gyy * deta;
-    }
-    __syncthreads();
-    // 4. transposed derivative: element residuals (stored over sue)
-    for (int el = lane_el; el < neb; el += EBW) {
-        const T* f1 = sf1 + el * P;
-        const T* f2 = sf2 + el * P;
-        T r = T(0);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) r += DTi[k] * f1[j * NP + k] + DTj[k] * f2[k * NP + i];
-        sue[el * P + q] = r;
+            for (int i = 0; i < NP; ++i) {
+                const float xi = (float)bs.x[i];
+                j01[i] = cf0.z + cf1.x * xi;
+                j11[i] = cf0.w + cf1.y * xi;
+                cB[i] = j11[i] * j11[i] + j01[i] * j01[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            float j00 = 0.f, j10 = 0.f, cA = 0.f;
+            if constexpr (BIL) {
+                const float eta = (float)bs.x[j];
+                j00 = cf0.x + cf1.x * eta;
+                j10 = cf0.y + cf1.y * eta;
+                cA = j10 * j10 + j00 * j00;
+            }
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const int q = j * NP + i;
+                T dxi = T(0), deta = T(0);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    dxi += bs.D[i * NP + k] * u[j * NP + k];
+                    deta += bs.D[j * NP + k] * u[k * NP + i];
+                }
+                T gxx, gxy, gyy;
+                if constexpr (BIL) {
+                    // w |J| / rho J^-1 J^-T = w / (rho |J|) adj(J) adj(J)^T
+                    const float det = j00 * j11[i] - j01[i] * j10;
+                    const float kk = __fdividef((float)bs.W[q] * cf1.z, det);
+                    gxx = kk * cB[i];
+                    gyy = kk * cA;
+                    gxy = -kk * (j10 * j11[i] + j00 * j01[i]);
+                } else {
+                    gxx = ld_stream(pl.G + (int64_t)q * pl.ne + e);
+                    gxy = ld_stream(pl.G + (int64_t)(P + q) * pl.ne + e);
+                    gyy = ld_stream(pl.G + (int64_t)(2 * P + q) * pl.ne + e);
+                }
+                const T F1 = gxx * dxi + gxy * deta;
+                const T F2 = gxy * dxi + gyy * deta;
+#pragma unroll
+                for (int m = 0; m < NP; ++m) {
+                    r[j * NP + m] += bs.D[i * NP + m] * F1;
+                    r[m * NP + i] += bs.D[j * NP + m] * F2;
+                }
+            }
+        }
+        T* re = sr + tid * P;
+#pragma unroll
+        for (int q = 0; q < P; ++q) re[q] = r[q];
     }
-    cp_async_wait<0>();
     __syncthreads();
-    // 5. assembly in fixed (slot-ascending) order; closed nodes are finished
-    //    here, open ones leave a partial sum
-    for (int l = tid; l < nent; l += NT) {
+
+    // C. assembly in fixed (slot-ascending) order
+    for (int l = tid; l < nent; l += nt) {
         const int r0 = lrow[l], r1 = lrow[l + 1];
         T acc = T(0);
-        for (int t = r0; t < r1; ++t) acc += sue[lsl[t]];
-        if (l >= nclosed) {
-            a.partial[pbase + (l - nclosed)] = acc;
-        } else if (STAGE) {
-            finish_node<T, MODE>(a, gid[l], acc, su[l], st0[l], st1[l], MODE == MODE_KAHAN ? st2[l] : T(0));
+        for (int t = r0; t < r1; ++t) acc += sr[lsl[t]];
+        const uint16_t ax = aux[l];
+        if (ax == CLOSED) {
+            const int32_t g = l < nown ? own_start + l : egid[l - nown];
+            if (MODE == MODE_APPLY) {
+                a.apply_out[g] = acc;
+            } else {
+                const int pos = entry_pos(l, nown, off, ulen);
+                const T f = (g == a.src_gid) ? (T)a.src_f[a.step] : T(0);
+                const Update<T, MODE> up = update_node<T, MODE>(su[pos], sx[pos], KAHAN ? sc[pos] : T(0), ss[pos], f, acc);
+                a.u_kp1[g] = up.u;
+                if (KAHAN) {
+                    a.x_kp1[g] = up.x;
+                    a.c_kp1[g] = up.c;
+                }
+                if (nrc > 0) {
+                    su[pos] = up.u;
+                    if (KAHAN) sc[pos] = up.c;
+                }
+            }
         } else {
-            finish_node<T, MODE>(a, gid[l], acc, su[l], T(0), T(0), T(0));
+            a.part_wr[obase[ax] + orank[ax]] = acc;
+        }
+    }
+    if (STATE && nrc > 0) {
+        __syncthreads();
+        for (int k = tid; k < nrc; k += nt) {
+            const int l = recs[2 * k], r = recs[2 * k + 1];
+            const int pos = entry_pos(l, nown, off, ulen);
+            a.trace[(int64_t)r * a.trace_cap + a.step] = trace_value<T, MODE>(su[pos], KAHAN ? sc[pos] : T(0));
         }
     }
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) sem_open_kernel(const Plan pl, const StepArgs<T> a) {
-    // receivers at closed nodes: their value is final once the block kernel ended
-    if (MODE != MODE_APPLY && blockIdx.x == 0 && a.nrec > 0) {
-        for (int r = threadIdx.x; r < a.nrec; r += kThreads)
-            if (a.rec_closed[r]) {
-                const int32_t g = a.rec_gid[r];
-                double v = (double)a.u_out[g];
-                if (MODE == MODE_KAHAN) v -= (double)a.comp[g];
-                a.trace[(int64_t)r * a.trace_cap + a.step] = v;
-            }
-    }
-    for (int k = blockIdx.x * kThreads + threadIdx.x; k < pl.nopen; k += gridDim.x * kThreads) {
-        const int p0 = pl.open_ptr[k], p1 = pl.open_ptr[k + 1];
-        T acc = T(0);
-        for (int t = p0; t < p1; ++t) acc += a.partial[pl.open_src[t]];
+__global__ void __launch_bounds__(kThreads) sem_open_finish_kernel(const Plan pl, const StepArgs<T> a) {
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < pl.nopen_nodes; k += gridDim.x * kThreads) {
+        const int32_t pb = pl.open_base[k];
+        const int cnt = pl.open_cnt[k];
+        const T acc = sum_partials(a.part_rd, pb, cnt);
         const int32_t g = pl.open_gid[k];
-        const T un = (MODE == MODE_APPLY) ? T(0) : a.u_cur[g];
-        const double v = finish_node_global<T, MODE>(a, g, acc, un);
-        if (MODE != MODE_APPLY && pl.open_rec != nullptr) {
-            const int r = pl.open_rec[k];
-            if (r >= 0) a.trace[(int64_t)r * a.trace_cap + a.step] = v;
+        if (MODE == MODE_APPLY) {
+            a.apply_out[g] = acc;
+            continue;
         }
+        const T f = (g == a.src_gid) ? (T)a.src_f[a.step] : T(0);
+        const Update<T, MODE> up =
+            update_node<T, MODE>(a.u_k[g], a.x_k[g], MODE == MODE_KAHAN ? a.c_k[g] : T(0), a.s[g], f, acc);
+        a.u_kp1[g] = up.u;
+        if (MODE == MODE_KAHAN) {
+            a.x_kp1[g] = up.x;
+            a.c_kp1[g] = up.c;
+        }
+        const int r = pl.open_rec[k];
+        if (r >= 0) a.trace[(int64_t)r * a.trace_cap + a.step] = trace_value<T, MODE>(up.u, up.c);
     }
 }
 
 // ------------------------------------------------------------ precompute
-__global__ void geometry_kernel(int np, const double* __restrict__ coords, const int32_t* __restrict__ quads,
-                                const double* __restrict__ rho, const double* __restrict__ vel, const Plan pl,
-                                const Basis<double> bs, uint8_t* packet, double* G64, double* mloc) {
+__global__ void geometry_kernel(int np, int64_t ne, const double* __restrict__ coords,
+                                const int32_t* __restrict__ quads, const double* __restrict__ rho,
+                                const double* __restrict__ vel, const Basis<double> bs, float4* coef, double* G64,
+                                double* mloc) {
     const int P = np * np;
-    const int64_t ne = pl.ne;
     const int64_t total = ne * P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -293,7 +393,7 @@ __global__ void geometry_kernel(int np, const double* __restrict__ coords, const
             X[c] = coords[(int64_t)v * 2];
             Y[c] = coords[(int64_t)v * 2 + 1];
         }
-        // bilinear coefficients: X = a + b xi + c eta + d xi eta
+        // bilinear map X = a + b xi + c eta + d xi eta
         const double bx = 0.25 * ((X[1] - X[0]) + (X[2] - X[3]));
         const double by = 0.25 * ((Y[1] - Y[0]) + (Y[2] - Y[3]));
         const double cx = 0.25 * ((X[3] - X[0]) + (X[2] - X[1]));
@@ -301,15 +401,9 @@ __global__ void geometry_kernel(int np, const double* __restrict__ coords, const
         const double dx = 0.25 * ((X[0] - X[1]) + (X[2] - X[3]));
         const double dy = 0.25 * ((Y[0] - Y[1]) + (Y[2] - Y[3]));
         const double rinv = 1.0 / rho[e];
-        if (q == 0 && packet != nullptr) {
-            const int b = (int)(e / pl.eb);
-            const int el = (int)(e - (int64_t)b * pl.eb);
-            const int neb = (int)min((int64_t)pl.eb, ne - (int64_t)b * pl.eb);
-            const int4 hd = pl.hdr[b];
-            const PacketOffsets L = packet_offsets(neb * P, hd.y, neb);
-            float4* cf = reinterpret_cast<float4*>(packet + (int64_t)hd.x * 16 + L.coef) + el * 2;
-            cf[0] = make_float4((float)bx, (float)by, (float)cx, (float)cy);
-            cf[1] = make_float4((float)dx, (float)dy, (float)rinv, 0.0f);
+        if (q == 0 && coef != nullptr) {
+            coef[e] = make_float4((float)bx, (float)by, (float)cx, (float)cy);
+            coef[ne + e] = make_float4((float)dx, (float)dy, (float)rinv, 0.0f);
         }
         const double xi = bs.x[i], eta = bs.x[j];
         const double j00 = bx + dx * eta, j10 = by + dy * eta;
@@ -318,9 +412,9 @@ __global__ void geometry_kernel(int np, const double* __restrict__ coords, const
         const double wq = bs.w[i] * bs.w[j];
         const double k = wq * rinv / det;
         if (G64 != nullptr) {
-            G64[t] = k * (j11 * j11 + j01 * j01);
-            G64[t + total] = -k * (j10 * j11 + j00 * j01);
-            G64[t + 2 * total] = k * (j10 * j10 + j00 * j00);
+            G64[(int64_t)q * ne + e] = k * (j11 * j11 + j01 * j01);
+            G64[(int64_t)(P + q) * ne + e] = -k * (j10 * j11 + j00 * j01);
+            G64[(int64_t)(2 * P + q) * ne + e] = k * (j10 * j10 + j00 * j00);
         }
         if (mloc != nullptr) mloc[t] = wq * det * rinv / (vel[e] * vel[e]);
     }
@@ -329,27 +423,33 @@ __global__ void geometry_kernel(int np, const double* __restrict__ coords, const
 __global__ void __launch_bounds__(kThreads) mass_block_kernel(const Plan pl, int P, const double* __restrict__ mloc,
                                                              double* partial, double* M) {
     const int b = blockIdx.x;
-    const int4 hd = pl.hdr[b];
+    const int4 h0 = pl.hdr[2 * b], h1 = pl.hdr[2 * b + 1];
+    const int nent = h0.y, nown = h0.z, own_start = h0.w, nopen = h1.x;
+    const int nrec = (int)((unsigned)h1.w >> 16) + (h1.w & 0xFFFF);
     const int64_t e0 = (int64_t)b * pl.eb;
     const int neb = (int)min((int64_t)pl.eb, pl.ne - e0);
-    const PacketOffsets L = packet_offsets(neb * P, hd.y, neb);
-    const uint8_t* pk = pl.packet + (int64_t)hd.x * 16;
+    const Offsets L = offsets(neb * P, nent, nown, nopen, nrec);
+    const uint8_t* pk = pl.packet + (int64_t)h0.x * 16;
     const uint16_t* lsl = reinterpret_cast<const uint16_t*>(pk + L.lsl);
     const uint16_t* lrow = reinterpret_cast<const uint16_t*>(pk + L.lrow);
-    const int32_t* gid = reinterpret_cast<const int32_t*>(pk + L.gid);
+    const uint16_t* aux = reinterpret_cast<const uint16_t*>(pk + L.aux);
+    const int32_t* egid = reinterpret_cast<const int32_t*>(pk + L.egid);
+    const int32_t* obase = reinterpret_cast<const int32_t*>(pk + L.obase);
+    const uint8_t* orank = pk + L.orank;
     const int64_t s0 = e0 * P;
-    for (int l = threadIdx.x; l < hd.y; l += kThreads) {
+    for (int l = threadIdx.x; l < nent; l += kThreads) {
         double acc = 0.0;
         for (int t = lrow[l]; t < lrow[l + 1]; ++t) acc += mloc[s0 + lsl[t]];
-        if (l >= hd.z) partial[hd.w + (l - hd.z)] = acc;
-        else M[gid[l]] = acc;
+        const uint16_t ax = aux[l];
+        if (ax == CLOSED) M[l < nown ? own_start + l : egid[l - nown]] = acc;
+        else partial[obase[ax] + orank[ax]] = acc;
     }
 }
 
 __global__ void mass_open_kernel(const Plan pl, const double* __restrict__ partial, double* M) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pl.nopen; k += gridDim.x * blockDim.x) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pl.nopen_nodes; k += gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int t = pl.open_ptr[k]; t < pl.open_ptr[k + 1]; ++t) acc += partial[pl.open_src[t]];
+        for (int t = 0; t < pl.open_cnt[k]; ++t) acc += partial[pl.open_base[k] + t];
         M[pl.open_gid[k]] = acc;
     }
 }
@@ -369,103 +469,89 @@ int grid_for(int64_t n, int threads) {
     return (int)g;
 }
 
-template <int NP, typename T, int MODE, bool BIL>
-cudaError_t launch_block_t(const Plan& pl, const void* args, const void* basis, int smem, cudaStream_t st) {
-    auto kern = sem_block_kernel<NP, T, MODE, BIL>;
+template <int NP, typename T, int MODE>
+cudaError_t launch_step_t(const Plan& pl, const void* args, const void* basis, int threads, int smem, cudaStream_t st) {
+    auto kern = sem_step_kernel<NP, T, MODE>;
     static int configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    kern<<<pl.nblocks, Lanes<NP>::THREADS, smem, st>>>(pl, *static_cast<const StepArgs<T>*>(args),
-                                             *static_cast<const Basis<T>*>(basis));
+    kern<<<pl.nblocks, threads, smem, st>>>(pl, *static_cast<const StepArgs<T>*>(args),
+                                            *static_cast<const Basis<T>*>(basis));
     return cudaGetLastError();
 }
 
-template <typename T, int MODE, bool BIL>
-cudaError_t dispatch_np(int np, const Plan& pl, const void* args, const void* basis, int smem, cudaStream_t st) {
+template <typename T, int MODE>
+cudaError_t dispatch_np(int np, const Plan& pl, const void* args, const void* basis, int threads, int smem,
+                        cudaStream_t st) {
     switch (np) {
-        case 2: return launch_block_t<2, T, MODE, BIL>(pl, args, basis, smem, st);
-        case 3: return launch_block_t<3, T, MODE, BIL>(pl, args, basis, smem, st);
-        case 4: return launch_block_t<4, T, MODE, BIL>(pl, args, basis, smem, st);
-        case 5: return launch_block_t<5, T, MODE, BIL>(pl, args, basis, smem, st);
-        case 6: return launch_block_t<6, T, MODE, BIL>(pl, args, basis, smem, st);
-        case 7: return launch_block_t<7, T, MODE, BIL>(pl, args, basis, smem, st);
-        case 8: return launch_block_t<8, T, MODE, BIL>(pl, args, basis, smem, st);
-        case 9: return launch_block_t<9, T, MODE, BIL>(pl, args, basis, smem, st);
+        case 2: return launch_step_t<2, T, MODE>(pl, args, basis, threads, smem, st);
+        case 3: return launch_step_t<3, T, MODE>(pl, args, basis, threads, smem, st);
+        case 4: return launch_step_t<4, T, MODE>(pl, args, basis, threads, smem, st);
+        case 5: return launch_step_t<5, T, MODE>(pl, args, basis, threads, smem, st);
+        case 6: return launch_step_t<6, T, MODE>(pl, args, basis, threads, smem, st);
+        case 7: return launch_step_t<7, T, MODE>(pl, args, basis, threads, smem, st);
+        case 8: return launch_step_t<8, T, MODE>(pl, args, basis, threads, smem, st);
+        case 9: return launch_step_t<9, T, MODE>(pl, args, basis, threads, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-int lanes_for(int np) {
-    switch (np) {
-        case 2: return Lanes<2>::EBW;
-        case 3: return Lanes<3>::EBW;
-        case 4: return Lanes<4>::EBW;
-        case 5: return Lanes<5>::EBW;
-        case 6: return Lanes<6>::EBW;
-        case 7: return Lanes<7>::EBW;
-        case 8: return Lanes<8>::EBW;
-        case 9: return Lanes<9>::EBW;
-        default: return 1;
-    }
+int step_threads(int eb) {
+    int t = (eb + 31) / 32 * 32;
+    return t < 32 ? 32 : t;
 }
 
-int smem_bytes_for(int P, int eb, int max_entries, int max_packet, bool fp64, int mode) {
+int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, bool fp64, int mode) {
     const int sz = fp64 ? 8 : 4;
     const int staged = mode == MODE_KAHAN ? 3 : (mode == MODE_THREE_LEVEL ? 2 : 0);
-    return max_packet + (max_entries * (1 + staged) + 3 * eb * P) * sz;
+    return max_packet + (sulen_pad + staged * slen_pad + eb * P) * sz;
 }
 
-cudaError_t launch_step(int np, bool fp64, int mode, bool bilinear, const Plan& pl, const void* args,
-                        const void* basis, int smem, cudaStream_t st) {
+cudaError_t launch_step(int np, bool fp64, int mode, const Plan& pl, const void* args, const void* basis,
+                        int threads, int smem, cudaStream_t st) {
+    if (threads < 1 || threads > kMaxStepThreads || threads < pl.eb) return cudaErrorInvalidValue;
     if (fp64) {
-        if (bilinear) return cudaErrorInvalidValue;
         switch (mode) {
-            case MODE_THREE_LEVEL: return dispatch_np<double, MODE_THREE_LEVEL, false>(np, pl, args, basis, smem, st);
-            case MODE_APPLY: return dispatch_np<double, MODE_APPLY, false>(np, pl, args, basis, smem, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    if (bilinear) {
-        switch (mode) {
-            case MODE_THREE_LEVEL: return dispatch_np<float, MODE_THREE_LEVEL, true>(np, pl, args, basis, smem, st);
-            case MODE_KAHAN: return dispatch_np<float, MODE_KAHAN, true>(np, pl, args, basis, smem, st);
-            case MODE_APPLY: return dispatch_np<float, MODE_APPLY, true>(np, pl, args, basis, smem, st);
+            case MODE_THREE_LEVEL: return dispatch_np<double, MODE_THREE_LEVEL>(np, pl, args, basis, threads, smem, st);
+            case MODE_APPLY: return dispatch_np<double, MODE_APPLY>(np, pl, args, basis, threads, smem, st);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (mode) {
-        case MODE_KAHAN: return dispatch_np<float, MODE_KAHAN, false>(np, pl, args, basis, smem, st);
-        case MODE_APPLY: return dispatch_np<float, MODE_APPLY, false>(np, pl, args, basis, smem, st);
+        case MODE_THREE_LEVEL: return dispatch_np<float, MODE_THREE_LEVEL>(np, pl, args, basis, threads, smem, st);
+        case MODE_KAHAN: return dispatch_np<float, MODE_KAHAN>(np, pl, args, basis, threads, smem, st);
+        case MODE_APPLY: return dispatch_np<float, MODE_APPLY>(np, pl, args, basis, threads, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_open(bool fp64, int mode, const Plan& pl, const void* args, cudaStream_t st) {
-    const int grid = grid_for(pl.nopen, kThreads);
+cudaError_t launch_open_finish(bool fp64, int mode, const Plan& pl, const void* args, cudaStream_t st) {
+    if (pl.nopen_nodes == 0) return cudaSuccess;
+    const int grid = grid_for(pl.nopen_nodes, kThreads);
     if (fp64) {
         const auto& a = *static_cast<const StepArgs<double>*>(args);
-        if (mode == MODE_THREE_LEVEL) sem_open_kernel<double, MODE_THREE_LEVEL><<<grid, kThreads, 0, st>>>(pl, a);
-        else if (mode == MODE_APPLY) sem_open_kernel<double, MODE_APPLY><<<grid, kThreads, 0, st>>>(pl, a);
+        if (mode == MODE_THREE_LEVEL) sem_open_finish_kernel<double, MODE_THREE_LEVEL><<<grid, kThreads, 0, st>>>(pl, a);
+        else if (mode == MODE_APPLY) sem_open_finish_kernel<double, MODE_APPLY><<<grid, kThreads, 0, st>>>(pl, a);
         else return cudaErrorInvalidValue;
     } else {
         const auto& a = *static_cast<const StepArgs<float>*>(args);
-        if (mode == MODE_THREE_LEVEL) sem_open_kernel<float, MODE_THREE_LEVEL><<<grid, kThreads, 0, st>>>(pl, a);
-        else if (mode == MODE_KAHAN) sem_open_kernel<float, MODE_KAHAN><<<grid, kThreads, 0, st>>>(pl, a);
-        else sem_open_kernel<float, MODE_APPLY><<<grid, kThreads, 0, st>>>(pl, a);
+        if (mode == MODE_THREE_LEVEL) sem_open_finish_kernel<float, MODE_THREE_LEVEL><<<grid, kThreads, 0, st>>>(pl, a);
+        else if (mode == MODE_KAHAN) sem_open_finish_kernel<float, MODE_KAHAN><<<grid, kThreads, 0, st>>>(pl, a);
+        else sem_open_finish_kernel<float, MODE_APPLY><<<grid, kThreads, 0, st>>>(pl, a);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_geometry(int np, const double* coords, const int32_t* quads_new, const double* rho,
-                            const double* vel, const Plan& plan, const Basis<double>& basis, uint8_t* packet,
-                            double* G64, double* mloc, cudaStream_t st) {
-    geometry_kernel<<<grid_for(plan.ne * np * np, kThreads), kThreads, 0, st>>>(np, coords, quads_new, rho, vel, plan,
-                                                                               basis, packet, G64, mloc);
+cudaError_t launch_geometry(int np, int64_t ne, const double* coords, const int32_t* quads_new, const double* rho,
+                            const double* vel, const Basis<double>& basis, float4* coef, double* G64, double* mloc,
+                            cudaStream_t st) {
+    geometry_kernel<<<grid_for(ne * np * np, kThreads), kThreads, 0, st>>>(np, ne, coords, quads_new, rho, vel, basis,
+                                                                          coef, G64, mloc);
     return cudaGetLastError();
 }
 
@@ -473,7 +559,7 @@ cudaError_t launch_mass(const Plan& pl, int P, const double* mloc, double* parti
     mass_block_kernel<<<pl.nblocks, kThreads, 0, st>>>(pl, P, mloc, partial, M);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    mass_open_kernel<<<grid_for(pl.nopen, kThreads), kThreads, 0, st>>>(pl, partial, M);
+    if (pl.nopen_nodes > 0) mass_open_kernel<<<grid_for(pl.nopen_nodes, kThreads), kThreads, 0, st>>>(pl, partial, M);
     return cudaGetLastError();
 }
 

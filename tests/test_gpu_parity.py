@@ -172,3 +172,43 @@ def test_state_roundtrip_and_errors(P):
     u, up, st = h.sem_get_state()
     assert st == 5 and np.all(u == 0)         # no source: the field stays zero
     h.sem_destroy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan", "fp32"])
+@pytest.mark.parametrize("kind", ["hilbert", "random"])
+def test_split_runs_bitwise(P, prec, kind):
+    """sem_step(60) equals sem_step(1), (2), (7), (50) in a row, bit for bit:
+    runs that stop and restart finish the shared nodes with the same
+    arithmetic as runs that carry them from step to step."""
+    m = gen.graded(20, seed=13)
+    S = osem.SEM(m["coords"], m["quads"], 4, m["vel"], m["rho"])
+    dt = 0.3 * S.cfl_dt()
+    rec = np.array([[0.5, 0.5], [0.1, 0.9], [0.9, 0.2], [0.42, 0.42]])
+    outs = []
+    for chunks in ([60], [1, 2, 7, 50]):
+        h = P.SEM(m["coords"], m["quads"], 4, prec)
+        h.sem_reorder(kind, 7)
+        h.sem_set_model(m["vel"], m["rho"])
+        h.sem_set_tuning(9)
+        h.sem_set_source(m["f0"], m["t0"], m["amp"], *m["src_xy"])
+        h.sem_set_receivers(rec, 60)
+        h.sem_set_dt(dt)
+        for c in chunks:
+            h.sem_step(c)
+        outs.append((h.sem_read_wavefield(), h.sem_read_traces(), h.sem_get_state()[1]))
+        h.sem_destroy()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_plain_fp32_three_level(P):
+    """SEM_FP32 (no compensation) on the homogeneous 32 x 32 case, 400 steps:
+    within 1e-4 of the FP64 oracle (the compensated mode is the one held to
+    1e-5)."""
+    m = gen.unit_square(32)
+    S = osem.SEM(m["coords"], m["quads"], 4, m["vel"], m["rho"])
+    dt = 0.3 * S.cfl_dt()
+    _, u_ref, tr_ref = oracle_run(m, 4, 400, dt, m["receivers"])
+    u, tr, _ = gpu_run(P, m, 4, "fp32", "hilbert", 400, dt, m["receivers"])
+    assert rel_l2(u, u_ref) < 1e-4, rel_l2(u, u_ref)
+    assert rel_l2(tr, tr_ref) < 1e-4

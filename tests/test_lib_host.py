@@ -134,3 +134,30 @@ def test_state_errors_before_device(lib):
     with pytest.raises(lib.SemError):
         h.sem_set_source(-1.0, 0.0, 1.0, 0.5, 0.5)
     h.sem_destroy()
+
+
+@pytest.mark.parametrize("kind", ["none", "rowmajor", "random", "hilbert"])
+@pytest.mark.parametrize("p", [1, 3, 4, 8])
+@pytest.mark.parametrize("eb", [1, 9, 64, 256])
+def test_block_plan_replay(lib, kind, p, eb):
+    """The step kernel's block plan, replayed on the host with every index
+    bounds-checked: each slot reads its own node, the assembled sum equals the
+    direct per-slot sum, and each receiver node is recorded by one block."""
+    m = gen.relabel(gen.graded(13, seed=p), seed=eb)
+    rec = np.array([[0.5, 0.5], [0.0, 0.0], [1.0, 1.0], [0.31, 0.77], [0.5, 0.5]])
+    for fp64 in (False, True):
+        st, info, msg = lib.sem_plan_check(m["coords"], m["quads"], p, kind, eb, fp64, rec)
+        assert st == lib.SEM_OK, msg
+        assert info["nblocks"] == -(-m["quads"].shape[0] // eb)
+        # first-touch numberings always give the contiguous (DENSE) layout
+        if kind in ("rowmajor", "hilbert"):
+            assert info["dense"] == 1
+        elif info["nblocks"] > 1:
+            assert info["dense"] == 0
+
+
+def test_block_plan_hilbert_has_fewer_open_nodes(lib):
+    m = gen.graded(64, seed=3)
+    opened = {k: lib.sem_plan_check(m["coords"], m["quads"], 4, k, 64)[1]["open_nodes"]
+              for k in ("hilbert", "rowmajor", "random")}
+    assert opened["hilbert"] < opened["rowmajor"] < opened["random"], opened
