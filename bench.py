@@ -355,7 +355,9 @@ def main():
 
     peak, peak_kind = read_peaks()
     blk_us = 1e3 * bms / max(bl, 1)
-    achieved = block_bytes / (blk_us * 1e-6) / 1e9
+    # algorithmic bytes of one step-kernel launch: the per-node-update figure
+    # of the hot path times the nodes one launch updates
+    achieved = ALGO_BYTES[args.precision] * N / (blk_us * 1e-6) / 1e9
     traffic = recorded_traffic(args.precision, args.ordering)
     value = world * N * K / el
     line = {
@@ -370,7 +372,9 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "sem_step_kernel", "peak_kind": peak_kind,
                      "step_kernel_us": blk_us, "open_kernel_us_per_run": 1e3 * oms / max(ol, 1),
-                     "step_bytes_per_launch": block_bytes, "open_bytes_per_launch": open_bytes,
+                     "algorithmic_bytes_per_launch": ALGO_BYTES[args.precision] * N,
+                     "compulsory_bytes_per_launch": block_bytes, "compulsory_gbs": block_bytes / (blk_us * 1e-6) / 1e9,
+                     "open_bytes_per_launch": open_bytes,
                      "open_nodes": nopen, "profiled_ms_per_step": 1e3 * prof_el / K,
                      "algorithmic_bytes_per_node_update": ALGO_BYTES[args.precision],
                      "algorithmic_gbs_per_step": ALGO_BYTES[args.precision] * N * K / el / 1e9},

@@ -210,10 +210,11 @@ sem_status sem_compute_ordering(const double* coords, int64_t nv, const int32_t*
  * the host with every index bounds-checked, on integer-valued residuals so
  * that sums are exact, and compares with the direct per-slot sum; also
  * checks that every distinct receiver node (rec_xy[nrec][2], snapped like
- * sem_set_receivers) is recorded by exactly one block. info[6] (may be
- * NULL): blocks, DENSE layout (1/0), open nodes, largest entry count,
- * largest packet bytes, partial-sum slots. msg (may be NULL) receives the
- * first violation. Returns SEM_OK when consistent, SEM_ERR_STATE on a
+ * sem_set_receivers) is recorded by exactly one block; checks that no two
+ * elements of one colour in a block share a node. info[7] (may be NULL):
+ * blocks, DENSE layout (1/0), open nodes, largest entry count, largest
+ * packet bytes, partial-sum slots, most colours in a block. msg (may be
+ * NULL) receives the first violation. Returns SEM_OK when consistent, SEM_ERR_STATE on a
  * violation, SEM_ERR_UNSUPPORTED when the plan cannot be built,
  * SEM_ERR_INVALID_ARG for bad input. No device is needed. */
 sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads, int64_t ne, int order,

@@ -196,12 +196,12 @@ def sem_plan_check(coords, quads, order: int, kind, eb: int, fp64: bool = False,
     c = np.ascontiguousarray(coords, dtype=np.float64)
     q = np.ascontiguousarray(quads, dtype=np.int32)
     rec = np.ascontiguousarray(np.zeros((0, 2)) if receivers is None else receivers, dtype=np.float64)
-    info = np.zeros(6, dtype=np.int64)
+    info = np.zeros(7, dtype=np.int64)
     msg = C.create_string_buffer(512)
     st = lib.sem_plan_check(_ptr(c, C.c_double), c.shape[0], _ptr(q, C.c_int32), q.shape[0], int(order), kind,
                             C.c_uint64(seed & (2 ** 64 - 1)), int(eb), int(bool(fp64)), _ptr(rec, C.c_double),
                             rec.shape[0], _ptr(info, C.c_int64), msg, 512)
-    keys = ("nblocks", "dense", "open_nodes", "max_entries", "max_packet", "npartial")
+    keys = ("nblocks", "dense", "open_nodes", "max_entries", "max_packet", "npartial", "max_colors")
     return st, dict(zip(keys, (int(v) for v in info))), msg.value.decode()
 
 

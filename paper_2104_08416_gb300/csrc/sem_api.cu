@@ -213,15 +213,29 @@ sem_status fill_source(sem_mesh* m, int64_t upto) {
 }
 
 int default_eb(int np) {
-    // about 1600 element points per block, at most 256 elements (threads)
+    // about 4800 element points per block, at most 256 elements (threads)
     const int P = np * np;
-    int eb = (1600 + P / 2) / P;
+    int eb = (4800 + P / 2) / P;
     if (eb > 256) eb = 256;
     if (eb < 1) eb = 1;
     return eb;
 }
 
 int vec_of(const sem_mesh* m) { return fp64(m) ? 2 : 4; }
+
+constexpr int kSmemLimit = 227 * 1024;
+
+// Shared memory the step kernel needs for the handle's plan (the larger of
+// the time-stepping and the stiffness-only mode).
+int plan_smem_bytes(const sem_mesh* m, int P) {
+    const auto& pl = m->plan;
+    const int v = vec_of(m);
+    const int sulen_pad = (pl.max_sulen + v - 1) / v * v;
+    const int slen_pad = (pl.max_slen + v - 1) / v * v;
+    const int a = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), mode_of(m));
+    const int b = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), semdev::MODE_APPLY);
+    return std::max(std::max(a, b), sulen_pad * 8);
+}
 
 // Node arrays are allocated to a multiple of 16 bytes plus one vector so
 // the kernels' aligned 16-byte copies of owned ranges never leave them.
@@ -264,11 +278,32 @@ sem_status build(sem_mesh* m) {
     int eb = m->eb_request > 0 ? m->eb_request : default_eb(M.np);
     if ((int64_t)eb * P > 65535) eb = 65535 / P;
     if (eb > 256) eb = 256;
-    std::string why = semhost::build_block_plan(conn_new, M.ne, P, M.nn, eb, true, vec_of(m), rec_gid, m->plan);
-    if (!why.empty()) return fail(m, SEM_ERR_UNSUPPORTED, "block plan: " + why);
+    // the default block size shrinks until the step kernel's shared memory
+    // fits (scattered orderings touch more distinct nodes per block)
+    for (;;) {
+        std::string why = semhost::build_block_plan(conn_new, M.ne, P, M.nn, eb, true, vec_of(m), rec_gid, m->plan);
+        if (!why.empty()) return fail(m, SEM_ERR_UNSUPPORTED, "block plan: " + why);
+        const int need = plan_smem_bytes(m, P);
+        if (need <= kSmemLimit || m->eb_request > 0 || eb <= 4) break;
+        eb = std::max(4, (int)((double)eb * 0.9 * kSmemLimit / need));
+    }
     conn_new.clear();
     conn_new.shrink_to_fit();
     const auto& pl = m->plan;
+    // element data in the plan's device order (blocks sorted by colour)
+    {
+        std::vector<int32_t> qd((size_t)M.ne * 4);
+        std::vector<double> rd((size_t)M.ne), vd((size_t)M.ne);
+        for (int64_t i = 0; i < M.ne; ++i) {
+            const int64_t en = pl.dev_order[(size_t)i];
+            for (int c = 0; c < 4; ++c) qd[(size_t)i * 4 + c] = quads_new[(size_t)en * 4 + c];
+            rd[(size_t)i] = rho_new[(size_t)en];
+            vd[(size_t)i] = vel_new[(size_t)en];
+        }
+        quads_new.swap(qd);
+        rho_new.swap(rd);
+        vel_new.swap(vd);
+    }
     const int v = vec_of(m);
     const int sulen_pad = (pl.max_sulen + v - 1) / v * v;
     const int slen_pad = (pl.max_slen + v - 1) / v * v;
@@ -276,7 +311,7 @@ sem_status build(sem_mesh* m) {
     m->smem = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), mode_of(m));
     const int smem_apply = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m),
                                                   semdev::MODE_APPLY);
-    if (std::max(m->smem, smem_apply) > 227 * 1024)
+    if (std::max(m->smem, smem_apply) > kSmemLimit)
         return fail(m, SEM_ERR_UNSUPPORTED, "block plan does not fit in shared memory; lower sem_set_tuning");
 
     sem_status st;
@@ -310,6 +345,7 @@ sem_status build(sem_mesh* m) {
     dp.sulen_pad = sulen_pad;
     dp.slen_pad = slen_pad;
     dp.dense = pl.dense ? 1 : 0;
+    dp.vec = vec_of(m);
 
     fill_basis(m->basis64, M.p);
     fill_basis(m->basis32, M.p);
@@ -339,7 +375,7 @@ sem_status build(sem_mesh* m) {
     }
     SEM_CUDA(semdev::launch_geometry(M.np, M.ne, m->d_coords, m->d_quads, m->d_rho, m->d_vel, m->basis64, coef,
                                      m->d_G64, m->d_mloc, m->stream));
-    SEM_CUDA(semdev::launch_mass(dp, P, m->d_mloc, (double*)m->d_part[0], m->d_M, m->stream));
+    SEM_CUDA(semdev::launch_mass(dp, M.np, m->d_mloc, (double*)m->d_part[0], m->d_M, m->stream));
 
     // time-stepping state
     const size_t nb = node_bytes(m);
@@ -483,7 +519,8 @@ sem_status launch_flush(sem_mesh* m) {
 // with `partial` as scratch for the open entries' partial sums.
 sem_status launch_apply(sem_mesh* m, const void* dev_in, void* dev_out, void* partial) {
     const bool f64 = fp64(m);
-    const bool vok = ((uintptr_t)dev_in % 16) == 0;
+    // 16-byte vector copies and stores need both vectors 16-byte aligned
+    const bool vok = ((uintptr_t)dev_in % 16) == 0 && ((uintptr_t)dev_out % 16) == 0;
     cudaError_t e;
     if (f64) {
         semdev::StepArgs<double> a{};
@@ -918,6 +955,7 @@ sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads
         info[3] = pl.max_entries;
         info[4] = pl.max_packet;
         info[5] = pl.npartial;
+        info[6] = pl.max_colors;
     }
     why = semhost::check_block_plan(pl, conn_new, vec);
     if (!why.empty()) {
@@ -928,10 +966,9 @@ sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads
     std::vector<int> seen((size_t)nrec, 0);
     for (int64_t b = 0; b < pl.nblocks; ++b) {
         const int32_t* h = &pl.hdr[(size_t)b * semplan::HDR_INTS];
-        const int nrc = h[semplan::H_NREC] >> 16, nro = h[semplan::H_NREC] & 0xFFFF;
-        const int neb = (int)std::min<int64_t>(elems_per_block, ne - b * elems_per_block);
-        const semplan::Offsets L =
-            semplan::offsets(neb * P, h[semplan::H_NENT], h[semplan::H_NOWN], h[semplan::H_NOPEN], nrc + nro);
+        const int nrc = h[semplan::H_NREC_CLOSED], nro = h[semplan::H_NREC_OPEN];
+        const semplan::Offsets L = semplan::offsets(h[semplan::H_SULEN], h[semplan::H_ULEN], h[semplan::H_NOPEN],
+                                                    h[semplan::H_NCOLORS], nrc + nro);
         const int32_t* recs = reinterpret_cast<const int32_t*>(pl.packet.data() + (size_t)h[0] * 16 + L.recs);
         for (int k = 0; k < nrc + nro; ++k) {
             const int r = recs[2 * k + 1];

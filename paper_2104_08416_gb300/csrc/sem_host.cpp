@@ -531,16 +531,18 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
     pl.nn = nn;
     pl.nblocks = (ne + eb - 1) / eb;
     const int64_t nb = pl.nblocks;
-    if ((int64_t)eb * P > 65535) return "elements per block x points per element above 65535";
+    if (eb < 1 || (int64_t)eb * P > 65535) return "elements per block x points per element above 65535";
     // blocks touching each node (blocks are visited in ascending order)
     std::vector<int32_t> nblk((size_t)nn, 0);
-    std::vector<int64_t> last((size_t)nn, -1);
-    for (int64_t s = 0; s < ne * P; ++s) {
-        const int32_t g = conn[(size_t)s];
-        const int64_t b = s / P / eb;
-        if (last[(size_t)g] != b) {
-            last[(size_t)g] = b;
-            nblk[(size_t)g]++;
+    {
+        std::vector<int64_t> last((size_t)nn, -1);
+        for (int64_t s = 0; s < ne * P; ++s) {
+            const int32_t g = conn[(size_t)s];
+            const int64_t b = s / P / eb;
+            if (last[(size_t)g] != b) {
+                last[(size_t)g] = b;
+                nblk[(size_t)g]++;
+            }
         }
     }
     // DENSE when the nodes first touched by each block are the next id range
@@ -585,24 +587,25 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
     for (size_t k = 0; k < pl.open_gid.size(); ++k) pl.open_rec[k] = rec_of[(size_t)pl.open_gid[k]];
 
     const int UPH = (P + 1) / 2;
+    pl.dev_order.resize((size_t)ne);
     pl.epos.assign((size_t)UPH * (size_t)ne, 0u);
     pl.hdr.assign((size_t)nb * HDR_INTS, 0);
     std::vector<int32_t> seen_rank((size_t)nn, 0);   // blocks that touched the node so far
     std::vector<int64_t> in_block((size_t)nn, -1);
     std::vector<int32_t> local((size_t)nn, -1);
+    std::vector<uint32_t> node_colors((size_t)nn, 0);
     std::vector<uint8_t> touched((size_t)nn, 0);
-    std::vector<int32_t> ent_gid, cnt, slot_ent;
-    std::vector<int32_t> recs;
+    std::vector<int32_t> ent_gid, elem_color, recs;
     int64_t own_next = 0;
     for (int64_t b = 0; b < nb; ++b) {
         const int64_t e0 = b * eb, e1 = std::min(ne, e0 + eb);
-        const int64_t s0 = e0 * P, nslot = (e1 - e0) * P;
+        const int neb = (int)(e1 - e0);
+        // entries: owned nodes in id order (DENSE), then the others by first appearance
         ent_gid.clear();
-        cnt.clear();
         int64_t own_start = 0, nown = 0;
         if (dense) {
             own_start = own_next;
-            for (int64_t t = s0; t < s0 + nslot; ++t) {
+            for (int64_t t = e0 * P; t < e1 * P; ++t) {
                 const int32_t g = conn[(size_t)t];
                 if (!touched[(size_t)g]) {
                     touched[(size_t)g] = 1;
@@ -614,21 +617,16 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
                 in_block[(size_t)g] = b;
                 local[(size_t)g] = (int32_t)l;
                 ent_gid.push_back(g);
-                cnt.push_back(0);
             }
             own_next = own_start + nown;
         }
-        slot_ent.assign((size_t)nslot, 0);
-        for (int64_t t = 0; t < nslot; ++t) {
-            const int32_t g = conn[(size_t)(s0 + t)];
+        for (int64_t t = e0 * P; t < e1 * P; ++t) {
+            const int32_t g = conn[(size_t)t];
             if (in_block[(size_t)g] != b) {
                 in_block[(size_t)g] = b;
                 local[(size_t)g] = (int32_t)ent_gid.size();
                 ent_gid.push_back(g);
-                cnt.push_back(0);
             }
-            slot_ent[(size_t)t] = local[(size_t)g];
-            cnt[(size_t)local[(size_t)g]]++;
         }
         const int64_t nent = (int64_t)ent_gid.size();
         const int64_t off = dense ? own_start % vec : 0;
@@ -636,18 +634,93 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         const int64_t sulen = ulen + (nent - nown);
         const int64_t slen = dense ? ulen : nent;
         if (nent > 65535 || sulen > 65535) return "too many nodes in one element block";
+        // colouring of the block's conflict graph (elements sharing a node)
+        // by DSatur: repeatedly colour the uncoloured element whose coloured
+        // neighbours use the most distinct colours (ties: most neighbours,
+        // then lowest index) with the smallest free colour
+        int ncolors = 0;
+        {
+            const int W = (neb + 63) / 64;
+            std::vector<uint64_t> adj((size_t)neb * W, 0);
+            for (int el = 0; el < neb; ++el)
+                for (int q = 0; q < P; ++q) {
+                    const int32_t g = conn[(size_t)((e0 + el) * P + q)];
+                    // node_colors doubles as "last element of this block that touched g, plus one"
+                    node_colors[(size_t)g] = 0;
+                }
+            std::vector<std::vector<int>> touch;
+            touch.reserve((size_t)nent);
+            for (int el = 0; el < neb; ++el)
+                for (int q = 0; q < P; ++q) {
+                    const int32_t g = conn[(size_t)((e0 + el) * P + q)];
+                    if (node_colors[(size_t)g] == 0) {
+                        touch.emplace_back();
+                        node_colors[(size_t)g] = (uint32_t)touch.size();
+                    }
+                    auto& lst = touch[(size_t)node_colors[(size_t)g] - 1];
+                    if (lst.empty() || lst.back() != el) lst.push_back(el);
+                }
+            for (int el = 0; el < neb; ++el)
+                for (int q = 0; q < P; ++q) node_colors[(size_t)conn[(size_t)((e0 + el) * P + q)]] = 0;
+            for (const auto& lst : touch)
+                for (size_t x = 0; x < lst.size(); ++x)
+                    for (size_t y = x + 1; y < lst.size(); ++y) {
+                        adj[(size_t)lst[x] * W + lst[y] / 64] |= 1ull << (lst[y] % 64);
+                        adj[(size_t)lst[y] * W + lst[x] / 64] |= 1ull << (lst[x] % 64);
+                    }
+            std::vector<int> deg((size_t)neb, 0);
+            for (int el = 0; el < neb; ++el)
+                for (int w = 0; w < W; ++w) deg[(size_t)el] += __builtin_popcountll(adj[(size_t)el * W + w]);
+            std::vector<uint32_t> sat((size_t)neb, 0);
+            elem_color.assign((size_t)neb, -1);
+            for (int it = 0; it < neb; ++it) {
+                int best = -1, bs = -1, bd = -1;
+                for (int el = 0; el < neb; ++el) {
+                    if (elem_color[(size_t)el] >= 0) continue;
+                    const int sv = __builtin_popcount(sat[(size_t)el]);
+                    if (sv > bs || (sv == bs && deg[(size_t)el] > bd)) {
+                        best = el;
+                        bs = sv;
+                        bd = deg[(size_t)el];
+                    }
+                }
+                const uint32_t used = sat[(size_t)best];
+                if (used == 0xFFFFFFFFu) return "more than 32 colours needed in one element block";
+                int c = 0;
+                while (used & (1u << c)) ++c;
+                elem_color[(size_t)best] = c;
+                ncolors = std::max(ncolors, c + 1);
+                for (int w = 0; w < W; ++w) {
+                    uint64_t bits = adj[(size_t)best * W + w];
+                    while (bits) {
+                        const int nb2 = w * 64 + __builtin_ctzll(bits);
+                        bits &= bits - 1;
+                        sat[(size_t)nb2] |= 1u << c;
+                    }
+                }
+            }
+        }
+        // device order: stable sort by colour inside the block
+        std::vector<int32_t> cstart((size_t)ncolors + 1, 0);
+        for (int el = 0; el < neb; ++el) cstart[(size_t)elem_color[(size_t)el] + 1]++;
+        for (int c = 0; c < ncolors; ++c) cstart[(size_t)c + 1] += cstart[(size_t)c];
+        {
+            std::vector<int32_t> fill(cstart.begin(), cstart.end() - 1);
+            for (int el = 0; el < neb; ++el)
+                pl.dev_order[(size_t)(e0 + fill[(size_t)elem_color[(size_t)el]]++)] = e0 + el;
+        }
         // open ranks in entry order
         std::vector<int32_t> orank_of((size_t)nent, -1);
         int64_t nopen = 0;
         for (int64_t l = 0; l < nent; ++l)
             if (nblk[(size_t)ent_gid[(size_t)l]] > 1) orank_of[(size_t)l] = (int32_t)nopen++;
-        if (nopen >= 65535) return "too many open nodes in one element block";
+        if (nopen > 65535) return "too many open nodes in one element block";
         recs.clear();
         int64_t nrc = 0, nro = 0;
         for (int64_t l = 0; l < nent; ++l) {
             const int32_t g = ent_gid[(size_t)l];
             if (rec_of[(size_t)g] >= 0 && orank_of[(size_t)l] < 0) {
-                recs.push_back((int32_t)l);
+                recs.push_back(entry_pos((int)l, (int)nown, (int)off, (int)ulen));
                 recs.push_back(rec_of[(size_t)g]);
                 nrc++;
             }
@@ -655,53 +728,48 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         for (int64_t l = 0; l < nent; ++l) {
             const int32_t g = ent_gid[(size_t)l];
             if (rec_of[(size_t)g] >= 0 && orank_of[(size_t)l] >= 0 && seen_rank[(size_t)g] == 0) {
-                recs.push_back(orank_of[(size_t)l]);
+                recs.push_back(entry_pos((int)l, (int)nown, (int)off, (int)ulen));
                 recs.push_back(rec_of[(size_t)g]);
                 nro++;
             }
         }
-        if (nrc > 65535 || nro > 65535) return "too many receivers in one element block";
-        const Offsets L = offsets((int)nslot, (int)nent, (int)nown, (int)nopen, (int)(nrc + nro));
+        const Offsets L = offsets((int)sulen, (int)ulen, (int)nopen, ncolors, (int)(nrc + nro));
         const int64_t start = (int64_t)pl.packet.size();
         pl.packet.resize((size_t)(start + L.bytes), 0);
         uint8_t* pk = pl.packet.data() + start;
-        uint16_t* lsl = reinterpret_cast<uint16_t*>(pk + L.lsl);
-        uint16_t* lrow = reinterpret_cast<uint16_t*>(pk + L.lrow);
-        uint16_t* aux = reinterpret_cast<uint16_t*>(pk + L.aux);
+        uint32_t* cmask = reinterpret_cast<uint32_t*>(pk + L.cmask);
         int32_t* egid = reinterpret_cast<int32_t*>(pk + L.egid);
         int32_t* obase = reinterpret_cast<int32_t*>(pk + L.obase);
-        uint16_t* oent = reinterpret_cast<uint16_t*>(pk + L.oent);
+        uint16_t* opos = reinterpret_cast<uint16_t*>(pk + L.opos);
         uint8_t* ocnt = pk + L.ocnt;
         uint8_t* orank = pk + L.orank;
+        uint16_t* pcs = reinterpret_cast<uint16_t*>(pk + L.cstart);
         int32_t* prec = reinterpret_cast<int32_t*>(pk + L.recs);
-        lrow[0] = 0;
-        for (int64_t l = 0; l < nent; ++l) lrow[l + 1] = (uint16_t)(lrow[l] + cnt[(size_t)l]);
-        {
-            std::vector<uint16_t> fill(lrow, lrow + nent);
-            for (int64_t t = 0; t < nslot; ++t) lsl[fill[(size_t)slot_ent[(size_t)t]]++] = (uint16_t)t;
-        }
         for (int64_t l = 0; l < nent; ++l) {
             const int32_t g = ent_gid[(size_t)l];
             const int32_t o = orank_of[(size_t)l];
+            const int pos = entry_pos((int)l, (int)nown, (int)off, (int)ulen);
             if (o < 0) {
-                aux[l] = CLOSED;
+                cmask[pos >> 5] |= 1u << (pos & 31);
                 pl.nclosed_total++;
             } else {
-                aux[l] = (uint16_t)o;
                 obase[o] = (int32_t)base[(size_t)g];
-                oent[o] = (uint16_t)l;
+                opos[o] = (uint16_t)pos;
                 ocnt[o] = (uint8_t)nblk[(size_t)g];
                 orank[o] = (uint8_t)seen_rank[(size_t)g];
             }
             seen_rank[(size_t)g]++;
-            if (l >= nown) egid[l - nown] = g;
+            if (l >= nown) egid[pos - ulen] = g;
         }
+        for (int c = 0; c <= ncolors; ++c) pcs[c] = (uint16_t)cstart[(size_t)c];
         std::copy(recs.begin(), recs.end(), prec);
-        for (int64_t t = 0; t < nslot; ++t) {
-            const int64_t e = e0 + t / P;
-            const int q = (int)(t % P);
-            const uint32_t pos = (uint32_t)entry_pos(slot_ent[(size_t)t], (int)nown, (int)off, (int)ulen);
-            pl.epos[(size_t)(q / 2) * (size_t)ne + (size_t)e] |= pos << (16 * (q & 1));
+        for (int i = 0; i < neb; ++i) {
+            const int64_t e = pl.dev_order[(size_t)(e0 + i)];
+            for (int q = 0; q < P; ++q) {
+                const int l = local[(size_t)conn[(size_t)(e * P + q)]];
+                const uint32_t pos = (uint32_t)entry_pos(l, (int)nown, (int)off, (int)ulen);
+                pl.epos[(size_t)(q / 2) * (size_t)ne + (size_t)(e0 + i)] |= pos << (16 * (q & 1));
+            }
         }
         int32_t* h = &pl.hdr[(size_t)b * HDR_INTS];
         h[H_START] = (int32_t)(start / 16);
@@ -711,11 +779,15 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         h[H_NOPEN] = (int32_t)nopen;
         h[H_ULEN] = (int32_t)ulen;
         h[H_SLEN] = (int32_t)slen;
-        h[H_NREC] = (int32_t)((nrc << 16) | nro);
+        h[H_SULEN] = (int32_t)sulen;
+        h[H_NCOLORS] = ncolors;
+        h[H_NREC_CLOSED] = (int32_t)nrc;
+        h[H_NREC_OPEN] = (int32_t)nro;
         pl.max_entries = std::max<int>(pl.max_entries, (int)nent);
         pl.max_sulen = std::max<int>(pl.max_sulen, (int)sulen);
         pl.max_slen = std::max<int>(pl.max_slen, (int)slen);
         pl.max_packet = std::max<int>(pl.max_packet, L.bytes);
+        pl.max_colors = std::max(pl.max_colors, ncolors);
         pl.nent_total += nent;
         pl.nopen_entries += nopen;
     }
@@ -727,8 +799,16 @@ std::string check_block_plan(const BlockPlan& pl, const std::vector<int32_t>& co
     using namespace semplan;
     const int P = pl.P;
     const int64_t ne = pl.ne, nn = pl.nn;
-    const int UPH = (P + 1) / 2;
     auto fail = [](int64_t b, const std::string& what) { return "block " + std::to_string(b) + ": " + what; };
+    // the device order permutes elements inside their blocks only
+    {
+        std::vector<uint8_t> hit((size_t)ne, 0);
+        for (int64_t i = 0; i < ne; ++i) {
+            const int64_t e = pl.dev_order[(size_t)i];
+            if (e < 0 || e >= ne || hit[(size_t)e] || e / pl.eb != i / pl.eb) return "device order is not a per-block permutation";
+            hit[(size_t)e] = 1;
+        }
+    }
     std::vector<double> u((size_t)nn), out((size_t)nn, std::nan("")), ref((size_t)nn, 0.0);
     for (int64_t g = 0; g < nn; ++g) u[(size_t)g] = (double)((g * 37) % 1001);
     for (int64_t s = 0; s < ne * P; ++s) {
@@ -736,102 +816,108 @@ std::string check_block_plan(const BlockPlan& pl, const std::vector<int32_t>& co
         ref[(size_t)conn[(size_t)s]] += u[(size_t)conn[(size_t)s]] + (double)((e % 7) * (s % P + 1));
     }
     std::vector<double> part((size_t)std::max<int64_t>(pl.npartial, 1), std::nan(""));
-    std::vector<double> su, sr;
+    std::vector<double> su, acc;
+    std::vector<int64_t> stamp;
+    int64_t phase = 0;
     for (int64_t b = 0; b < pl.nblocks; ++b) {
         const int32_t* h = &pl.hdr[(size_t)b * HDR_INTS];
         const int64_t e0 = b * pl.eb;
         const int neb = (int)std::min<int64_t>(pl.eb, ne - e0);
-        const int nslot = neb * P;
         const int nent = h[H_NENT], nown = h[H_NOWN], own_start = h[H_OWN_START], nopen = h[H_NOPEN];
-        const int ulen = h[H_ULEN], slen = h[H_SLEN];
-        const int nrc = h[H_NREC] >> 16, nro = h[H_NREC] & 0xFFFF;
+        const int ulen = h[H_ULEN], slen = h[H_SLEN], sulen = h[H_SULEN], ncolors = h[H_NCOLORS];
+        const int nrc = h[H_NREC_CLOSED], nro = h[H_NREC_OPEN];
         const int off = pl.dense ? own_start % vec : 0;
-        const int sulen = ulen + nent - nown;
+        const int64_t abase = (int64_t)own_start - off;
+        if (sulen != ulen + nent - nown) return fail(b, "position count mismatch");
         if (sulen > pl.max_sulen || slen > pl.max_slen || nent > pl.max_entries) return fail(b, "size above maximum");
-        if (pl.dense && (ulen % vec != 0 || (own_start - off) % vec != 0)) return fail(b, "owned range misaligned");
-        const Offsets L = offsets(nslot, nent, nown, nopen, nrc + nro);
+        if (slen > sulen) return fail(b, "staged range beyond positions");
+        if (pl.dense && (ulen % vec != 0 || abase % vec != 0 || slen != ulen)) return fail(b, "owned range misaligned");
+        if (ncolors < 1 || ncolors > MAX_COLORS) return fail(b, "colour count");
+        const Offsets L = offsets(sulen, ulen, nopen, ncolors, nrc + nro);
         const int64_t start = (int64_t)h[H_START] * 16;
         if (L.bytes > pl.max_packet || start + L.bytes > (int64_t)pl.packet.size()) return fail(b, "packet bounds");
         const uint8_t* pk = pl.packet.data() + start;
-        const uint16_t* lsl = reinterpret_cast<const uint16_t*>(pk + L.lsl);
-        const uint16_t* lrow = reinterpret_cast<const uint16_t*>(pk + L.lrow);
-        const uint16_t* aux = reinterpret_cast<const uint16_t*>(pk + L.aux);
+        const uint32_t* cmask = reinterpret_cast<const uint32_t*>(pk + L.cmask);
         const int32_t* egid = reinterpret_cast<const int32_t*>(pk + L.egid);
         const int32_t* obase = reinterpret_cast<const int32_t*>(pk + L.obase);
-        const uint16_t* oent = reinterpret_cast<const uint16_t*>(pk + L.oent);
+        const uint16_t* opos = reinterpret_cast<const uint16_t*>(pk + L.opos);
         const uint8_t* ocnt = pk + L.ocnt;
         const uint8_t* orank = pk + L.orank;
+        const uint16_t* cstart = reinterpret_cast<const uint16_t*>(pk + L.cstart);
         const int32_t* recs = reinterpret_cast<const int32_t*>(pk + L.recs);
-        auto gid = [&](int l) -> int64_t { return l < nown ? (int64_t)own_start + l : (int64_t)egid[l - nown]; };
-        // node values: owned range as aligned vectors, then the other entries
+        auto gid_at = [&](int p) -> int64_t { return p < ulen ? abase + p : (int64_t)egid[p - ulen]; };
+        auto closed = [&](int p) { return (cmask[p >> 5] >> (p & 31)) & 1u; };
+        // node values: owned range as aligned vectors, then the other positions
         su.assign((size_t)sulen, std::nan(""));
-        for (int t = 0; t < ulen; ++t) {
-            const int64_t g = (int64_t)own_start - off + t;
-            if (g >= 0 && g < nn) su[(size_t)t] = u[(size_t)g];
+        for (int p = 0; p < ulen; ++p) {
+            const int64_t g = abase + p;
+            if (g >= 0 && g < nn) su[(size_t)p] = u[(size_t)g];
         }
-        for (int l = nown; l < nent; ++l) {
-            const int64_t g = gid(l);
+        for (int p = ulen; p < sulen; ++p) {
+            const int64_t g = gid_at(p);
             if (g < 0 || g >= nn) return fail(b, "node id out of range");
-            su[(size_t)entry_pos(l, nown, off, ulen)] = u[(size_t)g];
+            su[(size_t)p] = u[(size_t)g];
         }
-        // element residuals through epos
-        sr.assign((size_t)nslot, 0.0);
-        for (int el = 0; el < neb; ++el)
-            for (int q = 0; q < P; ++q) {
-                const int64_t e = e0 + el;
-                const uint32_t w = pl.epos[(size_t)(q / 2) * (size_t)ne + (size_t)e];
-                const int pos = (int)((w >> (16 * (q & 1))) & 0xFFFF);
-                if (pos >= sulen) return fail(b, "epos beyond node values");
-                const int64_t g = conn[(size_t)(e * P + q)];
-                if (su[(size_t)pos] != u[(size_t)g]) return fail(b, "slot reads another node's value");
-                sr[(size_t)(el * P + q)] = su[(size_t)pos] + (double)((e % 7) * (q + 1));
-            }
-        (void)UPH;
-        // assembly
-        if (lrow[0] != 0 || lrow[nent] != nslot) return fail(b, "local CSR does not cover the slots");
-        int seen_open = 0;
-        for (int l = 0; l < nent; ++l) {
-            if (lrow[l + 1] < lrow[l]) return fail(b, "local CSR not monotone");
-            double acc = 0.0;
-            for (int t = lrow[l]; t < lrow[l + 1]; ++t) {
-                if (lsl[t] >= nslot) return fail(b, "slot index out of range");
-                const int el = lsl[t] / P, q = lsl[t] % P;
-                if (conn[(size_t)((e0 + el) * P + q)] != gid(l)) return fail(b, "slot listed under the wrong entry");
-                acc += sr[lsl[t]];
-            }
-            const int64_t g = gid(l);
-            if (aux[l] == CLOSED) {
-                if (entry_pos(l, nown, off, ulen) >= slen) return fail(b, "closed entry outside staged state");
-                if (!std::isnan(out[(size_t)g])) return fail(b, "node finished twice");
-                out[(size_t)g] = acc;
-            } else {
-                const int o = aux[l];
-                if (o >= nopen || oent[o] != l) return fail(b, "open rank mismatch");
-                if (orank[o] >= ocnt[o]) return fail(b, "open rank beyond its node's block count");
-                const int64_t pi = (int64_t)obase[o] + orank[o];
-                if (pi < 0 || pi >= pl.npartial) return fail(b, "partial index out of range");
-                if (!std::isnan(part[(size_t)pi])) return fail(b, "partial slot written twice");
-                part[(size_t)pi] = acc;
-                seen_open++;
+        // element residuals through epos, scattered colour by colour
+        if (cstart[0] != 0 || cstart[ncolors] != neb) return fail(b, "colour ranges do not cover the block");
+        acc.assign((size_t)sulen, 0.0);
+        stamp.assign((size_t)sulen, -1);
+        for (int c = 0; c < ncolors; ++c) {
+            if (cstart[c + 1] < cstart[c]) return fail(b, "colour ranges not monotone");
+            ++phase;
+            for (int i = cstart[c]; i < cstart[c + 1]; ++i) {
+                const int64_t e = pl.dev_order[(size_t)(e0 + i)];
+                for (int q = 0; q < P; ++q) {
+                    const uint32_t w = pl.epos[(size_t)(q / 2) * (size_t)ne + (size_t)(e0 + i)];
+                    const int pos = (int)((w >> (16 * (q & 1))) & 0xFFFF);
+                    if (pos >= sulen) return fail(b, "epos beyond node values");
+                    const int64_t g = conn[(size_t)(e * P + q)];
+                    if (su[(size_t)pos] != u[(size_t)g] || gid_at(pos) != g) return fail(b, "slot reads another node's value");
+                    if (stamp[(size_t)pos] == phase) return fail(b, "two elements of one colour share a node");
+                    stamp[(size_t)pos] = phase;
+                    acc[(size_t)pos] += su[(size_t)pos] + (double)((e % 7) * (q + 1));
+                }
             }
         }
-        if (seen_open != nopen) return fail(b, "open count mismatch");
-        for (int k = 0; k < nrc; ++k)
-            if (recs[2 * k] >= nent || aux[recs[2 * k]] != CLOSED) return fail(b, "closed receiver record");
-        for (int k = nrc; k < nrc + nro; ++k)
-            if (recs[2 * k] >= nopen || orank[recs[2 * k]] != 0 ||
-                entry_pos(oent[recs[2 * k]], nown, off, ulen) >= slen)
-                return fail(b, "open receiver record");
+        // closed positions finish their node, open entries leave a partial
+        int nclosed_seen = 0;
+        for (int p = 0; p < sulen; ++p) {
+            if (!closed(p)) continue;
+            if (p >= slen) return fail(b, "closed entry outside staged state");
+            if (p < ulen && (p < off || p >= off + nown)) return fail(b, "closed bit on a padding position");
+            const int64_t g = gid_at(p);
+            if (!std::isnan(out[(size_t)g])) return fail(b, "node finished twice");
+            out[(size_t)g] = acc[(size_t)p];
+            nclosed_seen++;
+        }
+        for (int o = 0; o < nopen; ++o) {
+            const int p = opos[o];
+            if (p >= sulen || closed(p)) return fail(b, "open position");
+            if (p < ulen && (p < off || p >= off + nown)) return fail(b, "open entry on a padding position");
+            if (orank[o] >= ocnt[o]) return fail(b, "open rank beyond its node's block count");
+            if (orank[o] == 0 && p >= slen) return fail(b, "owner's open entry outside staged state");
+            const int64_t pi = (int64_t)obase[o] + orank[o];
+            if (pi < 0 || pi >= pl.npartial) return fail(b, "partial index out of range");
+            if (!std::isnan(part[(size_t)pi])) return fail(b, "partial slot written twice");
+            part[(size_t)pi] = acc[(size_t)p];
+        }
+        if (nclosed_seen + nopen != nent) return fail(b, "closed + open != entries");
+        for (int k = 0; k < nrc + nro; ++k) {
+            const int p = recs[2 * k];
+            if (p >= slen) return fail(b, "receiver record outside staged state");
+            if (k < nrc && !closed(p)) return fail(b, "closed receiver record on an open entry");
+            if (k >= nrc && closed(p)) return fail(b, "open receiver record on a closed entry");
+        }
     }
     for (size_t k = 0; k < pl.open_gid.size(); ++k) {
-        double acc = 0.0;
+        double s = 0.0;
         for (int t = 0; t < pl.open_cnt[k]; ++t) {
             const double v = part[(size_t)(pl.open_base[k] + t)];
             if (std::isnan(v)) return "open node " + std::to_string(pl.open_gid[k]) + ": missing partial";
-            acc += v;
+            s += v;
         }
         if (!std::isnan(out[(size_t)pl.open_gid[k]])) return "open node also finished by a block";
-        out[(size_t)pl.open_gid[k]] = acc;
+        out[(size_t)pl.open_gid[k]] = s;
     }
     for (int64_t g = 0; g < nn; ++g)
         if (out[(size_t)g] != ref[(size_t)g]) return "node " + std::to_string(g) + ": assembled value differs";

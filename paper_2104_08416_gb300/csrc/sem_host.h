@@ -58,39 +58,45 @@ int64_t snap(const std::vector<double>& node_xy, double x, double y);
 double cfl_dt(const Mesh& m, const double* vel);
 
 // Block plan for deterministic, atomic-free assembly (layout and terms in
-// sem_plan.h). conn_new: [ne][P] new node ids, elements in the new order.
-// rec_gid: new node id of each receiver whose trace the kernels record, -1 for
-// none. vec: node values per 16 bytes (4 FP32, 2 FP64). allow_dense: use the
-// DENSE layout when the numbering permits it.
+// sem_plan.h). conn: [ne][P] new node ids, elements in the new (memory)
+// order. rec_gid: new node id of each receiver whose trace the kernels record,
+// -1 for none. vec: node values per 16 bytes (4 FP32, 2 FP64). allow_dense:
+// use the DENSE layout when the numbering permits it. The plan's device
+// element order (dev_order[i] = index into conn of the element that thread i
+// of block i / eb handles) is the memory order with each block sorted by
+// colour; all element-side device data follows it.
 struct BlockPlan {
     int eb = 0;
     int P = 0;
     bool dense = false;
     int64_t ne = 0, nn = 0, nblocks = 0;
     int max_entries = 0;                 // largest entry count of a block
-    int max_sulen = 0;                   // largest shared-memory node-value length
+    int max_sulen = 0;                   // largest node-value position count
     int max_slen = 0;                    // largest staged-state length
     int max_packet = 0;                  // largest packet (bytes)
+    int max_colors = 0;                  // most colours in a block
+    std::vector<int64_t> dev_order;      // [ne] device element order
     std::vector<uint8_t> packet;         // all packets, block after block
     std::vector<int32_t> hdr;            // [nblocks][HDR_INTS]
-    std::vector<uint32_t> epos;          // [(P+1)/2][ne] packed shared-memory positions
+    std::vector<uint32_t> epos;          // [(P+1)/2][ne] packed positions, device element order
     // open nodes (touched by more than one block), ascending id, for the
-    // kernels that finish them outside the block kernel
+    // kernels that finish them outside the step kernel
     std::vector<int32_t> open_gid, open_base, open_cnt, open_rec;
     int64_t npartial = 0;                // partial-sum slots (sum of open_cnt)
     int64_t nent_total = 0, nclosed_total = 0, nopen_entries = 0;
 };
 // Returns "" on success, else why the plan cannot be built (a limit of the
-// 16-bit / 8-bit fields exceeded).
-std::string build_block_plan(const std::vector<int32_t>& conn_new, int64_t ne, int P, int64_t nn, int eb,
+// 16-bit / 8-bit fields or of the colour count exceeded).
+std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P, int64_t nn, int eb,
                              bool allow_dense, int vec, const std::vector<int32_t>& rec_gid, BlockPlan& plan);
 
-// Host emulation of one block-kernel pass plus the open-node pass over the
+// Host emulation of one step-kernel assembly plus the open-node pass over the
 // plan, with every index bounds-checked, on integer-valued element residuals
-// r[e][q] = u[conn[e][q]] + (e mod 7) * (q + 1) so that sums are exact. Checks
-// that every slot reads its own node's value through epos and that the
-// assembled result equals the direct per-slot sum. Returns "" when the plan
-// is consistent, else the first violation.
-std::string check_block_plan(const BlockPlan& plan, const std::vector<int32_t>& conn_new, int vec);
+// r[e][q] = u[conn[e][q]] + (e mod 7) * (q + 1) so that sums are exact:
+// every slot must read its own node's value through epos, no two elements of
+// one colour may share a node, and the assembled result must equal the direct
+// per-slot sum. Returns "" when the plan is consistent, else the first
+// violation.
+std::string check_block_plan(const BlockPlan& plan, const std::vector<int32_t>& conn, int vec);
 
 }  // namespace semhost

@@ -31,6 +31,13 @@ using namespace semplan;
 
 constexpr int kThreads = 256;
 constexpr int kMaxStepThreads = 256;
+// Resident CTAs the compiler budgets registers for: three (80 registers a
+// thread, a few spilled values) for FP32 up to order 4, where the extra
+// resident warps outweigh the spills; one for larger elements and FP64.
+template <int NP, typename T>
+constexpr int step_min_blocks() {
+    return (sizeof(T) == 4 && NP <= 5) ? 3 : 1;
+}
 
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
@@ -75,7 +82,7 @@ template <typename T>
 __device__ __forceinline__ T sum_partials(const T* __restrict__ p, int32_t pb, int cnt) {
     T v[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) v[t] = (t < cnt) ? p[pb + t] : T(0);
+    for (int t = 0; t < 4; ++t) v[t] = (t < cnt) ? __ldcg(p + pb + t) : T(0);
     T s = add_rn(v[0], v[1]);
     if (cnt > 2) s = add_rn(s, v[2]);
     if (cnt > 3) s = add_rn(s, v[3]);
@@ -107,6 +114,30 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 
+// 16-byte shared-memory vector of VEC values.
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec(T (&v)[VEC], const T* p) {
+    const float4 w = *reinterpret_cast<const float4*>(p);
+    const T* t = reinterpret_cast<const T*>(&w);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v[k] = t[k];
+}
+// Stores the values whose bit is set; one 16-byte store when all are.
+template <typename T, int VEC>
+__device__ __forceinline__ void store_masked(T* g, const T (&v)[VEC], uint32_t bits) {
+    if (bits == (1u << VEC) - 1u) {
+        float4 w;
+        T* t = reinterpret_cast<T*>(&w);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) t[k] = v[k];
+        __stcg(reinterpret_cast<float4*>(g), w);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k)
+            if ((bits >> k) & 1u) __stcg(g + k, v[k]);
+    }
+}
+
 // Copies node values [abase, abase + len) of src (len a multiple of VEC,
 // abase a multiple of VEC) to dst with 16-byte copies, element by element
 // where the vector would cross the end nn or the arrays are not aligned.
@@ -127,8 +158,31 @@ __device__ __forceinline__ void stage_range(T* dst, const T* src, int64_t abase,
     }
 }
 
+// Header fields of block b (three int4).
+struct BlockHdr {
+    int start, nent, nown, own_start, nopen, ulen, slen, sulen, ncolors, nrc, nro;
+};
+__device__ __forceinline__ BlockHdr load_hdr(const int4* hdr, int b) {
+    const int4 h0 = hdr[3 * b], h1 = hdr[3 * b + 1], h2 = hdr[3 * b + 2];
+    BlockHdr h;
+    h.start = h0.x;
+    h.nent = h0.y;
+    h.nown = h0.z;
+    h.own_start = h0.w;
+    h.nopen = h1.x;
+    h.ulen = h1.y;
+    h.slen = h1.z;
+    h.sulen = h1.w;
+    h.ncolors = h2.x;
+    h.nrc = h2.y;
+    h.nro = h2.z;
+    return h;
+}
+
+__device__ __forceinline__ bool is_closed(const uint32_t* cmask, int p) { return (cmask[p >> 5] >> (p & 31)) & 1u; }
+
 template <int NP, typename T, int MODE>
-__global__ void __launch_bounds__(kMaxStepThreads) sem_step_kernel(const Plan pl, const StepArgs<T> a,
+__global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>())) sem_step_kernel(const Plan pl, const StepArgs<T> a,
                                                                    const Basis<T> bs) {
     constexpr int P = NP * NP;
     constexpr int UPH = (P + 1) / 2;
@@ -138,25 +192,27 @@ __global__ void __launch_bounds__(kMaxStepThreads) sem_step_kernel(const Plan pl
     constexpr int VEC = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint8_t* spk = smem_raw;
-    T* su = reinterpret_cast<T*>(smem_raw + pl.max_packet);   // node values of the entries
+    T* su = reinterpret_cast<T*>(smem_raw + pl.max_packet);   // node values at the positions
     T* ss = su + pl.sulen_pad;                                 // staged s
     T* sx = ss + (STATE ? pl.slen_pad : 0);                    // staged u^{k-1} or delta
     T* sc = sx + (STATE ? pl.slen_pad : 0);                    // staged compensation
-    T* sr = sc + (KAHAN ? pl.slen_pad : 0);                    // element residuals [eb][P]
+    T* acc = sc + (KAHAN ? pl.slen_pad : 0);                   // assembled K u at the positions
 
     const int b = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int4 h0 = pl.hdr[2 * b], h1 = pl.hdr[2 * b + 1];
-    const int nent = h0.y, nown = h0.z, own_start = h0.w;
-    const int nopen = h1.x, ulen = h1.y;
-    const int nrc = (int)((unsigned)h1.w >> 16), nro = h1.w & 0xFFFF;
+    const BlockHdr h = load_hdr(pl.hdr, b);
     const int64_t e0 = (int64_t)b * pl.eb;
     const int neb = (int)min((int64_t)pl.eb, pl.ne - e0);
-    const int nslot = neb * P;
-    const Offsets L = offsets(nslot, nent, nown, nopen, nrc + nro);
-    const int off = pl.dense ? own_start % VEC : 0;
-    const int64_t abase = (int64_t)own_start - off;
+    const Offsets L = offsets(h.sulen, h.ulen, h.nopen, h.ncolors, h.nrc + h.nro);
+    const int off = pl.dense ? h.own_start % VEC : 0;
+    const int64_t abase = (int64_t)h.own_start - off;
     const bool has_el = tid < neb;
+    // source values of this launch (the point source is one node)
+    T f_now = T(0), f_prev = T(0);
+    if (STATE && a.src_gid >= 0) {
+        f_now = (T)a.src_f[a.step];
+        if (a.pending) f_prev = (T)a.src_f[a.step - 1];
+    }
     const int64_t e = e0 + tid;
 
     // element-side data straight into registers (coalesced across threads)
@@ -164,74 +220,73 @@ __global__ void __launch_bounds__(kMaxStepThreads) sem_step_kernel(const Plan pl
     float4 cf0 = make_float4(0.f, 0.f, 0.f, 0.f), cf1 = cf0;
     if (has_el) {
 #pragma unroll
-        for (int h = 0; h < UPH; ++h) pw[h] = ld_stream(pl.epos + (int64_t)h * pl.ne + e);
+        for (int k = 0; k < UPH; ++k) pw[k] = ld_stream(pl.epos + (int64_t)k * pl.ne + e);
         if constexpr (BIL) {
             cf0 = ld_stream(pl.coef + e);
             cf1 = ld_stream(pl.coef + pl.ne + e);
         }
     }
 
-    // A1. packet and owned node range
+    // A1. packet, owned node range, zeroed accumulators
     {
-        const uint8_t* gpk = pl.packet + (int64_t)h0.x * 16;
+        const uint8_t* gpk = pl.packet + (int64_t)h.start * 16;
         for (int o = tid * 16; o < L.bytes; o += nt * 16) cp_async16(spk + o, gpk + o);
         if (pl.dense) {
             const bool vok = a.vec_ok != 0;
-            stage_range(su, a.u_k, abase, ulen, pl.nn, vok, tid, nt);
+            stage_range(su, a.u_k, abase, h.ulen, pl.nn, vok, tid, nt);
             if (STATE) {
-                stage_range(ss, a.s, abase, ulen, pl.nn, vok, tid, nt);
-                stage_range(sx, a.x_k, abase, ulen, pl.nn, vok, tid, nt);
-                if (KAHAN) stage_range(sc, a.c_k, abase, ulen, pl.nn, vok, tid, nt);
+                stage_range(ss, a.s, abase, h.ulen, pl.nn, vok, tid, nt);
+                stage_range(sx, a.x_k, abase, h.ulen, pl.nn, vok, tid, nt);
+                if (KAHAN) stage_range(sc, a.c_k, abase, h.ulen, pl.nn, vok, tid, nt);
             }
         }
         cp_async_commit();
+        float4* az = reinterpret_cast<float4*>(acc);
+        const int nz = (h.sulen * (int)sizeof(T) + 15) / 16;
+        for (int k = tid; k < nz; k += nt) az[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         cp_async_wait_all();
         __syncthreads();
     }
-    const uint16_t* lsl = reinterpret_cast<const uint16_t*>(spk + L.lsl);
-    const uint16_t* lrow = reinterpret_cast<const uint16_t*>(spk + L.lrow);
-    const uint16_t* aux = reinterpret_cast<const uint16_t*>(spk + L.aux);
+    const uint32_t* cmask = reinterpret_cast<const uint32_t*>(spk + L.cmask);
     const int32_t* egid = reinterpret_cast<const int32_t*>(spk + L.egid);
     const int32_t* obase = reinterpret_cast<const int32_t*>(spk + L.obase);
-    const uint16_t* oent = reinterpret_cast<const uint16_t*>(spk + L.oent);
+    const uint16_t* opos = reinterpret_cast<const uint16_t*>(spk + L.opos);
     const uint8_t* ocnt = spk + L.ocnt;
     const uint8_t* orank = spk + L.orank;
+    const uint16_t* cstart = reinterpret_cast<const uint16_t*>(spk + L.cstart);
     const int32_t* recs = reinterpret_cast<const int32_t*>(spk + L.recs);
 
-    // A2. closed entries of GATHER plans; open entries
+    // A2. closed positions of GATHER plans; open entries
     if (!pl.dense) {
-        for (int l = tid; l < nent; l += nt)
-            if (aux[l] == CLOSED) {
-                const int32_t g = egid[l];
-                cp_async_small<sizeof(T)>(su + l, a.u_k + g);
+        for (int p = tid; p < h.slen; p += nt)
+            if (is_closed(cmask, p)) {
+                const int32_t g = egid[p];
+                cp_async_small<sizeof(T)>(su + p, a.u_k + g);
                 if (STATE) {
-                    cp_async_small<sizeof(T)>(ss + l, a.s + g);
-                    cp_async_small<sizeof(T)>(sx + l, a.x_k + g);
-                    if (KAHAN) cp_async_small<sizeof(T)>(sc + l, a.c_k + g);
+                    cp_async_small<sizeof(T)>(ss + p, a.s + g);
+                    cp_async_small<sizeof(T)>(sx + p, a.x_k + g);
+                    if (KAHAN) cp_async_small<sizeof(T)>(sc + p, a.c_k + g);
                 }
             }
     }
     const bool pending = STATE && a.pending;
-    for (int o = tid; o < nopen; o += nt) {
-        const int l = oent[o];
-        const int32_t g = l < nown ? own_start + l : egid[l - nown];
-        const int pos = entry_pos(l, nown, off, ulen);
+    for (int o = tid; o < h.nopen; o += nt) {
+        const int pos = opos[o];
+        const int64_t g = pos < h.ulen ? abase + pos : (int64_t)egid[pos - h.ulen];
         if (!pending) {
             cp_async_small<sizeof(T)>(su + pos, a.u_k + g);
         } else {
-            const int32_t pb = obase[o];
-            const int cnt = ocnt[o];
-            const T ku = sum_partials(a.part_rd, pb, cnt);
-            const T f = (g == a.src_gid) ? (T)a.src_f[a.step - 1] : T(0);
-            const Update<T, MODE> up = update_node<T, MODE>(a.u_km1[g], a.x_km1[g], KAHAN ? a.c_km1[g] : T(0), a.s[g],
-                                                             f, ku);
+            const T ku = sum_partials(a.part_rd, obase[o], ocnt[o]);
+            const T f = (g == a.src_gid) ? f_prev : T(0);
+            const Update<T, MODE> up = update_node<T, MODE>(__ldcg(a.u_km1 + g), __ldcg(a.x_km1 + g),
+                                                             KAHAN ? __ldcg(a.c_km1 + g) : T(0), __ldcg(a.s + g), f, ku);
             su[pos] = up.u;
             if (orank[o] == 0) {
-                a.u_kw[g] = up.u;
+                __stcg(a.u_kw + g, up.u);
                 if (KAHAN) {
-                    a.x_kw[g] = up.x;
-                    a.c_kw[g] = up.c;
-                    sc[pos] = up.c;  // for a receiver record (owned entries lie in the staged range)
+                    __stcg(a.x_kw + g, up.x);
+                    __stcg(a.c_kw + g, up.c);
+                    sc[pos] = up.c;  // for a receiver record (the owner's entries lie in the staged range)
                 }
             }
         }
@@ -239,17 +294,17 @@ __global__ void __launch_bounds__(kMaxStepThreads) sem_step_kernel(const Plan pl
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    if (pending && nro > 0) {
-        for (int k = tid; k < nro; k += nt) {
-            const int o = recs[2 * (nrc + k)], r = recs[2 * (nrc + k) + 1];
-            const int pos = entry_pos(oent[o], nown, off, ulen);
+    if (pending && h.nro > 0) {
+        for (int k = tid; k < h.nro; k += nt) {
+            const int pos = recs[2 * (h.nrc + k)], r = recs[2 * (h.nrc + k) + 1];
             a.trace[(int64_t)r * a.trace_cap + a.step - 1] = trace_value<T, MODE>(su[pos], KAHAN ? sc[pos] : T(0));
         }
     }
 
     // B. element contraction in registers
+    T r[P];
     if (has_el) {
-        T u[P], r[P];
+        T u[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             u[q] = su[(pw[q / 2] >> (16 * (q & 1))) & 0xFFFFu];
@@ -307,46 +362,91 @@ __global__ void __launch_bounds__(kMaxStepThreads) sem_step_kernel(const Plan pl
                 }
             }
         }
-        T* re = sr + tid * P;
-#pragma unroll
-        for (int q = 0; q < P; ++q) re[q] = r[q];
     }
-    __syncthreads();
+    // colour-ordered scatter: in phase c only the threads of colour c add,
+    // and they share no node
+    // (an element's slots are distinct nodes, so all reads go first, then
+    // all writes, without read-after-write waits between slots)
+    for (int c = 0; c < h.ncolors; ++c) {
+        if (tid >= cstart[c] && tid < cstart[c + 1]) {
+            T v[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) v[q] = acc[(pw[q / 2] >> (16 * (q & 1))) & 0xFFFFu];
+#pragma unroll
+            for (int q = 0; q < P; ++q) acc[(pw[q / 2] >> (16 * (q & 1))) & 0xFFFFu] = v[q] + r[q];
+        }
+        __syncthreads();
+    }
 
-    // C. assembly in fixed (slot-ascending) order
-    for (int l = tid; l < nent; l += nt) {
-        const int r0 = lrow[l], r1 = lrow[l + 1];
-        T acc = T(0);
-        for (int t = r0; t < r1; ++t) acc += sr[lsl[t]];
-        const uint16_t ax = aux[l];
-        if (ax == CLOSED) {
-            const int32_t g = l < nown ? own_start + l : egid[l - nown];
+    // C. closed positions finish their node; open entries leave a partial sum
+    if (pl.dense) {
+        // VEC consecutive positions per thread: 16-byte shared-memory reads,
+        // and 16-byte stores where all VEC positions are closed
+        const int nch = h.slen / VEC;
+        for (int ch = tid; ch < nch; ch += nt) {
+            const int p0 = ch * VEC;
+            const uint32_t bits = (cmask[p0 >> 5] >> (p0 & 31)) & ((1u << VEC) - 1u);
+            if (bits == 0) continue;
+            const int64_t g0 = abase + p0;
+            T vu[VEC], vr[VEC], vx[VEC], vc[VEC], vs[VEC];
+            load_vec<T, VEC>(vr, acc + p0);
             if (MODE == MODE_APPLY) {
-                a.apply_out[g] = acc;
+                store_masked<T, VEC>(a.apply_out + g0, vr, a.vec_ok ? bits : (bits | (1u << VEC)));
+                continue;
+            }
+            load_vec<T, VEC>(vu, su + p0);
+            load_vec<T, VEC>(vx, sx + p0);
+            load_vec<T, VEC>(vs, ss + p0);
+            if (KAHAN) load_vec<T, VEC>(vc, sc + p0);
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) {
+                const T f = (g0 + t == a.src_gid) ? f_now : T(0);
+                const Update<T, MODE> up = update_node<T, MODE>(vu[t], vx[t], KAHAN ? vc[t] : T(0), vs[t], f, vr[t]);
+                vu[t] = up.u;
+                vx[t] = up.x;
+                vc[t] = up.c;
+            }
+            store_masked<T, VEC>(a.u_kp1 + g0, vu, bits);
+            if (KAHAN) {
+                store_masked<T, VEC>(a.x_kp1 + g0, vx, bits);
+                store_masked<T, VEC>(a.c_kp1 + g0, vc, bits);
+            }
+            if (h.nrc > 0) {
+#pragma unroll
+                for (int t = 0; t < VEC; ++t)
+                    if ((bits >> t) & 1u) {
+                        su[p0 + t] = vu[t];
+                        if (KAHAN) sc[p0 + t] = vc[t];
+                    }
+            }
+        }
+    } else {
+        for (int p = tid; p < h.slen; p += nt) {
+            if (!is_closed(cmask, p)) continue;
+            const int64_t g = egid[p];
+            if (MODE == MODE_APPLY) {
+                __stcg(a.apply_out + g, acc[p]);
             } else {
-                const int pos = entry_pos(l, nown, off, ulen);
-                const T f = (g == a.src_gid) ? (T)a.src_f[a.step] : T(0);
-                const Update<T, MODE> up = update_node<T, MODE>(su[pos], sx[pos], KAHAN ? sc[pos] : T(0), ss[pos], f, acc);
-                a.u_kp1[g] = up.u;
+                const T f = (g == a.src_gid) ? f_now : T(0);
+                const Update<T, MODE> up = update_node<T, MODE>(su[p], sx[p], KAHAN ? sc[p] : T(0), ss[p], f, acc[p]);
+                __stcg(a.u_kp1 + g, up.u);
                 if (KAHAN) {
-                    a.x_kp1[g] = up.x;
-                    a.c_kp1[g] = up.c;
+                    __stcg(a.x_kp1 + g, up.x);
+                    __stcg(a.c_kp1 + g, up.c);
                 }
-                if (nrc > 0) {
-                    su[pos] = up.u;
-                    if (KAHAN) sc[pos] = up.c;
+                if (h.nrc > 0) {
+                    su[p] = up.u;
+                    if (KAHAN) sc[p] = up.c;
                 }
             }
-        } else {
-            a.part_wr[obase[ax] + orank[ax]] = acc;
         }
     }
-    if (STATE && nrc > 0) {
+    for (int o = tid; o < h.nopen; o += nt) __stcg(a.part_wr + obase[o] + orank[o], acc[opos[o]]);
+    if (STATE && h.nrc > 0) {
         __syncthreads();
-        for (int k = tid; k < nrc; k += nt) {
-            const int l = recs[2 * k], r = recs[2 * k + 1];
-            const int pos = entry_pos(l, nown, off, ulen);
-            a.trace[(int64_t)r * a.trace_cap + a.step] = trace_value<T, MODE>(su[pos], KAHAN ? sc[pos] : T(0));
+        for (int k = tid; k < h.nrc; k += nt) {
+            const int pos = recs[2 * k], r2 = recs[2 * k + 1];
+            a.trace[(int64_t)r2 * a.trace_cap + a.step] = trace_value<T, MODE>(su[pos], KAHAN ? sc[pos] : T(0));
         }
     }
 }
@@ -420,30 +520,45 @@ __global__ void geometry_kernel(int np, int64_t ne, const double* __restrict__ c
     }
 }
 
-__global__ void __launch_bounds__(kThreads) mass_block_kernel(const Plan pl, int P, const double* __restrict__ mloc,
-                                                             double* partial, double* M) {
+// Lumped mass through the block plan: the same colour-ordered scatter as the
+// step kernel, in FP64, of w_q |J_q| / (rho c^2) per slot (mloc, device
+// element order); one thread per element.
+template <int NP>
+__global__ void __launch_bounds__(kMaxStepThreads) mass_block_kernel(const Plan pl, const double* __restrict__ mloc,
+                                                                    double* partial, double* M) {
+    constexpr int P = NP * NP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* acc = reinterpret_cast<double*>(smem_raw);
     const int b = blockIdx.x;
-    const int4 h0 = pl.hdr[2 * b], h1 = pl.hdr[2 * b + 1];
-    const int nent = h0.y, nown = h0.z, own_start = h0.w, nopen = h1.x;
-    const int nrec = (int)((unsigned)h1.w >> 16) + (h1.w & 0xFFFF);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const BlockHdr h = load_hdr(pl.hdr, b);
     const int64_t e0 = (int64_t)b * pl.eb;
     const int neb = (int)min((int64_t)pl.eb, pl.ne - e0);
-    const Offsets L = offsets(neb * P, nent, nown, nopen, nrec);
-    const uint8_t* pk = pl.packet + (int64_t)h0.x * 16;
-    const uint16_t* lsl = reinterpret_cast<const uint16_t*>(pk + L.lsl);
-    const uint16_t* lrow = reinterpret_cast<const uint16_t*>(pk + L.lrow);
-    const uint16_t* aux = reinterpret_cast<const uint16_t*>(pk + L.aux);
+    const Offsets L = offsets(h.sulen, h.ulen, h.nopen, h.ncolors, h.nrc + h.nro);
+    const uint8_t* pk = pl.packet + (int64_t)h.start * 16;
+    const uint32_t* cmask = reinterpret_cast<const uint32_t*>(pk + L.cmask);
     const int32_t* egid = reinterpret_cast<const int32_t*>(pk + L.egid);
     const int32_t* obase = reinterpret_cast<const int32_t*>(pk + L.obase);
+    const uint16_t* opos = reinterpret_cast<const uint16_t*>(pk + L.opos);
     const uint8_t* orank = pk + L.orank;
-    const int64_t s0 = e0 * P;
-    for (int l = threadIdx.x; l < nent; l += kThreads) {
-        double acc = 0.0;
-        for (int t = lrow[l]; t < lrow[l + 1]; ++t) acc += mloc[s0 + lsl[t]];
-        const uint16_t ax = aux[l];
-        if (ax == CLOSED) M[l < nown ? own_start + l : egid[l - nown]] = acc;
-        else partial[obase[ax] + orank[ax]] = acc;
+    const uint16_t* cstart = reinterpret_cast<const uint16_t*>(pk + L.cstart);
+    const int off = pl.dense ? h.own_start % pl.vec : 0;
+    const int64_t abase = (int64_t)h.own_start - off;
+    for (int p = tid; p < h.sulen; p += nt) acc[p] = 0.0;
+    __syncthreads();
+    for (int c = 0; c < h.ncolors; ++c) {
+        if (tid < neb && tid >= cstart[c] && tid < cstart[c + 1]) {
+            const int64_t e = e0 + tid;
+            for (int q = 0; q < P; ++q) {
+                const uint32_t w = pl.epos[(int64_t)(q / 2) * pl.ne + e];
+                acc[(w >> (16 * (q & 1))) & 0xFFFFu] += mloc[e * P + q];
+            }
+        }
+        __syncthreads();
     }
+    for (int p = tid; p < h.slen; p += nt)
+        if (is_closed(cmask, p)) M[p < h.ulen ? abase + p : (int64_t)egid[p - h.ulen]] = acc[p];
+    for (int o = tid; o < h.nopen; o += nt) partial[obase[o] + orank[o]] = acc[opos[o]];
 }
 
 __global__ void mass_open_kernel(const Plan pl, const double* __restrict__ partial, double* M) {
@@ -507,9 +622,11 @@ int step_threads(int eb) {
 }
 
 int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, bool fp64, int mode) {
+    (void)P;
+    (void)eb;
     const int sz = fp64 ? 8 : 4;
     const int staged = mode == MODE_KAHAN ? 3 : (mode == MODE_THREE_LEVEL ? 2 : 0);
-    return max_packet + (sulen_pad + staged * slen_pad + eb * P) * sz;
+    return max_packet + (2 * sulen_pad + staged * slen_pad) * sz;
 }
 
 cudaError_t launch_step(int np, bool fp64, int mode, const Plan& pl, const void* args, const void* basis,
@@ -555,9 +672,29 @@ cudaError_t launch_geometry(int np, int64_t ne, const double* coords, const int3
     return cudaGetLastError();
 }
 
-cudaError_t launch_mass(const Plan& pl, int P, const double* mloc, double* partial, double* M, cudaStream_t st) {
-    mass_block_kernel<<<pl.nblocks, kThreads, 0, st>>>(pl, P, mloc, partial, M);
-    cudaError_t e = cudaGetLastError();
+cudaError_t launch_mass(const Plan& pl, int np, const double* mloc, double* partial, double* M, cudaStream_t st) {
+    const int threads = step_threads(pl.eb);
+    const int smem = pl.sulen_pad * 8;
+    cudaError_t e = cudaSuccess;
+    switch (np) {
+#define SEM_MASS_CASE(N)                                                                                     \
+    case N:                                                                                                  \
+        e = cudaFuncSetAttribute(mass_block_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);   \
+        if (e == cudaSuccess) mass_block_kernel<N><<<pl.nblocks, threads, smem, st>>>(pl, mloc, partial, M); \
+        break;
+        SEM_MASS_CASE(2)
+        SEM_MASS_CASE(3)
+        SEM_MASS_CASE(4)
+        SEM_MASS_CASE(5)
+        SEM_MASS_CASE(6)
+        SEM_MASS_CASE(7)
+        SEM_MASS_CASE(8)
+        SEM_MASS_CASE(9)
+#undef SEM_MASS_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (pl.nopen_nodes > 0) mass_open_kernel<<<grid_for(pl.nopen_nodes, kThreads), kThreads, 0, st>>>(pl, partial, M);
     return cudaGetLastError();

@@ -24,7 +24,7 @@ struct Basis {
 // Block plan on the device (layout in sem_plan.h).
 struct Plan {
     const uint8_t* packet;
-    const int4* hdr;           // [nblocks][2]
+    const int4* hdr;           // [nblocks][3]
     const uint32_t* epos;      // [(P+1)/2][ne]
     const float4* coef;        // [2][ne] bilinear map (FP32 kernels)
     const double* G;           // [3P][ne] stored metric (FP64 kernels)
@@ -37,6 +37,7 @@ struct Plan {
     int max_packet;            // bytes, multiple of 16
     int sulen_pad, slen_pad;   // shared-memory array lengths (multiples of 16 bytes)
     int dense;
+    int vec;                   // node values per 16 bytes of the storage type
 };
 
 enum Mode : int {
@@ -92,14 +93,16 @@ cudaError_t launch_open_finish(bool fp64, int mode, const Plan& plan, const void
 cudaError_t launch_geometry(int np, int64_t ne, const double* coords, const int32_t* quads_new, const double* rho,
                             const double* vel, const Basis<double>& basis, float4* coef, double* G64, double* mloc,
                             cudaStream_t st);
-// Lumped mass through the block plan (deterministic), M[nn] in FP64.
-cudaError_t launch_mass(const Plan& plan, int P, const double* mloc, double* partial, double* M, cudaStream_t st);
+// Lumped mass through the block plan (deterministic), M[nn] in FP64; mloc
+// per slot in the device element order.
+cudaError_t launch_mass(const Plan& plan, int np, const double* mloc, double* partial, double* M, cudaStream_t st);
 // s = dt^2 / M (FP64 arithmetic, rounded once to the storage type).
 cudaError_t launch_scale(const double* M, int64_t nn, double dt, double* s64, float* s32, cudaStream_t st);
 
 // Threads of the step kernel for a block of eb elements (one per element,
 // rounded up to whole warps).
 int step_threads(int eb);
+// Dynamic shared memory of the step kernel.
 int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, bool fp64, int mode);
 
 }  // namespace semdev
