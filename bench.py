@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--precision", default="fp32_kahan", choices=["fp32_kahan", "fp64", "fp32"])
     ap.add_argument("--ordering", default="hilbert", choices=["hilbert", "rowmajor", "random", "none"])
     ap.add_argument("--n", type=int, default=512, help="quads per side of the graded mesh")
+    ap.add_argument("--workload", default="graded", choices=["graded", "layered"],
+                    help="graded 512x512 (default) or the layered 4096x1024 model (67M nodes)")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-ordering comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eb", type=int, default=0, help="elements per block (0 = library default)")
@@ -70,8 +72,8 @@ def dist_setup(args):
     return world, rank, local
 
 
-def workload(n, rank=0):
-    m = gen.graded(n)
+def workload(args, rank=0):
+    m = gen.layered(4096, 1024) if args.workload == "layered" else gen.graded(args.n)
     # replicas: each rank shoots from its own source position
     if rank:
         g = gen.SplitMix64(gen.DEFAULT_SEED + 100 + rank)
@@ -274,7 +276,8 @@ def main():
     P.sem_set_allocator_torch()
 
     K, W = args.steps, args.warmup
-    m = workload(args.n, rank)
+    m = workload(args, rank)
+    wname = "layered_4096x1024_p4" if args.workload == "layered" else (WORKLOAD if args.n == 512 else f"graded_{args.n}x{args.n}_p4")
     cap = W + 2 * K + 8
     h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads)
     N = h.n_nodes
@@ -347,7 +350,7 @@ def main():
         return
 
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload == "graded":
         v, k, nn = cpu_baseline(args.n)
         cpu = {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
                "sample": f"{k} leapfrog steps of the FP64 NumPy oracle on the full {WORKLOAD} mesh ({nn} nodes), "
@@ -358,13 +361,13 @@ def main():
     # algorithmic bytes of one step-kernel launch: the per-node-update figure
     # of the hot path times the nodes one launch updates
     achieved = ALGO_BYTES[args.precision] * N / (blk_us * 1e-6) / 1e9
-    traffic = recorded_traffic(args.precision, args.ordering)
+    traffic = recorded_traffic(args.precision, args.ordering) if wname == WORKLOAD else None
     value = world * N * K / el
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32_kahan": "f32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": N, "elements": m["quads"].shape[0], "order": 4,
+        "config": {"workload": wname, "nodes": N, "elements": m["quads"].shape[0], "order": 4,
                    "precision": args.precision, "ordering": args.ordering,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
