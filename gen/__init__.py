@@ -183,6 +183,26 @@ def relabel(mesh: dict, seed: int = DEFAULT_SEED) -> dict:
     return out
 
 
+def batched(n_shots: int = 64, nmin: int = 64, nmax: int = 1024, orders=(3, 4, 5, 6, 7),
+            seed: int = DEFAULT_SEED) -> list:
+    """Independent shots for the batched path: square layered models of
+    n x n quads over 10 km x 10 km with n uniform in [nmin, nmax], the order
+    uniform over `orders`, and the source at a uniformly drawn interior point
+    (stream seed+5: n, order, source x, source y per shot, in that order)."""
+    rng = SplitMix64(seed + 5)
+    shots = []
+    for k in range(n_shots):
+        n = nmin + min(int(rng.uniform() * (nmax - nmin + 1)), nmax - nmin)
+        p = orders[min(int(rng.uniform() * len(orders)), len(orders) - 1)]
+        sx, sy = 1000.0 + 8000.0 * rng.uniform(), 1000.0 + 8000.0 * rng.uniform()
+        m = layered(n, n, width=10000.0, depth=10000.0, seed=seed + 17 * k, n_receivers=32)
+        m["src_xy"] = (sx, sy)
+        m["order"] = p
+        m["name"] = f"shot{k}_{n}x{n}_p{p}"
+        shots.append(m)
+    return shots
+
+
 def config(name: str, seed: int = DEFAULT_SEED) -> dict:
     """The three single-GPU workloads by name, with their step counts."""
     if name == "homogeneous_32":

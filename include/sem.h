@@ -291,6 +291,47 @@ sem_status sem_transfer_bytes(const sem_mesh* m, int64_t* h2d, int64_t* d2h);
 #define SEM_NOALLOC_SCRATCH_BYTES (16u << 20)
 sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void* dev_Ku);
 
+/* Batched shots (many independent simulations advanced together). A batch
+ * groups mesh handles that are configured (model and dt set; source and
+ * receivers optional) with the same precision and stream; each keeps its own
+ * mesh, order, ordering, model and state, and is read back with the usual
+ * per-handle calls. The paper runs one simulation at a time; batching is the
+ * serving-style use of the same time step.
+ *   shots[nshots]   handles (distinct); the batch does not own them and must
+ *                   be destroyed before any of them.
+ *   autotune_steps  0: keep each handle's block size. > 0: for each order, the
+ *                   largest not yet built handle is timed for this many steps
+ *                   with each candidate elements-per-block (48..256), and every
+ *                   not yet built handle of that order without its own
+ *                   sem_set_tuning uses the fastest (the timed handle is then
+ *                   rebuilt from its initial state).
+ * Returns SEM_ERR_STATE if a handle lacks model or dt or the precisions or
+ * streams differ. */
+typedef struct sem_batch sem_batch;
+sem_status sem_batch_create(sem_mesh* const* shots, int32_t nshots, int32_t autotune_steps, sem_batch** out);
+
+/* Advance every shot nsteps leapfrog steps. Each step is one launch per
+ * polynomial order present (CTAs over the element blocks of all shots of
+ * that order) plus a step-counter update; a block of 16 steps is captured
+ * once as a CUDA graph and replayed, the remainder launched directly; after
+ * the last step each shot's open nodes are completed as by sem_step. The
+ * first call builds the shots' device data. Results equal those of sem_step
+ * on each handle with the same block size, bit for bit. Asynchronous on the
+ * stream. */
+sem_status sem_batch_step(sem_batch* b, int64_t nsteps);
+
+/* After the first sem_batch_step: number of order classes, and per class its
+ * polynomial order, elements per block (the largest in the class) and CTAs
+ * per step launch (any output may be NULL; arrays hold nclasses entries). */
+sem_status sem_batch_info(const sem_batch* b, int32_t* nclasses, int32_t* orders, int32_t* elems_per_block,
+                          int32_t* ctas);
+
+/* Message of the last failing batch call ("" if none). Never NULL. */
+const char* sem_batch_last_error(const sem_batch* b);
+
+/* Free the batch (not its handles). NULL is a no-op. */
+void sem_batch_destroy(sem_batch* b);
+
 /* Message of the last failing call on this handle ("" if none). Never NULL. */
 const char* sem_last_error(const sem_mesh* m);
 

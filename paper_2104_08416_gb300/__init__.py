@@ -38,7 +38,8 @@ EXPORTS = (
     "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info",
     "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
-    "sem_apply_stiffness_dev_noalloc", "sem_last_error", "sem_destroy",
+    "sem_apply_stiffness_dev_noalloc", "sem_batch_create", "sem_batch_step", "sem_batch_info",
+    "sem_batch_last_error", "sem_batch_destroy", "sem_last_error", "sem_destroy",
 )
 
 _lib = None
@@ -98,6 +99,9 @@ def load(path: str | None = None):
         "sem_traffic_model": (_P, _D, _D),
         "sem_transfer_bytes": (_P, _I64, _I64),
         "sem_apply_stiffness_dev_noalloc": (_P, _P, _P),
+        "sem_batch_create": (C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(_P)),
+        "sem_batch_step": (_P, C.c_int64),
+        "sem_batch_info": (_P, _I32, _I32, _I32, _I32),
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -107,6 +111,10 @@ def load(path: str | None = None):
     lib.sem_last_error.restype = C.c_char_p
     lib.sem_destroy.argtypes = [_P]
     lib.sem_destroy.restype = None
+    lib.sem_batch_last_error.argtypes = [_P]
+    lib.sem_batch_last_error.restype = C.c_char_p
+    lib.sem_batch_destroy.argtypes = [_P]
+    lib.sem_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -373,3 +381,47 @@ class SEM:
 
 def sem_mesh_create(coords, quads, order: int, precision="fp32_kahan", stream=None) -> SEM:
     return SEM(coords, quads, order, precision, stream)
+
+
+class SEMBatch:
+    """Batched shots (sem_batch*): advances several configured SEM handles
+    together. Methods mirror the C calls; the handles stay readable through
+    their own methods."""
+
+    def __init__(self, shots, autotune_steps: int = 0):
+        self._lib = load()
+        self.shots = list(shots)
+        arr = (_P * len(self.shots))(*[s.h for s in self.shots])
+        out = _P()
+        st = self._lib.sem_batch_create(arr, len(self.shots), int(autotune_steps), C.byref(out))
+        _check(st)
+        self.h = out
+
+    def _c(self, st):
+        if st != SEM_OK:
+            raise SemError(st, (self._lib.sem_batch_last_error(self.h) or b"").decode())
+
+    def sem_batch_step(self, nsteps: int):
+        self._c(self._lib.sem_batch_step(self.h, int(nsteps)))
+
+    def sem_batch_info(self):
+        n = C.c_int32()
+        self._c(self._lib.sem_batch_info(self.h, C.byref(n), None, None, None))
+        orders = np.zeros(n.value, dtype=np.int32)
+        eb = np.zeros(n.value, dtype=np.int32)
+        ctas = np.zeros(n.value, dtype=np.int32)
+        self._c(self._lib.sem_batch_info(self.h, C.byref(n), _ptr(orders, C.c_int32), _ptr(eb, C.c_int32),
+                                         _ptr(ctas, C.c_int32)))
+        return {"orders": orders.tolist(), "elems_per_block": eb.tolist(), "ctas": ctas.tolist()}
+
+    def sem_batch_destroy(self):
+        if self.h:
+            self._lib.sem_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.sem_batch_destroy()
+        except Exception:
+            pass
+

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -1170,6 +1171,355 @@ sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void*
     cudaError_t e = noalloc_scratch(&scratch);
     if (e != cudaSuccess) return cuda_fail(m, e, "cudaGetSymbolAddress");
     return launch_apply(m, dev_u, dev_Ku, scratch);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched shots
+struct sem_batch {
+    std::vector<sem_mesh*> shots;
+    cudaStream_t stream = nullptr;     // the shots' stream; NULL = legacy default
+    cudaStream_t own = nullptr;        // created when the shots use the legacy default stream
+    cudaStream_t run = nullptr;        // where the batch enqueues (graphs cannot capture the legacy stream)
+    sem_precision prec = SEM_FP64;
+    std::string err;
+    struct Class {
+        int np = 0;
+        int threads = 0, smem = 0, ctas = 0;
+        int eb = 0;
+        int32_t* d_cta_shot = nullptr;
+        int32_t* d_cta_block = nullptr;
+    };
+    std::vector<Class> classes;
+    void* d_desc = nullptr;
+    size_t desc_bytes = 0;
+    int64_t* d_step = nullptr;
+    int32_t* d_pending = nullptr;
+    std::vector<void*> allocs;
+    bool ready = false;
+    int graph_steps = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+sem_status bfail(sem_batch* b, sem_status st, const std::string& msg) {
+    if (b) b->err = msg;
+    return st;
+}
+
+void* balloc(sem_batch* b, size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    b->allocs.push_back(p);
+    return p;
+}
+
+// Frees a handle's device data so that it can be built again (used by the
+// autotuner); the handle's settings stay.
+void unbuild(sem_mesh* m) {
+    dev_free_all(m);
+    m->built = false;
+    m->step = 0;
+    m->d_src = nullptr;
+    m->src_cap = 0;
+    m->d_trace = nullptr;
+    m->d_apply_in = m->d_apply_out = nullptr;
+    for (auto& u : m->d_u) u = nullptr;
+    for (auto& x : m->d_x) x = nullptr;
+    for (auto& c : m->d_c) c = nullptr;
+    for (auto& p : m->d_part) p = nullptr;
+    m->plan = semhost::BlockPlan();
+}
+
+template <typename T>
+semdev::ShotDesc<T> shot_desc(const sem_mesh* m) {
+    semdev::ShotDesc<T> d{};
+    d.pl = m->dplan;
+    for (int k = 0; k < 3; ++k) d.u[k] = (T*)m->d_u[k];
+    for (int k = 0; k < 2; ++k) {
+        d.x[k] = (T*)m->d_x[k];
+        d.c[k] = (T*)m->d_c[k];
+        d.part[k] = (T*)m->d_part[k];
+    }
+    d.s = (const T*)m->d_s;
+    d.src_f = m->d_src;
+    d.trace = m->d_trace;
+    d.trace_cap = m->trace_cap;
+    d.src_gid = m->have_src ? (int32_t)m->node_new[(size_t)m->src_node] : -1;
+    return d;
+}
+
+// Per-shot descriptors (re-uploaded before every batch step: source tables
+// may have grown).
+sem_status upload_desc(sem_batch* b) {
+    const size_t n = b->shots.size();
+    std::vector<uint8_t> host;
+    if (b->prec == SEM_FP64) {
+        std::vector<semdev::ShotDesc<double>> v(n);
+        for (size_t i = 0; i < n; ++i) v[i] = shot_desc<double>(b->shots[i]);
+        host.assign(reinterpret_cast<uint8_t*>(v.data()), reinterpret_cast<uint8_t*>(v.data() + n));
+    } else {
+        std::vector<semdev::ShotDesc<float>> v(n);
+        for (size_t i = 0; i < n; ++i) v[i] = shot_desc<float>(b->shots[i]);
+        host.assign(reinterpret_cast<uint8_t*>(v.data()), reinterpret_cast<uint8_t*>(v.data() + n));
+    }
+    if (!b->d_desc) {
+        b->desc_bytes = host.size();
+        b->d_desc = balloc(b, b->desc_bytes);
+        if (!b->d_desc) return bfail(b, SEM_ERR_OOM, "device allocation failed");
+    }
+    if (cudaMemcpyAsync(b->d_desc, host.data(), host.size(), cudaMemcpyHostToDevice, b->run) != cudaSuccess ||
+        cudaStreamSynchronize(b->run) != cudaSuccess)
+        return bfail(b, SEM_ERR_CUDA, "descriptor upload failed");
+    return SEM_OK;
+}
+
+// Time per step of one handle (after two warm-up steps), in ms.
+sem_status time_handle(sem_mesh* m, int steps, double* ms) {
+    sem_status st;
+    if ((st = build(m)) != SEM_OK) return st;
+    if ((st = fill_source(m, steps + 2)) != SEM_OK) return st;
+    for (int k = 0; k < 2; ++k)
+        if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(m, SEM_ERR_CUDA, "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(m, SEM_ERR_CUDA, "event");
+    }
+    cudaEventRecord(e0, m->stream);
+    for (int k = 0; k < steps; ++k)
+        if ((st = launch_one_step(m, true)) != SEM_OK) break;
+    cudaEventRecord(e1, m->stream);
+    float t = 0.f;
+    if (st == SEM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        st = fail(m, SEM_ERR_CUDA, "event timing");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / steps;
+    return st;
+}
+
+// Launches of one batch step: every order class, then the counter advance.
+sem_status batch_launch_step(sem_batch* b) {
+    const bool f64 = b->prec == SEM_FP64;
+    const int mode = b->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
+    for (auto& c : b->classes) {
+        semdev::BatchArgs ba{b->d_desc, c.d_cta_shot, c.d_cta_block, b->d_step, b->d_pending};
+        const sem_mesh* m0 = nullptr;
+        for (auto* m : b->shots)
+            if (m->mesh.np == c.np) {
+                m0 = m;
+                break;
+            }
+        const void* basis = f64 ? (const void*)&m0->basis64 : (const void*)&m0->basis32;
+        cudaError_t e = semdev::launch_batch_step(c.np, f64, mode, false, ba, c.ctas, basis, c.threads, c.smem, b->run);
+        if (e != cudaSuccess) return bfail(b, SEM_ERR_CUDA, std::string("batch step launch: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = semdev::launch_batch_advance(b->d_step, b->d_pending, (int)b->shots.size(), b->run);
+    if (e != cudaSuccess) return bfail(b, SEM_ERR_CUDA, std::string("batch advance: ") + cudaGetErrorString(e));
+    return SEM_OK;
+}
+
+sem_status batch_prepare(sem_batch* b) {
+    if (b->ready) return SEM_OK;
+    if (!b->run) {
+        if (b->stream) {
+            b->run = b->stream;
+        } else {
+            if (cudaStreamCreate(&b->own) != cudaSuccess) return bfail(b, SEM_ERR_CUDA, "stream creation failed");
+            b->run = b->own;
+        }
+    }
+    const bool f64 = b->prec == SEM_FP64;
+    const int mode = b->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
+    for (auto* m : b->shots) {
+        sem_status st = build(m);
+        if (st != SEM_OK) return bfail(b, st, std::string("shot build: ") + m->err);
+    }
+    std::map<int, std::vector<int>> by_order;
+    for (size_t i = 0; i < b->shots.size(); ++i) by_order[b->shots[i]->mesh.np].push_back((int)i);
+    for (auto& kv : by_order) {
+        sem_batch::Class c;
+        c.np = kv.first;
+        std::vector<int32_t> cs, cb;
+        for (int i : kv.second) {
+            const sem_mesh* m = b->shots[(size_t)i];
+            c.threads = std::max(c.threads, m->threads);
+            c.smem = std::max(c.smem, m->smem);
+            c.eb = std::max(c.eb, m->plan.eb);
+            for (int64_t k = 0; k < m->plan.nblocks; ++k) {
+                cs.push_back(i);
+                cb.push_back((int32_t)k);
+            }
+        }
+        c.ctas = (int)cs.size();
+        c.d_cta_shot = (int32_t*)balloc(b, cs.size() * 4);
+        c.d_cta_block = (int32_t*)balloc(b, cb.size() * 4);
+        if (!c.d_cta_shot || !c.d_cta_block) return bfail(b, SEM_ERR_OOM, "device allocation failed");
+        if (cudaMemcpy(c.d_cta_shot, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(c.d_cta_block, cb.data(), cb.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bfail(b, SEM_ERR_CUDA, "cta map upload failed");
+        semdev::BatchArgs none{};
+        cudaError_t e = semdev::launch_batch_step(c.np, f64, mode, true, none, 0, nullptr, c.threads, c.smem, b->run);
+        if (e != cudaSuccess) return bfail(b, SEM_ERR_CUDA, std::string("batch kernel set-up: ") + cudaGetErrorString(e));
+        b->classes.push_back(c);
+    }
+    b->d_step = (int64_t*)balloc(b, b->shots.size() * 8);
+    b->d_pending = (int32_t*)balloc(b, b->shots.size() * 4);
+    if (!b->d_step || !b->d_pending) return bfail(b, SEM_ERR_OOM, "device allocation failed");
+    b->ready = true;
+    return SEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sem_status sem_batch_create(sem_mesh* const* shots, int32_t nshots, int32_t autotune_steps, sem_batch** out) {
+    if (!shots || nshots < 1 || !out || autotune_steps < 0) return SEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    sem_batch* b = new (std::nothrow) sem_batch();
+    if (!b) return SEM_ERR_OOM;
+    for (int32_t i = 0; i < nshots; ++i) {
+        sem_mesh* m = shots[i];
+        if (!m) {
+            delete b;
+            return SEM_ERR_INVALID_ARG;
+        }
+        for (auto* o : b->shots)
+            if (o == m) {
+                delete b;
+                return SEM_ERR_INVALID_ARG;
+            }
+        b->shots.push_back(m);
+    }
+    sem_mesh* m0 = b->shots[0];
+    b->stream = m0->stream;
+    b->prec = m0->prec;
+    for (auto* m : b->shots) {
+        if (m->prec != b->prec || m->stream != b->stream || !m->have_model || !m->have_dt) {
+            delete b;
+            return SEM_ERR_STATE;
+        }
+    }
+    // autotuner: per order, the largest shot that has not been built is
+    // timed with each candidate block size; every unbuilt shot of that order
+    // then uses the fastest
+    if (autotune_steps > 0) {
+        std::map<int, std::vector<sem_mesh*>> by_order;
+        for (auto* m : b->shots)
+            if (!m->built && m->eb_request == 0) by_order[m->mesh.np].push_back(m);
+        for (auto& kv : by_order) {
+            sem_mesh* big = kv.second[0];
+            for (auto* m : kv.second)
+                if (m->mesh.ne > big->mesh.ne) big = m;
+            const int P = kv.first * kv.first;
+            int best = 0;
+            double best_ms = 1e300;
+            for (int eb : {48, 64, 96, 128, 160, 192, 224, 256}) {
+                if ((int64_t)eb * P > 65535 || eb > std::max<int64_t>(big->mesh.ne, 48)) continue;
+                big->eb_request = eb;
+                double ms = 0.0;
+                const sem_status st = time_handle(big, autotune_steps, &ms);
+                unbuild(big);
+                if (st == SEM_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best = eb;
+                }
+            }
+            for (auto* m : kv.second) m->eb_request = best;
+        }
+    }
+    *out = b;
+    return SEM_OK;
+}
+
+sem_status sem_batch_step(sem_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return SEM_ERR_INVALID_ARG;
+    sem_status st = batch_prepare(b);
+    if (st != SEM_OK) return st;
+    if (nsteps == 0) return SEM_OK;
+    for (auto* m : b->shots) {
+        if (m->nrec > 0 && m->step + nsteps > m->trace_cap)
+            return bfail(b, SEM_ERR_INVALID_ARG, "steps beyond a shot's receiver max_steps");
+        if ((st = fill_source(m, m->step + nsteps)) != SEM_OK) return bfail(b, st, m->err);
+    }
+    if ((st = upload_desc(b)) != SEM_OK) return st;
+    const size_t n = b->shots.size();
+    std::vector<int64_t> steps(n);
+    for (size_t i = 0; i < n; ++i) steps[i] = b->shots[i]->step;
+    if (cudaMemcpyAsync(b->d_step, steps.data(), n * 8, cudaMemcpyHostToDevice, b->run) != cudaSuccess ||
+        cudaMemsetAsync(b->d_pending, 0, n * 4, b->run) != cudaSuccess ||
+        cudaStreamSynchronize(b->run) != cudaSuccess)
+        return bfail(b, SEM_ERR_CUDA, "step counters upload failed");
+    // a block of steps captured once as a CUDA graph and replayed; the
+    // remainder is launched directly
+    const int G = 16;
+    int64_t done = 0;
+    if (nsteps >= G) {
+        if (!b->graph) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(b->run, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return bfail(b, SEM_ERR_CUDA, "graph capture begin failed");
+            sem_status cst = SEM_OK;
+            for (int k = 0; k < G && cst == SEM_OK; ++k) cst = batch_launch_step(b);
+            const cudaError_t ce = cudaStreamEndCapture(b->run, &g);
+            if (cst != SEM_OK) {
+                if (g) cudaGraphDestroy(g);
+                return cst;
+            }
+            if (ce != cudaSuccess) return bfail(b, SEM_ERR_CUDA, "graph capture failed");
+            const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                b->graph = nullptr;
+                return bfail(b, SEM_ERR_CUDA, "graph instantiation failed");
+            }
+            b->graph_steps = G;
+        }
+        for (; done + G <= nsteps; done += G)
+            if (cudaGraphLaunch(b->graph, b->run) != cudaSuccess) return bfail(b, SEM_ERR_CUDA, "graph launch failed");
+    }
+    for (; done < nsteps; ++done)
+        if ((st = batch_launch_step(b)) != SEM_OK) return st;
+    // host step counters, then the open nodes of every shot
+    for (auto* m : b->shots) {
+        m->step += nsteps;
+        if ((st = launch_flush(m)) != SEM_OK) return bfail(b, st, m->err);
+        m->stepped_calls++;
+    }
+    return SEM_OK;
+}
+
+sem_status sem_batch_info(const sem_batch* b, int32_t* nclasses, int32_t* orders, int32_t* elems_per_block,
+                          int32_t* ctas) {
+    if (!b) return SEM_ERR_INVALID_ARG;
+    if (!b->ready) return SEM_ERR_STATE;
+    if (nclasses) *nclasses = (int32_t)b->classes.size();
+    for (size_t i = 0; i < b->classes.size(); ++i) {
+        if (orders) orders[i] = b->classes[i].np - 1;
+        if (elems_per_block) elems_per_block[i] = b->classes[i].eb;
+        if (ctas) ctas[i] = b->classes[i].ctas;
+    }
+    return SEM_OK;
+}
+
+const char* sem_batch_last_error(const sem_batch* b) {
+    if (!b) return "NULL batch";
+    return b->err.c_str();
+}
+
+void sem_batch_destroy(sem_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->run);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (void* p : b->allocs) cudaFree(p);
+    delete b;
 }
 
 }  // extern "C"

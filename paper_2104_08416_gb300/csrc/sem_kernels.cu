@@ -181,16 +181,16 @@ __device__ __forceinline__ BlockHdr load_hdr(const int4* hdr, int b) {
 
 __device__ __forceinline__ bool is_closed(const uint32_t* cmask, int p) { return (cmask[p >> 5] >> (p & 31)) & 1u; }
 
+// One block of one mesh, one CTA (the body of the step kernels).
 template <int NP, typename T, int MODE>
-__global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>())) sem_step_kernel(const Plan pl, const StepArgs<T> a,
-                                                                   const Basis<T> bs) {
+__device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a, const Basis<T>& bs, const int b,
+                                           unsigned char* smem_raw) {
     constexpr int P = NP * NP;
     constexpr int UPH = (P + 1) / 2;
     constexpr bool STATE = MODE != MODE_APPLY;
     constexpr bool KAHAN = MODE == MODE_KAHAN;
     constexpr bool BIL = sizeof(T) == 4;  // FP32: metric from the bilinear map; FP64: stored metric
     constexpr int VEC = 16 / sizeof(T);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     uint8_t* spk = smem_raw;
     T* su = reinterpret_cast<T*>(smem_raw + pl.max_packet);   // node values at the positions
     T* ss = su + pl.sulen_pad;                                 // staged s
@@ -198,7 +198,6 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>())) s
     T* sc = sx + (STATE ? pl.slen_pad : 0);                    // staged compensation
     T* acc = sc + (KAHAN ? pl.slen_pad : 0);                   // assembled K u at the positions
 
-    const int b = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
     const BlockHdr h = load_hdr(pl.hdr, b);
     const int64_t e0 = (int64_t)b * pl.eb;
@@ -451,6 +450,91 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>())) s
     }
 }
 
+// One step of one mesh: CTA b handles block b.
+template <int NP, typename T, int MODE>
+__global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
+    sem_step_kernel(const Plan pl, const StepArgs<T> a, const Basis<T> bs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_block<NP, T, MODE>(pl, a, bs, blockIdx.x, smem_raw);
+}
+
+// Arguments of launch k of a shot, from its level buffers (the same
+// assignment as the host's for a single mesh).
+template <typename T, int MODE>
+__device__ __forceinline__ StepArgs<T> shot_step_args(const ShotDesc<T>& d, int64_t k, int pending) {
+    StepArgs<T> a;
+    auto m3 = [](int64_t v) { return (int)(((v % 3) + 3) % 3); };
+    if (MODE == MODE_KAHAN) {
+        a.u_k = d.u[k & 1];
+        a.x_k = d.x[k & 1];
+        a.c_k = d.c[k & 1];
+        a.u_km1 = d.u[(k + 1) & 1];
+        a.x_km1 = d.x[(k + 1) & 1];
+        a.c_km1 = d.c[(k + 1) & 1];
+        a.u_kp1 = d.u[(k + 1) & 1];
+        a.x_kp1 = d.x[(k + 1) & 1];
+        a.c_kp1 = d.c[(k + 1) & 1];
+        a.u_kw = d.u[k & 1];
+        a.x_kw = d.x[k & 1];
+        a.c_kw = d.c[k & 1];
+    } else {
+        a.u_k = d.u[m3(k)];
+        a.x_k = d.u[m3(k - 1)];
+        a.c_k = nullptr;
+        a.u_km1 = d.u[m3(k - 1)];
+        a.x_km1 = d.u[m3(k - 2)];
+        a.c_km1 = nullptr;
+        a.u_kp1 = d.u[m3(k + 1)];
+        a.x_kp1 = nullptr;
+        a.c_kp1 = nullptr;
+        a.u_kw = d.u[m3(k)];
+        a.x_kw = nullptr;
+        a.c_kw = nullptr;
+    }
+    a.s = d.s;
+    a.part_rd = d.part[(k + 1) & 1];
+    a.part_wr = d.part[k & 1];
+    a.apply_out = nullptr;
+    a.src_f = d.src_f;
+    a.step = k;
+    a.src_gid = d.src_gid;
+    a.trace = d.trace;
+    a.trace_cap = d.trace_cap;
+    a.pending = pending;
+    a.vec_ok = 1;
+    return a;
+}
+
+// One step of every shot of a batch whose elements have this order: CTA i
+// handles block cta_block[i] of shot cta_shot[i]; the shot's step number and
+// whether its open nodes are pending come from device memory, so a captured
+// sequence of launches can be replayed.
+template <int NP, typename T, int MODE>
+__global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
+    sem_batch_step_kernel(const BatchArgs ba, const Basis<T> bs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Plan s_pl;
+    __shared__ StepArgs<T> s_a;
+    const int shot = ba.cta_shot[blockIdx.x];
+    if (threadIdx.x == 0) {
+        const ShotDesc<T>& d = static_cast<const ShotDesc<T>*>(ba.shots)[shot];
+        s_pl = d.pl;
+        s_a = shot_step_args<T, MODE>(d, ba.step[shot], ba.pending[shot]);
+    }
+    __syncthreads();
+    step_block<NP, T, MODE>(s_pl, s_a, bs, ba.cta_block[blockIdx.x], smem_raw);
+}
+
+// After a batch step: every shot's step number advances and its open nodes
+// are pending from now on.
+__global__ void batch_advance_kernel(int64_t* step, int32_t* pending, int nshots) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nshots) {
+        step[i] += 1;
+        pending[i] = 1;
+    }
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) sem_open_finish_kernel(const Plan pl, const StepArgs<T> a) {
     for (int k = blockIdx.x * kThreads + threadIdx.x; k < pl.nopen_nodes; k += gridDim.x * kThreads) {
@@ -614,7 +698,59 @@ cudaError_t dispatch_np(int np, const Plan& pl, const void* args, const void* ba
     }
 }
 
+template <int NP, typename T, int MODE>
+cudaError_t launch_batch_t(const BatchArgs& ba, int ctas, const void* basis, int threads, int smem, cudaStream_t st) {
+    auto kern = sem_batch_step_kernel<NP, T, MODE>;
+    kern<<<ctas, threads, smem, st>>>(ba, *static_cast<const Basis<T>*>(basis));
+    return cudaGetLastError();
+}
+
+template <int NP, typename T, int MODE>
+cudaError_t prepare_batch_t(int smem) {
+    return cudaFuncSetAttribute(sem_batch_step_kernel<NP, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <typename T, int MODE>
+cudaError_t dispatch_batch(int np, bool prepare_only, const BatchArgs& ba, int ctas, const void* basis, int threads,
+                           int smem, cudaStream_t st) {
+    switch (np) {
+#define SEM_BATCH_CASE(N)                                                                            \
+    case N:                                                                                          \
+        return prepare_only ? prepare_batch_t<N, T, MODE>(smem)                                      \
+                            : launch_batch_t<N, T, MODE>(ba, ctas, basis, threads, smem, st);
+        SEM_BATCH_CASE(2)
+        SEM_BATCH_CASE(3)
+        SEM_BATCH_CASE(4)
+        SEM_BATCH_CASE(5)
+        SEM_BATCH_CASE(6)
+        SEM_BATCH_CASE(7)
+        SEM_BATCH_CASE(8)
+        SEM_BATCH_CASE(9)
+#undef SEM_BATCH_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_step(int np, bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas,
+                              const void* basis, int threads, int smem, cudaStream_t st) {
+    if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
+    if (fp64) {
+        if (mode == MODE_THREE_LEVEL)
+            return dispatch_batch<double, MODE_THREE_LEVEL>(np, prepare_only, ba, ctas, basis, threads, smem, st);
+        return cudaErrorInvalidValue;
+    }
+    if (mode == MODE_THREE_LEVEL)
+        return dispatch_batch<float, MODE_THREE_LEVEL>(np, prepare_only, ba, ctas, basis, threads, smem, st);
+    if (mode == MODE_KAHAN) return dispatch_batch<float, MODE_KAHAN>(np, prepare_only, ba, ctas, basis, threads, smem, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cudaStream_t st) {
+    batch_advance_kernel<<<(nshots + 255) / 256, 256, 0, st>>>(step, pending, nshots);
+    return cudaGetLastError();
+}
 
 int step_threads(int eb) {
     int t = (eb + 31) / 32 * 32;

@@ -80,6 +80,33 @@ struct StepArgs {
     int vec_ok;           // node arrays 16-byte aligned (vector copies allowed)
 };
 
+// Per-shot data of a batch (device memory): the shot's plan and its level
+// buffers (three-level: u[0..2]; Kahan: u, x, c [0..1]), from which the
+// kernel forms the arguments of each step.
+template <typename T>
+struct ShotDesc {
+    Plan pl;
+    T* u[3];
+    T* x[2];
+    T* c[2];
+    T* part[2];
+    const T* s;
+    const double* src_f;
+    double* trace;
+    int64_t trace_cap;
+    int32_t src_gid;
+};
+
+// One batch launch: CTA i handles block cta_block[i] of shot cta_shot[i];
+// step[] and pending[] hold each shot's step number and pending flag.
+struct BatchArgs {
+    const void* shots;         // ShotDesc<T>[nshots]
+    const int32_t* cta_shot;
+    const int32_t* cta_block;
+    const int64_t* step;
+    const int32_t* pending;
+};
+
 // Launchers; return cudaSuccess or the launch error.
 cudaError_t launch_step(int np, bool fp64, int mode, const Plan& plan, const void* args, const void* basis,
                         int threads, int smem_bytes, cudaStream_t st);
@@ -104,5 +131,12 @@ cudaError_t launch_scale(const double* M, int64_t nn, double dt, double* s64, fl
 int step_threads(int eb);
 // Dynamic shared memory of the step kernel.
 int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, bool fp64, int mode);
+
+// Batch step (all shots of one order) and the step-counter advance.
+// prepare_only sets the kernel's shared-memory limit (done before a graph
+// capture) and launches nothing.
+cudaError_t launch_batch_step(int np, bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas,
+                              const void* basis, int threads, int smem, cudaStream_t st);
+cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cudaStream_t st);
 
 }  // namespace semdev
