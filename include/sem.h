@@ -300,8 +300,9 @@ sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void*
  *   shots[nshots]   handles (distinct); the batch does not own them and must
  *                   be destroyed before any of them.
  *   autotune_steps  0: keep each handle's block size. > 0: for each order, the
- *                   largest not yet built handle is timed for this many steps
- *                   with each candidate elements-per-block (48..256), and every
+ *                   not yet built handle whose element count is closest to
+ *                   65,536 is timed for this many steps with each candidate
+ *                   elements-per-block (48..256), and every
  *                   not yet built handle of that order without its own
  *                   sem_set_tuning uses the fastest (the timed handle is then
  *                   rebuilt from its initial state).

@@ -7,7 +7,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <thread>
 #include <mutex>
 #include <new>
 #include <string>
@@ -62,8 +64,11 @@ struct sem_mesh {
     int eb_request = 0;
     int threads_request = 0;
 
-    // device state
+    // device state (host_* hold the host part of the build until the device part)
     bool built = false;
+    bool host_ready = false;
+    std::vector<int32_t> host_quads;
+    std::vector<double> host_rho, host_vel;
     int64_t step = 0;
     int64_t stepped_calls = 0;
     semhost::BlockPlan plan;
@@ -245,8 +250,11 @@ size_t node_bytes(const sem_mesh* m) {
     return (size_t)(((m->mesh.nn + v - 1) / v + 1) * v) * tsize(m);
 }
 
-sem_status build(sem_mesh* m) {
-    if (m->built) return SEM_OK;
+// Host part of the device data: orderings, receivers, block plan, and the
+// element data in the plan's device order (kept until the device part). No
+// CUDA calls, so several handles can run it in parallel threads.
+sem_status build_host(sem_mesh* m) {
+    if (m->built || m->host_ready) return SEM_OK;
     if (!m->have_model) return fail(m, SEM_ERR_STATE, "sem_set_model must come first");
     const auto& M = m->mesh;
     const int P = M.P;
@@ -301,10 +309,24 @@ sem_status build(sem_mesh* m) {
             rd[(size_t)i] = rho_new[(size_t)en];
             vd[(size_t)i] = vel_new[(size_t)en];
         }
-        quads_new.swap(qd);
-        rho_new.swap(rd);
-        vel_new.swap(vd);
+        m->host_quads.swap(qd);
+        m->host_rho.swap(rd);
+        m->host_vel.swap(vd);
     }
+    m->host_ready = true;
+    return SEM_OK;
+}
+
+sem_status build(sem_mesh* m) {
+    if (m->built) return SEM_OK;
+    sem_status st = build_host(m);
+    if (st != SEM_OK) return st;
+    const auto& M = m->mesh;
+    const int P = M.P;
+    const auto& pl = m->plan;
+    const std::vector<int32_t>& quads_new = m->host_quads;
+    const std::vector<double>& rho_new = m->host_rho;
+    const std::vector<double>& vel_new = m->host_vel;
     const int v = vec_of(m);
     const int sulen_pad = (pl.max_sulen + v - 1) / v * v;
     const int slen_pad = (pl.max_slen + v - 1) / v * v;
@@ -315,7 +337,6 @@ sem_status build(sem_mesh* m) {
     if (std::max(m->smem, smem_apply) > kSmemLimit)
         return fail(m, SEM_ERR_UNSUPPORTED, "block plan does not fit in shared memory; lower sem_set_tuning");
 
-    sem_status st;
     uint8_t* packet;
     int32_t *hdr, *open_gid, *open_base, *open_cnt, *open_rec;
     uint32_t* epos;
@@ -401,6 +422,10 @@ sem_status build(sem_mesh* m) {
     }
     cudaError_t e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(m, e, "build");
+    std::vector<int32_t>().swap(m->host_quads);
+    std::vector<double>().swap(m->host_rho);
+    std::vector<double>().swap(m->host_vel);
+    m->host_ready = false;
     m->built = true;
     return SEM_OK;
 }
@@ -1233,6 +1258,7 @@ void unbuild(sem_mesh* m) {
     for (auto& c : m->d_c) c = nullptr;
     for (auto& p : m->d_part) p = nullptr;
     m->plan = semhost::BlockPlan();
+    m->host_ready = false;
 }
 
 template <typename T>
@@ -1337,6 +1363,17 @@ sem_status batch_prepare(sem_batch* b) {
     }
     const bool f64 = b->prec == SEM_FP64;
     const int mode = b->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
+    {
+        // host parts of all shots in parallel, then the device parts in order
+        std::atomic<size_t> next(0);
+        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> workers;
+        for (unsigned w = 0; w < hw; ++w)
+            workers.emplace_back([&]() {
+                for (size_t i = next++; i < b->shots.size(); i = next++) build_host(b->shots[i]);
+            });
+        for (auto& t : workers) t.join();
+    }
     for (auto* m : b->shots) {
         sem_status st = build(m);
         if (st != SEM_OK) return bfail(b, st, std::string("shot build: ") + m->err);
@@ -1407,17 +1444,19 @@ sem_status sem_batch_create(sem_mesh* const* shots, int32_t nshots, int32_t auto
             return SEM_ERR_STATE;
         }
     }
-    // autotuner: per order, the largest shot that has not been built is
-    // timed with each candidate block size; every unbuilt shot of that order
-    // then uses the fastest
+    // autotuner: per order, the not yet built shot whose element count is
+    // closest to 65,536 (large enough to fill the GPU, small enough to plan
+    // quickly) is timed with each candidate block size; every unbuilt shot of
+    // that order then uses the fastest
     if (autotune_steps > 0) {
         std::map<int, std::vector<sem_mesh*>> by_order;
         for (auto* m : b->shots)
             if (!m->built && m->eb_request == 0) by_order[m->mesh.np].push_back(m);
         for (auto& kv : by_order) {
             sem_mesh* big = kv.second[0];
+            auto dist = [](const sem_mesh* m) { return std::llabs((long long)m->mesh.ne - 65536LL); };
             for (auto* m : kv.second)
-                if (m->mesh.ne > big->mesh.ne) big = m;
+                if (dist(m) < dist(big)) big = m;
             const int P = kv.first * kv.first;
             int best = 0;
             double best_ms = 1e300;
