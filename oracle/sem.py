@@ -194,6 +194,48 @@ class SEM:
                 callback(n + 1, u, up)
         return u, up, traces
 
+    def misfit_gradient(self, nsteps: int, dt: float, src, receivers, d_obs):
+        """L2 trace misfit of a run from rest and its gradient with respect to
+        the per-element wave speeds, by the discrete adjoint of the leapfrog.
+
+        The run is the one of `run` (u^0 = u^-1 = 0); with traces d_r^n = u^{n+1}
+        at receiver r, J = 1/2 sum_r sum_n (d_r^n - d_obs[r, n])^2 dt. Write step
+        n as R^n = M (u^{n+1} - 2 u^n + u^{n-1}) + dt^2 K u^n - dt^2 f_n e_s = 0
+        and J's Lagrangian as J + sum_n lambda^{n+1} . R^n. Stationarity in
+        u^m (m = 1..N) gives, with lambda^{N+1} = lambda^{N+2} = 0,
+            lambda^m = 2 lambda^{m+1} - lambda^{m+2} - dt^2 M^-1 K lambda^{m+1}
+                       - M^-1 g^m,   g^m = dt sum_r (u^m_r - d_obs[r, m-1]) e_r,
+        and, since the speed c_e enters only the lumped mass (M = 1/K with
+        K = rho c^2, Section 4.1), dJ/dc_e = sum_nu dM_nu/dc_e C_nu with
+        C_nu = sum_{m=1..N} lambda^m_nu (u^m - 2 u^{m-1} + u^{m-2})_nu and
+        dM_nu/dc_e = -2 sum_{q in e, mu(q,e) = nu} w_q |J_q| / (rho_e c_e^3).
+        Returns (J, grad[E], traces[R, N]). Keeps every state: small meshes only.
+        """
+        d_obs = np.asarray(d_obs, dtype=np.float64)
+        states = [np.zeros(self.n_nodes), np.zeros(self.n_nodes)]        # u^-1, u^0
+
+        def keep(n, u, up):
+            states.append(u.copy())
+
+        _, _, traces = self.run(nsteps, dt, src=src, receivers=receivers, callback=keep)
+        J = 0.5 * dt * float(np.sum((traces - d_obs) ** 2))
+        rec_nodes = np.array([snap(self.node_xy, x, y) for x, y in np.asarray(receivers)], dtype=np.int64)
+        minv = 1.0 / self.M
+        lam1 = np.zeros(self.n_nodes)      # lambda^{m+1}
+        lam2 = np.zeros(self.n_nodes)      # lambda^{m+2}
+        C = np.zeros(self.n_nodes)
+        for m in range(nsteps, 0, -1):
+            g = np.zeros(self.n_nodes)
+            np.add.at(g, rec_nodes, dt * (traces[:, m - 1] - d_obs[:, m - 1]))
+            lam = 2.0 * lam1 - lam2 - dt * dt * (minv * self.apply_K(lam1)) - minv * g
+            # states[k] = u^{k-1}
+            a = states[m + 1] - 2.0 * states[m] + states[m - 1]
+            C += lam * a
+            lam2, lam1 = lam1, lam
+        dM = -2.0 * self.w2[None, :] * self.detJ / (self.rho * self.vel ** 3)[:, None]   # [E, P]
+        grad = np.sum(dM * C[self.conn], axis=1)
+        return J, grad, traces
+
 
 def _find(conn, nu):
     idx = np.flatnonzero(conn.ravel() == nu)

@@ -210,3 +210,41 @@ def test_apply_K_at_matches_full():
     u = np.sin(3 * S.node_xy[:, 0]) * np.cos(2 * S.node_xy[:, 1])
     nodes = np.array([0, 5, 17, S.n_nodes - 1])
     np.testing.assert_allclose(S.apply_K_at(u, nodes), S.apply_K(u)[nodes], atol=1e-13)
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """The oracle's discrete adjoint against central finite differences of the
+    misfit in single element speeds (layered-like heterogeneous model)."""
+    m = gen.graded(6, seed=11)
+    p, n = 3, 160
+    vel_true = np.asarray(m["vel"], dtype=np.float64)
+    vel = vel_true * (1.0 + 0.05 * np.sin(np.arange(vel_true.size)))
+    rec = np.array([[0.1, 0.9], [0.8, 0.85], [0.5, 0.2], [0.95, 0.4]])
+    src = (m["src_xy"][0], m["src_xy"][1], m["f0"], m["t0"], m["amp"])
+    S_true = sem.SEM(m["coords"], m["quads"], p, vel_true, m["rho"])
+    dt = 0.3 * S_true.cfl_dt()
+    _, _, d_obs = S_true.run(n, dt, src=src, receivers=rec)
+    S = sem.SEM(m["coords"], m["quads"], p, vel, m["rho"])
+    J, grad, _ = S.misfit_gradient(n, dt, src, rec, d_obs)
+    assert J > 0
+    for e in (0, 7, 15, 22, 35):
+        h = 1e-5 * vel[e]
+        vp, vm = vel.copy(), vel.copy()
+        vp[e] += h
+        vm[e] -= h
+        Jp = 0.5 * dt * np.sum((sem.SEM(m["coords"], m["quads"], p, vp, m["rho"]).run(n, dt, src=src, receivers=rec)[2] - d_obs) ** 2)
+        Jm = 0.5 * dt * np.sum((sem.SEM(m["coords"], m["quads"], p, vm, m["rho"]).run(n, dt, src=src, receivers=rec)[2] - d_obs) ** 2)
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(fd - grad[e]) <= 1e-5 * np.abs(grad).max(), (e, fd, grad[e])
+
+
+def test_adjoint_gradient_vanishes_at_the_true_model():
+    m = gen.graded(5, seed=3)
+    p, n = 2, 80
+    rec = np.array([[0.2, 0.8], [0.7, 0.7]])
+    src = (m["src_xy"][0], m["src_xy"][1], m["f0"], m["t0"], m["amp"])
+    S = sem.SEM(m["coords"], m["quads"], p, m["vel"], m["rho"])
+    dt = 0.3 * S.cfl_dt()
+    _, _, d_obs = S.run(n, dt, src=src, receivers=rec)
+    J, grad, _ = S.misfit_gradient(n, dt, src, rec, d_obs)
+    assert J == 0.0 and np.all(grad == 0.0)
