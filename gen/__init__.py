@@ -203,6 +203,24 @@ def batched(n_shots: int = 64, nmin: int = 64, nmax: int = 1024, orders=(3, 4, 5
     return shots
 
 
+def adjoint_case(n: int = 256, n_shots: int = 8, n_receivers: int = 64, width: float = 1000.0,
+                 f0: float = 30.0, smooth: int = 16, seed: int = DEFAULT_SEED) -> dict:
+    """Velocity-gradient case: a layered true model on n x n quads over a
+    width x width square (surface at the top), a start model smoothed from it
+    by a (2 smooth + 1)^2 moving average over the element grid, n_shots
+    sources evenly spaced just below the surface and n_receivers on it."""
+    m = layered(n, n, width=width, depth=width, seed=seed, f0=f0, n_receivers=n_receivers)
+    v = np.asarray(m["vel"], dtype=np.float64).reshape(n, n)
+    pad = np.pad(v, smooth, mode="edge")
+    c = np.cumsum(np.cumsum(np.pad(pad, ((1, 0), (1, 0))), axis=0), axis=1)
+    k = 2 * smooth + 1
+    sm = (c[k:, k:] - c[:-k, k:] - c[k:, :-k] + c[:-k, :-k]) / (k * k)
+    xs = (np.arange(n_shots) + 0.5) * (width / n_shots)
+    return dict(mesh=m, vel_true=m["vel"], vel_start=sm.ravel(),
+                sources=[(float(x), 0.97 * width) for x in xs], receivers=m["receivers"],
+                f0=f0, t0=1.2 / f0, amp=1.0)
+
+
 def config(name: str, seed: int = DEFAULT_SEED) -> dict:
     """The three single-GPU workloads by name, with their step counts."""
     if name == "homogeneous_32":

@@ -115,8 +115,10 @@ sem_status sem_reorder(sem_mesh* m, sem_ordering kind, uint64_t seed);
 
 /* Per-element material (Section 4.1: rho and K = rho c^2, constant per
  * element as assumed before Eq. u_change). vel[ne] > 0 (wave speed c);
- * rho[ne] > 0, or NULL for rho = 1. Original element order. Before the first
- * step only. */
+ * rho[ne] > 0, or NULL for rho = 1. Original element order. Called again
+ * after the device data exists, it recomputes the geometric factors, the
+ * lumped mass and dt^2/M on the device and keeps the plan and the state (the
+ * way to re-evaluate a misfit for a new model without rebuilding). */
 sem_status sem_set_model(sem_mesh* m, const double* vel, const double* rho);
 
 /* Point source (Eq. def_u_2 source term; Algorithm 3): a Ricker wavelet
@@ -332,6 +334,27 @@ const char* sem_batch_last_error(const sem_batch* b);
 
 /* Free the batch (not its handles). NULL is a no-op. */
 void sem_batch_destroy(sem_batch* b);
+
+/* L2 trace misfit and its gradient with respect to the per-element wave
+ * speeds, by the discrete adjoint of the leapfrog time step (the paper has no
+ * adjoint; the speed enters the scheme only through the lumped mass of
+ * Eq. Abar with M = 1/K, K = rho c^2).
+ *   d_obs[nrec][nsteps]  observed traces, receiver-major, host array;
+ *   misfit               J = 1/2 sum_r sum_n (d_r^n - d_obs[r][n])^2 dt, where
+ *                        d_r^n = u^{n+1} at receiver r (as sem_read_traces);
+ *   grad_vel[ne]         dJ/dc_e, original element order (NULL: misfit only).
+ * The run starts from rest (u^0 = u^-1 = 0) with the handle's source; the
+ * adjoint lambda^m = 2 lambda^{m+1} - lambda^{m+2} - s (K lambda^{m+1} +
+ * g^m / dt^2), g^m = dt (d^{m-1} - d_obs^{m-1}) at the receivers, runs backward
+ * from lambda^{N+1} = lambda^{N+2} = 0 and dJ/dc_e = -(2/c_e) sum_q w_q |J_q| /
+ * (rho_e c_e^2) sum_{m} lambda^m (u^m - 2 u^{m-1} + u^{m-2}) at the element's
+ * nodes. Forward states are kept as checkpoints every checkpoint_every steps
+ * (0 = ceil(sqrt(nsteps))) and recomputed one segment at a time on the way
+ * back (sqrt(T) memory). Needs receivers with max_steps >= nsteps; SEM_FP64 or
+ * SEM_FP32 handles (SEM_FP32_KAHAN returns SEM_ERR_UNSUPPORTED). Leaves the
+ * handle at step nsteps of the forward run. Synchronises. */
+sem_status sem_misfit_gradient(sem_mesh* m, const double* d_obs, int64_t nsteps, int64_t checkpoint_every,
+                               double* misfit, double* grad_vel);
 
 /* Message of the last failing call on this handle ("" if none). Never NULL. */
 const char* sem_last_error(const sem_mesh* m);

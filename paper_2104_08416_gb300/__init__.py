@@ -38,7 +38,7 @@ EXPORTS = (
     "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info",
     "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
-    "sem_apply_stiffness_dev_noalloc", "sem_batch_create", "sem_batch_step", "sem_batch_info",
+    "sem_apply_stiffness_dev_noalloc", "sem_misfit_gradient", "sem_batch_create", "sem_batch_step", "sem_batch_info",
     "sem_batch_last_error", "sem_batch_destroy", "sem_last_error", "sem_destroy",
 )
 
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "sem_traffic_model": (_P, _D, _D),
         "sem_transfer_bytes": (_P, _I64, _I64),
         "sem_apply_stiffness_dev_noalloc": (_P, _P, _P),
+        "sem_misfit_gradient": (_P, _D, C.c_int64, C.c_int64, _D, _D),
         "sem_batch_create": (C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(_P)),
         "sem_batch_step": (_P, C.c_int64),
         "sem_batch_info": (_P, _I32, _I32, _I32, _I32),
@@ -360,6 +361,16 @@ class SEM:
         """K u on device arrays (storage order, handle's storage type) without
         any allocation; enqueued on the handle's stream, not synchronised."""
         self._c(self._lib.sem_apply_stiffness_dev_noalloc(self.h, _P(dev_u_ptr), _P(dev_Ku_ptr)))
+
+    def sem_misfit_gradient(self, d_obs, nsteps: int, checkpoint_every: int = 0, gradient: bool = True):
+        """(J, dJ/dvel) of a run from rest against observed traces
+        d_obs[nrec][nsteps]; the gradient is None when gradient=False."""
+        obs = np.ascontiguousarray(d_obs, dtype=np.float64)
+        J = C.c_double()
+        g = np.zeros(self.n_elems, dtype=np.float64) if gradient else None
+        self._c(self._lib.sem_misfit_gradient(self.h, _ptr(obs, C.c_double), int(nsteps), int(checkpoint_every),
+                                              C.byref(J), _ptr(g, C.c_double) if gradient else None))
+        return J.value, g
 
     def sem_destroy(self):
         if getattr(self, "h", None):

@@ -98,6 +98,18 @@ struct sem_mesh {
     double* d_src = nullptr;
     int64_t src_cap = 0;
     double* d_trace = nullptr;
+    // adjoint (allocated by the first sem_misfit_gradient)
+    int64_t adj_steps = 0, adj_kc = 0;
+    void* d_lam[3] = {nullptr, nullptr, nullptr};
+    void* d_klam = nullptr;
+    double* d_C = nullptr;
+    double* d_obs = nullptr;
+    double* d_grad = nullptr;
+    int32_t* d_conn_dev = nullptr;
+    int32_t* d_rec_node = nullptr;
+    int32_t* d_rec_row = nullptr;
+    std::vector<void*> d_chk;   // per checkpoint: u^{n0}, u^{n0-1}
+    std::vector<void*> d_seg;   // recomputed states of one segment
     // measurement
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -430,7 +442,37 @@ sem_status build(sem_mesh* m) {
     return SEM_OK;
 }
 
-// Buffers of level m.
+// Element data of the current model in the plan's device order.
+void device_order_model(const sem_mesh* m, std::vector<double>& rho_d, std::vector<double>& vel_d) {
+    const int64_t ne = m->mesh.ne;
+    rho_d.resize((size_t)ne);
+    vel_d.resize((size_t)ne);
+    for (int64_t i = 0; i < ne; ++i) {
+        const int64_t eo = m->elem_order[(size_t)m->plan.dev_order[(size_t)i]];
+        rho_d[(size_t)i] = m->rho[(size_t)eo];
+        vel_d[(size_t)i] = m->vel[(size_t)eo];
+    }
+}
+
+// New model on a built handle: geometry factors, lumped mass and dt^2/M are
+// recomputed on the device; the plan and the state stay.
+sem_status refresh_model(sem_mesh* m) {
+    std::vector<double> rd, vd;
+    device_order_model(m, rd, vd);
+    SEM_CUDA(cudaMemcpyAsync(m->d_rho, rd.data(), rd.size() * 8, cudaMemcpyHostToDevice, m->stream));
+    SEM_CUDA(cudaMemcpyAsync(m->d_vel, vd.data(), vd.size() * 8, cudaMemcpyHostToDevice, m->stream));
+    m->h2d += (int64_t)(rd.size() + vd.size()) * 8;
+    SEM_CUDA(semdev::launch_geometry(m->mesh.np, m->mesh.ne, m->d_coords, m->d_quads, m->d_rho, m->d_vel, m->basis64,
+                                     const_cast<float4*>(m->dplan.coef), m->d_G64, m->d_mloc, m->stream));
+    SEM_CUDA(semdev::launch_mass(m->dplan, m->mesh.np, m->d_mloc, (double*)m->d_part[0], m->d_M, m->stream));
+    if (m->have_dt)
+        SEM_CUDA(semdev::launch_scale(m->d_M, m->mesh.nn, m->dt, fp64(m) ? (double*)m->d_s : nullptr,
+                                      fp64(m) ? nullptr : (float*)m->d_s, m->stream));
+    SEM_CUDA(cudaStreamSynchronize(m->stream));
+    return SEM_OK;
+}
+
+// Buffers of level m.// Buffers of level m.
 void* level_u(const sem_mesh* m, int64_t lv) {
     return m->prec == SEM_FP32_KAHAN ? m->d_u[lv & 1] : m->d_u[((lv % 3) + 3) % 3];
 }
@@ -688,7 +730,6 @@ sem_status sem_reorder(sem_mesh* m, sem_ordering kind, uint64_t seed) {
 
 sem_status sem_set_model(sem_mesh* m, const double* vel, const double* rho) {
     if (!m || !vel) return m ? fail(m, SEM_ERR_INVALID_ARG, "vel is NULL") : SEM_ERR_INVALID_ARG;
-    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_model after the device data was built");
     const int64_t ne = m->mesh.ne;
     for (int64_t e = 0; e < ne; ++e) {
         if (!(vel[e] > 0.0) || !std::isfinite(vel[e])) return fail(m, SEM_ERR_INVALID_ARG, "vel must be > 0");
@@ -698,6 +739,7 @@ sem_status sem_set_model(sem_mesh* m, const double* vel, const double* rho) {
     if (rho) m->rho.assign(rho, rho + ne);
     else m->rho.assign((size_t)ne, 1.0);
     m->have_model = true;
+    if (m->built) return refresh_model(m);
     return SEM_OK;
 }
 
@@ -1150,6 +1192,169 @@ void sem_destroy(sem_mesh* m) {
     for (auto& pr : m->ev_open) m->ev_pool.push_back(pr.first), m->ev_pool.push_back(pr.second);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     delete m;
+}
+
+// ------------------------------------------------ misfit gradient (adjoint)
+}  // extern "C"
+
+namespace {
+
+sem_status adjoint_alloc(sem_mesh* m, int64_t nsteps, int64_t kc) {
+    const size_t nb = node_bytes(m);
+    if (!m->d_C) {
+        for (auto& l : m->d_lam)
+            if (!(l = dev_alloc(m, nb))) return fail(m, SEM_ERR_OOM, "device allocation failed");
+        m->d_klam = dev_alloc(m, nb);
+        m->d_C = (double*)dev_alloc(m, (size_t)m->mesh.nn * 8);
+        m->d_grad = (double*)dev_alloc(m, (size_t)m->mesh.ne * 8);
+        m->d_rec_node = (int32_t*)dev_alloc(m, (size_t)std::max(m->nrec, 1) * 4);
+        m->d_rec_row = (int32_t*)dev_alloc(m, (size_t)std::max(m->nrec, 1) * 4);
+        if (!m->d_klam || !m->d_C || !m->d_grad || !m->d_rec_node || !m->d_rec_row)
+            return fail(m, SEM_ERR_OOM, "device allocation failed");
+        // connectivity in the device element order (new node ids)
+        const auto& M = m->mesh;
+        std::vector<int32_t> cd((size_t)(M.ne * M.P));
+        for (int64_t i = 0; i < M.ne; ++i) {
+            const int64_t eo = m->elem_order[(size_t)m->plan.dev_order[(size_t)i]];
+            for (int q = 0; q < M.P; ++q)
+                cd[(size_t)(i * M.P + q)] = (int32_t)m->node_new[(size_t)M.conn[(size_t)(eo * M.P + q)]];
+        }
+        sem_status st = upload(m, &m->d_conn_dev, cd.data(), cd.size());
+        if (st != SEM_OK) return st;
+        std::vector<int32_t> rn((size_t)m->nrec), rr((size_t)m->nrec);
+        for (int32_t r = 0; r < m->nrec; ++r) {
+            rn[(size_t)r] = (int32_t)m->node_new[(size_t)m->rec_nodes[(size_t)r]];
+            rr[(size_t)r] = m->rec_row[(size_t)r] >= 0 ? m->rec_row[(size_t)r] : r;
+        }
+        SEM_CUDA(cudaMemcpyAsync(m->d_rec_node, rn.data(), rn.size() * 4, cudaMemcpyHostToDevice, m->stream));
+        SEM_CUDA(cudaMemcpyAsync(m->d_rec_row, rr.data(), rr.size() * 4, cudaMemcpyHostToDevice, m->stream));
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+    }
+    if (nsteps > m->adj_steps || kc != m->adj_kc) {
+        // checkpoints and segment buffers (the old ones stay until sem_destroy)
+        const int64_t nchk = (nsteps + kc - 1) / kc + 1;
+        m->d_chk.assign((size_t)(2 * nchk), nullptr);
+        for (auto& c : m->d_chk)
+            if (!(c = dev_alloc(m, nb))) return fail(m, SEM_ERR_OOM, "device allocation failed (checkpoints)");
+        m->d_seg.assign((size_t)(kc + 1), nullptr);
+        for (auto& c : m->d_seg)
+            if (!(c = dev_alloc(m, nb))) return fail(m, SEM_ERR_OOM, "device allocation failed (segment)");
+        m->d_obs = (double*)dev_alloc(m, (size_t)std::max(m->nrec, 1) * (size_t)nsteps * 8);
+        if (!m->d_obs) return fail(m, SEM_ERR_OOM, "device allocation failed");
+        m->adj_steps = nsteps;
+        m->adj_kc = kc;
+    }
+    return SEM_OK;
+}
+
+sem_status copy_dev(sem_mesh* m, void* dst, const void* src) {
+    SEM_CUDA(cudaMemcpyAsync(dst, src, (size_t)m->mesh.nn * tsize(m), cudaMemcpyDeviceToDevice, m->stream));
+    return SEM_OK;
+}
+
+// n steps from a stored level (one launch per step, open nodes completed).
+sem_status run_steps(sem_mesh* m, int64_t n) {
+    sem_status st;
+    for (int64_t k = 0; k < n; ++k)
+        if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+    return n > 0 ? launch_flush(m) : SEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sem_status sem_misfit_gradient(sem_mesh* m, const double* d_obs, int64_t nsteps, int64_t checkpoint_every,
+                               double* misfit, double* grad_vel) {
+    if (!m || !d_obs || nsteps < 1 || checkpoint_every < 0) return SEM_ERR_INVALID_ARG;
+    if (m->prec == SEM_FP32_KAHAN)
+        return fail(m, SEM_ERR_UNSUPPORTED, "the adjoint runs on SEM_FP64 or SEM_FP32 (three-level) handles");
+    if (!m->have_model || !m->have_dt) return fail(m, SEM_ERR_STATE, "model and dt must be set first");
+    if (m->nrec < 1 || m->trace_cap < nsteps)
+        return fail(m, SEM_ERR_STATE, "receivers with max_steps >= nsteps must be set first");
+    sem_status st = build(m);
+    if (st != SEM_OK) return st;
+    if ((st = fill_source(m, nsteps)) != SEM_OK) return st;
+    int64_t kc = checkpoint_every;
+    if (kc == 0) kc = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)nsteps)));
+    kc = std::min(kc, nsteps);
+    if ((st = adjoint_alloc(m, nsteps, kc)) != SEM_OK) return st;
+    const bool f64 = fp64(m);
+    const size_t nb = (size_t)m->mesh.nn * tsize(m);
+    const int64_t nchk = (nsteps + kc - 1) / kc;
+    // forward from rest, a checkpoint (u^{n0}, u^{n0-1}) every kc steps
+    for (auto* u : m->d_u) SEM_CUDA(cudaMemsetAsync(u, 0, nb, m->stream));
+    SEM_CUDA(cudaMemsetAsync(m->d_trace, 0, (size_t)m->nrec * (size_t)m->trace_cap * 8, m->stream));
+    m->step = 0;
+    for (int64_t c = 0; c < nchk; ++c) {
+        const int64_t n0 = c * kc;
+        if ((st = copy_dev(m, m->d_chk[(size_t)(2 * c)], level_u(m, n0))) != SEM_OK) return st;
+        if ((st = copy_dev(m, m->d_chk[(size_t)(2 * c + 1)], level_x(m, n0))) != SEM_OK) return st;
+        if ((st = run_steps(m, std::min(kc, nsteps - n0))) != SEM_OK) return st;
+    }
+    // the final state, restored at the end
+    void* fin_u = m->d_chk[(size_t)(2 * nchk)];
+    void* fin_x = m->d_chk[(size_t)(2 * nchk + 1)];
+    if ((st = copy_dev(m, fin_u, level_u(m, nsteps))) != SEM_OK) return st;
+    if ((st = copy_dev(m, fin_x, level_x(m, nsteps))) != SEM_OK) return st;
+    // misfit from the traces
+    std::vector<double> tr((size_t)m->nrec * (size_t)nsteps);
+    if ((st = sem_read_traces(m, tr.data(), nsteps)) != SEM_OK) return st;
+    double J = 0.0;
+    for (size_t k = 0; k < tr.size(); ++k) {
+        const double d = tr[k] - d_obs[k];
+        J += d * d;
+    }
+    J *= 0.5 * m->dt;
+    if (misfit) *misfit = J;
+    if (!grad_vel) {
+        m->step = nsteps;
+        return SEM_OK;
+    }
+    SEM_CUDA(cudaMemcpyAsync(m->d_obs, d_obs, tr.size() * 8, cudaMemcpyHostToDevice, m->stream));
+    m->h2d += (int64_t)(tr.size() * 8);
+    // backward: lambda^{N+1} = lambda^{N+2} = 0, segments last to first
+    for (auto* l : m->d_lam) SEM_CUDA(cudaMemsetAsync(l, 0, nb, m->stream));
+    SEM_CUDA(cudaMemsetAsync(m->d_C, 0, (size_t)m->mesh.nn * 8, m->stream));
+    auto lam = [&](int64_t k) { return m->d_lam[(size_t)(((k % 3) + 3) % 3)]; };
+    const double inv_dt = 1.0 / m->dt;
+    for (int64_t c = nchk - 1; c >= 0; --c) {
+        const int64_t n0 = c * kc, n1 = std::min(n0 + kc, nsteps);
+        // recompute u^{n0..n1} from the checkpoint
+        if ((st = copy_dev(m, level_u(m, n0), m->d_chk[(size_t)(2 * c)])) != SEM_OK) return st;
+        if ((st = copy_dev(m, level_x(m, n0), m->d_chk[(size_t)(2 * c + 1)])) != SEM_OK) return st;
+        m->step = n0;
+        if ((st = copy_dev(m, m->d_seg[0], m->d_chk[(size_t)(2 * c)])) != SEM_OK) return st;
+        for (int64_t j = 1; j <= n1 - n0; ++j) {
+            if ((st = run_steps(m, 1)) != SEM_OK) return st;
+            if ((st = copy_dev(m, m->d_seg[(size_t)j], level_u(m, n0 + j))) != SEM_OK) return st;
+        }
+        auto u_at = [&](int64_t k) -> const void* {
+            return k >= n0 ? m->d_seg[(size_t)(k - n0)] : m->d_chk[(size_t)(2 * c + 1)];
+        };
+        for (int64_t mm = n1; mm > n0; --mm) {
+            if ((st = launch_apply(m, lam(mm + 1), m->d_klam, m->d_part[0])) != SEM_OK) return st;
+            SEM_CUDA(semdev::launch_adjoint_update(f64, m->mesh.nn, lam(mm), lam(mm + 1), lam(mm + 2), m->d_s, m->d_klam,
+                                                   m->stream));
+            SEM_CUDA(semdev::launch_adjoint_receivers(f64, m->nrec, lam(mm), m->d_s, m->d_rec_node, m->d_rec_row,
+                                                      m->d_trace, m->trace_cap, m->d_obs, nsteps, mm, inv_dt,
+                                                      m->stream));
+            SEM_CUDA(semdev::launch_correlate(f64, m->mesh.nn, m->d_C, lam(mm), u_at(mm), u_at(mm - 1), u_at(mm - 2),
+                                              m->stream));
+        }
+    }
+    SEM_CUDA(semdev::launch_gradient(m->mesh.ne, m->mesh.P, m->d_conn_dev, m->d_mloc, m->d_C, m->d_vel, m->d_grad,
+                                     m->stream));
+    std::vector<double> g((size_t)m->mesh.ne);
+    SEM_CUDA(cudaMemcpyAsync(g.data(), m->d_grad, g.size() * 8, cudaMemcpyDeviceToHost, m->stream));
+    m->d2h += (int64_t)(g.size() * 8);
+    // restore the state after the forward run
+    if ((st = copy_dev(m, level_u(m, nsteps), fin_u)) != SEM_OK) return st;
+    if ((st = copy_dev(m, level_x(m, nsteps), fin_x)) != SEM_OK) return st;
+    SEM_CUDA(cudaStreamSynchronize(m->stream));
+    m->step = nsteps;
+    for (int64_t i = 0; i < m->mesh.ne; ++i) grad_vel[(size_t)m->elem_order[(size_t)m->plan.dev_order[(size_t)i]]] = g[(size_t)i];
+    return SEM_OK;
 }
 
 // ------------------------------------------------ allocation-free variant

@@ -661,6 +661,51 @@ __global__ void scale_kernel(const double* __restrict__ M, int64_t nn, double dt
     }
 }
 
+// ------------------------------------------------------------ adjoint
+// lambda^m = 2 lambda^{m+1} - lambda^{m+2} - s (K lambda^{m+1}) (the
+// leapfrog recurrence run backward; receiver residuals are added after).
+template <typename T>
+__global__ void adjoint_update_kernel(int64_t nn, T* lam, const T* __restrict__ lam1, const T* __restrict__ lam2,
+                                      const T* __restrict__ s, const T* __restrict__ klam1) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
+        lam[g] = fma_rn(-s[g], klam1[g], sub_rn(add_rn(lam1[g], lam1[g]), lam2[g]));
+}
+
+// Receiver residuals of step m: lambda^m[node_r] -= s (trace_r^{m-1} - obs_r^{m-1}) / dt,
+// receivers in ascending order by one thread (two receivers may share a node).
+template <typename T>
+__global__ void adjoint_receivers_kernel(int nrec, T* lam, const T* __restrict__ s, const int32_t* rec_node,
+                                         const int32_t* rec_row, const double* trace, int64_t trace_cap,
+                                         const double* obs, int64_t obs_cap, int64_t m, double inv_dt) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int r = 0; r < nrec; ++r) {
+        const int32_t g = rec_node[r];
+        const double res = trace[(int64_t)rec_row[r] * trace_cap + m - 1] - obs[(int64_t)r * obs_cap + m - 1];
+        lam[g] = (T)((double)lam[g] - (double)s[g] * res * inv_dt);
+    }
+}
+
+// C += lambda^m (u^m - 2 u^{m-1} + u^{m-2}), accumulated in FP64.
+template <typename T>
+__global__ void correlate_kernel(int64_t nn, double* C, const T* __restrict__ lam, const T* __restrict__ um,
+                                 const T* __restrict__ um1, const T* __restrict__ um2) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        const double a = ((double)um[g] - 2.0 * (double)um1[g]) + (double)um2[g];
+        C[g] = fma((double)lam[g], a, C[g]);
+    }
+}
+
+// dJ/dc_e = sum_q dM/dc_e C = -(2 / c_e) sum_q mloc[e, q] C[node(e, q)],
+// mloc = w_q |J_q| / (rho_e c_e^2); one thread per element, points in order.
+__global__ void gradient_kernel(int64_t ne, int P, const int32_t* __restrict__ conn, const double* __restrict__ mloc,
+                                const double* __restrict__ C, const double* __restrict__ vel, double* grad) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < P; ++q) acc = fma(mloc[e * P + q], C[conn[e * P + q]], acc);
+        grad[e] = -2.0 * acc / vel[e];
+    }
+}
+
 int grid_for(int64_t n, int threads) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -797,6 +842,50 @@ cudaError_t launch_open_finish(bool fp64, int mode, const Plan& pl, const void* 
         else if (mode == MODE_KAHAN) sem_open_finish_kernel<float, MODE_KAHAN><<<grid, kThreads, 0, st>>>(pl, a);
         else sem_open_finish_kernel<float, MODE_APPLY><<<grid, kThreads, 0, st>>>(pl, a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_update(bool fp64, int64_t nn, void* lam, const void* lam1, const void* lam2, const void* s,
+                                  const void* klam1, cudaStream_t st) {
+    const int grid = grid_for(nn, kThreads);
+    if (fp64)
+        adjoint_update_kernel<double><<<grid, kThreads, 0, st>>>(nn, (double*)lam, (const double*)lam1,
+                                                                (const double*)lam2, (const double*)s,
+                                                                (const double*)klam1);
+    else
+        adjoint_update_kernel<float><<<grid, kThreads, 0, st>>>(nn, (float*)lam, (const float*)lam1,
+                                                               (const float*)lam2, (const float*)s,
+                                                               (const float*)klam1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_receivers(bool fp64, int nrec, void* lam, const void* s, const int32_t* rec_node,
+                                     const int32_t* rec_row, const double* trace, int64_t trace_cap, const double* obs,
+                                     int64_t obs_cap, int64_t m, double inv_dt, cudaStream_t st) {
+    if (fp64)
+        adjoint_receivers_kernel<double><<<1, 32, 0, st>>>(nrec, (double*)lam, (const double*)s, rec_node, rec_row,
+                                                           trace, trace_cap, obs, obs_cap, m, inv_dt);
+    else
+        adjoint_receivers_kernel<float><<<1, 32, 0, st>>>(nrec, (float*)lam, (const float*)s, rec_node, rec_row,
+                                                          trace, trace_cap, obs, obs_cap, m, inv_dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correlate(bool fp64, int64_t nn, double* C, const void* lam, const void* um, const void* um1,
+                             const void* um2, cudaStream_t st) {
+    const int grid = grid_for(nn, kThreads);
+    if (fp64)
+        correlate_kernel<double><<<grid, kThreads, 0, st>>>(nn, C, (const double*)lam, (const double*)um,
+                                                           (const double*)um1, (const double*)um2);
+    else
+        correlate_kernel<float><<<grid, kThreads, 0, st>>>(nn, C, (const float*)lam, (const float*)um,
+                                                          (const float*)um1, (const float*)um2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(int64_t ne, int P, const int32_t* conn, const double* mloc, const double* C,
+                            const double* vel, double* grad, cudaStream_t st) {
+    gradient_kernel<<<grid_for(ne, kThreads), kThreads, 0, st>>>(ne, P, conn, mloc, C, vel, grad);
     return cudaGetLastError();
 }
 

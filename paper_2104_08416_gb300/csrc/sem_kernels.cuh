@@ -126,6 +126,20 @@ cudaError_t launch_mass(const Plan& plan, int np, const double* mloc, double* pa
 // s = dt^2 / M (FP64 arithmetic, rounded once to the storage type).
 cudaError_t launch_scale(const double* M, int64_t nn, double dt, double* s64, float* s32, cudaStream_t st);
 
+// Discrete adjoint of the leapfrog (FP64 or FP32 three-level storage): the
+// backward update, the receiver residuals of step m, the correlation
+// C += lambda^m (u^m - 2u^{m-1} + u^{m-2}) and the per-element gradient
+// dJ/dc_e = -(2/c_e) sum_q mloc[e,q] C[conn[e,q]] (device element order).
+cudaError_t launch_adjoint_update(bool fp64, int64_t nn, void* lam, const void* lam1, const void* lam2, const void* s,
+                                  const void* klam1, cudaStream_t st);
+cudaError_t launch_adjoint_receivers(bool fp64, int nrec, void* lam, const void* s, const int32_t* rec_node,
+                                     const int32_t* rec_row, const double* trace, int64_t trace_cap, const double* obs,
+                                     int64_t obs_cap, int64_t m, double inv_dt, cudaStream_t st);
+cudaError_t launch_correlate(bool fp64, int64_t nn, double* C, const void* lam, const void* um, const void* um1,
+                             const void* um2, cudaStream_t st);
+cudaError_t launch_gradient(int64_t ne, int P, const int32_t* conn, const double* mloc, const double* C,
+                            const double* vel, double* grad, cudaStream_t st);
+
 // Threads of the step kernel for a block of eb elements (one per element,
 // rounded up to whole warps).
 int step_threads(int eb);
