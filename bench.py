@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--precision", default="fp32_kahan", choices=["fp32_kahan", "fp64", "fp32"])
     ap.add_argument("--ordering", default="hilbert", choices=["hilbert", "rowmajor", "random", "none"])
     ap.add_argument("--n", type=int, default=512, help="quads per side of the graded mesh")
-    ap.add_argument("--workload", default="graded", choices=["graded", "layered", "batched"],
+    ap.add_argument("--workload", default="graded", choices=["graded", "layered", "batched", "adjoint"],
                     help="graded 512x512 (default), the layered 4096x1024 model (67M nodes), or batched shots")
     ap.add_argument("--batch-shots", type=int, default=64)
     ap.add_argument("--batch-nmin", type=int, default=64)
@@ -320,6 +320,66 @@ def run_batched(args, P, torch):
     print(json.dumps(line))
 
 
+def run_adjoint(args, P, torch):
+    """Velocity gradient of the L2 trace misfit: 256 x 256 quads, order 4,
+    layered true model, smoothed start model, 8 shots, 3000 steps; the
+    gradient from sem_misfit_gradient (forward with checkpoints, recompute,
+    adjoint), FP64 and FP32, timed per gradient over all shots."""
+    from paper_2104_08416_gb300.autograd import Survey
+    c = gen.adjoint_case()
+    m = c["mesh"]
+    n = args.steps if args.steps != 2000 else 3000
+    h = P.SEM(m["coords"], m["quads"], 4, "fp64")
+    h.sem_reorder(args.ordering)
+    h.sem_set_model(c["vel_true"], m["rho"])
+    dt = 0.3 * h.sem_cfl_dt()
+    N = h.n_nodes
+    h.sem_destroy()
+    d_obs = []
+    for sx, sy in c["sources"]:
+        t = P.SEM(m["coords"], m["quads"], 4, "fp64")
+        t.sem_reorder(args.ordering)
+        t.sem_set_model(c["vel_true"], m["rho"])
+        t.sem_set_source(c["f0"], c["t0"], c["amp"], sx, sy)
+        t.sem_set_receivers(c["receivers"], n)
+        t.sem_set_dt(dt)
+        t.sem_step(n)
+        d_obs.append(t.sem_read_traces())
+        t.sem_destroy()
+    v0 = np.asarray(c["vel_start"], dtype=np.float64)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        sv = Survey(m["coords"], m["quads"], 4, c["sources"], c["receivers"], d_obs, n, dt, c["f0"], c["t0"],
+                    c["amp"], rho=m["rho"], precision=prec, ordering=args.ordering)
+        sv.misfit_and_gradient(v0)                     # warm-up (builds the handles)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 2
+        for _ in range(reps):
+            J, g = sv.misfit_and_gradient(v0)
+        torch.cuda.synchronize()
+        el = (time.perf_counter() - t0) / reps
+        sv.close()
+        res[prec] = (J, g, el)
+    J64, g64, t64 = res["fp64"]
+    J32, g32, t32 = res["fp32"]
+    shots = len(c["sources"])
+    # a gradient = forward + recomputed forward + adjoint: three passes of
+    # N x n node updates per shot
+    line = {
+        "metric": "adjoint gradient, node-updates/s (3 passes per shot)", "value": 3 * shots * N * n / t64,
+        "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": 1, "ms_per_step": 1e3 * t64 / (shots * n),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "adjoint_256x256_p4_8shots", "nodes": N, "shots": shots, "steps": n,
+                   "checkpoints": "ceil(sqrt(steps))", "ordering": args.ordering},
+        "seconds_per_gradient": {"fp64": t64, "fp32": t32},
+        "misfit": {"fp64": J64, "fp32": J32},
+        "fp32_vs_fp64": {"gradient_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+                         "misfit_rel": abs(J32 - J64) / J64},
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -340,9 +400,9 @@ def main():
     import paper_2104_08416_gb300 as P
     P.load()
     P.sem_set_allocator_torch()
-    if args.workload == "batched":
+    if args.workload in ("batched", "adjoint"):
         if rank == 0:
-            run_batched(args, P, torch)
+            (run_batched if args.workload == "batched" else run_adjoint)(args, P, torch)
         if world > 1:
             dist.destroy_process_group()
         return
