@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32_kahan", choices=["fp32_kahan", "fp64", "fp32"])
-    ap.add_argument("--ordering", default="hilbert", choices=["hilbert", "rowmajor", "random", "none"])
+    ap.add_argument("--ordering", default="hilbert",
+                    choices=["hilbert", "rowmajor", "random", "none", "connectivity", "distance"])
     ap.add_argument("--n", type=int, default=512, help="quads per side of the graded mesh")
     ap.add_argument("--workload", default="graded", choices=["graded", "layered", "batched", "adjoint"],
                     help="graded 512x512 (default), the layered 4096x1024 model (67M nodes), or batched shots")
@@ -461,7 +462,7 @@ def main():
     if rank == 0 and not args.no_compare:
         orderings = {}
         kk = min(K, 500)
-        for kind in ("hilbert", "rowmajor", "random", "none"):
+        for kind in ("hilbert", "rowmajor", "random", "none", "connectivity", "distance"):
             hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb, args.threads)
             hh.sem_step(W)
             t_ord = time_steps(torch, hh, kk)

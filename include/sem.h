@@ -77,9 +77,18 @@ typedef enum {
                                node procedure of Section 4.3                     */
     SEM_ORDER_RANDOM = 2,   /* Fisher-Yates shuffles of elements (splitmix64
                                stream seed+2) and of nodes (stream seed+3)       */
-    SEM_ORDER_HILBERT = 3   /* Section 4.3: elements along a generalized Hilbert
+    SEM_ORDER_HILBERT = 3,  /* Section 4.3: elements along a generalized Hilbert
                                curve over the centroid grid, nodes renumbered by
                                first touch, ascending degree                     */
+    SEM_ORDER_CONNECTIVITY = 4, /* Section 6.1 "Node Connectivity": a walk over
+                               nodes (connected = sharing an element) from the
+                               node with the fewest connections, always to the
+                               unvisited connected node with the fewest; at a
+                               dead end back along the walk; elements listed as
+                               their nodes are first visited (ascending id)      */
+    SEM_ORDER_DISTANCE = 5  /* Section 6.1 "Node Distance": the same walk by
+                               squared distance to the lower-left corner of the
+                               bounding box (ties to the lower node id)          */
 } sem_ordering;
 
 typedef enum { SEM_SRC_RICKER = 0 } sem_source_kind;

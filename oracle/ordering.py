@@ -25,7 +25,8 @@ exports the inverse maps (new id of each old id); ``inverse`` converts.
   nodes stream seed+3 (independently).
 * ``orderings(kind)`` -- NONE: identity for both; ROWMAJOR: input element
   order with nodes renumbered as above; RANDOM: random elements and random
-  nodes; HILBERT: the curve order with nodes renumbered as above.
+  nodes; HILBERT: the curve order with nodes renumbered as above;
+  CONNECTIVITY / DISTANCE: Section 6.1's node walks (``node_walk``).
 """
 from __future__ import annotations
 
@@ -133,10 +134,71 @@ def renumber_nodes(conn, elem_order, degree) -> np.ndarray:
     return nodes[idx].astype(np.int64)
 
 
-def orderings(kind: str, coords, quads, conn, n_nodes, seed: int = 2104084160, degree=None):
-    """(elem_order, node_order) for kind in none/rowmajor/random/hilbert."""
+def node_walk(conn, n_nodes: int, key) -> tuple:
+    """Section 6.1's node walks ("Node Connectivity", "Node Distance"): from
+    the node of smallest key, always to the connected (element-sharing),
+    not yet visited node of smallest key; ties go to the lower node id. The
+    paper does not say what happens when no such node exists; reading: back up
+    along the walk to the latest node that has one, and when the connected part
+    is exhausted restart at the unvisited node of smallest key. Each visited
+    node is appended to the node order, and the elements containing it that
+    are not yet listed are appended, in ascending id, to the element order.
+    key[n_nodes]: number of connections, or squared distance to the reference
+    point. Plain loops over an explicit adjacency (small meshes)."""
+    E, P = conn.shape
+    A = sp.csr_matrix((np.ones(E * P, dtype=np.int8), (np.repeat(np.arange(E), P), conn.ravel())),
+                      shape=(E, n_nodes))
+    nbr = (A.T.astype(np.int32) @ A.astype(np.int32)).tocsr()
+    node_elems = A.T.tocsr()
+    rank = sorted(range(n_nodes), key=lambda v: (key[v], v))
+    visited = np.zeros(n_nodes, dtype=bool)
+    listed = np.zeros(E, dtype=bool)
+    eo, no = [], []
+
+    def visit(v):
+        visited[v] = True
+        no.append(v)
+        for e in sorted(node_elems.indices[node_elems.indptr[v]:node_elems.indptr[v + 1]]):
+            if not listed[e]:
+                listed[e] = True
+                eo.append(int(e))
+
+    for start in rank:
+        if visited[start]:
+            continue
+        visit(start)
+        path = [start]
+        while path:
+            top = path[-1]
+            cand = [int(w) for w in nbr.indices[nbr.indptr[top]:nbr.indptr[top + 1]] if not visited[w]]
+            if not cand:
+                path.pop()
+                continue
+            nxt = min(cand, key=lambda w: (key[w], w))
+            visit(nxt)
+            path.append(nxt)
+    return np.array(eo, dtype=np.int64), np.array(no, dtype=np.int64)
+
+
+def orderings(kind: str, coords, quads, conn, n_nodes, seed: int = 2104084160, degree=None, node_xy=None):
+    """(elem_order, node_order) for kind in none/rowmajor/random/hilbert/
+    connectivity/distance (node_xy needed for distance)."""
     E = conn.shape[0]
     kind = kind.lower()
+    if kind == "connectivity":
+        return node_walk(conn, n_nodes, node_degrees(conn, n_nodes) if degree is None else degree)
+    if kind == "distance":
+        # reference point: the lower-left corner of the bounding box (Section
+        # 6.1); reading: squared distances compared in units of 2^-30 of the
+        # box diagonal squared (floor), so mirror-equal distances tie exactly
+        xy = np.asarray(node_xy, dtype=np.float64)
+        c = np.asarray(coords, dtype=np.float64)
+        x0, y0 = c[:, 0].min(), c[:, 1].min()
+        w, h = c[:, 0].max() - x0, c[:, 1].max() - y0
+        dx = xy[:, 0] - x0
+        dy = xy[:, 1] - y0
+        key = np.floor((dx * dx + dy * dy) / (w * w + h * h) * 2.0 ** 30).astype(np.int64)
+        return node_walk(conn, n_nodes, key)
     if kind == "none":
         return np.arange(E, dtype=np.int64), np.arange(n_nodes, dtype=np.int64)
     if kind == "random":

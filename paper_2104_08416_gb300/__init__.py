@@ -23,10 +23,11 @@ LIB_PATH = os.path.join(_PKG, "libsem.so")
 SEM_OK, SEM_ERR_INVALID_ARG, SEM_ERR_STATE, SEM_ERR_CUDA, SEM_ERR_OOM, SEM_ERR_TIMEOUT, SEM_ERR_UNSUPPORTED = range(7)
 SEM_FP64, SEM_FP32_KAHAN, SEM_FP32 = 0, 1, 2
 SEM_ORDER_NONE, SEM_ORDER_ROWMAJOR, SEM_ORDER_RANDOM, SEM_ORDER_HILBERT = 0, 1, 2, 3
+SEM_ORDER_CONNECTIVITY, SEM_ORDER_DISTANCE = 4, 5
 SEM_SRC_RICKER = 0
 PRECISIONS = {"fp64": SEM_FP64, "fp32_kahan": SEM_FP32_KAHAN, "fp32": SEM_FP32}
 ORDERINGS = {"none": SEM_ORDER_NONE, "rowmajor": SEM_ORDER_ROWMAJOR, "random": SEM_ORDER_RANDOM,
-             "hilbert": SEM_ORDER_HILBERT}
+             "hilbert": SEM_ORDER_HILBERT, "connectivity": SEM_ORDER_CONNECTIVITY, "distance": SEM_ORDER_DISTANCE}
 DEFAULT_SEED = 2104084160
 
 # every symbol include/sem.h declares

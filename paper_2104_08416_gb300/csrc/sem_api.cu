@@ -716,7 +716,7 @@ sem_status sem_mesh_create(const double* coords, int64_t nv, const int32_t* quad
 
 sem_status sem_reorder(sem_mesh* m, sem_ordering kind, uint64_t seed) {
     if (!m) return SEM_ERR_INVALID_ARG;
-    if ((int)kind < 0 || (int)kind > 3) return fail(m, SEM_ERR_INVALID_ARG, "unknown ordering");
+    if ((int)kind < 0 || (int)kind > 5) return fail(m, SEM_ERR_INVALID_ARG, "unknown ordering");
     if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_reorder after the device data was built");
     m->ordering = (int)kind;
     m->seed = seed;
@@ -978,7 +978,7 @@ sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads
     };
     say("");
     if (!coords || !quads || (nrec > 0 && !rec_xy) || nrec < 0) return SEM_ERR_INVALID_ARG;
-    if ((int)kind < 0 || (int)kind > 3 || elems_per_block < 1 || elems_per_block > 256) return SEM_ERR_INVALID_ARG;
+    if ((int)kind < 0 || (int)kind > 5 || elems_per_block < 1 || elems_per_block > 256) return SEM_ERR_INVALID_ARG;
     const std::string bad = semhost::validate(coords, nv, quads, ne, order);
     if (!bad.empty()) {
         say(bad);
@@ -1079,7 +1079,7 @@ sem_status sem_count_nodes(const int32_t* quads, int64_t nv, int64_t ne, int ord
 sem_status sem_compute_ordering(const double* coords, int64_t nv, const int32_t* quads, int64_t ne, int order,
                                 sem_ordering kind, uint64_t seed, int64_t* elem_order, int64_t* node_order) {
     if (!coords || !quads || !elem_order || !node_order) return SEM_ERR_INVALID_ARG;
-    if ((int)kind < 0 || (int)kind > 3) return SEM_ERR_INVALID_ARG;
+    if ((int)kind < 0 || (int)kind > 5) return SEM_ERR_INVALID_ARG;
     if (!semhost::validate(coords, nv, quads, ne, order).empty()) return SEM_ERR_INVALID_ARG;
     semhost::Mesh mm;
     mm.p = order;

@@ -442,7 +442,106 @@ void random_order(int64_t n, uint64_t seed, std::vector<int64_t>& order) {
     }
 }
 
+// Node walks of Section 6.1's "Node Connectivity" (kind 4) and "Node
+// Distance" (kind 5) strategies. Nodes are connected when they share an
+// element. The walk starts at the best node (fewest connections, or closest to
+// the lower-left corner of the bounding box; ties to the lower id) and
+// repeatedly moves to the best unvisited node connected to the
+// current one; at a dead end it backs up along the walk to the latest node
+// that still has an unvisited connected node, and when the walk has visited
+// its whole connected part it restarts at the best unvisited node. Visiting a
+// node appends it to the node order and appends the elements that contain it
+// (ascending id, each once) to the element order.
+void walk_orders(const Mesh& m, int kind, std::vector<int64_t>& eo, std::vector<int64_t>& no) {
+    const int P = m.P;
+    const int64_t nn = m.nn, ne = m.ne;
+    std::vector<int64_t> nptr((size_t)nn + 1, 0);
+    for (int64_t s = 0; s < ne * P; ++s) nptr[(size_t)m.conn[(size_t)s] + 1]++;
+    for (size_t k = 1; k < nptr.size(); ++k) nptr[k] += nptr[k - 1];
+    std::vector<int64_t> nel((size_t)(ne * P));
+    {
+        std::vector<int64_t> fill(nptr.begin(), nptr.end() - 1);
+        for (int64_t e = 0; e < ne; ++e)
+            for (int q = 0; q < P; ++q) nel[(size_t)fill[(size_t)m.conn[(size_t)(e * P + q)]]++] = e;
+    }
+    // integer keys: the number of connections, or the squared distance to the
+    // reference point in units of 2^-30 of the bounding-box diagonal squared
+    // (floor), so that nodes at mirror-equal distances tie exactly whatever the
+    // last bit of their coordinates
+    std::vector<int64_t> key((size_t)nn);
+    if (kind == 4) {
+        std::vector<int32_t> deg;
+        node_degrees(m, deg);
+        for (int64_t g = 0; g < nn; ++g) key[(size_t)g] = deg[(size_t)g];
+    } else {
+        std::vector<double> xy;
+        node_coordinates(m, xy);
+        double x0 = std::numeric_limits<double>::infinity(), y0 = x0, x1 = -x0, y1 = -x0;
+        for (int64_t v = 0; v < m.nv; ++v) {
+            x0 = std::min(x0, m.coords[(size_t)v * 2]);
+            y0 = std::min(y0, m.coords[(size_t)v * 2 + 1]);
+            x1 = std::max(x1, m.coords[(size_t)v * 2]);
+            y1 = std::max(y1, m.coords[(size_t)v * 2 + 1]);
+        }
+        const double diag2 = (x1 - x0) * (x1 - x0) + (y1 - y0) * (y1 - y0);
+        for (int64_t g = 0; g < nn; ++g) {
+            const double dx = xy[(size_t)g * 2] - x0, dy = xy[(size_t)g * 2 + 1] - y0;
+            key[(size_t)g] = (int64_t)std::floor((dx * dx + dy * dy) / diag2 * 1073741824.0);
+        }
+    }
+    auto better = [&](int64_t a, int64_t b) {
+        return key[(size_t)a] < key[(size_t)b] || (key[(size_t)a] == key[(size_t)b] && a < b);
+    };
+    std::vector<int64_t> by_key((size_t)nn);
+    std::iota(by_key.begin(), by_key.end(), 0);
+    std::sort(by_key.begin(), by_key.end(), [&](int64_t a, int64_t b) { return better(a, b); });
+    std::vector<uint8_t> visited((size_t)nn, 0), listed((size_t)ne, 0);
+    eo.clear();
+    no.clear();
+    eo.reserve((size_t)ne);
+    no.reserve((size_t)nn);
+    auto visit = [&](int64_t g) {
+        visited[(size_t)g] = 1;
+        no.push_back(g);
+        for (int64_t k = nptr[(size_t)g]; k < nptr[(size_t)g + 1]; ++k) {
+            const int64_t e = nel[(size_t)k];
+            if (!listed[(size_t)e]) {
+                listed[(size_t)e] = 1;
+                eo.push_back(e);
+            }
+        }
+    };
+    std::vector<int64_t> stack;
+    size_t cursor = 0;
+    while ((int64_t)no.size() < nn) {
+        while (visited[(size_t)by_key[cursor]]) ++cursor;
+        visit(by_key[cursor]);
+        stack.assign(1, by_key[cursor]);
+        while (!stack.empty()) {
+            const int64_t top = stack.back();
+            int64_t best = -1;
+            for (int64_t k = nptr[(size_t)top]; k < nptr[(size_t)top + 1]; ++k) {
+                const int32_t* c = &m.conn[(size_t)nel[(size_t)k] * P];
+                for (int q = 0; q < P; ++q) {
+                    const int64_t g = c[q];
+                    if (!visited[(size_t)g] && (best < 0 || better(g, best))) best = g;
+                }
+            }
+            if (best < 0) {
+                stack.pop_back();
+            } else {
+                visit(best);
+                stack.push_back(best);
+            }
+        }
+    }
+}
+
 void orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_t>& eo, std::vector<int64_t>& no) {
+    if (kind == 4 || kind == 5) {
+        walk_orders(m, kind, eo, no);
+        return;
+    }
     if (kind == 0) {
         eo.resize((size_t)m.ne);
         std::iota(eo.begin(), eo.end(), 0);

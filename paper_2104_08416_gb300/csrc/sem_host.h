@@ -47,7 +47,8 @@ void node_degrees(const Mesh& m, std::vector<int32_t>& deg);
 void renumber_nodes(const Mesh& m, const std::vector<int64_t>& elem_order,
                     const std::vector<int32_t>& deg, std::vector<int64_t>& node_order);
 void random_order(int64_t n, uint64_t seed, std::vector<int64_t>& order);
-// kind: 0 none, 1 rowmajor, 2 random, 3 hilbert.
+// kind: 0 none, 1 rowmajor, 2 random, 3 hilbert, 4 node connectivity,
+// 5 node distance (Section 6.1's strategies).
 void orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_t>& elem_order,
                std::vector<int64_t>& node_order);
 

@@ -49,12 +49,13 @@ def _meshes():
     yield "unit_relab", gen.relabel(gen.unit_square(10), seed=1)
 
 
-@pytest.mark.parametrize("kind", ["none", "rowmajor", "random", "hilbert"])
+@pytest.mark.parametrize("kind", ["none", "rowmajor", "random", "hilbert", "connectivity", "distance"])
 @pytest.mark.parametrize("p", [1, 2, 4])
 def test_orderings_bit_exact(lib, kind, p):
     for name, m in _meshes():
-        conn, n, _ = mesh.canonical_numbering(m["quads"], m["coords"].shape[0], p)
-        eo_ref, no_ref = ordering.orderings(kind, m["coords"], m["quads"], conn, n, seed=12345)
+        conn, n, edges = mesh.canonical_numbering(m["quads"], m["coords"].shape[0], p)
+        xy = mesh.node_coordinates(m["coords"], m["quads"], p, conn, edges)
+        eo_ref, no_ref = ordering.orderings(kind, m["coords"], m["quads"], conn, n, seed=12345, node_xy=xy)
         eo, no = lib.sem_compute_ordering(m["coords"], m["quads"], p, kind, seed=12345)
         np.testing.assert_array_equal(eo, eo_ref, err_msg=name)
         np.testing.assert_array_equal(no, no_ref, err_msg=name)

@@ -138,3 +138,40 @@ def test_wavefield_independent_of_input_labels():
     scale = np.abs(out[0][0]).max()
     np.testing.assert_allclose(out[0][0], out[1][0], atol=1e-12 * scale)
     np.testing.assert_allclose(out[0][1], out[1][1], atol=1e-12 * scale)
+
+
+def test_node_walks_hand_traced_two_quads():
+    """Section 6.1's node walks traced by hand on two unit quads side by side
+    (order 1, nodes = vertices 0..5: bottom row 0,1,2, top row 3,4,5).
+    Connections (sharing a quad): degrees 3,5,3,3,5,3. Connectivity walk:
+    0 (fewest) -> 3 (deg 3) -> 1 (deg 5, lower id than 4) -> 2 (deg 3, lower id
+    than 5) -> 5 -> 4. Distance walk from (0, 0): 0 -> 1 (d^2 1, ties with 3,
+    lower id) -> 3 (d^2 1) -> 4 (d^2 2) -> 2 (d^2 4) -> 5. Elements are listed
+    as their nodes are first reached: [0, 1] in both."""
+    coords = np.array([[0, 0], [1, 0], [2, 0], [0, 1], [1, 1], [2, 1]], dtype=np.float64)
+    quads = np.array([[0, 1, 4, 3], [1, 2, 5, 4]], dtype=np.int64)
+    conn, n, edges = mesh.canonical_numbering(quads, 6, 1)
+    xy = mesh.node_coordinates(coords, quads, 1, conn, edges)
+    eo, no = ordering.orderings("connectivity", coords, quads, conn, n)
+    assert no.tolist() == [0, 3, 1, 2, 5, 4] and eo.tolist() == [0, 1]
+    eo, no = ordering.orderings("distance", coords, quads, conn, n, node_xy=xy)
+    assert no.tolist() == [0, 1, 3, 4, 2, 5] and eo.tolist() == [0, 1]
+
+
+@pytest.mark.parametrize("kind", ["connectivity", "distance"])
+def test_node_walks_are_permutations_and_mostly_adjacent(kind):
+    m = gen.graded(12, seed=2)
+    conn, n, edges = mesh.canonical_numbering(m["quads"], m["coords"].shape[0], 3)
+    xy = mesh.node_coordinates(m["coords"], m["quads"], 3, conn, edges)
+    eo, no = ordering.orderings(kind, m["coords"], m["quads"], conn, n, node_xy=xy)
+    assert sorted(eo.tolist()) == list(range(conn.shape[0]))
+    assert sorted(no.tolist()) == list(range(n))
+    # consecutive nodes share an element except right after a back-up
+    share = 0
+    elems_of = [set() for _ in range(n)]
+    for e, row in enumerate(conn):
+        for v in row:
+            elems_of[v].add(e)
+    for a, b in zip(no[:-1], no[1:]):
+        share += bool(elems_of[a] & elems_of[b])
+    assert share >= 0.9 * (n - 1)
