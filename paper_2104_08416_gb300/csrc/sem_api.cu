@@ -231,9 +231,9 @@ sem_status fill_source(sem_mesh* m, int64_t upto) {
 }
 
 int default_eb(int np) {
-    // about 4800 element points per block, at most 256 elements (threads)
+    // about 6400 element points per block, at most 256 elements (threads)
     const int P = np * np;
-    int eb = (4800 + P / 2) / P;
+    int eb = (6400 + P / 2) / P;
     if (eb > 256) eb = 256;
     if (eb < 1) eb = 1;
     return eb;
@@ -250,8 +250,9 @@ int plan_smem_bytes(const sem_mesh* m, int P) {
     const int v = vec_of(m);
     const int sulen_pad = (pl.max_sulen + v - 1) / v * v;
     const int slen_pad = (pl.max_slen + v - 1) / v * v;
-    const int a = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), mode_of(m));
-    const int b = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), semdev::MODE_APPLY);
+    const int a = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), mode_of(m), pl.dense);
+    const int b =
+        semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), semdev::MODE_APPLY, pl.dense);
     return std::max(std::max(a, b), sulen_pad * 8);
 }
 
@@ -343,9 +344,9 @@ sem_status build(sem_mesh* m) {
     const int sulen_pad = (pl.max_sulen + v - 1) / v * v;
     const int slen_pad = (pl.max_slen + v - 1) / v * v;
     m->threads = std::max(semdev::step_threads(pl.eb), m->threads_request);
-    m->smem = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), mode_of(m));
+    m->smem = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m), mode_of(m), pl.dense);
     const int smem_apply = semdev::smem_bytes_for(P, pl.eb, pl.max_packet, sulen_pad, slen_pad, fp64(m),
-                                                  semdev::MODE_APPLY);
+                                                  semdev::MODE_APPLY, pl.dense);
     if (std::max(m->smem, smem_apply) > kSmemLimit)
         return fail(m, SEM_ERR_UNSUPPORTED, "block plan does not fit in shared memory; lower sem_set_tuning");
 

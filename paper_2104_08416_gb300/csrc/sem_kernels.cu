@@ -122,6 +122,15 @@ __device__ __forceinline__ void load_vec(T (&v)[VEC], const T* p) {
 #pragma unroll
     for (int k = 0; k < VEC; ++k) v[k] = t[k];
 }
+// 16-byte global vector of VEC values (L2 only: it is read once).
+template <typename T, int VEC>
+__device__ __forceinline__ void load_global_vec(T (&v)[VEC], const T* p) {
+    const float4 w = __ldcg(reinterpret_cast<const float4*>(p));
+    const T* t = reinterpret_cast<const T*>(&w);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v[k] = t[k];
+}
+
 // Stores the values whose bit is set; one 16-byte store when all are.
 template <typename T, int VEC>
 __device__ __forceinline__ void store_masked(T* g, const T (&v)[VEC], uint32_t bits) {
@@ -193,10 +202,14 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     constexpr int VEC = 16 / sizeof(T);
     uint8_t* spk = smem_raw;
     T* su = reinterpret_cast<T*>(smem_raw + pl.max_packet);   // node values at the positions
-    T* ss = su + pl.sulen_pad;                                 // staged s
-    T* sx = ss + (STATE ? pl.slen_pad : 0);                    // staged u^{k-1} or delta
-    T* sc = sx + (STATE ? pl.slen_pad : 0);                    // staged compensation
-    T* acc = sc + (KAHAN ? pl.slen_pad : 0);                   // assembled K u at the positions
+    // DENSE plans read s and the compensation straight from global memory in
+    // phase C (contiguous, 16-byte loads one chunk ahead) instead of staging
+    // them: less shared memory per block, more resident blocks
+    const bool direct = pl.dense;
+    T* ss = su + pl.sulen_pad;                                        // staged s
+    T* sx = ss + (STATE && !direct ? pl.slen_pad : 0);                // staged u^{k-1} or delta
+    T* sc = sx + (STATE ? pl.slen_pad : 0);                           // staged compensation
+    T* acc = sc + (KAHAN && !direct ? pl.slen_pad : 0);               // assembled K u at the positions
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const BlockHdr h = load_hdr(pl.hdr, b);
@@ -234,9 +247,9 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             const bool vok = a.vec_ok != 0;
             stage_range(su, a.u_k, abase, h.ulen, pl.nn, vok, tid, nt);
             if (STATE) {
-                stage_range(ss, a.s, abase, h.ulen, pl.nn, vok, tid, nt);
+                if (!direct) stage_range(ss, a.s, abase, h.ulen, pl.nn, vok, tid, nt);
                 stage_range(sx, a.x_k, abase, h.ulen, pl.nn, vok, tid, nt);
-                if (KAHAN) stage_range(sc, a.c_k, abase, h.ulen, pl.nn, vok, tid, nt);
+                if (KAHAN && !direct) stage_range(sc, a.c_k, abase, h.ulen, pl.nn, vok, tid, nt);
             }
         }
         cp_async_commit();
@@ -285,7 +298,7 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 if (KAHAN) {
                     __stcg(a.x_kw + g, up.x);
                     __stcg(a.c_kw + g, up.c);
-                    sc[pos] = up.c;  // for a receiver record (the owner's entries lie in the staged range)
+                    if (!direct) sc[pos] = up.c;  // for a receiver record (the owner's entries are staged)
                 }
             }
         }
@@ -296,7 +309,9 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     if (pending && h.nro > 0) {
         for (int k = tid; k < h.nro; k += nt) {
             const int pos = recs[2 * (h.nrc + k)], r = recs[2 * (h.nrc + k) + 1];
-            a.trace[(int64_t)r * a.trace_cap + a.step - 1] = trace_value<T, MODE>(su[pos], KAHAN ? sc[pos] : T(0));
+            // the owner's entries lie in the owned range (DENSE) or the staged one
+            const T cw = KAHAN ? (direct ? __ldcg(a.c_kw + abase + pos) : sc[pos]) : T(0);
+            a.trace[(int64_t)r * a.trace_cap + a.step - 1] = trace_value<T, MODE>(su[pos], cw);
         }
     }
 
@@ -382,12 +397,29 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
         // VEC consecutive positions per thread: 16-byte shared-memory reads,
         // and 16-byte stores where all VEC positions are closed
         const int nch = h.slen / VEC;
+        T s_nx[VEC], c_nx[VEC];
+        if (STATE && direct && tid < nch) {
+            load_global_vec<T, VEC>(s_nx, a.s + abase + (int64_t)tid * VEC);
+            if (KAHAN) load_global_vec<T, VEC>(c_nx, a.c_k + abase + (int64_t)tid * VEC);
+        }
         for (int ch = tid; ch < nch; ch += nt) {
             const int p0 = ch * VEC;
+            T vu[VEC], vr[VEC], vx[VEC], vc[VEC], vs[VEC];
+            if (STATE && direct) {
+#pragma unroll
+                for (int t = 0; t < VEC; ++t) {
+                    vs[t] = s_nx[t];
+                    vc[t] = KAHAN ? c_nx[t] : T(0);
+                }
+                const int chn = ch + nt;
+                if (chn < nch) {
+                    load_global_vec<T, VEC>(s_nx, a.s + abase + (int64_t)chn * VEC);
+                    if (KAHAN) load_global_vec<T, VEC>(c_nx, a.c_k + abase + (int64_t)chn * VEC);
+                }
+            }
             const uint32_t bits = (cmask[p0 >> 5] >> (p0 & 31)) & ((1u << VEC) - 1u);
             if (bits == 0) continue;
             const int64_t g0 = abase + p0;
-            T vu[VEC], vr[VEC], vx[VEC], vc[VEC], vs[VEC];
             load_vec<T, VEC>(vr, acc + p0);
             if (MODE == MODE_APPLY) {
                 store_masked<T, VEC>(a.apply_out + g0, vr, a.vec_ok ? bits : (bits | (1u << VEC)));
@@ -395,8 +427,10 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             }
             load_vec<T, VEC>(vu, su + p0);
             load_vec<T, VEC>(vx, sx + p0);
-            load_vec<T, VEC>(vs, ss + p0);
-            if (KAHAN) load_vec<T, VEC>(vc, sc + p0);
+            if (!direct) {
+                load_vec<T, VEC>(vs, ss + p0);
+                if (KAHAN) load_vec<T, VEC>(vc, sc + p0);
+            }
 #pragma unroll
             for (int t = 0; t < VEC; ++t) {
                 const T f = (g0 + t == a.src_gid) ? f_now : T(0);
@@ -415,7 +449,7 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 for (int t = 0; t < VEC; ++t)
                     if ((bits >> t) & 1u) {
                         su[p0 + t] = vu[t];
-                        if (KAHAN) sc[p0 + t] = vc[t];
+                        if (KAHAN) (direct ? acc : sc)[p0 + t] = vc[t];   // acc[p] is no longer needed
                     }
             }
         }
@@ -445,7 +479,8 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
         __syncthreads();
         for (int k = tid; k < h.nrc; k += nt) {
             const int pos = recs[2 * k], r2 = recs[2 * k + 1];
-            a.trace[(int64_t)r2 * a.trace_cap + a.step] = trace_value<T, MODE>(su[pos], KAHAN ? sc[pos] : T(0));
+            a.trace[(int64_t)r2 * a.trace_cap + a.step] =
+                trace_value<T, MODE>(su[pos], KAHAN ? (direct ? acc : sc)[pos] : T(0));
         }
     }
 }
@@ -802,11 +837,12 @@ int step_threads(int eb) {
     return t < 32 ? 32 : t;
 }
 
-int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, bool fp64, int mode) {
+int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, bool fp64, int mode, bool dense) {
     (void)P;
     (void)eb;
     const int sz = fp64 ? 8 : 4;
-    const int staged = mode == MODE_KAHAN ? 3 : (mode == MODE_THREE_LEVEL ? 2 : 0);
+    const bool direct = dense;
+    const int staged = mode == MODE_APPLY ? 0 : (direct ? 1 : (mode == MODE_KAHAN ? 3 : 2));
     return max_packet + (2 * sulen_pad + staged * slen_pad) * sz;
 }
 

@@ -144,7 +144,7 @@ cudaError_t launch_gradient(int64_t ne, int P, const int32_t* conn, const double
 // rounded up to whole warps).
 int step_threads(int eb);
 // Dynamic shared memory of the step kernel.
-int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, bool fp64, int mode);
+int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, bool fp64, int mode, bool dense);
 
 // Batch step (all shots of one order) and the step-counter advance.
 // prepare_only sets the kernel's shared-memory limit (done before a graph
