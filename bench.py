@@ -69,6 +69,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(torch, dist, x, world, device):
+    """The largest of every rank's x (the job takes as long as its slowest
+    rank); x itself for one rank."""
+    if world <= 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, nodes_per_rank, steps, seconds):
+    """Whole-job node-updates/s: every rank advances its own replica (weak
+    scaling), timed by the slowest rank."""
+    return world * nodes_per_rank * steps / seconds
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -423,10 +439,7 @@ def main():
     if world > 1:
         dist.barrier()
     el = time_steps(torch, h, K)
-    if world > 1:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(torch, dist, el, world, "cuda")
     # second pass with per-kernel events for the roofline
     h.sem_profile_enable(True)
     prof_el = time_steps(torch, h, K)
@@ -452,10 +465,7 @@ def main():
     e2e_el = time.perf_counter() - t0
     h2d, d2h = h2.sem_transfer_bytes()
     h2.sem_destroy()
-    if world > 1:
-        t = torch.tensor([e2e_el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_el = float(t.item())
+    e2e_el = max_over_ranks(torch, dist, e2e_el, world, "cuda")
 
     # ordering comparison (the paper's locality claim, restated on the GPU)
     orderings = None
@@ -495,7 +505,7 @@ def main():
     # of the hot path times the nodes one launch updates
     achieved = ALGO_BYTES[args.precision] * N / (blk_us * 1e-6) / 1e9
     traffic = recorded_traffic(args.precision, args.ordering) if wname == WORKLOAD else None
-    value = world * N * K / el
+    value = job_rate(world, N, K, el)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
