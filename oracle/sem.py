@@ -93,6 +93,7 @@ class SEM:
         J = _mesh.jacobians(self.coords, self.quads, self.p)
         self.detJ = J[..., 0, 0] * J[..., 1, 1] - J[..., 0, 1] * J[..., 1, 0]
         Jinv = np.linalg.inv(J)                             # K^(e) at each point
+        self.Jinv = Jinv
         metric = Jinv @ np.swapaxes(Jinv, -1, -2)           # J^-1 J^-T
         self.G = (self.w2[None, :] * self.detJ / self.rho[:, None])[..., None, None] * metric
         B = reference_gradient(self.p)
@@ -235,6 +236,52 @@ class SEM:
         dM = -2.0 * self.w2[None, :] * self.detJ / (self.rho * self.vel ** 3)[:, None]   # [E, P]
         grad = np.sum(dM * C[self.conn], axis=1)
         return J, grad, traces
+
+    # ---------------------------------------------------------- first-order form
+    def first_order_rhs(self, U, V, y_node=None, y=0.0):
+        """Rates of the paper's first-order system (Section 4.1 with M = 1/K,
+        B_kk = -1, F_kk = 1/rho, D = E = 0), discretised as in Section 4.2:
+        V (E, P, 2) holds the discontinuous velocity at every element's local
+        nodes (physical x, y components), U the continuous pressure.
+            dV/dt at local node q of e   = (1/rho_e) grad u (x_q)   (Eq. v_change)
+            dU/dt at global node nu      = (R_nu + y_nu) / M_nu       (Eq. u_change)
+            R_nu = - sum_{e, q; p: mu(p,e) = nu} w_q |J_q| V_q . grad phi_p (x_q)
+        (Eq. u_change_r_effic with B = -I), grad = J^-T grad_ref."""
+        ue = np.asarray(U)[self.conn]                                     # (E, P)
+        gref = np.einsum("qda,ea->eqd", self.B, ue)                      # reference gradient
+        gphys = np.einsum("eqdj,eqd->eqj", self.Jinv, gref)             # J^-T grad_ref
+        Vdot = gphys / self.rho[:, None, None]
+        wref = np.einsum("eqdj,eqj->eqd", self.Jinv, V)                  # J^-1 V
+        re = -np.einsum("q,eq,eqd,qda->ea", self.w2, self.detJ, wref, self.B)
+        R = np.bincount(self.conn.ravel(), weights=re.ravel(), minlength=self.n_nodes)
+        if y_node is not None:
+            R[y_node] += y
+        return R / self.M, Vdot
+
+    def run_heun(self, nsteps: int, h: float, src=None, receivers=None, U0=None, V0=None):
+        """Heun's predictor-corrector (Section 4.2, Time Integration) on the
+        first-order system from U = V = 0 (Eq. initial_cond) or (U0, V0); the
+        source y(t) = Ricker at the node nearest src, added to dU/dt.
+        Returns (U^N, V^N, traces[R, N]) with traces[r, n-1] = U^n."""
+        U = np.zeros(self.n_nodes) if U0 is None else np.array(U0, dtype=np.float64)
+        V = np.zeros((self.conn.shape[0], self.conn.shape[1], 2)) if V0 is None else np.array(V0, dtype=np.float64)
+        s_node = None
+        if src is not None:
+            sx, sy, f0, t0, amp = src
+            s_node = snap(self.node_xy, sx, sy)
+        rec_nodes = np.zeros(0, dtype=np.int64)
+        if receivers is not None and len(receivers):
+            rec_nodes = np.array([snap(self.node_xy, x, y) for x, y in np.asarray(receivers)], dtype=np.int64)
+        traces = np.zeros((rec_nodes.size, nsteps))
+        yt = (lambda t: float(ricker(t, f0, t0, amp))) if s_node is not None else (lambda t: 0.0)
+        for n in range(nsteps):
+            Ud1, Vd1 = self.first_order_rhs(U, V, s_node, yt(n * h))
+            Up, Vp = U + h * Ud1, V + h * Vd1
+            Ud2, Vd2 = self.first_order_rhs(Up, Vp, s_node, yt((n + 1) * h))
+            U = U + 0.5 * h * (Ud1 + Ud2)
+            V = V + 0.5 * h * (Vd1 + Vd2)
+            traces[:, n] = U[rec_nodes]
+        return U, V, traces
 
 
 def _find(conn, nu):

@@ -248,3 +248,37 @@ def test_adjoint_gradient_vanishes_at_the_true_model():
     _, _, d_obs = S.run(n, dt, src=src, receivers=rec)
     J, grad, _ = S.misfit_gradient(n, dt, src, rec, d_obs)
     assert J == 0.0 and np.all(grad == 0.0)
+
+
+def test_first_order_divergence_of_gradient_is_minus_stiffness():
+    """R(V) with V = grad u / rho at the local nodes equals -K u exactly (up to
+    rounding): the first-order form (Section 4.2, Eqs. v_change, u_change_r_effic)
+    and the assembled stiffness describe the same operator."""
+    for p in (1, 3, 5):
+        m = gen.relabel(gen.graded(5, seed=p), seed=p)
+        rho = 0.5 + np.random.default_rng(p).random(m["quads"].shape[0])
+        S = sem.SEM(m["coords"], m["quads"], p, m["vel"], rho)
+        u = np.random.default_rng(p + 1).standard_normal(S.n_nodes)
+        Ud, Vd = S.first_order_rhs(u, np.zeros((S.conn.shape[0], S.conn.shape[1], 2)))
+        assert np.all(Ud == 0.0)
+        R_over_M, _ = S.first_order_rhs(np.zeros(S.n_nodes), Vd)
+        ref = -S.apply_K(u)
+        assert np.linalg.norm(R_over_M * S.M - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_heun_standing_mode_second_order():
+    """Heun on the first-order system from U = cos(pi x) cos(pi y), V = 0 in
+    the Neumann unit square: error against cos(pi x) cos(pi y) cos(pi sqrt2 t)
+    at p = 7 falls by about 4 when the step halves."""
+    m = gen.unit_square(2)
+    p = 7
+    S = sem.SEM(m["coords"], m["quads"], p, 1.0, 1.0)
+    x, y = S.node_xy[:, 0], S.node_xy[:, 1]
+    u0 = np.cos(np.pi * x) * np.cos(np.pi * y)
+    T = 0.25
+    errs = []
+    for nsteps in (100, 200):
+        h = T / nsteps
+        U, _, _ = S.run_heun(nsteps, h, U0=u0)
+        errs.append(np.abs(U - u0 * np.cos(np.pi * np.sqrt(2) * T)).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
