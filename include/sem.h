@@ -93,6 +93,18 @@ typedef enum {
 
 typedef enum { SEM_SRC_RICKER = 0 } sem_source_kind;
 
+typedef enum {
+    SEM_SCHEME_LEAPFROG = 0, /* second-order form M u_tt = f e_s - K u, leapfrog
+                                (the default; see sem_precision)                 */
+    SEM_SCHEME_HEUN = 1      /* the paper's own scheme (Section 4.2, Time
+                                Integration): the first-order pressure/velocity
+                                system, velocity V stored at every element's local
+                                nodes (Eq. v_change), pressure U at the global nodes
+                                (Eq. u_change with B = -I, F = I/rho), advanced by
+                                Heun's predictor-corrector; the source y(t) enters
+                                dU/dt. SEM_FP64 or SEM_FP32 only                   */
+} sem_scheme;
+
 typedef struct sem_mesh sem_mesh;
 
 /* Optional device allocator (e.g. a framework's caching allocator). alloc
@@ -149,6 +161,15 @@ sem_status sem_set_receivers(sem_mesh* m, const double* xy, int32_t nrec, int64_
  * meets the CFL condition (Section 6.2); this is the definition used here.
  * Needs the model. */
 sem_status sem_cfl_dt(const sem_mesh* m, double* dt_cfl);
+
+/* Time integration scheme (sem_scheme), before the device data is built.
+ * SEM_SCHEME_HEUN with SEM_FP32_KAHAN returns SEM_ERR_UNSUPPORTED. With Heun,
+ * sem_step advances Heun steps (two right-hand-side evaluations each, every
+ * evaluation one step-kernel launch plus one open-node launch), traces record
+ * U after each step, sem_read_wavefield / sem_get_state return U (u_prev gets
+ * zeros), sem_set_state sets U and V = 0 (u_prev is ignored); the batched and
+ * adjoint calls are leapfrog-only (SEM_ERR_STATE / SEM_ERR_UNSUPPORTED). */
+sem_status sem_set_scheme(sem_mesh* m, int scheme);
 
 /* Time step dt > 0 (values above sem_cfl_dt are accepted; stability is the
  * caller's business). Before the first step only. */

@@ -25,6 +25,8 @@ SEM_FP64, SEM_FP32_KAHAN, SEM_FP32 = 0, 1, 2
 SEM_ORDER_NONE, SEM_ORDER_ROWMAJOR, SEM_ORDER_RANDOM, SEM_ORDER_HILBERT = 0, 1, 2, 3
 SEM_ORDER_CONNECTIVITY, SEM_ORDER_DISTANCE = 4, 5
 SEM_SRC_RICKER = 0
+SEM_SCHEME_LEAPFROG, SEM_SCHEME_HEUN = 0, 1
+SCHEMES = {"leapfrog": SEM_SCHEME_LEAPFROG, "heun": SEM_SCHEME_HEUN}
 PRECISIONS = {"fp64": SEM_FP64, "fp32_kahan": SEM_FP32_KAHAN, "fp32": SEM_FP32}
 ORDERINGS = {"none": SEM_ORDER_NONE, "rowmajor": SEM_ORDER_ROWMAJOR, "random": SEM_ORDER_RANDOM,
              "hilbert": SEM_ORDER_HILBERT, "connectivity": SEM_ORDER_CONNECTIVITY, "distance": SEM_ORDER_DISTANCE}
@@ -33,7 +35,7 @@ DEFAULT_SEED = 2104084160
 # every symbol include/sem.h declares
 EXPORTS = (
     "sem_set_allocator", "sem_mesh_create", "sem_reorder", "sem_set_model", "sem_set_source",
-    "sem_set_receivers", "sem_cfl_dt", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
+    "sem_set_receivers", "sem_cfl_dt", "sem_set_scheme", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
     "sem_read_wavefield", "sem_set_state", "sem_get_state", "sem_apply_stiffness", "sem_read_mass",
     "sem_get_permutation", "sem_get_sizes", "sem_node_coordinates", "sem_get_snapped",
     "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info",
@@ -76,6 +78,7 @@ def load(path: str | None = None):
         "sem_set_receivers": (_P, _D, C.c_int32, C.c_int64),
         "sem_cfl_dt": (_P, _D),
         "sem_set_dt": (_P, C.c_double),
+        "sem_set_scheme": (_P, C.c_int),
         "sem_step": (_P, C.c_int64),
         "sem_get_step": (_P, _I64),
         "sem_read_traces": (_P, _D, C.c_int64),
@@ -267,6 +270,10 @@ class SEM:
         d = C.c_double()
         self._c(self._lib.sem_cfl_dt(self.h, C.byref(d)))
         return d.value
+
+    def sem_set_scheme(self, scheme):
+        scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        self._c(self._lib.sem_set_scheme(self.h, scheme))
 
     def sem_set_dt(self, dt: float):
         self._c(self._lib.sem_set_dt(self.h, float(dt)))

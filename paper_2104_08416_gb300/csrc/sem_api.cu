@@ -62,6 +62,7 @@ struct sem_mesh {
     bool have_dt = false;
     double dt = 0;
     int eb_request = 0;
+    int scheme = 0;             // SEM_SCHEME_LEAPFROG or SEM_SCHEME_HEUN
     int threads_request = 0;
 
     // device state (host_* hold the host part of the build until the device part)
@@ -83,6 +84,10 @@ struct sem_mesh {
     double* d_vel = nullptr;
     uint8_t* d_packet = nullptr;
     double* d_G64 = nullptr;
+    double* d_coef64 = nullptr;   // FP64 bilinear map (first-order system, FP64)
+    void* d_v[2] = {nullptr, nullptr};   // first-order system: V, V~ ([2P][ne])
+    void* d_vd1 = nullptr;               // predictor rate of V
+    void* d_ud1 = nullptr;               // predictor rate of U
     double* d_mloc = nullptr;
     double* d_M = nullptr;
     void* d_s = nullptr;
@@ -182,6 +187,9 @@ sem_status zeros(sem_mesh* m, void** dst, size_t bytes) {
 
 bool fp64(const sem_mesh* m) { return m->prec == SEM_FP64; }
 size_t tsize(const sem_mesh* m) { return fp64(m) ? 8 : 4; }
+// s = dt^2 / M for the leapfrog, 1 / M for the first-order system.
+double scale_numerator(const sem_mesh* m) { return m->scheme == SEM_SCHEME_HEUN ? 1.0 : m->dt * m->dt; }
+
 int mode_of(const sem_mesh* m) {
     return m->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
 }
@@ -408,8 +416,13 @@ sem_status build(sem_mesh* m) {
         if (!coef) return fail(m, SEM_ERR_OOM, "device allocation failed");
         dp.coef = coef;
     }
+    if (m->scheme == SEM_SCHEME_HEUN && fp64(m)) {
+        m->d_coef64 = (double*)dev_alloc(m, (size_t)M.ne * 8 * 8);
+        if (!m->d_coef64) return fail(m, SEM_ERR_OOM, "device allocation failed");
+        dp.coef64 = m->d_coef64;
+    }
     SEM_CUDA(semdev::launch_geometry(M.np, M.ne, m->d_coords, m->d_quads, m->d_rho, m->d_vel, m->basis64, coef,
-                                     m->d_G64, m->d_mloc, m->stream));
+                                     m->d_G64, m->d_mloc, m->d_coef64, m->stream));
     SEM_CUDA(semdev::launch_mass(dp, M.np, m->d_mloc, (double*)m->d_part[0], m->d_M, m->stream));
 
     // time-stepping state
@@ -424,8 +437,15 @@ sem_status build(sem_mesh* m) {
             if ((st = zeros(m, &m->d_c[k], nb)) != SEM_OK) return st;
         }
     }
+    if (m->scheme == SEM_SCHEME_HEUN) {
+        const size_t vb = (size_t)M.ne * (size_t)P * 2 * tsize(m);
+        for (auto& v : m->d_v)
+            if ((st = zeros(m, &v, vb)) != SEM_OK) return st;
+        if ((st = zeros(m, &m->d_vd1, vb)) != SEM_OK) return st;
+        if ((st = zeros(m, &m->d_ud1, nb)) != SEM_OK) return st;
+    }
     if (m->have_dt) {
-        SEM_CUDA(semdev::launch_scale(m->d_M, M.nn, m->dt, fp64(m) ? (double*)m->d_s : nullptr,
+        SEM_CUDA(semdev::launch_scale(m->d_M, M.nn, scale_numerator(m), fp64(m) ? (double*)m->d_s : nullptr,
                                       fp64(m) ? nullptr : (float*)m->d_s, m->stream));
     }
     if (m->nrec > 0) {
@@ -464,10 +484,10 @@ sem_status refresh_model(sem_mesh* m) {
     SEM_CUDA(cudaMemcpyAsync(m->d_vel, vd.data(), vd.size() * 8, cudaMemcpyHostToDevice, m->stream));
     m->h2d += (int64_t)(rd.size() + vd.size()) * 8;
     SEM_CUDA(semdev::launch_geometry(m->mesh.np, m->mesh.ne, m->d_coords, m->d_quads, m->d_rho, m->d_vel, m->basis64,
-                                     const_cast<float4*>(m->dplan.coef), m->d_G64, m->d_mloc, m->stream));
+                                     const_cast<float4*>(m->dplan.coef), m->d_G64, m->d_mloc, m->d_coef64, m->stream));
     SEM_CUDA(semdev::launch_mass(m->dplan, m->mesh.np, m->d_mloc, (double*)m->d_part[0], m->d_M, m->stream));
     if (m->have_dt)
-        SEM_CUDA(semdev::launch_scale(m->d_M, m->mesh.nn, m->dt, fp64(m) ? (double*)m->d_s : nullptr,
+        SEM_CUDA(semdev::launch_scale(m->d_M, m->mesh.nn, scale_numerator(m), fp64(m) ? (double*)m->d_s : nullptr,
                                       fp64(m) ? nullptr : (float*)m->d_s, m->stream));
     SEM_CUDA(cudaStreamSynchronize(m->stream));
     return SEM_OK;
@@ -583,6 +603,53 @@ sem_status launch_flush(sem_mesh* m) {
     if (m->profiling) m->ev_open.push_back({e0, e1});
     return SEM_OK;
 }
+
+// One step of Heun's method on the first-order system: predictor and
+// corrector, each a step-kernel launch plus the open-node launch.
+template <typename T>
+sem_status heun_launches(sem_mesh* m) {
+    const bool f64 = fp64(m);
+    semdev::StepArgs<T> a{};
+    a.s = (const T*)m->d_s;
+    a.src_f = m->d_src;
+    a.src_gid = m->have_src ? (int32_t)m->node_new[(size_t)m->src_node] : -1;
+    a.trace = m->d_trace;
+    a.trace_cap = m->trace_cap;
+    a.vec_ok = 1;
+    a.h = m->dt;
+    a.u_d1 = (T*)m->d_ud1;
+    a.v_d1 = (T*)m->d_vd1;
+    a.part_wr = (T*)m->d_part[0];
+    a.part_rd = (const T*)m->d_part[0];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (m->profiling) {
+        e0 = take_event(m);
+        e1 = take_event(m);
+        if (!e0 || !e1) return fail(m, SEM_ERR_CUDA, "cudaEventCreate failed");
+        SEM_CUDA(cudaEventRecord(e0, m->stream));
+    }
+    for (int phase = 0; phase < 2; ++phase) {
+        const int mode = phase == 0 ? semdev::MODE_HEUN_P : semdev::MODE_HEUN_C;
+        a.step = m->step + phase;                       // source at t_n, then t_{n+1}
+        a.u_k = (const T*)m->d_u[phase];                // U, then U~
+        a.u_kp1 = (T*)m->d_u[phase == 0 ? 1 : 0];       // U~, then U (in place)
+        a.u_old = (const T*)m->d_u[0];
+        a.v_in = (const T*)m->d_v[phase];               // V, then V~
+        a.v_out = (T*)m->d_v[phase == 0 ? 1 : 0];       // V~, then V (in place)
+        a.v_old = (const T*)m->d_v[0];
+        SEM_CUDA(semdev::launch_step(m->mesh.np, f64, mode, m->dplan, &a, basis_of(m), m->threads, m->smem,
+                                     m->stream));
+        SEM_CUDA(semdev::launch_open_finish(f64, mode, m->dplan, &a, m->stream));
+    }
+    if (m->profiling) {
+        SEM_CUDA(cudaEventRecord(e1, m->stream));
+        m->ev_block.push_back({e0, e1});
+    }
+    m->step++;
+    return SEM_OK;
+}
+
+sem_status launch_heun_step(sem_mesh* m) { return fp64(m) ? heun_launches<double>(m) : heun_launches<float>(m); }
 
 // K u for u in the library's storage type and order (dev_in), into dev_out,
 // with `partial` as scratch for the open entries' partial sums.
@@ -784,6 +851,16 @@ sem_status sem_cfl_dt(const sem_mesh* m, double* dt_cfl) {
     return SEM_OK;
 }
 
+sem_status sem_set_scheme(sem_mesh* m, int scheme) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (scheme != SEM_SCHEME_LEAPFROG && scheme != SEM_SCHEME_HEUN) return fail(m, SEM_ERR_INVALID_ARG, "unknown scheme");
+    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_scheme after the device data was built");
+    if (scheme == SEM_SCHEME_HEUN && m->prec == SEM_FP32_KAHAN)
+        return fail(m, SEM_ERR_UNSUPPORTED, "the first-order scheme runs on SEM_FP64 or SEM_FP32");
+    m->scheme = scheme;
+    return SEM_OK;
+}
+
 sem_status sem_set_dt(sem_mesh* m, double dt) {
     if (!m) return SEM_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(m, SEM_ERR_INVALID_ARG, "dt must be > 0");
@@ -814,7 +891,13 @@ sem_status sem_step(sem_mesh* m, int64_t nsteps) {
     if (m->nrec > 0 && m->step + nsteps > m->trace_cap)
         return fail(m, SEM_ERR_INVALID_ARG, "steps beyond the receivers' max_steps");
     if (nsteps == 0) return SEM_OK;
-    if ((st = fill_source(m, m->step + nsteps)) != SEM_OK) return st;
+    if ((st = fill_source(m, m->step + nsteps + 1)) != SEM_OK) return st;
+    if (m->scheme == SEM_SCHEME_HEUN) {
+        for (int64_t k = 0; k < nsteps; ++k)
+            if ((st = launch_heun_step(m)) != SEM_OK) return st;
+        m->stepped_calls++;
+        return SEM_OK;
+    }
     // the first launch reads a fully stored level; later ones finish the
     // open nodes of the previous launch themselves; the flush completes the
     // open nodes after the last launch
@@ -862,6 +945,13 @@ sem_status sem_set_state(sem_mesh* m, const double* u, const double* u_prev, int
     if (st != SEM_OK) return st;
     if (m->nrec > 0 && step > m->trace_cap) return fail(m, SEM_ERR_INVALID_ARG, "step beyond max_steps");
     m->step = step;
+    if (m->scheme == SEM_SCHEME_HEUN) {
+        if ((st = write_nodes(m, m->d_u[0], u)) != SEM_OK) return st;
+        const size_t vb = (size_t)m->mesh.ne * (size_t)m->mesh.P * 2 * tsize(m);
+        SEM_CUDA(cudaMemsetAsync(m->d_v[0], 0, vb, m->stream));
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+        return SEM_OK;
+    }
     if ((st = write_nodes(m, level_u(m, step), u)) != SEM_OK) return st;
     if (m->prec == SEM_FP32_KAHAN) {
         std::vector<double> d((size_t)m->mesh.nn);
@@ -885,6 +975,13 @@ sem_status sem_get_state(sem_mesh* m, double* u, double* u_prev, int64_t* step) 
         return SEM_OK;
     }
     std::vector<double> un, tmp;
+    if (m->scheme == SEM_SCHEME_HEUN) {
+        sem_status st = read_nodes(m, m->d_u[0], fp64(m), un);
+        if (st != SEM_OK) return st;
+        if (u) to_original(m, un, u);
+        if (u_prev) std::fill(u_prev, u_prev + nn, 0.0);
+        return SEM_OK;
+    }
     sem_status st = read_nodes(m, level_u(m, m->step), fp64(m), un);
     if (st != SEM_OK) return st;
     if (m->prec == SEM_FP32_KAHAN) {
@@ -1268,8 +1365,8 @@ extern "C" {
 sem_status sem_misfit_gradient(sem_mesh* m, const double* d_obs, int64_t nsteps, int64_t checkpoint_every,
                                double* misfit, double* grad_vel) {
     if (!m || !d_obs || nsteps < 1 || checkpoint_every < 0) return SEM_ERR_INVALID_ARG;
-    if (m->prec == SEM_FP32_KAHAN)
-        return fail(m, SEM_ERR_UNSUPPORTED, "the adjoint runs on SEM_FP64 or SEM_FP32 (three-level) handles");
+    if (m->prec == SEM_FP32_KAHAN || m->scheme != SEM_SCHEME_LEAPFROG)
+        return fail(m, SEM_ERR_UNSUPPORTED, "the adjoint runs on leapfrog SEM_FP64 or SEM_FP32 (three-level) handles");
     if (!m->have_model || !m->have_dt) return fail(m, SEM_ERR_STATE, "model and dt must be set first");
     if (m->nrec < 1 || m->trace_cap < nsteps)
         return fail(m, SEM_ERR_STATE, "receivers with max_steps >= nsteps must be set first");
@@ -1645,7 +1742,8 @@ sem_status sem_batch_create(sem_mesh* const* shots, int32_t nshots, int32_t auto
     b->stream = m0->stream;
     b->prec = m0->prec;
     for (auto* m : b->shots) {
-        if (m->prec != b->prec || m->stream != b->stream || !m->have_model || !m->have_dt) {
+        if (m->prec != b->prec || m->stream != b->stream || !m->have_model || !m->have_dt ||
+            m->scheme != SEM_SCHEME_LEAPFROG) {
             delete b;
             return SEM_ERR_STATE;
         }

@@ -190,13 +190,98 @@ __device__ __forceinline__ BlockHdr load_hdr(const int4* hdr, int b) {
 
 __device__ __forceinline__ bool is_closed(const uint32_t* cmask, int p) { return (cmask[p >> 5] >> (p & 31)) & 1u; }
 
+// First-order node update of Heun's method: dU = s (K-side sum + f) with
+// s = 1/M; predictor U~ = U + h dU (and dU kept), corrector
+// U + h/2 (dU_pred + dU). ui is U (predictor) or U~ (corrector).
+template <typename T, int MODE>
+__device__ __forceinline__ T heun_node(const StepArgs<T>& a, int64_t g, T ui, T ksum, T f) {
+    const T du = __ldcg(a.s + g) * add_rn(ksum, f);
+    if (MODE == MODE_HEUN_P) {
+        __stcg(a.u_d1 + g, du);
+        return fma_rn((T)a.h, du, ui);
+    }
+    const T sum = add_rn(__ldcg(a.u_d1 + g), du);
+    return fma_rn((T)(0.5 * a.h), sum, __ldcg(a.u_old + g));
+}
+
+// Element part of the first-order system (Section 4.2): dV = grad u / rho at
+// each local node (Eq. v_change with F = I/rho, grad = J^-T grad_ref) and the
+// element's share of R (Eq. u_change_r_effic with B = -I):
+// -sum_q w_q |J_q| V_q . grad phi_p(x_q) = -(D^T W) with W = w adj(J) V
+// (|J| J^-1 = adj(J)). V advances in place of the element (predictor or
+// corrector); r receives the negated contraction.
+template <int NP, typename T, int MODE>
+__device__ __forceinline__ void heun_element(const Plan& pl, const StepArgs<T>& a, const Basis<T>& bs, int64_t e,
+                                             const uint32_t* pw, float4 cf0, float4 cf1, const T* su, T* r) {
+    constexpr int P = NP * NP;
+    T u[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        u[q] = su[(pw[q / 2] >> (16 * (q & 1))) & 0xFFFFu];
+        r[q] = T(0);
+    }
+    T bx, by, cx, cy, dx, dy, rinv;
+    if constexpr (sizeof(T) == 4) {
+        bx = cf0.x; by = cf0.y; cx = cf0.z; cy = cf0.w; dx = cf1.x; dy = cf1.y; rinv = cf1.z;
+    } else {
+        bx = __ldcs(pl.coef64 + 0 * pl.ne + e);
+        by = __ldcs(pl.coef64 + 1 * pl.ne + e);
+        cx = __ldcs(pl.coef64 + 2 * pl.ne + e);
+        cy = __ldcs(pl.coef64 + 3 * pl.ne + e);
+        dx = __ldcs(pl.coef64 + 4 * pl.ne + e);
+        dy = __ldcs(pl.coef64 + 5 * pl.ne + e);
+        rinv = __ldcs(pl.coef64 + 6 * pl.ne + e);
+    }
+    const T h = (T)a.h, h2 = (T)(0.5 * a.h);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const T eta = bs.x[j];
+        const T j00 = bx + dx * eta, j10 = by + dy * eta;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const int q = j * NP + i;
+            const T xi = bs.x[i];
+            const T j01 = cx + dx * xi, j11 = cy + dy * xi;
+            T dxi = T(0), deta = T(0);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                dxi += bs.D[i * NP + k] * u[j * NP + k];
+                deta += bs.D[j * NP + k] * u[k * NP + i];
+            }
+            const T rdet = T(1) / (j00 * j11 - j01 * j10);
+            const T vdx = (j11 * dxi - j10 * deta) * rdet * rinv;    // (J^-T grad_ref u)_x / rho
+            const T vdy = (j00 * deta - j01 * dxi) * rdet * rinv;
+            const int64_t ix = (int64_t)q * pl.ne + e, iy = (int64_t)(P + q) * pl.ne + e;
+            const T vx = __ldcs(a.v_in + ix), vy = __ldcs(a.v_in + iy);
+            const T wq = bs.W[q];
+            const T wxi = wq * (j11 * vx - j01 * vy);
+            const T weta = wq * (j00 * vy - j10 * vx);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) {
+                r[j * NP + m] -= bs.D[i * NP + m] * wxi;
+                r[m * NP + i] -= bs.D[j * NP + m] * weta;
+            }
+            if (MODE == MODE_HEUN_P) {
+                __stcg(a.v_d1 + ix, vdx);
+                __stcg(a.v_d1 + iy, vdy);
+                __stcg(a.v_out + ix, fma_rn(h, vdx, vx));
+                __stcg(a.v_out + iy, fma_rn(h, vdy, vy));
+            } else {
+                __stcg(a.v_out + ix, fma_rn(h2, add_rn(__ldcs(a.v_d1 + ix), vdx), __ldcs(a.v_old + ix)));
+                __stcg(a.v_out + iy, fma_rn(h2, add_rn(__ldcs(a.v_d1 + iy), vdy), __ldcs(a.v_old + iy)));
+            }
+        }
+    }
+}
+
 // One block of one mesh, one CTA (the body of the step kernels).
 template <int NP, typename T, int MODE>
 __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a, const Basis<T>& bs, const int b,
                                            unsigned char* smem_raw) {
     constexpr int P = NP * NP;
     constexpr int UPH = (P + 1) / 2;
-    constexpr bool STATE = MODE != MODE_APPLY;
+    constexpr bool HEUN = MODE == MODE_HEUN_P || MODE == MODE_HEUN_C;
+    constexpr bool STATE = MODE == MODE_THREE_LEVEL || MODE == MODE_KAHAN;   // leapfrog state staged
     constexpr bool KAHAN = MODE == MODE_KAHAN;
     constexpr bool BIL = sizeof(T) == 4;  // FP32: metric from the bilinear map; FP64: stored metric
     constexpr int VEC = 16 / sizeof(T);
@@ -221,9 +306,9 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     const bool has_el = tid < neb;
     // source values of this launch (the point source is one node)
     T f_now = T(0), f_prev = T(0);
-    if (STATE && a.src_gid >= 0) {
+    if ((STATE || HEUN) && a.src_gid >= 0) {
         f_now = (T)a.src_f[a.step];
-        if (a.pending) f_prev = (T)a.src_f[a.step - 1];
+        if (STATE && a.pending) f_prev = (T)a.src_f[a.step - 1];
     }
     const int64_t e = e0 + tid;
 
@@ -317,7 +402,9 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
 
     // B. element contraction in registers
     T r[P];
-    if (has_el) {
+    if (HEUN && has_el) {
+        heun_element<NP, T, MODE>(pl, a, bs, e, pw, cf0, cf1, su, r);
+    } else if (has_el) {
         T u[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) {
@@ -420,6 +507,23 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             const uint32_t bits = (cmask[p0 >> 5] >> (p0 & 31)) & ((1u << VEC) - 1u);
             if (bits == 0) continue;
             const int64_t g0 = abase + p0;
+            if constexpr (HEUN) {
+                T ui[VEC], ku[VEC], out[VEC];
+                load_vec<T, VEC>(ui, su + p0);
+                load_vec<T, VEC>(ku, acc + p0);
+#pragma unroll
+                for (int t = 0; t < VEC; ++t) {
+                    const T f = (g0 + t == a.src_gid) ? f_now : T(0);
+                    out[t] = heun_node<T, MODE>(a, g0 + t, ui[t], ku[t], f);
+                }
+                store_masked<T, VEC>(a.u_kp1 + g0, out, bits);
+                if (MODE == MODE_HEUN_C && h.nrc > 0) {
+#pragma unroll
+                    for (int t = 0; t < VEC; ++t)
+                        if ((bits >> t) & 1u) su[p0 + t] = out[t];
+                }
+                continue;
+            }
             load_vec<T, VEC>(vr, acc + p0);
             if (MODE == MODE_APPLY) {
                 store_masked<T, VEC>(a.apply_out + g0, vr, a.vec_ok ? bits : (bits | (1u << VEC)));
@@ -459,6 +563,11 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             const int64_t g = egid[p];
             if (MODE == MODE_APPLY) {
                 __stcg(a.apply_out + g, acc[p]);
+            } else if constexpr (HEUN) {
+                const T f = (g == a.src_gid) ? f_now : T(0);
+                const T out = heun_node<T, MODE>(a, g, su[p], acc[p], f);
+                __stcg(a.u_kp1 + g, out);
+                if (MODE == MODE_HEUN_C && h.nrc > 0) su[p] = out;
             } else {
                 const T f = (g == a.src_gid) ? f_now : T(0);
                 const Update<T, MODE> up = update_node<T, MODE>(su[p], sx[p], KAHAN ? sc[p] : T(0), ss[p], f, acc[p]);
@@ -475,11 +584,13 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
         }
     }
     for (int o = tid; o < h.nopen; o += nt) __stcg(a.part_wr + obase[o] + orank[o], acc[opos[o]]);
-    if (STATE && h.nrc > 0) {
+    if ((STATE || MODE == MODE_HEUN_C) && h.nrc > 0) {
         __syncthreads();
+        // the corrector of step n runs with a.step = n + 1 (source at t_{n+1})
+        const int64_t tix = HEUN ? a.step - 1 : a.step;
         for (int k = tid; k < h.nrc; k += nt) {
             const int pos = recs[2 * k], r2 = recs[2 * k + 1];
-            a.trace[(int64_t)r2 * a.trace_cap + a.step] =
+            a.trace[(int64_t)r2 * a.trace_cap + tix] =
                 trace_value<T, MODE>(su[pos], KAHAN ? (direct ? acc : sc)[pos] : T(0));
         }
     }
@@ -581,6 +692,14 @@ __global__ void __launch_bounds__(kThreads) sem_open_finish_kernel(const Plan pl
             a.apply_out[g] = acc;
             continue;
         }
+        if constexpr (MODE == MODE_HEUN_P || MODE == MODE_HEUN_C) {
+            const T f = (g == a.src_gid) ? (T)a.src_f[a.step] : T(0);
+            const T out = heun_node<T, MODE>(a, g, a.u_k[g], acc, f);
+            a.u_kp1[g] = out;
+            const int r = pl.open_rec[k];
+            if (MODE == MODE_HEUN_C && r >= 0) a.trace[(int64_t)r * a.trace_cap + a.step - 1] = (double)out;
+            continue;
+        } else {
         const T f = (g == a.src_gid) ? (T)a.src_f[a.step] : T(0);
         const Update<T, MODE> up =
             update_node<T, MODE>(a.u_k[g], a.x_k[g], MODE == MODE_KAHAN ? a.c_k[g] : T(0), a.s[g], f, acc);
@@ -591,6 +710,7 @@ __global__ void __launch_bounds__(kThreads) sem_open_finish_kernel(const Plan pl
         }
         const int r = pl.open_rec[k];
         if (r >= 0) a.trace[(int64_t)r * a.trace_cap + a.step] = trace_value<T, MODE>(up.u, up.c);
+        }
     }
 }
 
@@ -598,7 +718,7 @@ __global__ void __launch_bounds__(kThreads) sem_open_finish_kernel(const Plan pl
 __global__ void geometry_kernel(int np, int64_t ne, const double* __restrict__ coords,
                                 const int32_t* __restrict__ quads, const double* __restrict__ rho,
                                 const double* __restrict__ vel, const Basis<double> bs, float4* coef, double* G64,
-                                double* mloc) {
+                                double* mloc, double* coef64) {
     const int P = np * np;
     const int64_t total = ne * P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -623,6 +743,10 @@ __global__ void geometry_kernel(int np, int64_t ne, const double* __restrict__ c
         if (q == 0 && coef != nullptr) {
             coef[e] = make_float4((float)bx, (float)by, (float)cx, (float)cy);
             coef[ne + e] = make_float4((float)dx, (float)dy, (float)rinv, 0.0f);
+        }
+        if (q == 0 && coef64 != nullptr) {
+            const double c8[8] = {bx, by, cx, cy, dx, dy, rinv, 0.0};
+            for (int k = 0; k < 8; ++k) coef64[(int64_t)k * ne + e] = c8[k];
         }
         const double xi = bs.x[i], eta = bs.x[j];
         const double j00 = bx + dx * eta, j10 = by + dy * eta;
@@ -688,9 +812,9 @@ __global__ void mass_open_kernel(const Plan pl, const double* __restrict__ parti
     }
 }
 
-__global__ void scale_kernel(const double* __restrict__ M, int64_t nn, double dt, double* s64, float* s32) {
+__global__ void scale_kernel(const double* __restrict__ M, int64_t nn, double num, double* s64, float* s32) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (dt * dt) / M[g];
+        const double v = num / M[g];
         if (s64) s64[g] = v;
         if (s32) s32[g] = (float)v;
     }
@@ -842,7 +966,8 @@ int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, b
     (void)eb;
     const int sz = fp64 ? 8 : 4;
     const bool direct = dense;
-    const int staged = mode == MODE_APPLY ? 0 : (direct ? 1 : (mode == MODE_KAHAN ? 3 : 2));
+    const bool leap = mode == MODE_THREE_LEVEL || mode == MODE_KAHAN;
+    const int staged = !leap ? 0 : (direct ? 1 : (mode == MODE_KAHAN ? 3 : 2));
     return max_packet + (2 * sulen_pad + staged * slen_pad) * sz;
 }
 
@@ -853,6 +978,8 @@ cudaError_t launch_step(int np, bool fp64, int mode, const Plan& pl, const void*
         switch (mode) {
             case MODE_THREE_LEVEL: return dispatch_np<double, MODE_THREE_LEVEL>(np, pl, args, basis, threads, smem, st);
             case MODE_APPLY: return dispatch_np<double, MODE_APPLY>(np, pl, args, basis, threads, smem, st);
+            case MODE_HEUN_P: return dispatch_np<double, MODE_HEUN_P>(np, pl, args, basis, threads, smem, st);
+            case MODE_HEUN_C: return dispatch_np<double, MODE_HEUN_C>(np, pl, args, basis, threads, smem, st);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -860,6 +987,8 @@ cudaError_t launch_step(int np, bool fp64, int mode, const Plan& pl, const void*
         case MODE_THREE_LEVEL: return dispatch_np<float, MODE_THREE_LEVEL>(np, pl, args, basis, threads, smem, st);
         case MODE_KAHAN: return dispatch_np<float, MODE_KAHAN>(np, pl, args, basis, threads, smem, st);
         case MODE_APPLY: return dispatch_np<float, MODE_APPLY>(np, pl, args, basis, threads, smem, st);
+        case MODE_HEUN_P: return dispatch_np<float, MODE_HEUN_P>(np, pl, args, basis, threads, smem, st);
+        case MODE_HEUN_C: return dispatch_np<float, MODE_HEUN_C>(np, pl, args, basis, threads, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -871,12 +1000,17 @@ cudaError_t launch_open_finish(bool fp64, int mode, const Plan& pl, const void* 
         const auto& a = *static_cast<const StepArgs<double>*>(args);
         if (mode == MODE_THREE_LEVEL) sem_open_finish_kernel<double, MODE_THREE_LEVEL><<<grid, kThreads, 0, st>>>(pl, a);
         else if (mode == MODE_APPLY) sem_open_finish_kernel<double, MODE_APPLY><<<grid, kThreads, 0, st>>>(pl, a);
+        else if (mode == MODE_HEUN_P) sem_open_finish_kernel<double, MODE_HEUN_P><<<grid, kThreads, 0, st>>>(pl, a);
+        else if (mode == MODE_HEUN_C) sem_open_finish_kernel<double, MODE_HEUN_C><<<grid, kThreads, 0, st>>>(pl, a);
         else return cudaErrorInvalidValue;
     } else {
         const auto& a = *static_cast<const StepArgs<float>*>(args);
         if (mode == MODE_THREE_LEVEL) sem_open_finish_kernel<float, MODE_THREE_LEVEL><<<grid, kThreads, 0, st>>>(pl, a);
         else if (mode == MODE_KAHAN) sem_open_finish_kernel<float, MODE_KAHAN><<<grid, kThreads, 0, st>>>(pl, a);
-        else sem_open_finish_kernel<float, MODE_APPLY><<<grid, kThreads, 0, st>>>(pl, a);
+        else if (mode == MODE_APPLY) sem_open_finish_kernel<float, MODE_APPLY><<<grid, kThreads, 0, st>>>(pl, a);
+        else if (mode == MODE_HEUN_P) sem_open_finish_kernel<float, MODE_HEUN_P><<<grid, kThreads, 0, st>>>(pl, a);
+        else if (mode == MODE_HEUN_C) sem_open_finish_kernel<float, MODE_HEUN_C><<<grid, kThreads, 0, st>>>(pl, a);
+        else return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
@@ -927,9 +1061,9 @@ cudaError_t launch_gradient(int64_t ne, int P, const int32_t* conn, const double
 
 cudaError_t launch_geometry(int np, int64_t ne, const double* coords, const int32_t* quads_new, const double* rho,
                             const double* vel, const Basis<double>& basis, float4* coef, double* G64, double* mloc,
-                            cudaStream_t st) {
+                            double* coef64, cudaStream_t st) {
     geometry_kernel<<<grid_for(ne * np * np, kThreads), kThreads, 0, st>>>(np, ne, coords, quads_new, rho, vel, basis,
-                                                                          coef, G64, mloc);
+                                                                          coef, G64, mloc, coef64);
     return cudaGetLastError();
 }
 
@@ -961,8 +1095,8 @@ cudaError_t launch_mass(const Plan& pl, int np, const double* mloc, double* part
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale(const double* M, int64_t nn, double dt, double* s64, float* s32, cudaStream_t st) {
-    scale_kernel<<<grid_for(nn, kThreads), kThreads, 0, st>>>(M, nn, dt, s64, s32);
+cudaError_t launch_scale(const double* M, int64_t nn, double num, double* s64, float* s32, cudaStream_t st) {
+    scale_kernel<<<grid_for(nn, kThreads), kThreads, 0, st>>>(M, nn, num, s64, s32);
     return cudaGetLastError();
 }
 

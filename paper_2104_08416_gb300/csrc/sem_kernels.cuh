@@ -28,6 +28,7 @@ struct Plan {
     const uint32_t* epos;      // [(P+1)/2][ne]
     const float4* coef;        // [2][ne] bilinear map (FP32 kernels)
     const double* G;           // [3P][ne] stored metric (FP64 kernels)
+    const double* coef64;      // [8][ne] FP64 bilinear map, 1/rho (FP64 first-order kernels)
     const int32_t* open_gid;   // open nodes, ascending
     const int32_t* open_base;
     const int32_t* open_cnt;
@@ -43,7 +44,9 @@ struct Plan {
 enum Mode : int {
     MODE_THREE_LEVEL = 0,  // u^{n+1} = 2u^n - u^{n-1} + s (f e_src - K u^n)
     MODE_KAHAN = 1,        // delta += s (f e_src - K u); u += delta, Kahan-compensated
-    MODE_APPLY = 2         // out = K u
+    MODE_APPLY = 2,        // out = K u
+    MODE_HEUN_P = 3,       // Heun predictor on the first-order system (see StepArgs)
+    MODE_HEUN_C = 4        // Heun corrector
 };
 
 // Node state of "level" m: three-level mode (u^m, u^{m-1}); Kahan mode
@@ -78,6 +81,20 @@ struct StepArgs {
     int64_t trace_cap;
     int pending;
     int vec_ok;           // node arrays 16-byte aligned (vector copies allowed)
+    // first-order system (Section 4.1-4.2: pressure U at global nodes,
+    // velocity V at every element's local nodes, layout [2P][ne]) advanced by
+    // Heun's method: the predictor reads U (u_k) and V (v_in), writes
+    // U~ = U + h dU (u_kp1), V~ = V + h dV (v_out) and the rates dU (u_d1),
+    // dV (v_d1); the corrector reads U~ (u_k), V~ (v_in), U (u_old), V (v_old)
+    // and the rates, and writes U + h/2 (dU + dU~) (u_kp1), V + h/2 (dV + dV~)
+    // (v_out). s holds 1/M; the source value is f(t_step).
+    const T* v_in;
+    T* v_out;
+    const T* v_old;
+    T* v_d1;
+    const T* u_old;
+    T* u_d1;
+    double h;
 };
 
 // Per-shot data of a batch (device memory): the shot's plan and its level
@@ -119,12 +136,13 @@ cudaError_t launch_open_finish(bool fp64, int mode, const Plan& plan, const void
 // metric (G64 non-null) and w_q |J_q| / (rho c^2) per slot (mloc).
 cudaError_t launch_geometry(int np, int64_t ne, const double* coords, const int32_t* quads_new, const double* rho,
                             const double* vel, const Basis<double>& basis, float4* coef, double* G64, double* mloc,
-                            cudaStream_t st);
+                            double* coef64, cudaStream_t st);
 // Lumped mass through the block plan (deterministic), M[nn] in FP64; mloc
 // per slot in the device element order.
 cudaError_t launch_mass(const Plan& plan, int np, const double* mloc, double* partial, double* M, cudaStream_t st);
-// s = dt^2 / M (FP64 arithmetic, rounded once to the storage type).
-cudaError_t launch_scale(const double* M, int64_t nn, double dt, double* s64, float* s32, cudaStream_t st);
+// s = num / M (num = dt^2 for the leapfrog, 1 for the first-order system;
+// FP64 arithmetic, rounded once to the storage type).
+cudaError_t launch_scale(const double* M, int64_t nn, double num, double* s64, float* s32, cudaStream_t st);
 
 // Discrete adjoint of the leapfrog (FP64 or FP32 three-level storage): the
 // backward update, the receiver residuals of step m, the correlation
