@@ -45,6 +45,10 @@ L2_BYTES = 129 * 2 ** 20
 # node state: FP32 three-level u r/w, u_prev r, s r; Kahan u, delta, c r/w,
 # s r; FP64 three-level as FP32 with 8-byte values)
 ALGO_BYTES = {"fp32": 41.0, "fp32_kahan": 53.0, "fp64": 76.0}
+# the first-order system with Heun steps, per node-update at p = 4: velocity
+# per slot (2 values) read/written 7 times, connectivity twice, node values
+# (U, U~, dU, s) read/written 9 times
+ALGO_BYTES_HEUN = {"fp32": 136.0, "fp64": 272.0}
 
 
 def parse():
@@ -64,6 +68,8 @@ def parse():
     ap.add_argument("--batch-nmax", type=int, default=1024)
     ap.add_argument("--no-compare", action="store_true", help="skip the per-ordering comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scheme", default="leapfrog", choices=["leapfrog", "heun"],
+                    help="leapfrog (default) or the paper's first-order system with Heun steps")
     ap.add_argument("--eb", type=int, default=0, help="elements per block (0 = library default)")
     ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = library default)")
     return ap.parse_args()
@@ -164,8 +170,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_handle(P, m, precision, ordering, nsteps_cap, eb=0, threads=0):
+def make_handle(P, m, precision, ordering, nsteps_cap, eb=0, threads=0, scheme="leapfrog"):
     h = P.SEM(m["coords"], m["quads"], 4, precision)
+    if scheme != "leapfrog":
+        h.sem_set_scheme(scheme)
     h.sem_reorder(ordering)
     h.sem_set_model(m["vel"], m["rho"])
     if eb or threads:
@@ -428,7 +436,7 @@ def main():
     m = workload(args, rank)
     wname = "layered_4096x1024_p4" if args.workload == "layered" else (WORKLOAD if args.n == 512 else f"graded_{args.n}x{args.n}_p4")
     cap = W + 2 * K + 8
-    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads)
+    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads, args.scheme)
     N = h.n_nodes
     # warm-up (the first call builds the device data)
     h.sem_step(W)
@@ -457,7 +465,7 @@ def main():
     # traces and wavefield back to the host, all inside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb, args.threads)
+    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb, args.threads, args.scheme)
     h2.sem_step(K)
     tr = h2.sem_read_traces()
     u2 = h2.sem_read_wavefield()
@@ -473,7 +481,7 @@ def main():
         orderings = {}
         kk = min(K, 500)
         for kind in ("hilbert", "rowmajor", "random", "none", "connectivity", "distance"):
-            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb, args.threads)
+            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb, args.threads, args.scheme)
             hh.sem_step(W)
             t_ord = time_steps(torch, hh, kk)
             hh.sem_profile_enable(True)
@@ -503,7 +511,8 @@ def main():
     blk_us = 1e3 * bms / max(bl, 1)
     # algorithmic bytes of one step-kernel launch: the per-node-update figure
     # of the hot path times the nodes one launch updates
-    achieved = ALGO_BYTES[args.precision] * N / (blk_us * 1e-6) / 1e9
+    algo = (ALGO_BYTES_HEUN if args.scheme == "heun" else ALGO_BYTES)[args.precision]
+    achieved = algo * N / (blk_us * 1e-6) / 1e9
     traffic = recorded_traffic(args.precision, args.ordering) if wname == WORKLOAD else None
     value = job_rate(world, N, K, el)
     line = {
@@ -511,19 +520,19 @@ def main():
         "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32_kahan": "f32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": wname, "nodes": N, "elements": m["quads"].shape[0], "order": 4,
-                   "precision": args.precision, "ordering": args.ordering,
+                   "precision": args.precision, "ordering": args.ordering, "scheme": args.scheme,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
                    "finite": finite},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "sem_step_kernel", "peak_kind": peak_kind,
                      "step_kernel_us": blk_us, "open_kernel_us_per_run": 1e3 * oms / max(ol, 1),
-                     "algorithmic_bytes_per_launch": ALGO_BYTES[args.precision] * N,
+                     "algorithmic_bytes_per_launch": algo * N,
                      "compulsory_bytes_per_launch": block_bytes, "compulsory_gbs": block_bytes / (blk_us * 1e-6) / 1e9,
                      "open_bytes_per_launch": open_bytes,
                      "open_nodes": nopen, "profiled_ms_per_step": 1e3 * prof_el / K,
-                     "algorithmic_bytes_per_node_update": ALGO_BYTES[args.precision],
-                     "algorithmic_gbs_per_step": ALGO_BYTES[args.precision] * N * K / el / 1e9},
+                     "algorithmic_bytes_per_node_update": algo,
+                     "algorithmic_gbs_per_step": algo * N * K / el / 1e9},
         "cpu_baseline": cpu,
         "e2e": {"value": world * N * K / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K, "includes": "mesh set-up, reordering, precompute, K steps, read-back"},
