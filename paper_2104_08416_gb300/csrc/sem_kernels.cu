@@ -34,9 +34,12 @@ constexpr int kMaxStepThreads = 256;
 // Resident CTAs the compiler budgets registers for: three (80 registers a
 // thread, a few spilled values) for FP32 up to order 4, where the extra
 // resident warps outweigh the spills; one for larger elements and FP64.
+#ifndef SEM_STEP_MINB
+#define SEM_STEP_MINB 3
+#endif
 template <int NP, typename T>
 constexpr int step_min_blocks() {
-    return (sizeof(T) == 4 && NP <= 5) ? 3 : 1;
+    return (sizeof(T) == 4 && NP <= 5) ? SEM_STEP_MINB : 1;
 }
 
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }

@@ -212,3 +212,25 @@ def test_plain_fp32_three_level(P):
     u, tr, _ = gpu_run(P, m, 4, "fp32", "hilbert", 400, dt, m["receivers"])
     assert rel_l2(u, u_ref) < 1e-4, rel_l2(u, u_ref)
     assert rel_l2(tr, tr_ref) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
+def test_degenerate_meshes(P, prec):
+    """One element; a 1 x 9 strip; one element per block; zero steps."""
+    tol = FP64_TOL if prec == "fp64" else FP32_TOL
+    one = dict(gen.unit_square(1))
+    strip = gen.layered(9, 1, width=9.0, depth=1.0, n_receivers=3)
+    strip["src_xy"], strip["f0"], strip["t0"] = (4.5, 0.5), 2.0, 0.6
+    for m, p, eb in ((one, 4, 0), (one, 1, 1), (strip, 3, 1), (strip, 5, 2)):
+        S = osem.SEM(m["coords"], m["quads"], p, m["vel"], m["rho"])
+        dt = 0.3 * S.cfl_dt()
+        rec = np.asarray(m["receivers"])
+        _, u_ref, tr_ref = oracle_run(m, p, 40, dt, rec)
+        u, tr, _ = gpu_run(P, m, p, prec, "hilbert", 40, dt, rec, eb=eb)
+        assert rel_l2(u, u_ref) < tol and rel_l2(tr, tr_ref) < tol
+    h = P.SEM(one["coords"], one["quads"], 2, prec)
+    h.sem_set_model(one["vel"])
+    h.sem_set_dt(1e-3)
+    h.sem_step(0)
+    assert h.sem_get_step() == 0 and np.all(h.sem_read_wavefield() == 0)
+    h.sem_destroy()
