@@ -9,6 +9,8 @@
 #include <limits>
 #include <numeric>
 #include <unordered_map>
+#include <atomic>
+#include <thread>
 
 namespace semhost {
 
@@ -689,78 +691,95 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
     pl.dev_order.resize((size_t)ne);
     pl.epos.assign((size_t)UPH * (size_t)ne, 0u);
     pl.hdr.assign((size_t)nb * HDR_INTS, 0);
-    std::vector<int32_t> seen_rank((size_t)nn, 0);   // blocks that touched the node so far
-    std::vector<int64_t> in_block((size_t)nn, -1);
-    std::vector<int32_t> local((size_t)nn, -1);
-    std::vector<uint32_t> node_colors((size_t)nn, 0);
-    std::vector<uint8_t> touched((size_t)nn, 0);
-    std::vector<int32_t> ent_gid, elem_color, recs;
-    int64_t own_next = 0;
-    for (int64_t b = 0; b < nb; ++b) {
-        const int64_t e0 = b * eb, e1 = std::min(ne, e0 + eb);
-        const int neb = (int)(e1 - e0);
-        // entries: owned nodes in id order (DENSE), then the others by first appearance
-        ent_gid.clear();
-        int64_t own_start = 0, nown = 0;
-        if (dense) {
-            own_start = own_next;
+
+    // pass 1 (sequential, linear): the entries of every block (owned nodes in
+    // id order for DENSE, then the others by first appearance) and, per entry,
+    // the rank of the block among the blocks that touch its node
+    std::vector<int64_t> ent_ptr((size_t)nb + 1, 0), own_start_b((size_t)nb, 0), nown_b((size_t)nb, 0);
+    std::vector<int32_t> ent_all;
+    std::vector<uint8_t> rank_all;
+    ent_all.reserve((size_t)(nn + nn / 4));
+    rank_all.reserve((size_t)(nn + nn / 4));
+    {
+        std::vector<int32_t> seen_rank((size_t)nn, 0);
+        std::vector<int64_t> in_block((size_t)nn, -1);
+        std::vector<uint8_t> touched((size_t)nn, 0);
+        int64_t own_next = 0;
+        for (int64_t b = 0; b < nb; ++b) {
+            const int64_t e0 = b * eb, e1 = std::min(ne, e0 + eb);
+            if (dense) {
+                int64_t nown = 0;
+                for (int64_t t = e0 * P; t < e1 * P; ++t) {
+                    const int32_t g = conn[(size_t)t];
+                    if (!touched[(size_t)g]) {
+                        touched[(size_t)g] = 1;
+                        nown++;
+                    }
+                }
+                own_start_b[(size_t)b] = own_next;
+                nown_b[(size_t)b] = nown;
+                for (int64_t l = 0; l < nown; ++l) {
+                    const int32_t g = (int32_t)(own_next + l);
+                    in_block[(size_t)g] = b;
+                    ent_all.push_back(g);
+                }
+                own_next += nown;
+            }
             for (int64_t t = e0 * P; t < e1 * P; ++t) {
                 const int32_t g = conn[(size_t)t];
-                if (!touched[(size_t)g]) {
-                    touched[(size_t)g] = 1;
-                    nown++;
+                if (in_block[(size_t)g] != b) {
+                    in_block[(size_t)g] = b;
+                    ent_all.push_back(g);
                 }
             }
-            for (int64_t l = 0; l < nown; ++l) {
-                const int32_t g = (int32_t)(own_start + l);
-                in_block[(size_t)g] = b;
-                local[(size_t)g] = (int32_t)l;
-                ent_gid.push_back(g);
-            }
-            own_next = own_start + nown;
+            for (size_t k = (size_t)ent_ptr[(size_t)b]; k < ent_all.size(); ++k)
+                rank_all.push_back((uint8_t)seen_rank[(size_t)ent_all[k]]++);
+            ent_ptr[(size_t)b + 1] = (int64_t)ent_all.size();
         }
-        for (int64_t t = e0 * P; t < e1 * P; ++t) {
-            const int32_t g = conn[(size_t)t];
-            if (in_block[(size_t)g] != b) {
-                in_block[(size_t)g] = b;
-                local[(size_t)g] = (int32_t)ent_gid.size();
-                ent_gid.push_back(g);
-            }
-        }
-        const int64_t nent = (int64_t)ent_gid.size();
+    }
+
+    // pass 2 (blocks in parallel): colouring, device order, local lists and
+    // the packet body of each block, into per-block buffers; every write to
+    // the shared outputs (hdr, dev_order, epos) touches the block's own part
+    std::vector<std::vector<uint8_t>> bodies((size_t)nb);
+    std::vector<int64_t> nclosed_b((size_t)nb, 0), nopen_b((size_t)nb, 0);
+    std::vector<std::string> errs((size_t)nb);
+    auto plan_block = [&](int64_t b) -> std::string {
+        const int64_t e0 = b * eb, e1 = std::min(ne, e0 + eb);
+        const int neb = (int)(e1 - e0);
+        const int32_t* ent_gid = ent_all.data() + ent_ptr[(size_t)b];
+        const uint8_t* rank = rank_all.data() + ent_ptr[(size_t)b];
+        const int64_t nent = ent_ptr[(size_t)b + 1] - ent_ptr[(size_t)b];
+        const int64_t own_start = own_start_b[(size_t)b], nown = nown_b[(size_t)b];
         const int64_t off = dense ? own_start % vec : 0;
         const int64_t ulen = dense ? align_up(off + nown, vec) : 0;
         const int64_t sulen = ulen + (nent - nown);
         const int64_t slen = dense ? ulen : nent;
         if (nent > 65535 || sulen > 65535) return "too many nodes in one element block";
+        // entry of each slot: node ids sorted with their entry index
+        std::vector<std::pair<int32_t, int32_t>> idx((size_t)nent);
+        for (int64_t l = 0; l < nent; ++l) idx[(size_t)l] = {ent_gid[l], (int32_t)l};
+        std::sort(idx.begin(), idx.end());
+        std::vector<int32_t> slot_ent((size_t)neb * P);
+        for (int64_t t = 0; t < (int64_t)neb * P; ++t) {
+            const int32_t g = conn[(size_t)(e0 * P + t)];
+            slot_ent[(size_t)t] = std::lower_bound(idx.begin(), idx.end(), std::make_pair(g, (int32_t)-1))->second;
+        }
         // colouring of the block's conflict graph (elements sharing a node)
         // by DSatur: repeatedly colour the uncoloured element whose coloured
         // neighbours use the most distinct colours (ties: most neighbours,
         // then lowest index) with the smallest free colour
+        std::vector<int32_t> elem_color((size_t)neb, -1);
         int ncolors = 0;
         {
             const int W = (neb + 63) / 64;
             std::vector<uint64_t> adj((size_t)neb * W, 0);
+            std::vector<std::vector<int>> touch((size_t)nent);
             for (int el = 0; el < neb; ++el)
                 for (int q = 0; q < P; ++q) {
-                    const int32_t g = conn[(size_t)((e0 + el) * P + q)];
-                    // node_colors doubles as "last element of this block that touched g, plus one"
-                    node_colors[(size_t)g] = 0;
-                }
-            std::vector<std::vector<int>> touch;
-            touch.reserve((size_t)nent);
-            for (int el = 0; el < neb; ++el)
-                for (int q = 0; q < P; ++q) {
-                    const int32_t g = conn[(size_t)((e0 + el) * P + q)];
-                    if (node_colors[(size_t)g] == 0) {
-                        touch.emplace_back();
-                        node_colors[(size_t)g] = (uint32_t)touch.size();
-                    }
-                    auto& lst = touch[(size_t)node_colors[(size_t)g] - 1];
+                    auto& lst = touch[(size_t)slot_ent[(size_t)(el * P + q)]];
                     if (lst.empty() || lst.back() != el) lst.push_back(el);
                 }
-            for (int el = 0; el < neb; ++el)
-                for (int q = 0; q < P; ++q) node_colors[(size_t)conn[(size_t)((e0 + el) * P + q)]] = 0;
             for (const auto& lst : touch)
                 for (size_t x = 0; x < lst.size(); ++x)
                     for (size_t y = x + 1; y < lst.size(); ++y) {
@@ -771,7 +790,6 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
             for (int el = 0; el < neb; ++el)
                 for (int w = 0; w < W; ++w) deg[(size_t)el] += __builtin_popcountll(adj[(size_t)el * W + w]);
             std::vector<uint32_t> sat((size_t)neb, 0);
-            elem_color.assign((size_t)neb, -1);
             for (int it = 0; it < neb; ++it) {
                 int best = -1, bs = -1, bd = -1;
                 for (int el = 0; el < neb; ++el) {
@@ -803,21 +821,22 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         std::vector<int32_t> cstart((size_t)ncolors + 1, 0);
         for (int el = 0; el < neb; ++el) cstart[(size_t)elem_color[(size_t)el] + 1]++;
         for (int c = 0; c < ncolors; ++c) cstart[(size_t)c + 1] += cstart[(size_t)c];
+        std::vector<int32_t> order_in_block((size_t)neb);
         {
             std::vector<int32_t> fill(cstart.begin(), cstart.end() - 1);
-            for (int el = 0; el < neb; ++el)
-                pl.dev_order[(size_t)(e0 + fill[(size_t)elem_color[(size_t)el]]++)] = e0 + el;
+            for (int el = 0; el < neb; ++el) order_in_block[(size_t)fill[(size_t)elem_color[(size_t)el]]++] = el;
         }
+        for (int i = 0; i < neb; ++i) pl.dev_order[(size_t)(e0 + i)] = e0 + order_in_block[(size_t)i];
         // open ranks in entry order
         std::vector<int32_t> orank_of((size_t)nent, -1);
         int64_t nopen = 0;
         for (int64_t l = 0; l < nent; ++l)
-            if (nblk[(size_t)ent_gid[(size_t)l]] > 1) orank_of[(size_t)l] = (int32_t)nopen++;
+            if (nblk[(size_t)ent_gid[l]] > 1) orank_of[(size_t)l] = (int32_t)nopen++;
         if (nopen > 65535) return "too many open nodes in one element block";
-        recs.clear();
+        std::vector<int32_t> recs;
         int64_t nrc = 0, nro = 0;
         for (int64_t l = 0; l < nent; ++l) {
-            const int32_t g = ent_gid[(size_t)l];
+            const int32_t g = ent_gid[l];
             if (rec_of[(size_t)g] >= 0 && orank_of[(size_t)l] < 0) {
                 recs.push_back(entry_pos((int)l, (int)nown, (int)off, (int)ulen));
                 recs.push_back(rec_of[(size_t)g]);
@@ -825,17 +844,17 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
             }
         }
         for (int64_t l = 0; l < nent; ++l) {
-            const int32_t g = ent_gid[(size_t)l];
-            if (rec_of[(size_t)g] >= 0 && orank_of[(size_t)l] >= 0 && seen_rank[(size_t)g] == 0) {
+            const int32_t g = ent_gid[l];
+            if (rec_of[(size_t)g] >= 0 && orank_of[(size_t)l] >= 0 && rank[l] == 0) {
                 recs.push_back(entry_pos((int)l, (int)nown, (int)off, (int)ulen));
                 recs.push_back(rec_of[(size_t)g]);
                 nro++;
             }
         }
         const Offsets L = offsets((int)sulen, (int)ulen, (int)nopen, ncolors, (int)(nrc + nro));
-        const int64_t start = (int64_t)pl.packet.size();
-        pl.packet.resize((size_t)(start + L.bytes), 0);
-        uint8_t* pk = pl.packet.data() + start;
+        std::vector<uint8_t>& body = bodies[(size_t)b];
+        body.assign((size_t)L.bytes, 0);
+        uint8_t* pk = body.data();
         uint32_t* cmask = reinterpret_cast<uint32_t*>(pk + L.cmask);
         int32_t* egid = reinterpret_cast<int32_t*>(pk + L.egid);
         int32_t* obase = reinterpret_cast<int32_t*>(pk + L.obase);
@@ -844,34 +863,33 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         uint8_t* orank = pk + L.orank;
         uint16_t* pcs = reinterpret_cast<uint16_t*>(pk + L.cstart);
         int32_t* prec = reinterpret_cast<int32_t*>(pk + L.recs);
+        int64_t nclosed = 0;
         for (int64_t l = 0; l < nent; ++l) {
-            const int32_t g = ent_gid[(size_t)l];
+            const int32_t g = ent_gid[l];
             const int32_t o = orank_of[(size_t)l];
             const int pos = entry_pos((int)l, (int)nown, (int)off, (int)ulen);
             if (o < 0) {
                 cmask[pos >> 5] |= 1u << (pos & 31);
-                pl.nclosed_total++;
+                nclosed++;
             } else {
                 obase[o] = (int32_t)base[(size_t)g];
                 opos[o] = (uint16_t)pos;
                 ocnt[o] = (uint8_t)nblk[(size_t)g];
-                orank[o] = (uint8_t)seen_rank[(size_t)g];
+                orank[o] = rank[l];
             }
-            seen_rank[(size_t)g]++;
             if (l >= nown) egid[pos - ulen] = g;
         }
         for (int c = 0; c <= ncolors; ++c) pcs[c] = (uint16_t)cstart[(size_t)c];
         std::copy(recs.begin(), recs.end(), prec);
         for (int i = 0; i < neb; ++i) {
-            const int64_t e = pl.dev_order[(size_t)(e0 + i)];
+            const int el = order_in_block[(size_t)i];
             for (int q = 0; q < P; ++q) {
-                const int l = local[(size_t)conn[(size_t)(e * P + q)]];
+                const int l = slot_ent[(size_t)(el * P + q)];
                 const uint32_t pos = (uint32_t)entry_pos(l, (int)nown, (int)off, (int)ulen);
                 pl.epos[(size_t)(q / 2) * (size_t)ne + (size_t)(e0 + i)] |= pos << (16 * (q & 1));
             }
         }
         int32_t* h = &pl.hdr[(size_t)b * HDR_INTS];
-        h[H_START] = (int32_t)(start / 16);
         h[H_NENT] = (int32_t)nent;
         h[H_NOWN] = (int32_t)nown;
         h[H_OWN_START] = (int32_t)own_start;
@@ -882,13 +900,45 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         h[H_NCOLORS] = ncolors;
         h[H_NREC_CLOSED] = (int32_t)nrc;
         h[H_NREC_OPEN] = (int32_t)nro;
-        pl.max_entries = std::max<int>(pl.max_entries, (int)nent);
-        pl.max_sulen = std::max<int>(pl.max_sulen, (int)sulen);
-        pl.max_slen = std::max<int>(pl.max_slen, (int)slen);
-        pl.max_packet = std::max<int>(pl.max_packet, L.bytes);
-        pl.max_colors = std::max(pl.max_colors, ncolors);
-        pl.nent_total += nent;
-        pl.nopen_entries += nopen;
+        nclosed_b[(size_t)b] = nclosed;
+        nopen_b[(size_t)b] = nopen;
+        return "";
+    };
+    {
+        std::atomic<int64_t> next(0);
+        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        const unsigned nthr = (unsigned)std::min<int64_t>(hw, std::max<int64_t>(1, nb / 8));
+        auto work = [&]() {
+            for (int64_t b = next++; b < nb; b = next++) errs[(size_t)b] = plan_block(b);
+        };
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < nthr; ++t) pool.emplace_back(work);
+        work();
+        for (auto& t : pool) t.join();
+    }
+    for (int64_t b = 0; b < nb; ++b)
+        if (!errs[(size_t)b].empty()) return errs[(size_t)b];
+
+    // pass 3: the packets block after block, and the plan's maxima
+    size_t total = 0;
+    for (const auto& body : bodies) total += body.size();
+    pl.packet.resize(total);
+    size_t start = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const auto& body = bodies[(size_t)b];
+        std::memcpy(pl.packet.data() + start, body.data(), body.size());
+        int32_t* h = &pl.hdr[(size_t)b * HDR_INTS];
+        h[H_START] = (int32_t)(start / 16);
+        start += body.size();
+        pl.max_entries = std::max<int>(pl.max_entries, h[H_NENT]);
+        pl.max_sulen = std::max<int>(pl.max_sulen, h[H_SULEN]);
+        pl.max_slen = std::max<int>(pl.max_slen, h[H_SLEN]);
+        pl.max_packet = std::max<int>(pl.max_packet, (int)body.size());
+        pl.max_colors = std::max(pl.max_colors, h[H_NCOLORS]);
+        pl.nent_total += h[H_NENT];
+        pl.nopen_entries += nopen_b[(size_t)b];
+        pl.nclosed_total += nclosed_b[(size_t)b];
+        std::vector<uint8_t>().swap(bodies[(size_t)b]);
     }
     if ((int64_t)pl.packet.size() / 16 > INT32_MAX) return "packet array too large";
     return "";
