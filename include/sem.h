@@ -108,8 +108,10 @@ typedef enum {
 typedef struct sem_mesh sem_mesh;
 
 /* Optional device allocator (e.g. a framework's caching allocator). alloc
- * returns a device pointer of at least `bytes` bytes usable on `stream`, or
- * NULL on failure; free releases it. Applies to handles created afterwards
+ * returns a 16-byte aligned device pointer of at least `bytes` bytes usable
+ * on `stream`, or NULL on failure; free releases it. A pointer that is not
+ * 16-byte aligned is released again and the call that needed it fails with
+ * SEM_ERR_OOM. Applies to handles created afterwards
  * in this process. Pass NULLs to restore cudaMalloc/cudaFree. */
 typedef void* (*sem_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*sem_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);

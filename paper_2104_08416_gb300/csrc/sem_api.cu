@@ -145,6 +145,12 @@ void* dev_alloc(sem_mesh* m, size_t bytes) {
     void* p = nullptr;
     if (m->alloc) {
         p = m->alloc(bytes, (void*)m->stream, m->alloc_ctx);
+        // the kernels copy node arrays with 16-byte vectors: a pointer off
+        // that boundary is handed back and reported as a failed allocation
+        if (p && ((uintptr_t)p % 16) != 0) {
+            if (m->free_fn) m->free_fn(p, bytes, (void*)m->stream, m->alloc_ctx);
+            p = nullptr;
+        }
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
@@ -493,7 +499,7 @@ sem_status refresh_model(sem_mesh* m) {
     return SEM_OK;
 }
 
-// Buffers of level m.// Buffers of level m.
+// Buffers of level m.
 void* level_u(const sem_mesh* m, int64_t lv) {
     return m->prec == SEM_FP32_KAHAN ? m->d_u[lv & 1] : m->d_u[((lv % 3) + 3) % 3];
 }
