@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32_kahan", choices=["fp32_kahan", "fp64", "fp32"])
     ap.add_argument("--ordering", default="hilbert",
-                    choices=["hilbert", "rowmajor", "random", "none", "connectivity", "distance"])
+                    choices=["hilbert", "rowmajor", "random", "none", "connectivity", "distance", "hilbert_wide"])
     ap.add_argument("--n", type=int, default=512, help="quads per side of the graded mesh")
     ap.add_argument("--workload", default="graded", choices=["graded", "layered", "batched", "adjoint"],
                     help="graded 512x512 (default), the layered 4096x1024 model (67M nodes), or batched shots")
@@ -72,6 +72,8 @@ def parse():
                     help="leapfrog (default) or the paper's first-order system with Heun steps")
     ap.add_argument("--eb", type=int, default=0, help="elements per block (0 = library default)")
     ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = library default)")
+    ap.add_argument("--stream", type=int, default=-1,
+                    help="steps per streamed launch (0 = one launch per step; -1 = library default)")
     return ap.parse_args()
 
 
@@ -170,10 +172,12 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_handle(P, m, precision, ordering, nsteps_cap, eb=0, threads=0, scheme="leapfrog"):
+def make_handle(P, m, precision, ordering, nsteps_cap, eb=0, threads=0, scheme="leapfrog", stream=-1):
     h = P.SEM(m["coords"], m["quads"], 4, precision)
     if scheme != "leapfrog":
         h.sem_set_scheme(scheme)
+    if stream >= 0:
+        h.sem_set_stream(stream)
     h.sem_reorder(ordering)
     h.sem_set_model(m["vel"], m["rho"])
     if eb or threads:
@@ -236,7 +240,7 @@ def recorded_traffic(precision, ordering):
             tj = json.load(fh)
         if (tj.get("workload") == WORKLOAD and tj.get("precision") == precision and tj.get("ordering") == ordering
                 and tj.get("kernel_sha256") == kernel_source_digest()):
-            return float(tj["dram_bytes_per_launch"])
+            return float(tj["dram_bytes_per_launch"]) / float(tj.get("steps_per_launch", 1))
     except (OSError, ValueError, KeyError, TypeError):
         pass
     return None
@@ -436,7 +440,7 @@ def main():
     m = workload(args, rank)
     wname = "layered_4096x1024_p4" if args.workload == "layered" else (WORKLOAD if args.n == 512 else f"graded_{args.n}x{args.n}_p4")
     cap = W + 2 * K + 8
-    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads, args.scheme)
+    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads, args.scheme, args.stream)
     N = h.n_nodes
     # warm-up (the first call builds the device data)
     h.sem_step(W)
@@ -454,7 +458,7 @@ def main():
     bms, bl, oms, ol = h.sem_profile_read()
     h.sem_profile_enable(False)
     block_bytes, open_bytes = h.sem_traffic_model()
-    _, nopen = h.sem_launch_info()
+    spl, nopen = h.sem_launch_info()
     time.sleep(0.2)
     clocks = ClockSampler.summarize(sampler.stop()) if sampler else None
     u = h.sem_read_wavefield()
@@ -465,7 +469,7 @@ def main():
     # traces and wavefield back to the host, all inside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb, args.threads, args.scheme)
+    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb, args.threads, args.scheme, args.stream)
     h2.sem_step(K)
     tr = h2.sem_read_traces()
     u2 = h2.sem_read_wavefield()
@@ -480,18 +484,18 @@ def main():
     if rank == 0 and not args.no_compare:
         orderings = {}
         kk = min(K, 500)
-        for kind in ("hilbert", "rowmajor", "random", "none", "connectivity", "distance"):
-            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb, args.threads, args.scheme)
+        for kind in ("hilbert", "rowmajor", "random", "none", "connectivity", "distance", "hilbert_wide"):
+            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb, args.threads, args.scheme, args.stream)
             hh.sem_step(W)
             t_ord = time_steps(torch, hh, kk)
             hh.sem_profile_enable(True)
             time_steps(torch, hh, kk)
-            b_ms, b_l, o_ms, o_l = hh.sem_profile_read()
+            b_ms, b_l, o_ms, o_l = hh.sem_profile_read()   # kk steps
             bb, ob = hh.sem_traffic_model()
             _, no = hh.sem_launch_info()
             hh.sem_destroy()
             orderings[kind] = {"node_updates_per_s": N * kk / t_ord, "ms_per_step": 1e3 * t_ord / kk,
-                               "step_kernel_us": 1e3 * b_ms / max(b_l, 1), "open_nodes": no,
+                               "step_kernel_us": 1e3 * b_ms / kk, "open_nodes": no,
                                "step_bytes_model": bb}
     if world > 1:
         dist.barrier()
@@ -508,12 +512,17 @@ def main():
                          "set-up excluded"}
 
     peak, peak_kind = read_peaks()
-    blk_us = 1e3 * bms / max(bl, 1)
+    # the profiled pass covers K steps in bl step-kernel launches (one step
+    # each, or several when the time loop is streamed)
+    blk_us = 1e3 * bms / K
+    launch_us = 1e3 * bms / max(bl, 1)
+    steps_per_launch = K / max(bl, 1)
     # algorithmic bytes of one step-kernel launch: the per-node-update figure
-    # of the hot path times the nodes one launch updates
+    # of the hot path times the node updates one launch makes
     algo = (ALGO_BYTES_HEUN if args.scheme == "heun" else ALGO_BYTES)[args.precision]
-    achieved = algo * N / (blk_us * 1e-6) / 1e9
-    traffic = recorded_traffic(args.precision, args.ordering) if wname == WORKLOAD else None
+    achieved = algo * N * steps_per_launch / (launch_us * 1e-6) / 1e9
+    traffic_step = recorded_traffic(args.precision, args.ordering) if wname == WORKLOAD else None
+    traffic = None if traffic_step is None else traffic_step * steps_per_launch
     value = job_rate(world, N, K, el)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -525,10 +534,12 @@ def main():
                    "l2": f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
                    "finite": finite},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "sem_step_kernel", "peak_kind": peak_kind,
+                     "traffic": traffic, "traffic_per_step": traffic_step,
+                     "kernel": "sem_stream_kernel" if spl > 1 else "sem_step_kernel", "peak_kind": peak_kind,
+                     "steps_per_launch": steps_per_launch, "launch_us": launch_us,
                      "step_kernel_us": blk_us, "open_kernel_us_per_run": 1e3 * oms / max(ol, 1),
-                     "algorithmic_bytes_per_launch": algo * N,
-                     "compulsory_bytes_per_launch": block_bytes, "compulsory_gbs": block_bytes / (blk_us * 1e-6) / 1e9,
+                     "algorithmic_bytes_per_launch": algo * N * steps_per_launch,
+                     "compulsory_bytes_per_step": block_bytes, "compulsory_gbs": block_bytes / (blk_us * 1e-6) / 1e9,
                      "open_bytes_per_launch": open_bytes,
                      "open_nodes": nopen, "profiled_ms_per_step": 1e3 * prof_el / K,
                      "algorithmic_bytes_per_node_update": algo,

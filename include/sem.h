@@ -86,9 +86,16 @@ typedef enum {
                                unvisited connected node with the fewest; at a
                                dead end back along the walk; elements listed as
                                their nodes are first visited (ascending id)      */
-    SEM_ORDER_DISTANCE = 5  /* Section 6.1 "Node Distance": the same walk by
+    SEM_ORDER_DISTANCE = 5, /* Section 6.1 "Node Distance": the same walk by
                                squared distance to the lower-left corner of the
                                bounding box (ties to the lower node id)          */
+    SEM_ORDER_HILBERT_WIDE = 6 /* SEM_ORDER_HILBERT with the other bounding box
+                               Section 4.3 offers for changing how many elements
+                               fall in a curve cell (w_b = sqrt(n_e) r, h_b =
+                               sqrt(n_e)): H = ceil(sqrt(E)) cells high, W =
+                               max(1, ceil(H r)) wide, r = w_m / h_m; the same
+                               node renumbering. SEM_ERR_UNSUPPORTED when W x H
+                               exceeds 2^30 cells                                */
 } sem_ordering;
 
 typedef enum { SEM_SRC_RICKER = 0 } sem_source_kind;
@@ -264,12 +271,29 @@ sem_status sem_count_nodes(const int32_t* quads, int64_t nv, int64_t ne, int ord
  * (x, y) of the k-th visited cell, out cells[W*H][2]. Host only. */
 sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells);
 
-/* Launch accounting of the time loop: kernel launches per step (one step
- * kernel; each sem_step call adds one open-node launch after its last step)
- * and the number of open nodes, i.e. nodes whose elements span more than one
- * element block (-1 before the device data is built). Either pointer may be
- * NULL. */
-sem_status sem_launch_info(const sem_mesh* m, int64_t* launches_per_step, int64_t* open_nodes);
+/* Launch accounting of the time loop: steps per step-kernel launch (1, or
+ * the streamed launch length of sem_set_stream when the time loop is
+ * streamed; each sem_step call adds one open-node launch after its last
+ * step) and the number of open nodes, i.e. nodes whose elements span more
+ * than one element block (-1 before the device data is built). Either
+ * pointer may be NULL. */
+sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t* open_nodes);
+
+/* Streamed time loop. With steps_per_launch = N >= 1 (default 256) sem_step
+ * runs up to N leapfrog steps per launch of a persistent step kernel: as
+ * many CTAs as fit on the GPU at once take (step, element block) units in
+ * order from a work counter, and a unit starts as soon as the previous step
+ * has finished at its block and at every block sharing a node with it, so
+ * consecutive steps overlap and no launch boundary or partly filled last
+ * wave separates them. The arithmetic per unit is the per-step kernel's: the
+ * results are bitwise those of N = 0 (one launch per step). Used for DENSE
+ * block plans (the node numbering of Section 4.3 along the element order)
+ * and the leapfrog scheme; other cases launch once per step. Waits are
+ * bounded: a wait that gives up (which no correct run does) raises a device
+ * error flag, the remaining steps of the run are skipped, and the next
+ * sem_read_wavefield, sem_get_state or sem_read_traces returns SEM_ERR_CUDA.
+ * Any time. */
+sem_status sem_set_stream(sem_mesh* m, int steps_per_launch);
 
 /* Launch shape of the step kernel: elements per block (0 = default, about
  * 1600 element points per block; at most 256, one thread per element) and
@@ -281,7 +305,8 @@ sem_status sem_set_tuning(sem_mesh* m, int elems_per_block, int threads_per_bloc
 
 /* Per-kernel device timing for measurement. While enabled, sem_step records
  * CUDA events on the handle's stream around every step-kernel launch
- * ("block") and every open-node launch ("open"). sem_profile_read
+ * ("block", one or, streamed, several steps) and every open-node launch
+ * ("open"). sem_profile_read
  * synchronises the stream and returns the summed durations (milliseconds)
  * and launch counts since the last read, then resets them. Any output pointer
  * may be NULL. */

@@ -71,17 +71,28 @@ def isqrt_ceil(n: int) -> int:
     return r if r * r == n else r + 1
 
 
-def hilbert_grid(coords: np.ndarray, quads: np.ndarray):
-    """Return (W, H, ix[E], iy[E]): the curve grid and each element's cell."""
+def hilbert_grid(coords: np.ndarray, quads: np.ndarray, wide: bool = False):
+    """Return (W, H, ix[E], iy[E]): the curve grid and each element's cell.
+
+    Section 4.3 sizes the bounding box w_b = sqrt(n_e), h_b = sqrt(n_e) / r
+    (r = w_m / h_m); read with integer cells: W = ceil(sqrt(E)), H =
+    max(1, ceil(W / r)). `wide` takes the alternative the same section offers
+    for changing how many elements fall in one step of the curve, w_b =
+    sqrt(n_e) r and h_b = sqrt(n_e): H = ceil(sqrt(E)), W = max(1, ceil(H r)).
+    """
     coords = np.asarray(coords, dtype=np.float64)
     quads = np.asarray(quads, dtype=np.int64)
     E = quads.shape[0]
     xmin, ymin = coords[:, 0].min(), coords[:, 1].min()
     wm = coords[:, 0].max() - xmin
     hm = coords[:, 1].max() - ymin
-    W = isqrt_ceil(E)
     r = wm / hm
-    H = max(1, math.ceil(W / r))
+    if not wide:
+        W = isqrt_ceil(E)
+        H = max(1, math.ceil(W / r))
+    else:
+        H = isqrt_ceil(E)
+        W = max(1, math.ceil(H * r))
     c = coords[quads]                                     # (E, 4, 2)
     xc = ((c[:, 0, 0] + c[:, 1, 0]) + (c[:, 2, 0] + c[:, 3, 0])) * 0.25
     yc = ((c[:, 0, 1] + c[:, 1, 1]) + (c[:, 2, 1] + c[:, 3, 1])) * 0.25
@@ -90,9 +101,9 @@ def hilbert_grid(coords: np.ndarray, quads: np.ndarray):
     return W, H, np.maximum(ix, 0), np.maximum(iy, 0)
 
 
-def hilbert_element_order(coords, quads) -> np.ndarray:
+def hilbert_element_order(coords, quads, wide: bool = False) -> np.ndarray:
     """The list L of Section 4.3 as order[new] = old element id."""
-    W, H, ix, iy = hilbert_grid(coords, quads)
+    W, H, ix, iy = hilbert_grid(coords, quads, wide)
     rank = _hilbert.rank_grid(W, H)
     key = rank[ix, iy]
     return np.argsort(key, kind="stable").astype(np.int64)   # ties: ascending input id
@@ -182,7 +193,7 @@ def node_walk(conn, n_nodes: int, key) -> tuple:
 
 def orderings(kind: str, coords, quads, conn, n_nodes, seed: int = 2104084160, degree=None, node_xy=None):
     """(elem_order, node_order) for kind in none/rowmajor/random/hilbert/
-    connectivity/distance (node_xy needed for distance)."""
+    connectivity/distance/hilbert_wide (node_xy needed for distance)."""
     E = conn.shape[0]
     kind = kind.lower()
     if kind == "connectivity":
@@ -207,6 +218,8 @@ def orderings(kind: str, coords, quads, conn, n_nodes, seed: int = 2104084160, d
         eo = np.arange(E, dtype=np.int64)
     elif kind == "hilbert":
         eo = hilbert_element_order(coords, quads)
+    elif kind == "hilbert_wide":
+        eo = hilbert_element_order(coords, quads, wide=True)
     else:
         raise ValueError(kind)
     if degree is None:

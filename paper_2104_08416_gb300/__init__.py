@@ -23,13 +23,14 @@ LIB_PATH = os.path.join(_PKG, "libsem.so")
 SEM_OK, SEM_ERR_INVALID_ARG, SEM_ERR_STATE, SEM_ERR_CUDA, SEM_ERR_OOM, SEM_ERR_TIMEOUT, SEM_ERR_UNSUPPORTED = range(7)
 SEM_FP64, SEM_FP32_KAHAN, SEM_FP32 = 0, 1, 2
 SEM_ORDER_NONE, SEM_ORDER_ROWMAJOR, SEM_ORDER_RANDOM, SEM_ORDER_HILBERT = 0, 1, 2, 3
-SEM_ORDER_CONNECTIVITY, SEM_ORDER_DISTANCE = 4, 5
+SEM_ORDER_CONNECTIVITY, SEM_ORDER_DISTANCE, SEM_ORDER_HILBERT_WIDE = 4, 5, 6
 SEM_SRC_RICKER = 0
 SEM_SCHEME_LEAPFROG, SEM_SCHEME_HEUN = 0, 1
 SCHEMES = {"leapfrog": SEM_SCHEME_LEAPFROG, "heun": SEM_SCHEME_HEUN}
 PRECISIONS = {"fp64": SEM_FP64, "fp32_kahan": SEM_FP32_KAHAN, "fp32": SEM_FP32}
 ORDERINGS = {"none": SEM_ORDER_NONE, "rowmajor": SEM_ORDER_ROWMAJOR, "random": SEM_ORDER_RANDOM,
-             "hilbert": SEM_ORDER_HILBERT, "connectivity": SEM_ORDER_CONNECTIVITY, "distance": SEM_ORDER_DISTANCE}
+             "hilbert": SEM_ORDER_HILBERT, "connectivity": SEM_ORDER_CONNECTIVITY, "distance": SEM_ORDER_DISTANCE,
+             "hilbert_wide": SEM_ORDER_HILBERT_WIDE}
 DEFAULT_SEED = 2104084160
 
 # every symbol include/sem.h declares
@@ -38,7 +39,7 @@ EXPORTS = (
     "sem_set_receivers", "sem_cfl_dt", "sem_set_scheme", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
     "sem_read_wavefield", "sem_set_state", "sem_get_state", "sem_apply_stiffness", "sem_read_mass",
     "sem_get_permutation", "sem_get_sizes", "sem_node_coordinates", "sem_get_snapped",
-    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info",
+    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info", "sem_set_stream",
     "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
     "sem_apply_stiffness_dev_noalloc", "sem_misfit_gradient", "sem_batch_create", "sem_batch_step", "sem_batch_info",
@@ -97,6 +98,7 @@ def load(path: str | None = None):
         "sem_plan_check": (_D, C.c_int64, _I32, C.c_int64, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int, _D,
                            C.c_int32, _I64, C.c_char_p, C.c_size_t),
         "sem_launch_info": (_P, _I64, _I64),
+        "sem_set_stream": (_P, C.c_int),
         "sem_set_tuning": (_P, C.c_int, C.c_int),
         "sem_profile_enable": (_P, C.c_int),
         "sem_profile_read": (_P, _D, _I64, _D, _I64),
@@ -344,6 +346,9 @@ class SEM:
         a, b = C.c_int64(), C.c_int64()
         self._c(self._lib.sem_launch_info(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def sem_set_stream(self, steps_per_launch: int):
+        self._c(self._lib.sem_set_stream(self.h, int(steps_per_launch)))
 
     def sem_profile_enable(self, enable: bool = True):
         self._c(self._lib.sem_profile_enable(self.h, 1 if enable else 0))

@@ -76,6 +76,17 @@ struct sem_mesh {
     semdev::Plan dplan{};
     int smem = 0;
     int threads = 0;
+    // streamed time loop (sem_set_stream): up to stream_steps steps per
+    // launch of the persistent step kernel, stream_ctas CTAs (0: per-step
+    // launches), per-block neighbour lists and done flags
+    int stream_steps = 256;
+    int stream_ctas = 0;
+    int32_t* d_dep_ptr = nullptr;
+    int32_t* d_dep = nullptr;
+    uint32_t* d_done = nullptr;
+    unsigned long long* d_counter = nullptr;
+    int32_t* d_err = nullptr;
+    uint32_t serial = 1;              // serial of the next streamed step
     semdev::Basis<double> basis64{};
     semdev::Basis<float> basis32{};
     double* d_coords = nullptr;
@@ -216,12 +227,17 @@ void fill_basis(semdev::Basis<T>& b, int p) {
         for (int i = 0; i < n; ++i) b.W[j * n + i] = (T)(w[(size_t)i] * w[(size_t)j]);
 }
 
-void compute_orderings(sem_mesh* m) {
-    semhost::orderings(m->mesh, m->ordering, m->seed, m->elem_order, m->node_order);
+sem_status compute_orderings(sem_mesh* m) {
+    std::vector<int64_t> eo, no;
+    const std::string why = semhost::orderings(m->mesh, m->ordering, m->seed, eo, no);
+    if (!why.empty()) return fail(m, SEM_ERR_UNSUPPORTED, why);
+    m->elem_order.swap(eo);
+    m->node_order.swap(no);
     m->elem_new.assign(m->elem_order.size(), 0);
     m->node_new.assign(m->node_order.size(), 0);
     for (size_t k = 0; k < m->elem_order.size(); ++k) m->elem_new[(size_t)m->elem_order[k]] = (int64_t)k;
     for (size_t k = 0; k < m->node_order.size(); ++k) m->node_new[(size_t)m->node_order[k]] = (int64_t)k;
+    return SEM_OK;
 }
 
 sem_status fill_source(sem_mesh* m, int64_t upto) {
@@ -285,7 +301,10 @@ sem_status build_host(sem_mesh* m) {
     if (!m->have_model) return fail(m, SEM_ERR_STATE, "sem_set_model must come first");
     const auto& M = m->mesh;
     const int P = M.P;
-    if (m->elem_order.empty()) compute_orderings(m);
+    if (m->elem_order.empty()) {
+        sem_status so = compute_orderings(m);
+        if (so != SEM_OK) return so;
+    }
     // permuted connectivity and element data
     std::vector<int32_t> conn_new((size_t)(M.ne * P));
     std::vector<int32_t> quads_new((size_t)M.ne * 4);
@@ -459,6 +478,24 @@ sem_status build(sem_mesh* m) {
         if ((st = zeros(m, &tr, (size_t)m->nrec * (size_t)m->trace_cap * 8)) != SEM_OK) return st;
         m->d_trace = (double*)tr;
     }
+    // streamed time loop: leapfrog on a DENSE plan
+    m->stream_ctas = 0;
+    const int md = mode_of(m);
+    if (pl.dense && m->scheme == SEM_SCHEME_LEAPFROG && (md == semdev::MODE_KAHAN || md == semdev::MODE_THREE_LEVEL)) {
+        if ((st = upload(m, &m->d_dep_ptr, pl.dep_ptr.data(), pl.dep_ptr.size())) != SEM_OK) return st;
+        if ((st = upload(m, &m->d_dep, pl.dep.data(), pl.dep.size())) != SEM_OK) return st;
+        void *done = nullptr, *ctr = nullptr, *er = nullptr;
+        if ((st = zeros(m, &done, (size_t)pl.nblocks * 4)) != SEM_OK) return st;
+        if ((st = zeros(m, &ctr, 8)) != SEM_OK) return st;
+        if ((st = zeros(m, &er, 4)) != SEM_OK) return st;
+        m->d_done = (uint32_t*)done;
+        m->d_counter = (unsigned long long*)ctr;
+        m->d_err = (int32_t*)er;
+        m->serial = 1;
+        int ctas = 0;
+        SEM_CUDA(semdev::stream_max_ctas(M.np, fp64(m), md, m->threads, m->smem, &ctas));
+        m->stream_ctas = ctas;
+    }
     cudaError_t e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(m, e, "build");
     std::vector<int32_t>().swap(m->host_quads);
@@ -551,6 +588,101 @@ cudaEvent_t take_event(sem_mesh* m) {
 
 const void* basis_of(const sem_mesh* m) {
     return fp64(m) ? (const void*)&m->basis64 : (const void*)&m->basis32;
+}
+
+// Device descriptor of the mesh's plan and level buffers (streamed
+// launches and batches form each step's arguments from it).
+template <typename T>
+semdev::ShotDesc<T> shot_desc(const sem_mesh* m) {
+    semdev::ShotDesc<T> d{};
+    d.pl = m->dplan;
+    for (int k = 0; k < 3; ++k) d.u[k] = (T*)m->d_u[k];
+    for (int k = 0; k < 2; ++k) {
+        d.x[k] = (T*)m->d_x[k];
+        d.c[k] = (T*)m->d_c[k];
+        d.part[k] = (T*)m->d_part[k];
+    }
+    d.s = (const T*)m->d_s;
+    d.src_f = m->d_src;
+    d.trace = m->d_trace;
+    d.trace_cap = m->trace_cap;
+    d.src_gid = m->have_src ? (int32_t)m->node_new[(size_t)m->src_node] : -1;
+    return d;
+}
+
+bool streamed(const sem_mesh* m) { return m->stream_steps > 0 && m->stream_ctas > 0; }
+
+// Steps k = m->step .. m->step + n - 1 as one streamed launch (pending: the
+// open nodes of step m->step - 1 are not finished yet), recorded with events
+// when profiling.
+sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
+    semdev::StreamArgs sa{};
+    sa.counter = m->d_counter;
+    sa.base = 0;
+    sa.done = m->d_done;
+    sa.dep_ptr = m->d_dep_ptr;
+    sa.dep = m->d_dep;
+    sa.err = m->d_err;
+    sa.step0 = m->step;
+    sa.nsteps = (int32_t)n;
+    sa.pending0 = pending ? 1 : 0;
+    sa.serial0 = m->serial;
+    const int64_t units = n * m->plan.nblocks;
+    const int ctas = (int)std::min<int64_t>(m->stream_ctas, units);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (m->profiling) {
+        e0 = take_event(m);
+        e1 = take_event(m);
+        if (!e0 || !e1) return fail(m, SEM_ERR_CUDA, "cudaEventCreate failed");
+    }
+    cudaError_t e = e0 ? cudaEventRecord(e0, m->stream) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_counter, 0, 8, m->stream);
+    if (e == cudaSuccess) {
+        if (fp64(m)) {
+            auto d = shot_desc<double>(m);
+            e = semdev::launch_stream(m->mesh.np, true, mode_of(m), &d, sa, basis_of(m), m->threads, m->smem, ctas,
+                                      m->stream);
+        } else {
+            auto d = shot_desc<float>(m);
+            e = semdev::launch_stream(m->mesh.np, false, mode_of(m), &d, sa, basis_of(m), m->threads, m->smem, ctas,
+                                      m->stream);
+        }
+    }
+    if (e == cudaSuccess && e1) e = cudaEventRecord(e1, m->stream);
+    if (e != cudaSuccess) return cuda_fail(m, e, "streamed step launch");
+    if (m->profiling) m->ev_block.push_back({e0, e1});
+    m->serial += (uint32_t)n;
+    m->step += n;
+    return SEM_OK;
+}
+
+sem_status launch_one_step(sem_mesh* m, bool pending);
+
+// Steps of one sem_step call: streamed launches of up to stream_steps steps,
+// else one launch per step.
+sem_status launch_steps(sem_mesh* m, int64_t nsteps) {
+    sem_status st;
+    for (int64_t k = 0; k < nsteps;) {
+        if (streamed(m)) {
+            const int64_t n = std::min<int64_t>(nsteps - k, m->stream_steps);
+            if ((st = launch_stream_steps(m, n, k > 0)) != SEM_OK) return st;
+            k += n;
+        } else {
+            if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+            k += 1;
+        }
+    }
+    return SEM_OK;
+}
+
+// A wait of a streamed launch that gave up leaves the error flag raised.
+sem_status check_stream_error(sem_mesh* m) {
+    if (!m->d_err) return SEM_OK;
+    int32_t h = 0;
+    SEM_CUDA(cudaMemcpyAsync(&h, m->d_err, 4, cudaMemcpyDeviceToHost, m->stream));
+    SEM_CUDA(cudaStreamSynchronize(m->stream));
+    if (h != 0) return fail(m, SEM_ERR_CUDA, "a streamed step gave up waiting for a neighbouring block");
+    return SEM_OK;
 }
 
 // Launch k of a run: the step kernel (pending = not the first launch of the
@@ -790,16 +922,23 @@ sem_status sem_mesh_create(const double* coords, int64_t nv, const int32_t* quad
 
 sem_status sem_reorder(sem_mesh* m, sem_ordering kind, uint64_t seed) {
     if (!m) return SEM_ERR_INVALID_ARG;
-    if ((int)kind < 0 || (int)kind > 5) return fail(m, SEM_ERR_INVALID_ARG, "unknown ordering");
+    if ((int)kind < 0 || (int)kind > 6) return fail(m, SEM_ERR_INVALID_ARG, "unknown ordering");
     if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_reorder after the device data was built");
+    const int old_kind = m->ordering;
+    const uint64_t old_seed = m->seed;
     m->ordering = (int)kind;
     m->seed = seed;
+    sem_status st;
     try {
-        compute_orderings(m);
+        st = compute_orderings(m);
     } catch (const std::bad_alloc&) {
-        return fail(m, SEM_ERR_OOM, "host allocation failed");
+        st = fail(m, SEM_ERR_OOM, "host allocation failed");
     }
-    return SEM_OK;
+    if (st != SEM_OK) {
+        m->ordering = old_kind;
+        m->seed = old_seed;
+    }
+    return st;
 }
 
 sem_status sem_set_model(sem_mesh* m, const double* vel, const double* rho) {
@@ -888,6 +1027,14 @@ sem_status sem_set_tuning(sem_mesh* m, int elems_per_block, int threads_per_bloc
     return SEM_OK;
 }
 
+sem_status sem_set_stream(sem_mesh* m, int steps_per_launch) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (steps_per_launch < 0 || steps_per_launch > 65536)
+        return fail(m, SEM_ERR_INVALID_ARG, "steps_per_launch must be in 0..65536");
+    m->stream_steps = steps_per_launch;
+    return SEM_OK;
+}
+
 sem_status sem_step(sem_mesh* m, int64_t nsteps) {
     if (!m) return SEM_ERR_INVALID_ARG;
     if (nsteps < 0) return fail(m, SEM_ERR_INVALID_ARG, "nsteps < 0");
@@ -907,8 +1054,7 @@ sem_status sem_step(sem_mesh* m, int64_t nsteps) {
     // the first launch reads a fully stored level; later ones finish the
     // open nodes of the previous launch themselves; the flush completes the
     // open nodes after the last launch
-    for (int64_t k = 0; k < nsteps; ++k)
-        if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+    if ((st = launch_steps(m, nsteps)) != SEM_OK) return st;
     if ((st = launch_flush(m)) != SEM_OK) return st;
     m->stepped_calls++;
     return SEM_OK;
@@ -927,6 +1073,8 @@ sem_status sem_read_traces(sem_mesh* m, double* out, int64_t cap) {
         std::fill(out, out + (size_t)m->nrec * (size_t)cap, 0.0);
         return SEM_OK;
     }
+    sem_status st = check_stream_error(m);
+    if (st != SEM_OK) return st;
     const int64_t n = std::min(cap, m->step);
     std::fill(out, out + (size_t)m->nrec * (size_t)cap, 0.0);
     if (n > 0) {
@@ -980,6 +1128,7 @@ sem_status sem_get_state(sem_mesh* m, double* u, double* u_prev, int64_t* step) 
         if (u_prev) std::fill(u_prev, u_prev + nn, 0.0);
         return SEM_OK;
     }
+    if (sem_status se = check_stream_error(m)) return se;
     std::vector<double> un, tmp;
     if (m->scheme == SEM_SCHEME_HEUN) {
         sem_status st = read_nodes(m, m->d_u[0], fp64(m), un);
@@ -1042,7 +1191,10 @@ sem_status sem_read_mass(sem_mesh* m, double* mass) {
 sem_status sem_get_permutation(const sem_mesh* mc, int64_t* elem_new_of_old, int64_t* node_new_of_old) {
     sem_mesh* m = const_cast<sem_mesh*>(mc);
     if (!m) return SEM_ERR_INVALID_ARG;
-    if (m->elem_order.empty()) compute_orderings(m);
+    if (m->elem_order.empty()) {
+        sem_status so = compute_orderings(m);
+        if (so != SEM_OK) return so;
+    }
     if (elem_new_of_old) std::copy(m->elem_new.begin(), m->elem_new.end(), elem_new_of_old);
     if (node_new_of_old) std::copy(m->node_new.begin(), m->node_new.end(), node_new_of_old);
     return SEM_OK;
@@ -1082,7 +1234,7 @@ sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads
     };
     say("");
     if (!coords || !quads || (nrec > 0 && !rec_xy) || nrec < 0) return SEM_ERR_INVALID_ARG;
-    if ((int)kind < 0 || (int)kind > 5 || elems_per_block < 1 || elems_per_block > 256) return SEM_ERR_INVALID_ARG;
+    if ((int)kind < 0 || (int)kind > 6 || elems_per_block < 1 || elems_per_block > 256) return SEM_ERR_INVALID_ARG;
     const std::string bad = semhost::validate(coords, nv, quads, ne, order);
     if (!bad.empty()) {
         say(bad);
@@ -1096,7 +1248,13 @@ sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads
     mm.quads.assign(quads, quads + ne * 4);
     semhost::number_nodes(mm);
     std::vector<int64_t> eo, no;
-    semhost::orderings(mm, (int)kind, seed, eo, no);
+    {
+        const std::string why = semhost::orderings(mm, (int)kind, seed, eo, no);
+        if (!why.empty()) {
+            say(why);
+            return SEM_ERR_UNSUPPORTED;
+        }
+    }
     std::vector<int64_t> nnew(no.size());
     for (size_t k = 0; k < no.size(); ++k) nnew[(size_t)no[k]] = (int64_t)k;
     const int P = mm.P;
@@ -1183,7 +1341,7 @@ sem_status sem_count_nodes(const int32_t* quads, int64_t nv, int64_t ne, int ord
 sem_status sem_compute_ordering(const double* coords, int64_t nv, const int32_t* quads, int64_t ne, int order,
                                 sem_ordering kind, uint64_t seed, int64_t* elem_order, int64_t* node_order) {
     if (!coords || !quads || !elem_order || !node_order) return SEM_ERR_INVALID_ARG;
-    if ((int)kind < 0 || (int)kind > 5) return SEM_ERR_INVALID_ARG;
+    if ((int)kind < 0 || (int)kind > 6) return SEM_ERR_INVALID_ARG;
     if (!semhost::validate(coords, nv, quads, ne, order).empty()) return SEM_ERR_INVALID_ARG;
     semhost::Mesh mm;
     mm.p = order;
@@ -1193,7 +1351,7 @@ sem_status sem_compute_ordering(const double* coords, int64_t nv, const int32_t*
     mm.quads.assign(quads, quads + ne * 4);
     semhost::number_nodes(mm);
     std::vector<int64_t> eo, no;
-    semhost::orderings(mm, (int)kind, seed, eo, no);
+    if (!semhost::orderings(mm, (int)kind, seed, eo, no).empty()) return SEM_ERR_UNSUPPORTED;
     std::copy(eo.begin(), eo.end(), elem_order);
     std::copy(no.begin(), no.end(), node_order);
     return SEM_OK;
@@ -1207,9 +1365,9 @@ sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells) {
     return SEM_OK;
 }
 
-sem_status sem_launch_info(const sem_mesh* m, int64_t* launches_per_step, int64_t* open_nodes) {
+sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t* open_nodes) {
     if (!m) return SEM_ERR_INVALID_ARG;
-    if (launches_per_step) *launches_per_step = 1;
+    if (steps_per_launch) *steps_per_launch = m->built && streamed(m) ? m->stream_steps : 1;
     if (open_nodes) *open_nodes = m->built ? (int64_t)m->plan.open_gid.size() : -1;
     return SEM_OK;
 }
@@ -1356,11 +1514,10 @@ sem_status copy_dev(sem_mesh* m, void* dst, const void* src) {
     return SEM_OK;
 }
 
-// n steps from a stored level (one launch per step, open nodes completed).
+// n steps from a stored level (open nodes completed).
 sem_status run_steps(sem_mesh* m, int64_t n) {
     sem_status st;
-    for (int64_t k = 0; k < n; ++k)
-        if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+    if ((st = launch_steps(m, n)) != SEM_OK) return st;
     return n > 0 ? launch_flush(m) : SEM_OK;
 }
 
@@ -1570,23 +1727,6 @@ void unbuild(sem_mesh* m) {
     m->host_ready = false;
 }
 
-template <typename T>
-semdev::ShotDesc<T> shot_desc(const sem_mesh* m) {
-    semdev::ShotDesc<T> d{};
-    d.pl = m->dplan;
-    for (int k = 0; k < 3; ++k) d.u[k] = (T*)m->d_u[k];
-    for (int k = 0; k < 2; ++k) {
-        d.x[k] = (T*)m->d_x[k];
-        d.c[k] = (T*)m->d_c[k];
-        d.part[k] = (T*)m->d_part[k];
-    }
-    d.s = (const T*)m->d_s;
-    d.src_f = m->d_src;
-    d.trace = m->d_trace;
-    d.trace_cap = m->trace_cap;
-    d.src_gid = m->have_src ? (int32_t)m->node_new[(size_t)m->src_node] : -1;
-    return d;
-}
 
 // Per-shot descriptors (re-uploaded before every batch step: source tables
 // may have grown).

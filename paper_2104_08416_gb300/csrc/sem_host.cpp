@@ -305,9 +305,13 @@ static int64_t ceil_sqrt(int64_t n) {
     return r * r == n ? r : r + 1;
 }
 
-void element_order_hilbert(const Mesh& m, std::vector<int64_t>& order) {
+std::string element_order_hilbert(const Mesh& m, std::vector<int64_t>& order, bool wide) {
     // Section 4.3: element centroids on a W x H grid over the bounding box,
     // cells walked along the curve, elements of a cell appended in input order.
+    // Box sizes: W = ceil(sqrt(E)), H = max(1, ceil(W / r)); or, with `wide`,
+    // the alternative the section gives for changing how many elements fall
+    // in a cell (w_b = sqrt(E) r, h_b = sqrt(E)): H = ceil(sqrt(E)),
+    // W = max(1, ceil(H r)). r = w_m / h_m in FP64.
     double xmin = std::numeric_limits<double>::infinity(), ymin = xmin;
     double xmax = -xmin, ymax = -xmin;
     for (int64_t v = 0; v < m.nv; ++v) {
@@ -317,10 +321,18 @@ void element_order_hilbert(const Mesh& m, std::vector<int64_t>& order) {
         ymax = std::max(ymax, m.coords[(size_t)v * 2 + 1]);
     }
     const double wm = xmax - xmin, hm = ymax - ymin;
-    const int64_t W = ceil_sqrt(m.ne);
     const double r = wm / hm;
-    int64_t H = (int64_t)std::ceil((double)W / r);
-    if (H < 1) H = 1;
+    int64_t W, H;
+    if (!wide) {
+        W = ceil_sqrt(m.ne);
+        H = std::max<int64_t>(1, (int64_t)std::ceil((double)W / r));
+    } else {
+        H = ceil_sqrt(m.ne);
+        const double wd = std::ceil((double)H * r);
+        if (!(wd < 2147483647.0)) return "Hilbert grid too large for this aspect ratio";
+        W = std::max<int64_t>(1, (int64_t)wd);
+    }
+    if (W * H > 2147483647LL / 2) return "Hilbert grid too large for this aspect ratio";
     std::vector<int32_t> cells;
     hilbert_cells(W, H, cells);
     std::vector<int64_t> rank((size_t)(W * H));
@@ -345,6 +357,7 @@ void element_order_hilbert(const Mesh& m, std::vector<int64_t>& order) {
     for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
     order.assign((size_t)m.ne, 0);
     for (int64_t e = 0; e < m.ne; ++e) order[(size_t)cnt[(size_t)key[(size_t)e]]++] = e;
+    return "";
 }
 
 void node_degrees(const Mesh& m, std::vector<int32_t>& deg) {
@@ -539,32 +552,34 @@ void walk_orders(const Mesh& m, int kind, std::vector<int64_t>& eo, std::vector<
     }
 }
 
-void orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_t>& eo, std::vector<int64_t>& no) {
+std::string orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_t>& eo, std::vector<int64_t>& no) {
     if (kind == 4 || kind == 5) {
         walk_orders(m, kind, eo, no);
-        return;
+        return "";
     }
     if (kind == 0) {
         eo.resize((size_t)m.ne);
         std::iota(eo.begin(), eo.end(), 0);
         no.resize((size_t)m.nn);
         std::iota(no.begin(), no.end(), 0);
-        return;
+        return "";
     }
     if (kind == 2) {
         random_order(m.ne, seed + 2, eo);
         random_order(m.nn, seed + 3, no);
-        return;
+        return "";
     }
     if (kind == 1) {
         eo.resize((size_t)m.ne);
         std::iota(eo.begin(), eo.end(), 0);
     } else {
-        element_order_hilbert(m, eo);
+        std::string why = element_order_hilbert(m, eo, kind == 6);
+        if (!why.empty()) return why;
     }
     std::vector<int32_t> deg;
     node_degrees(m, deg);
     renumber_nodes(m, eo, deg, no);
+    return "";
 }
 
 int64_t snap(const std::vector<double>& xy, double x, double y) {
@@ -698,6 +713,7 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
     std::vector<int64_t> ent_ptr((size_t)nb + 1, 0), own_start_b((size_t)nb, 0), nown_b((size_t)nb, 0);
     std::vector<int32_t> ent_all;
     std::vector<uint8_t> rank_all;
+    std::vector<int32_t> slot_block((size_t)pl.npartial, -1);  // block of each partial-sum slot
     ent_all.reserve((size_t)(nn + nn / 4));
     rank_all.reserve((size_t)(nn + nn / 4));
     {
@@ -732,8 +748,11 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
                     ent_all.push_back(g);
                 }
             }
-            for (size_t k = (size_t)ent_ptr[(size_t)b]; k < ent_all.size(); ++k)
-                rank_all.push_back((uint8_t)seen_rank[(size_t)ent_all[k]]++);
+            for (size_t k = (size_t)ent_ptr[(size_t)b]; k < ent_all.size(); ++k) {
+                const int32_t g = ent_all[k];
+                if (nblk[(size_t)g] > 1) slot_block[(size_t)(base[(size_t)g] + seen_rank[(size_t)g])] = (int32_t)b;
+                rank_all.push_back((uint8_t)seen_rank[(size_t)g]++);
+            }
             ent_ptr[(size_t)b + 1] = (int64_t)ent_all.size();
         }
     }
@@ -742,6 +761,7 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
     // the packet body of each block, into per-block buffers; every write to
     // the shared outputs (hdr, dev_order, epos) touches the block's own part
     std::vector<std::vector<uint8_t>> bodies((size_t)nb);
+    std::vector<std::vector<int32_t>> deps((size_t)nb);
     std::vector<int64_t> nclosed_b((size_t)nb, 0), nopen_b((size_t)nb, 0);
     std::vector<std::string> errs((size_t)nb);
     auto plan_block = [&](int64_t b) -> std::string {
@@ -902,6 +922,15 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         h[H_NREC_OPEN] = (int32_t)nro;
         nclosed_b[(size_t)b] = nclosed;
         nopen_b[(size_t)b] = nopen;
+        std::vector<int32_t>& dl = deps[(size_t)b];
+        dl.push_back((int32_t)b);
+        for (int64_t l = 0; l < nent; ++l) {
+            const int32_t g = ent_gid[l];
+            if (nblk[(size_t)g] > 1)
+                for (int r = 0; r < nblk[(size_t)g]; ++r) dl.push_back(slot_block[(size_t)(base[(size_t)g] + r)]);
+        }
+        std::sort(dl.begin(), dl.end());
+        dl.erase(std::unique(dl.begin(), dl.end()), dl.end());
         return "";
     };
     {
@@ -941,6 +970,13 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         std::vector<uint8_t>().swap(bodies[(size_t)b]);
     }
     if ((int64_t)pl.packet.size() / 16 > INT32_MAX) return "packet array too large";
+    pl.dep_ptr.assign((size_t)nb + 1, 0);
+    for (int64_t b = 0; b < nb; ++b) {
+        pl.dep_ptr[(size_t)b + 1] = pl.dep_ptr[(size_t)b] + (int32_t)deps[(size_t)b].size();
+        pl.max_deps = std::max(pl.max_deps, (int)deps[(size_t)b].size());
+    }
+    pl.dep.reserve((size_t)pl.dep_ptr[(size_t)nb]);
+    for (auto& dl : deps) pl.dep.insert(pl.dep.end(), dl.begin(), dl.end());
     return "";
 }
 
@@ -1070,6 +1106,32 @@ std::string check_block_plan(const BlockPlan& pl, const std::vector<int32_t>& co
     }
     for (int64_t g = 0; g < nn; ++g)
         if (out[(size_t)g] != ref[(size_t)g]) return "node " + std::to_string(g) + ": assembled value differs";
+    // neighbour lists: exactly the blocks sharing a node with the block
+    // (itself included), ascending, from the connectivity directly
+    {
+        const int64_t nbk = pl.nblocks;
+        if ((int64_t)pl.dep_ptr.size() != nbk + 1 || pl.dep_ptr[0] != 0 ||
+            (int64_t)pl.dep.size() != (int64_t)pl.dep_ptr[(size_t)nbk])
+            return "neighbour lists: bad sizes";
+        std::vector<std::vector<int32_t>> node_blocks((size_t)nn);
+        for (int64_t t = 0; t < pl.ne * pl.P; ++t) {
+            auto& v = node_blocks[(size_t)conn[(size_t)t]];
+            const int32_t b = (int32_t)(t / pl.P / pl.eb);
+            if (std::find(v.begin(), v.end(), b) == v.end()) v.push_back(b);
+        }
+        std::vector<std::vector<int32_t>> want((size_t)nbk);
+        for (const auto& v : node_blocks)
+            for (int32_t x : v)
+                for (int32_t y : v) want[(size_t)x].push_back(y);
+        for (int64_t b = 0; b < nbk; ++b) {
+            auto& w = want[(size_t)b];
+            w.push_back((int32_t)b);
+            std::sort(w.begin(), w.end());
+            w.erase(std::unique(w.begin(), w.end()), w.end());
+            const std::vector<int32_t> got(pl.dep.begin() + pl.dep_ptr[(size_t)b], pl.dep.begin() + pl.dep_ptr[(size_t)b + 1]);
+            if (got != w) return "block " + std::to_string(b) + ": neighbour list differs";
+        }
+    }
     return "";
 }
 

@@ -42,14 +42,16 @@ void node_coordinates(const Mesh& m, std::vector<double>& xy);
 void hilbert_cells(int64_t W, int64_t H, std::vector<int32_t>& cells);
 
 // Orderings as order arrays (order[new] = old id).
-void element_order_hilbert(const Mesh& m, std::vector<int64_t>& order);
+// (Returns "" or why the curve grid cannot be built.)
+std::string element_order_hilbert(const Mesh& m, std::vector<int64_t>& order, bool wide = false);
 void node_degrees(const Mesh& m, std::vector<int32_t>& deg);
 void renumber_nodes(const Mesh& m, const std::vector<int64_t>& elem_order,
                     const std::vector<int32_t>& deg, std::vector<int64_t>& node_order);
 void random_order(int64_t n, uint64_t seed, std::vector<int64_t>& order);
 // kind: 0 none, 1 rowmajor, 2 random, 3 hilbert, 4 node connectivity,
-// 5 node distance (Section 6.1's strategies).
-void orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_t>& elem_order,
+// 5 node distance (Section 6.1's strategies), 6 hilbert with the wide
+// bounding box of Section 4.3. Returns "" or why the ordering cannot be built.
+std::string orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_t>& elem_order,
                std::vector<int64_t>& node_order);
 
 // Nearest global node (original id) to (x, y), ties to the lowest id.
@@ -85,6 +87,10 @@ struct BlockPlan {
     std::vector<int32_t> open_gid, open_base, open_cnt, open_rec;
     int64_t npartial = 0;                // partial-sum slots (sum of open_cnt)
     int64_t nent_total = 0, nclosed_total = 0, nopen_entries = 0;
+    // neighbours of each block: the blocks sharing a node with it, itself
+    // included, ascending (CSR: dep[dep_ptr[b] .. dep_ptr[b+1]))
+    std::vector<int32_t> dep_ptr, dep;
+    int max_deps = 0;
 };
 // Returns "" on success, else why the plan cannot be built (a limit of the
 // 16-bit / 8-bit fields or of the colour count exceeded).

@@ -89,7 +89,7 @@ __device__ __forceinline__ T sum_partials(const T* __restrict__ p, int32_t pb, i
     T s = add_rn(v[0], v[1]);
     if (cnt > 2) s = add_rn(s, v[2]);
     if (cnt > 3) s = add_rn(s, v[3]);
-    for (int t = 4; t < cnt; ++t) s = add_rn(s, p[pb + t]);
+    for (int t = 4; t < cnt; ++t) s = add_rn(s, __ldcg(p + pb + t));
     return s;
 }
 
@@ -165,7 +165,7 @@ __device__ __forceinline__ void stage_range(T* dst, const T* src, int64_t abase,
         } else {
 #pragma unroll
             for (int t = 0; t < VEC; ++t)
-                if (g + t < nn) cp_async_small<sizeof(T)>(dst + ch * VEC + t, src + g + t);
+                if (g + t < nn) dst[ch * VEC + t] = __ldcg(src + g + t);
         }
     }
 }
@@ -280,7 +280,7 @@ __device__ __forceinline__ void heun_element(const Plan& pl, const StepArgs<T>& 
 // One block of one mesh, one CTA (the body of the step kernels).
 template <int NP, typename T, int MODE>
 __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a, const Basis<T>& bs, const int b,
-                                           unsigned char* smem_raw) {
+                                           unsigned char* smem_raw, const int64_t step, const int pend) {
     constexpr int P = NP * NP;
     constexpr int UPH = (P + 1) / 2;
     constexpr bool HEUN = MODE == MODE_HEUN_P || MODE == MODE_HEUN_C;
@@ -310,8 +310,8 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     // source values of this launch (the point source is one node)
     T f_now = T(0), f_prev = T(0);
     if ((STATE || HEUN) && a.src_gid >= 0) {
-        f_now = (T)a.src_f[a.step];
-        if (STATE && a.pending) f_prev = (T)a.src_f[a.step - 1];
+        f_now = (T)a.src_f[step];
+        if (STATE && pend) f_prev = (T)a.src_f[step - 1];
     }
     const int64_t e = e0 + tid;
 
@@ -369,12 +369,12 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 }
             }
     }
-    const bool pending = STATE && a.pending;
+    const bool pending = STATE && pend;
     for (int o = tid; o < h.nopen; o += nt) {
         const int pos = opos[o];
         const int64_t g = pos < h.ulen ? abase + pos : (int64_t)egid[pos - h.ulen];
         if (!pending) {
-            cp_async_small<sizeof(T)>(su + pos, a.u_k + g);
+            su[pos] = __ldcg(a.u_k + g);
         } else {
             const T ku = sum_partials(a.part_rd, obase[o], ocnt[o]);
             const T f = (g == a.src_gid) ? f_prev : T(0);
@@ -399,7 +399,7 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             const int pos = recs[2 * (h.nrc + k)], r = recs[2 * (h.nrc + k) + 1];
             // the owner's entries lie in the owned range (DENSE) or the staged one
             const T cw = KAHAN ? (direct ? __ldcg(a.c_kw + abase + pos) : sc[pos]) : T(0);
-            a.trace[(int64_t)r * a.trace_cap + a.step - 1] = trace_value<T, MODE>(su[pos], cw);
+            a.trace[(int64_t)r * a.trace_cap + step - 1] = trace_value<T, MODE>(su[pos], cw);
         }
     }
 
@@ -589,8 +589,8 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     for (int o = tid; o < h.nopen; o += nt) __stcg(a.part_wr + obase[o] + orank[o], acc[opos[o]]);
     if ((STATE || MODE == MODE_HEUN_C) && h.nrc > 0) {
         __syncthreads();
-        // the corrector of step n runs with a.step = n + 1 (source at t_{n+1})
-        const int64_t tix = HEUN ? a.step - 1 : a.step;
+        // the corrector of step n runs with step = n + 1 (source at t_{n+1})
+        const int64_t tix = HEUN ? step - 1 : step;
         for (int k = tid; k < h.nrc; k += nt) {
             const int pos = recs[2 * k], r2 = recs[2 * k + 1];
             a.trace[(int64_t)r2 * a.trace_cap + tix] =
@@ -604,13 +604,13 @@ template <int NP, typename T, int MODE>
 __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     sem_step_kernel(const Plan pl, const StepArgs<T> a, const Basis<T> bs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_block<NP, T, MODE>(pl, a, bs, blockIdx.x, smem_raw);
+    step_block<NP, T, MODE>(pl, a, bs, blockIdx.x, smem_raw, a.step, a.pending);
 }
 
 // Arguments of launch k of a shot, from its level buffers (the same
 // assignment as the host's for a single mesh).
 template <typename T, int MODE>
-__device__ __forceinline__ StepArgs<T> shot_step_args(const ShotDesc<T>& d, int64_t k, int pending) {
+__host__ __device__ __forceinline__ StepArgs<T> shot_step_args(const ShotDesc<T>& d, int64_t k, int pending) {
     StepArgs<T> a;
     auto m3 = [](int64_t v) { return (int)(((v % 3) + 3) % 3); };
     if (MODE == MODE_KAHAN) {
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
         s_a = shot_step_args<T, MODE>(d, ba.step[shot], ba.pending[shot]);
     }
     __syncthreads();
-    step_block<NP, T, MODE>(s_pl, s_a, bs, ba.cta_block[blockIdx.x], smem_raw);
+    step_block<NP, T, MODE>(s_pl, s_a, bs, ba.cta_block[blockIdx.x], smem_raw, s_a.step, s_a.pending);
 }
 
 // After a batch step: every shot's step number advances and its open nodes
@@ -681,6 +681,106 @@ __global__ void batch_advance_kernel(int64_t* step, int32_t* pending, int nshots
     if (i < nshots) {
         step[i] += 1;
         pending[i] = 1;
+    }
+}
+
+// ------------------------------------------------------- streamed time loop
+// Kahan-mode arguments of even and odd steps (step and pending are set per unit).
+template <typename T>
+struct StepPair {
+    StepArgs<T> even, odd;
+};
+template <typename T, int MODE>
+StepArgs<T> shot_step_args_host(const ShotDesc<T>& d, int64_t parity) {
+    return shot_step_args<T, MODE>(d, parity, 1);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_gpu(const int32_t* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Polls of one done flag before a wait gives up (with the back-off below,
+// well over a second; a unit normally waits microseconds at most).
+constexpr int kWaitPolls = 1 << 21;
+
+// Several steps of one mesh in one launch. CTAs take units u = i * nblocks
+// + b (step i of the launch, block b) in increasing order from a work
+// counter. Unit (i, b) first waits until step i-1 has finished at b and at
+// every block sharing a node with b: those are exactly the blocks whose
+// partial sums, open-node states and closed-node values it reads, and whose
+// reads of the buffers it overwrites (the level buffers and the partial-sum
+// buffers rotate with the step) precede its writes. A unit waits only on
+// units taken earlier, which belong to CTAs that are running, so the waits
+// end; each is still bounded, and on giving up the CTA raises the error flag
+// and stops, as does every CTA that sees the flag raised. The arithmetic per
+// unit is step_block's, so the result is bitwise that of one launch per
+// step. DENSE plans only: the gathers of GATHER plans stage through L1,
+// which is not coherent with the other CTAs' writes within a launch.
+template <int NP, typename T, int MODE>
+__global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
+    sem_stream_kernel(const ShotDesc<T> d, const StreamArgs sa, const StepPair<T> kp, const Basis<T> bs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ StepArgs<T> s_a;
+    __shared__ long long s_unit;
+    __shared__ int s_fail;
+    const int nb = d.pl.nblocks;
+    const long long total = (long long)sa.nsteps * nb;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            // a raised error flag (this launch or an earlier one) stops the CTA
+            s_unit = ld_relaxed_gpu(sa.err) != 0 ? total : (long long)(atomicAdd(sa.counter, 1ull) - sa.base);
+            s_fail = 0;
+        }
+        __syncthreads();
+        const long long u = s_unit;
+        if (u < 0 || u >= total) break;
+        const int i = (int)(u / nb);
+        const int b = (int)(u - (long long)i * nb);
+        if (i > 0) {
+            const uint32_t need = sa.serial0 + (uint32_t)(i - 1);
+            const int d1 = sa.dep_ptr[b + 1];
+            for (int t = sa.dep_ptr[b] + threadIdx.x; t < d1; t += blockDim.x) {
+                const uint32_t* f = sa.done + sa.dep[t];
+                for (int n = 0; (int32_t)(ld_acquire_gpu(f) - need) < 0; ++n) {
+                    if (n >= kWaitPolls || ((n & 63) == 63 && ld_relaxed_gpu(sa.err) != 0)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+        }
+        const int64_t k = sa.step0 + i;
+        const int pend = (i > 0 || sa.pending0) ? 1 : 0;
+        if (MODE != MODE_KAHAN && threadIdx.x == 0) s_a = shot_step_args<T, MODE>(d, k, pend);
+        __syncthreads();
+        if (s_fail) {
+            if (threadIdx.x == 0) atomicExch(sa.err, 1);
+            break;
+        }
+        if constexpr (MODE == MODE_KAHAN) {
+            // the Kahan buffers alternate with the step: the arguments stay in
+            // the kernel's parameter space (no registers held for them)
+            step_block<NP, T, MODE>(d.pl, (k & 1) ? kp.odd : kp.even, bs, b, smem_raw, k, pend);
+        } else {
+            step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend);
+        }
+        // every thread's stores of the unit precede the flag
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
+        }
     }
 }
 
@@ -957,6 +1057,83 @@ cudaError_t launch_batch_step(int np, bool fp64, int mode, bool prepare_only, co
 cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cudaStream_t st) {
     batch_advance_kernel<<<(nshots + 255) / 256, 256, 0, st>>>(step, pending, nshots);
     return cudaGetLastError();
+}
+
+namespace {
+
+template <int NP, typename T, int MODE>
+cudaError_t stream_t(bool query, const void* shot, const StreamArgs& sa, const void* basis, int threads, int smem,
+                     int ctas, int* max_ctas, cudaStream_t st) {
+    auto kern = sem_stream_kernel<NP, T, MODE>;
+    static int configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    if (query) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        *max_ctas = per_sm * sms;
+        return cudaSuccess;
+    }
+    ShotDesc<T> dv = *static_cast<const ShotDesc<T>*>(shot);
+    StreamArgs av = sa;
+    StepPair<T> kp;
+    kp.even = shot_step_args_host<T, MODE>(dv, 0);
+    kp.odd = shot_step_args_host<T, MODE>(dv, 1);
+    Basis<T> bv = *static_cast<const Basis<T>*>(basis);
+    void* args[] = {&dv, &av, &kp, &bv};
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(ctas), dim3(threads), args, (size_t)smem, st);
+}
+
+template <typename T, int MODE>
+cudaError_t dispatch_stream(int np, bool query, const void* shot, const StreamArgs& sa, const void* basis, int threads,
+                            int smem, int ctas, int* max_ctas, cudaStream_t st) {
+    switch (np) {
+#define SEM_STREAM_CASE(N) \
+    case N: return stream_t<N, T, MODE>(query, shot, sa, basis, threads, smem, ctas, max_ctas, st);
+        SEM_STREAM_CASE(2)
+        SEM_STREAM_CASE(3)
+        SEM_STREAM_CASE(4)
+        SEM_STREAM_CASE(5)
+        SEM_STREAM_CASE(6)
+        SEM_STREAM_CASE(7)
+        SEM_STREAM_CASE(8)
+        SEM_STREAM_CASE(9)
+#undef SEM_STREAM_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t stream_any(int np, bool fp64, int mode, bool query, const void* shot, const StreamArgs& sa,
+                       const void* basis, int threads, int smem, int ctas, int* max_ctas, cudaStream_t st) {
+    if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
+    if (fp64) {
+        if (mode == MODE_THREE_LEVEL)
+            return dispatch_stream<double, MODE_THREE_LEVEL>(np, query, shot, sa, basis, threads, smem, ctas, max_ctas, st);
+        return cudaErrorInvalidValue;
+    }
+    if (mode == MODE_THREE_LEVEL)
+        return dispatch_stream<float, MODE_THREE_LEVEL>(np, query, shot, sa, basis, threads, smem, ctas, max_ctas, st);
+    if (mode == MODE_KAHAN)
+        return dispatch_stream<float, MODE_KAHAN>(np, query, shot, sa, basis, threads, smem, ctas, max_ctas, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t stream_max_ctas(int np, bool fp64, int mode, int threads, int smem, int* max_ctas) {
+    StreamArgs sa{};
+    return stream_any(np, fp64, mode, true, nullptr, sa, nullptr, threads, smem, 0, max_ctas, nullptr);
+}
+
+cudaError_t launch_stream(int np, bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis,
+                          int threads, int smem, int ctas, cudaStream_t st) {
+    return stream_any(np, fp64, mode, false, shot, sa, basis, threads, smem, ctas, nullptr, st);
 }
 
 int step_threads(int eb) {

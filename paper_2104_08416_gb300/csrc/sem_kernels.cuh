@@ -124,6 +124,21 @@ struct BatchArgs {
     const int32_t* pending;
 };
 
+// A streamed launch: several steps of one mesh (the shot's plan and level
+// buffers) in one persistent launch; see sem_stream_kernel.
+struct StreamArgs {
+    unsigned long long* counter;  // work counter
+    unsigned long long base;      // its value when this launch starts
+    uint32_t* done;               // per block: serial of its last finished step
+    const int32_t* dep_ptr;       // [nblocks + 1]
+    const int32_t* dep;           // blocks sharing a node with the block, itself included
+    int32_t* err;                 // raised when a wait gave up
+    int64_t step0;                // step number of the launch's first step
+    int32_t nsteps;               // steps in this launch
+    int32_t pending0;             // open nodes pending before the first step
+    uint32_t serial0;             // serial of the first step (done flags)
+};
+
 // Launchers; return cudaSuccess or the launch error.
 cudaError_t launch_step(int np, bool fp64, int mode, const Plan& plan, const void* args, const void* basis,
                         int threads, int smem_bytes, cudaStream_t st);
@@ -170,5 +185,12 @@ int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, b
 cudaError_t launch_batch_step(int np, bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas,
                               const void* basis, int threads, int smem, cudaStream_t st);
 cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cudaStream_t st);
+
+// Streamed steps (leapfrog modes of DENSE plans): CTAs resident at once for
+// this launch shape, and the cooperative launch of `ctas` CTAs (at most that
+// many) running sa.nsteps steps of the shot (a host ShotDesc<T>).
+cudaError_t stream_max_ctas(int np, bool fp64, int mode, int threads, int smem, int* max_ctas);
+cudaError_t launch_stream(int np, bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis,
+                          int threads, int smem, int ctas, cudaStream_t st);
 
 }  // namespace semdev

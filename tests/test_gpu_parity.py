@@ -10,7 +10,7 @@ from oracle import mesh, ordering, sem as osem
 from tests._gpu_common import FP32_TOL, FP64_TOL, gpu_run, need_gpu, oracle_run, rel_l2
 
 pytestmark = pytest.mark.gpu
-ORDERINGS = ["none", "rowmajor", "random", "hilbert", "connectivity", "distance"]
+ORDERINGS = ["none", "rowmajor", "random", "hilbert", "connectivity", "distance", "hilbert_wide"]
 
 
 @pytest.fixture(scope="module")

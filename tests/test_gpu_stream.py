@@ -1,0 +1,112 @@
+"""The streamed time loop (sem_set_stream): several leapfrog steps per launch
+of the persistent step kernel, units (step, block) taken in order, each
+waiting for the previous step at its block's neighbours. Its arithmetic per
+unit is the per-step kernel's, so wavefields and traces must be bitwise those
+of one launch per step, on meshes with few and with many blocks, at launch
+lengths that split runs at every possible point, in the three leapfrog
+storage precisions, and across sem_step calls that switch between the two.
+"""
+import numpy as np
+import pytest
+
+import gen
+from tests._gpu_common import FP32_TOL, FP64_TOL, need_gpu, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _handle(P, m, p, prec, order, eb, stream, nsteps):
+    h = P.SEM(m["coords"], m["quads"], p, prec)
+    h.sem_reorder(order, 3)
+    h.sem_set_model(m["vel"], m["rho"])
+    if eb:
+        h.sem_set_tuning(eb, 0)
+    h.sem_set_stream(stream)
+    h.sem_set_source(m["f0"], m["t0"], m["amp"], *m["src_xy"])
+    h.sem_set_receivers(m["receivers"], nsteps)
+    h.sem_set_dt(0.3 * h.sem_cfl_dt())
+    return h
+
+
+def _run(P, m, p, prec, order, eb, stream, calls):
+    h = _handle(P, m, p, prec, order, eb, stream, sum(calls))
+    for n in calls:
+        h.sem_step(n)
+    out = (h.sem_read_wavefield(), h.sem_read_traces(), h.sem_launch_info()[0])
+    h.sem_destroy()
+    return out
+
+
+CASES = [
+    # n, p, precision, elements per block, steps per sem_step call
+    (40, 4, "fp32_kahan", 0, [61]),
+    (40, 4, "fp32_kahan", 16, [1, 2, 40]),
+    (64, 4, "fp32_kahan", 32, [100]),
+    (33, 3, "fp64", 0, [45]),
+    (30, 5, "fp32", 24, [30, 7]),
+    (24, 2, "fp32_kahan", 8, [50]),
+    (20, 7, "fp64", 12, [19]),
+    (18, 8, "fp32_kahan", 6, [23]),
+]
+
+
+@pytest.mark.parametrize("n,p,prec,eb,calls", CASES)
+def test_streamed_bitwise_per_step(n, p, prec, eb, calls):
+    P = need_gpu()
+    m = gen.graded(n, seed=n + p)
+    u0, tr0, spl0 = _run(P, m, p, prec, "hilbert", eb, 0, calls)
+    assert spl0 == 1
+    assert np.isfinite(u0).all() and np.linalg.norm(u0) > 0
+    for stream in (1, 3, 256):
+        u, tr, spl = _run(P, m, p, prec, "hilbert", eb, stream, calls)
+        assert spl == stream  # the Hilbert node numbering gives a DENSE plan
+        assert np.array_equal(u, u0), (stream, rel_l2(u, u0))
+        assert np.array_equal(tr, tr0), (stream, rel_l2(tr, tr0))
+
+
+def test_streamed_against_oracle():
+    P = need_gpu()
+    m = gen.graded(36, seed=9)
+    n = 80
+    h = _handle(P, m, 4, "fp64", "hilbert", 16, 256, n)
+    dt = 0.3 * h.sem_cfl_dt()
+    h.sem_set_dt(dt)
+    h.sem_step(n)
+    u, tr = h.sem_read_wavefield(), h.sem_read_traces()
+    h.sem_destroy()
+    _, u_ref, tr_ref = oracle_run(m, 4, n, dt, receivers=m["receivers"])
+    assert rel_l2(u, u_ref) < FP64_TOL
+    assert rel_l2(tr, tr_ref) < FP64_TOL
+    h = _handle(P, m, 4, "fp32_kahan", "hilbert", 16, 256, n)
+    h.sem_set_dt(dt)
+    h.sem_step(n)
+    u32 = h.sem_read_wavefield()
+    h.sem_destroy()
+    assert rel_l2(u32, u_ref) < FP32_TOL
+
+
+def test_switching_between_streamed_and_per_step():
+    P = need_gpu()
+    m = gen.graded(48, seed=21)
+    calls = [5, 9, 2, 30]
+    u0, tr0, _ = _run(P, m, 4, "fp32_kahan", "hilbert", 32, 0, calls)
+    h = _handle(P, m, 4, "fp32_kahan", "hilbert", 32, 4, sum(calls))
+    for k, c in enumerate(calls):
+        h.sem_set_stream(4 if k % 2 == 0 else 0)
+        h.sem_step(c)
+    u, tr = h.sem_read_wavefield(), h.sem_read_traces()
+    h.sem_destroy()
+    assert np.array_equal(u, u0)
+    assert np.array_equal(tr, tr0)
+
+
+@pytest.mark.parametrize("order", ["random", "none"])
+def test_gather_plans_launch_per_step(order):
+    P = need_gpu()
+    m = gen.relabel(gen.graded(30, seed=5), seed=6)
+    u0, tr0, _ = _run(P, m, 4, "fp32_kahan", order, 32, 0, [25])
+    u, tr, spl = _run(P, m, 4, "fp32_kahan", order, 32, 256, [25])
+    if order == "random":
+        assert spl == 1
+    assert np.array_equal(u, u0)
+    assert np.array_equal(tr, tr0)

@@ -49,7 +49,7 @@ def _meshes():
     yield "unit_relab", gen.relabel(gen.unit_square(10), seed=1)
 
 
-@pytest.mark.parametrize("kind", ["none", "rowmajor", "random", "hilbert", "connectivity", "distance"])
+@pytest.mark.parametrize("kind", ["none", "rowmajor", "random", "hilbert", "connectivity", "distance", "hilbert_wide"])
 @pytest.mark.parametrize("p", [1, 2, 4])
 def test_orderings_bit_exact(lib, kind, p):
     for name, m in _meshes():

@@ -43,6 +43,49 @@ def test_hilbert_grid_sizes_of_the_workloads():
     assert ix.max() == 31 and iy.max() == 7
 
 
+def _rectangle(nx, ny, w, h):
+    xs, ys = np.linspace(0.0, w, nx + 1), np.linspace(0.0, h, ny + 1)
+    coords = np.array([(x, y) for y in ys for x in xs])
+    quads = np.array([(j * (nx + 1) + i, j * (nx + 1) + i + 1, (j + 1) * (nx + 1) + i + 1, (j + 1) * (nx + 1) + i)
+                      for j in range(ny) for i in range(nx)], dtype=np.int32)
+    return coords, quads
+
+
+def test_hilbert_wide_box_sizes():
+    """The alternative box of Section 4.3 (w_b = sqrt(n_e) r, h_b = sqrt(n_e)):
+    the same grid as the default on a square domain, r times more columns
+    than rows otherwise."""
+    m = gen.unit_square(32)
+    assert ordering.hilbert_grid(m["coords"], m["quads"], wide=True)[:2] == (32, 32)
+    np.testing.assert_array_equal(ordering.hilbert_element_order(m["coords"], m["quads"], wide=True),
+                                  ordering.hilbert_element_order(m["coords"], m["quads"]))
+    coords, quads = _rectangle(30, 10, 3.0, 1.0)          # E = 300, r = 3
+    assert ordering.hilbert_grid(coords, quads)[:2] == (18, 6)          # W = ceil(sqrt 300), H = W / r
+    assert ordering.hilbert_grid(coords, quads, wide=True)[:2] == (54, 18)  # H = ceil(sqrt 300), W = H r
+    m = gen.layered(64, 16)
+    assert ordering.hilbert_grid(m["coords"], m["quads"], wide=True)[:2] == (128, 32)
+
+
+def test_hilbert_wide_order_brute_force():
+    """Cells found by scanning every column and row interval (no floor
+    formula); the list L is the elements sorted by the curve rank of their
+    cell. With 54 x 18 cells over 30 x 10 elements no centroid lies on a cell
+    edge and no cell holds two elements."""
+    coords, quads = _rectangle(30, 10, 3.0, 1.0)
+    W, H = 54, 18
+    cx = coords[quads][:, :, 0].mean(axis=1)
+    cy = coords[quads][:, :, 1].mean(axis=1)
+    ix = np.array([next(k for k in range(W) if k * 3.0 / W < x < (k + 1) * 3.0 / W) for x in cx])
+    iy = np.array([next(k for k in range(H) if k * 1.0 / H < y < (k + 1) * 1.0 / H) for y in cy])
+    assert len(set(zip(ix.tolist(), iy.tolist()))) == quads.shape[0]
+    rank = hilbert.rank_grid(W, H)
+    expect = np.argsort(rank[ix, iy], kind="stable")
+    L = ordering.hilbert_element_order(coords, quads, wide=True)
+    np.testing.assert_array_equal(L, expect)
+    # the default box (18 x 6 cells, several elements per cell) orders differently
+    assert not np.array_equal(ordering.hilbert_element_order(coords, quads), L)
+
+
 def test_homogeneous_32x32_element_order_is_listing1_order5():
     """On the 32 x 32 unit square each curve cell holds exactly one element, so
     the element list L is the standard curve of order 5 (Listing 1)."""
@@ -110,7 +153,7 @@ def test_node_renumbering_vectorised_equals_loop(kind):
     assert np.all(np.diff(d)[same] >= 0)
 
 
-@pytest.mark.parametrize("kind", ["none", "rowmajor", "random", "hilbert"])
+@pytest.mark.parametrize("kind", ["none", "rowmajor", "random", "hilbert", "hilbert_wide"])
 def test_orderings_are_permutations(kind):
     m = gen.graded(9, seed=3)
     conn, n, _ = mesh.canonical_numbering(m["quads"], m["coords"].shape[0], 2)
