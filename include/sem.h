@@ -279,20 +279,23 @@ sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells);
  * pointer may be NULL. */
 sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t* open_nodes);
 
-/* Streamed time loop. With steps_per_launch = N >= 1 (default 256) sem_step
- * runs up to N leapfrog steps per launch of a persistent step kernel: as
- * many CTAs as fit on the GPU at once take (step, element block) units in
- * order from a work counter, and a unit starts as soon as the previous step
- * has finished at its block and at every block sharing a node with it, so
- * consecutive steps overlap and no launch boundary or partly filled last
- * wave separates them. The arithmetic per unit is the per-step kernel's: the
- * results are bitwise those of N = 0 (one launch per step). Used for DENSE
- * block plans (the node numbering of Section 4.3 along the element order)
- * and the leapfrog scheme; other cases launch once per step. Waits are
- * bounded: a wait that gives up (which no correct run does) raises a device
- * error flag, the remaining steps of the run are skipped, and the next
- * sem_read_wavefield, sem_get_state or sem_read_traces returns SEM_ERR_CUDA.
- * Any time. */
+/* Streamed time loop. With steps_per_launch = N >= 1 sem_step runs up to N
+ * leapfrog steps per launch: one CTA per (step, element block) unit, each
+ * CTA taking the next unit in order from a work counter once it runs; a
+ * unit starts as soon as the previous step has finished at its block and at
+ * every block sharing a node with it, so consecutive steps overlap and no
+ * launch boundary or partly filled last wave separates them. The arithmetic
+ * per unit is the per-step kernel's: the results are bitwise those of N = 0
+ * (one launch per step). Used for DENSE block plans (the node numbering of
+ * Section 4.3 along the element order) and the leapfrog scheme; other cases
+ * launch once per step. N = -1 (the default) streams 256 steps per launch
+ * where a step has fewer element blocks than 8 times the step CTAs resident
+ * on the GPU at once (there the partly filled last wave of a launch per step
+ * costs more than the units' waits) and launches once per step otherwise.
+ * Waits are bounded: a wait that gives up (which no correct run does) raises
+ * a device error flag, the remaining steps of the run are skipped, and the
+ * next sem_read_wavefield, sem_get_state or sem_read_traces returns
+ * SEM_ERR_CUDA. Any time. */
 sem_status sem_set_stream(sem_mesh* m, int steps_per_launch);
 
 /* Launch shape of the step kernel: elements per block (0 = default, about

@@ -77,10 +77,11 @@ struct sem_mesh {
     int smem = 0;
     int threads = 0;
     // streamed time loop (sem_set_stream): up to stream_steps steps per
-    // launch of the persistent step kernel, stream_ctas CTAs (0: per-step
-    // launches), per-block neighbour lists and done flags
-    int stream_steps = 256;
-    int stream_ctas = 0;
+    // launch (0: one launch per step) where the plan allows it (stream_ok),
+    // per-block neighbour lists and done flags
+    int stream_steps = -1;            // -1: automatic (see streamed())
+    bool stream_ok = false;
+    int resident_ctas = 0;            // step CTAs resident on the GPU at once
     int32_t* d_dep_ptr = nullptr;
     int32_t* d_dep = nullptr;
     uint32_t* d_done = nullptr;
@@ -479,7 +480,7 @@ sem_status build(sem_mesh* m) {
         m->d_trace = (double*)tr;
     }
     // streamed time loop: leapfrog on a DENSE plan
-    m->stream_ctas = 0;
+    m->stream_ok = false;
     const int md = mode_of(m);
     if (pl.dense && m->scheme == SEM_SCHEME_LEAPFROG && (md == semdev::MODE_KAHAN || md == semdev::MODE_THREE_LEVEL)) {
         if ((st = upload(m, &m->d_dep_ptr, pl.dep_ptr.data(), pl.dep_ptr.size())) != SEM_OK) return st;
@@ -492,9 +493,10 @@ sem_status build(sem_mesh* m) {
         m->d_counter = (unsigned long long*)ctr;
         m->d_err = (int32_t*)er;
         m->serial = 1;
-        int ctas = 0;
-        SEM_CUDA(semdev::stream_max_ctas(M.np, fp64(m), md, m->threads, m->smem, &ctas));
-        m->stream_ctas = ctas;
+        int res = 0;
+        SEM_CUDA(semdev::stream_resident_ctas(M.np, fp64(m), md, m->threads, m->smem, &res));
+        m->resident_ctas = res;
+        m->stream_ok = res > 0;
     }
     cudaError_t e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(m, e, "build");
@@ -610,7 +612,18 @@ semdev::ShotDesc<T> shot_desc(const sem_mesh* m) {
     return d;
 }
 
-bool streamed(const sem_mesh* m) { return m->stream_steps > 0 && m->stream_ctas > 0; }
+// Streamed where the plan allows it and either asked for, or (automatic)
+// where one launch per step would leave much of the GPU idle: fewer than 8
+// waves of resident CTAs per step, so that the partly filled last wave and
+// the launch boundary cost more than the streamed units' own waits.
+constexpr int kAutoStreamSteps = 256;
+constexpr int kAutoStreamWaves = 8;
+bool streamed(const sem_mesh* m) {
+    if (!m->stream_ok || m->stream_steps == 0) return false;
+    if (m->stream_steps > 0) return true;
+    return m->plan.nblocks < (int64_t)kAutoStreamWaves * m->resident_ctas;
+}
+int64_t stream_len(const sem_mesh* m) { return m->stream_steps > 0 ? m->stream_steps : kAutoStreamSteps; }
 
 // Steps k = m->step .. m->step + n - 1 as one streamed launch (pending: the
 // open nodes of step m->step - 1 are not finished yet), recorded with events
@@ -627,8 +640,6 @@ sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
     sa.nsteps = (int32_t)n;
     sa.pending0 = pending ? 1 : 0;
     sa.serial0 = m->serial;
-    const int64_t units = n * m->plan.nblocks;
-    const int ctas = (int)std::min<int64_t>(m->stream_ctas, units);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (m->profiling) {
         e0 = take_event(m);
@@ -640,12 +651,12 @@ sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
     if (e == cudaSuccess) {
         if (fp64(m)) {
             auto d = shot_desc<double>(m);
-            e = semdev::launch_stream(m->mesh.np, true, mode_of(m), &d, sa, basis_of(m), m->threads, m->smem, ctas,
-                                      m->stream);
+            e = semdev::launch_stream(m->mesh.np, true, mode_of(m), &d, sa, basis_of(m), m->threads, m->smem,
+                                      (int)m->plan.nblocks, m->stream);
         } else {
             auto d = shot_desc<float>(m);
-            e = semdev::launch_stream(m->mesh.np, false, mode_of(m), &d, sa, basis_of(m), m->threads, m->smem, ctas,
-                                      m->stream);
+            e = semdev::launch_stream(m->mesh.np, false, mode_of(m), &d, sa, basis_of(m), m->threads, m->smem,
+                                      (int)m->plan.nblocks, m->stream);
         }
     }
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, m->stream);
@@ -664,7 +675,9 @@ sem_status launch_steps(sem_mesh* m, int64_t nsteps) {
     sem_status st;
     for (int64_t k = 0; k < nsteps;) {
         if (streamed(m)) {
-            const int64_t n = std::min<int64_t>(nsteps - k, m->stream_steps);
+            // at most 2^31 - 1 CTAs per launch
+            const int64_t cap = std::max<int64_t>(1, 2147483647LL / std::max<int64_t>(1, m->plan.nblocks));
+            const int64_t n = std::min<int64_t>(std::min<int64_t>(nsteps - k, stream_len(m)), cap);
             if ((st = launch_stream_steps(m, n, k > 0)) != SEM_OK) return st;
             k += n;
         } else {
@@ -1029,8 +1042,8 @@ sem_status sem_set_tuning(sem_mesh* m, int elems_per_block, int threads_per_bloc
 
 sem_status sem_set_stream(sem_mesh* m, int steps_per_launch) {
     if (!m) return SEM_ERR_INVALID_ARG;
-    if (steps_per_launch < 0 || steps_per_launch > 65536)
-        return fail(m, SEM_ERR_INVALID_ARG, "steps_per_launch must be in 0..65536");
+    if (steps_per_launch < -1 || steps_per_launch > 65536)
+        return fail(m, SEM_ERR_INVALID_ARG, "steps_per_launch must be in -1..65536");
     m->stream_steps = steps_per_launch;
     return SEM_OK;
 }
@@ -1367,7 +1380,7 @@ sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells) {
 
 sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t* open_nodes) {
     if (!m) return SEM_ERR_INVALID_ARG;
-    if (steps_per_launch) *steps_per_launch = m->built && streamed(m) ? m->stream_steps : 1;
+    if (steps_per_launch) *steps_per_launch = m->built && streamed(m) ? stream_len(m) : 1;
     if (open_nodes) *open_nodes = m->built ? (int64_t)m->plan.open_gid.size() : -1;
     return SEM_OK;
 }

@@ -278,9 +278,18 @@ __device__ __forceinline__ void heun_element(const Plan& pl, const StepArgs<T>& 
 }
 
 // One block of one mesh, one CTA (the body of the step kernels).
-template <int NP, typename T, int MODE>
+// Called by every thread of a block after the loads that do not depend on
+// the previous step (element data, packet) are issued and before the node
+// state is read; returns false (the same in every thread) to abandon the
+// block. The plain step kernel has nothing to wait for.
+struct NoWait {
+    __device__ __forceinline__ bool operator()() const { return true; }
+};
+
+template <int NP, typename T, int MODE, typename Ready = NoWait>
 __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a, const Basis<T>& bs, const int b,
-                                           unsigned char* smem_raw, const int64_t step, const int pend) {
+                                           unsigned char* smem_raw, const int64_t step, const int pend,
+                                           const Ready& ready = Ready()) {
     constexpr int P = NP * NP;
     constexpr int UPH = (P + 1) / 2;
     constexpr bool HEUN = MODE == MODE_HEUN_P || MODE == MODE_HEUN_C;
@@ -314,16 +323,21 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
         if (STATE && pend) f_prev = (T)a.src_f[step - 1];
     }
     const int64_t e = e0 + tid;
+    // the element-array stride, opaque to the compiler: a kernel that runs
+    // several blocks in a loop would otherwise compute the per-slot addresses
+    // once, ahead of the loop, and hold them in registers throughout
+    int64_t nes = pl.ne;
+    asm volatile("" : "+l"(nes));
 
     // element-side data straight into registers (coalesced across threads)
     uint32_t pw[UPH];
     float4 cf0 = make_float4(0.f, 0.f, 0.f, 0.f), cf1 = cf0;
     if (has_el) {
 #pragma unroll
-        for (int k = 0; k < UPH; ++k) pw[k] = ld_stream(pl.epos + (int64_t)k * pl.ne + e);
+        for (int k = 0; k < UPH; ++k) pw[k] = ld_stream(pl.epos + (int64_t)k * nes + e);
         if constexpr (BIL) {
             cf0 = ld_stream(pl.coef + e);
-            cf1 = ld_stream(pl.coef + pl.ne + e);
+            cf1 = ld_stream(pl.coef + nes + e);
         }
     }
 
@@ -331,6 +345,14 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     {
         const uint8_t* gpk = pl.packet + (int64_t)h.start * 16;
         for (int o = tid * 16; o < L.bytes; o += nt * 16) cp_async16(spk + o, gpk + o);
+        float4* az = reinterpret_cast<float4*>(acc);
+        const int nz = (h.sulen * (int)sizeof(T) + 15) / 16;
+        for (int k = tid; k < nz; k += nt) az[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!ready()) {
+            cp_async_commit();
+            cp_async_wait_all();
+            return;
+        }
         if (pl.dense) {
             const bool vok = a.vec_ok != 0;
             stage_range(su, a.u_k, abase, h.ulen, pl.nn, vok, tid, nt);
@@ -341,9 +363,6 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             }
         }
         cp_async_commit();
-        float4* az = reinterpret_cast<float4*>(acc);
-        const int nz = (h.sulen * (int)sizeof(T) + 15) / 16;
-        for (int k = tid; k < nz; k += nt) az[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         cp_async_wait_all();
         __syncthreads();
     }
@@ -453,9 +472,9 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                     gyy = kk * cA;
                     gxy = -kk * (j10 * j11[i] + j00 * j01[i]);
                 } else {
-                    gxx = ld_stream(pl.G + (int64_t)q * pl.ne + e);
-                    gxy = ld_stream(pl.G + (int64_t)(P + q) * pl.ne + e);
-                    gyy = ld_stream(pl.G + (int64_t)(2 * P + q) * pl.ne + e);
+                    gxx = ld_stream(pl.G + (int64_t)q * nes + e);
+                    gxy = ld_stream(pl.G + (int64_t)(P + q) * nes + e);
+                    gyy = ld_stream(pl.G + (int64_t)(2 * P + q) * nes + e);
                 }
                 const T F1 = gxx * dxi + gxy * deta;
                 const T F2 = gxy * dxi + gyy * deta;
@@ -610,7 +629,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
 // Arguments of launch k of a shot, from its level buffers (the same
 // assignment as the host's for a single mesh).
 template <typename T, int MODE>
-__host__ __device__ __forceinline__ StepArgs<T> shot_step_args(const ShotDesc<T>& d, int64_t k, int pending) {
+__device__ __forceinline__ StepArgs<T> shot_step_args(const ShotDesc<T>& d, int64_t k, int pending) {
     StepArgs<T> a;
     auto m3 = [](int64_t v) { return (int)(((v % 3) + 3) % 3); };
     if (MODE == MODE_KAHAN) {
@@ -685,15 +704,6 @@ __global__ void batch_advance_kernel(int64_t* step, int32_t* pending, int nshots
 }
 
 // ------------------------------------------------------- streamed time loop
-// Kahan-mode arguments of even and odd steps (step and pending are set per unit).
-template <typename T>
-struct StepPair {
-    StepArgs<T> even, odd;
-};
-template <typename T, int MODE>
-StepArgs<T> shot_step_args_host(const ShotDesc<T>& d, int64_t parity) {
-    return shot_step_args<T, MODE>(d, parity, 1);
-}
 
 __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
     uint32_t v;
@@ -713,74 +723,83 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int32_t* p) {
 // well over a second; a unit normally waits microseconds at most).
 constexpr int kWaitPolls = 1 << 21;
 
-// Several steps of one mesh in one launch. CTAs take units u = i * nblocks
-// + b (step i of the launch, block b) in increasing order from a work
-// counter. Unit (i, b) first waits until step i-1 has finished at b and at
-// every block sharing a node with b: those are exactly the blocks whose
-// partial sums, open-node states and closed-node values it reads, and whose
-// reads of the buffers it overwrites (the level buffers and the partial-sum
-// buffers rotate with the step) precede its writes. A unit waits only on
-// units taken earlier, which belong to CTAs that are running, so the waits
-// end; each is still bounded, and on giving up the CTA raises the error flag
-// and stops, as does every CTA that sees the flag raised. The arithmetic per
-// unit is step_block's, so the result is bitwise that of one launch per
-// step. DENSE plans only: the gathers of GATHER plans stage through L1,
-// which is not coherent with the other CTAs' writes within a launch.
+// Wait of unit (i, b) for step i-1 at b's neighbours (active when i > 0):
+// the threads poll one neighbour's done flag each (acquire), then the block
+// synchronises; a poll that gives up marks the unit failed.
+struct DepWait {
+    const StreamArgs* sa;
+    int b;
+    uint32_t need;
+    bool active;
+    int* fail;
+    __device__ __forceinline__ bool operator()() const {
+        if (!active) return true;
+        const int d1 = sa->dep_ptr[b + 1];
+        for (int t = sa->dep_ptr[b] + (int)threadIdx.x; t < d1; t += (int)blockDim.x) {
+            const uint32_t* f = sa->done + sa->dep[t];
+            for (int n = 0; (int32_t)(ld_acquire_gpu(f) - need) < 0; ++n) {
+                if (n >= kWaitPolls || ((n & 63) == 63 && ld_relaxed_gpu(sa->err) != 0)) {
+                    *fail = 1;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __syncthreads();
+        return *fail == 0;
+    }
+};
+
+// Several steps of one mesh in one launch of nsteps * nblocks CTAs. Each
+// CTA, once running, takes the next unit u = i * nblocks + b (step i of the
+// launch, block b) from a work counter, so units start in increasing order
+// whatever order the hardware runs CTAs in. Unit (i, b) first waits until
+// step i-1 has finished at b and at every block sharing a node with b: those
+// are exactly the blocks whose partial sums, open-node states and closed-node
+// values it reads, and whose reads of the buffers it overwrites (the level
+// buffers and the partial-sum buffers rotate with the step) precede its
+// writes. A unit waits only on units taken earlier, by CTAs that are running
+// or finished, so the waits end; each is still bounded, and a wait that
+// gives up raises the error flag, after which every unit still to start
+// returns at once. The arithmetic per unit is step_block's, so the result is
+// bitwise that of one launch per step. DENSE plans only: the gathers of
+// GATHER plans stage through L1, which is not coherent with the other CTAs'
+// writes within a launch.
 template <int NP, typename T, int MODE>
 __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
-    sem_stream_kernel(const ShotDesc<T> d, const StreamArgs sa, const StepPair<T> kp, const Basis<T> bs) {
+    sem_stream_kernel(const ShotDesc<T> d, const StreamArgs sa, const Basis<T> bs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ StepArgs<T> s_a;
     __shared__ long long s_unit;
     __shared__ int s_fail;
     const int nb = d.pl.nblocks;
     const long long total = (long long)sa.nsteps * nb;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            // a raised error flag (this launch or an earlier one) stops the CTA
-            s_unit = ld_relaxed_gpu(sa.err) != 0 ? total : (long long)(atomicAdd(sa.counter, 1ull) - sa.base);
-            s_fail = 0;
-        }
-        __syncthreads();
-        const long long u = s_unit;
-        if (u < 0 || u >= total) break;
-        const int i = (int)(u / nb);
-        const int b = (int)(u - (long long)i * nb);
-        if (i > 0) {
-            const uint32_t need = sa.serial0 + (uint32_t)(i - 1);
-            const int d1 = sa.dep_ptr[b + 1];
-            for (int t = sa.dep_ptr[b] + threadIdx.x; t < d1; t += blockDim.x) {
-                const uint32_t* f = sa.done + sa.dep[t];
-                for (int n = 0; (int32_t)(ld_acquire_gpu(f) - need) < 0; ++n) {
-                    if (n >= kWaitPolls || ((n & 63) == 63 && ld_relaxed_gpu(sa.err) != 0)) {
-                        s_fail = 1;
-                        break;
-                    }
-                    __nanosleep(128);
-                }
-            }
-        }
-        const int64_t k = sa.step0 + i;
-        const int pend = (i > 0 || sa.pending0) ? 1 : 0;
-        if (MODE != MODE_KAHAN && threadIdx.x == 0) s_a = shot_step_args<T, MODE>(d, k, pend);
-        __syncthreads();
-        if (s_fail) {
-            if (threadIdx.x == 0) atomicExch(sa.err, 1);
-            break;
-        }
-        if constexpr (MODE == MODE_KAHAN) {
-            // the Kahan buffers alternate with the step: the arguments stay in
-            // the kernel's parameter space (no registers held for them)
-            step_block<NP, T, MODE>(d.pl, (k & 1) ? kp.odd : kp.even, bs, b, smem_raw, k, pend);
-        } else {
-            step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend);
-        }
-        // every thread's stores of the unit precede the flag
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
-        }
+    if (threadIdx.x == 0) {
+        s_unit = ld_relaxed_gpu(sa.err) != 0 ? total : (long long)(atomicAdd(sa.counter, 1ull) - sa.base);
+        s_fail = 0;
+    }
+    __syncthreads();
+    const long long u = s_unit;
+    if (u < 0 || u >= total) return;
+    const int i = (int)(u / nb);
+    const int b = (int)(u - (long long)i * nb);
+    const int64_t k = sa.step0 + i;
+    const int pend = (i > 0 || sa.pending0) ? 1 : 0;
+    if (threadIdx.x == 0) s_a = shot_step_args<T, MODE>(d, k, pend);
+    __syncthreads();
+    // the neighbours' previous step, awaited while the block's element data
+    // and packet are already on their way
+    const DepWait w{&sa, b, sa.serial0 + (uint32_t)(i - 1), i > 0, &s_fail};
+    step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend, w);
+    // every thread's stores of the unit precede the flag
+    __syncthreads();
+    if (s_fail) {
+        if (threadIdx.x == 0) atomicExch(sa.err, 1);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
     }
 }
 
@@ -1062,8 +1081,8 @@ cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cu
 namespace {
 
 template <int NP, typename T, int MODE>
-cudaError_t stream_t(bool query, const void* shot, const StreamArgs& sa, const void* basis, int threads, int smem,
-                     int ctas, int* max_ctas, cudaStream_t st) {
+cudaError_t stream_t(const void* shot, const StreamArgs& sa, const void* basis, int threads, int smem, int64_t ctas,
+                     cudaStream_t st) {
     auto kern = sem_stream_kernel<NP, T, MODE>;
     static int configured = 0;
     if (smem > configured) {
@@ -1071,31 +1090,48 @@ cudaError_t stream_t(bool query, const void* shot, const StreamArgs& sa, const v
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    if (query) {
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        *max_ctas = per_sm * sms;
-        return cudaSuccess;
-    }
-    ShotDesc<T> dv = *static_cast<const ShotDesc<T>*>(shot);
-    StreamArgs av = sa;
-    StepPair<T> kp;
-    kp.even = shot_step_args_host<T, MODE>(dv, 0);
-    kp.odd = shot_step_args_host<T, MODE>(dv, 1);
-    Basis<T> bv = *static_cast<const Basis<T>*>(basis);
-    void* args[] = {&dv, &av, &kp, &bv};
-    return cudaLaunchCooperativeKernel((const void*)kern, dim3(ctas), dim3(threads), args, (size_t)smem, st);
+    if (ctas < 1 || ctas > 2147483647LL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)ctas, threads, smem, st>>>(*static_cast<const ShotDesc<T>*>(shot), sa,
+                                                *static_cast<const Basis<T>*>(basis));
+    return cudaGetLastError();
+}
+
+template <int NP, typename T, int MODE>
+cudaError_t stream_resident_t(int threads, int smem, int* out) {
+    auto kern = sem_stream_kernel<NP, T, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0, dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) *out = per_sm * sms;
+    return e;
 }
 
 template <typename T, int MODE>
-cudaError_t dispatch_stream(int np, bool query, const void* shot, const StreamArgs& sa, const void* basis, int threads,
-                            int smem, int ctas, int* max_ctas, cudaStream_t st) {
+cudaError_t dispatch_resident(int np, int threads, int smem, int* out) {
+    switch (np) {
+#define SEM_RES_CASE(N) \
+    case N: return stream_resident_t<N, T, MODE>(threads, smem, out);
+        SEM_RES_CASE(2)
+        SEM_RES_CASE(3)
+        SEM_RES_CASE(4)
+        SEM_RES_CASE(5)
+        SEM_RES_CASE(6)
+        SEM_RES_CASE(7)
+        SEM_RES_CASE(8)
+        SEM_RES_CASE(9)
+#undef SEM_RES_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int MODE>
+cudaError_t dispatch_stream(int np, const void* shot, const StreamArgs& sa, const void* basis, int threads, int smem,
+                            int64_t ctas, cudaStream_t st) {
     switch (np) {
 #define SEM_STREAM_CASE(N) \
-    case N: return stream_t<N, T, MODE>(query, shot, sa, basis, threads, smem, ctas, max_ctas, st);
+    case N: return stream_t<N, T, MODE>(shot, sa, basis, threads, smem, ctas, st);
         SEM_STREAM_CASE(2)
         SEM_STREAM_CASE(3)
         SEM_STREAM_CASE(4)
@@ -1109,31 +1145,31 @@ cudaError_t dispatch_stream(int np, bool query, const void* shot, const StreamAr
     }
 }
 
-cudaError_t stream_any(int np, bool fp64, int mode, bool query, const void* shot, const StreamArgs& sa,
-                       const void* basis, int threads, int smem, int ctas, int* max_ctas, cudaStream_t st) {
-    if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
+}  // namespace
+
+cudaError_t stream_resident_ctas(int np, bool fp64, int mode, int threads, int smem, int* out) {
+    *out = 0;
     if (fp64) {
-        if (mode == MODE_THREE_LEVEL)
-            return dispatch_stream<double, MODE_THREE_LEVEL>(np, query, shot, sa, basis, threads, smem, ctas, max_ctas, st);
+        if (mode == MODE_THREE_LEVEL) return dispatch_resident<double, MODE_THREE_LEVEL>(np, threads, smem, out);
         return cudaErrorInvalidValue;
     }
-    if (mode == MODE_THREE_LEVEL)
-        return dispatch_stream<float, MODE_THREE_LEVEL>(np, query, shot, sa, basis, threads, smem, ctas, max_ctas, st);
-    if (mode == MODE_KAHAN)
-        return dispatch_stream<float, MODE_KAHAN>(np, query, shot, sa, basis, threads, smem, ctas, max_ctas, st);
+    if (mode == MODE_THREE_LEVEL) return dispatch_resident<float, MODE_THREE_LEVEL>(np, threads, smem, out);
+    if (mode == MODE_KAHAN) return dispatch_resident<float, MODE_KAHAN>(np, threads, smem, out);
     return cudaErrorInvalidValue;
 }
 
-}  // namespace
-
-cudaError_t stream_max_ctas(int np, bool fp64, int mode, int threads, int smem, int* max_ctas) {
-    StreamArgs sa{};
-    return stream_any(np, fp64, mode, true, nullptr, sa, nullptr, threads, smem, 0, max_ctas, nullptr);
-}
-
 cudaError_t launch_stream(int np, bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis,
-                          int threads, int smem, int ctas, cudaStream_t st) {
-    return stream_any(np, fp64, mode, false, shot, sa, basis, threads, smem, ctas, nullptr, st);
+                          int threads, int smem, int nblocks, cudaStream_t st) {
+    if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
+    const int64_t ctas = (int64_t)sa.nsteps * (int64_t)nblocks;
+    if (fp64) {
+        if (mode == MODE_THREE_LEVEL)
+            return dispatch_stream<double, MODE_THREE_LEVEL>(np, shot, sa, basis, threads, smem, ctas, st);
+        return cudaErrorInvalidValue;
+    }
+    if (mode == MODE_THREE_LEVEL) return dispatch_stream<float, MODE_THREE_LEVEL>(np, shot, sa, basis, threads, smem, ctas, st);
+    if (mode == MODE_KAHAN) return dispatch_stream<float, MODE_KAHAN>(np, shot, sa, basis, threads, smem, ctas, st);
+    return cudaErrorInvalidValue;
 }
 
 int step_threads(int eb) {

@@ -125,7 +125,7 @@ struct BatchArgs {
 };
 
 // A streamed launch: several steps of one mesh (the shot's plan and level
-// buffers) in one persistent launch; see sem_stream_kernel.
+// buffers) in one launch; see sem_stream_kernel.
 struct StreamArgs {
     unsigned long long* counter;  // work counter
     unsigned long long base;      // its value when this launch starts
@@ -186,11 +186,12 @@ cudaError_t launch_batch_step(int np, bool fp64, int mode, bool prepare_only, co
                               const void* basis, int threads, int smem, cudaStream_t st);
 cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cudaStream_t st);
 
-// Streamed steps (leapfrog modes of DENSE plans): CTAs resident at once for
-// this launch shape, and the cooperative launch of `ctas` CTAs (at most that
-// many) running sa.nsteps steps of the shot (a host ShotDesc<T>).
-cudaError_t stream_max_ctas(int np, bool fp64, int mode, int threads, int smem, int* max_ctas);
+// Streamed steps (leapfrog modes of DENSE plans): sa.nsteps steps of the
+// shot (a host ShotDesc<T> whose plan has nblocks blocks) in one launch of
+// sa.nsteps * nblocks CTAs, one (step, block) unit each.
 cudaError_t launch_stream(int np, bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis,
-                          int threads, int smem, int ctas, cudaStream_t st);
+                          int threads, int smem, int nblocks, cudaStream_t st);
+// CTAs of that launch shape resident on the whole GPU at once.
+cudaError_t stream_resident_ctas(int np, bool fp64, int mode, int threads, int smem, int* out);
 
 }  // namespace semdev

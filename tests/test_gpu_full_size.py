@@ -88,6 +88,8 @@ def test_graded_2000_steps_fp32_kahan_vs_fp64(P, graded):
         h = _handle(P, m, prec, nsteps=n, dt=dt)
         h.sem_step(n)
         out[prec] = (h.sem_read_wavefield(), h.sem_read_traces())
+        # 1024 element blocks per step: the time loop is streamed by default
+        assert h.sem_launch_info()[0] == 256
         h.sem_destroy()
     u64, tr64 = out["fp64"]
     u32, tr32 = out["fp32_kahan"]
@@ -120,6 +122,9 @@ def test_layered_3000_steps_fp32_kahan_vs_fp64(P):
             dt = h.sem_cfl_dt() * 0.3
         h.sem_set_dt(dt)
         h.sem_step(n)
+        if prec == "fp32_kahan":
+            # 16,384 element blocks per step: one launch per step by default
+            assert h.sem_launch_info()[0] == 1
         out[prec] = (h.sem_read_wavefield()[::16], h.sem_read_traces())
         h.sem_destroy()
     u64, tr64 = out["fp64"]
