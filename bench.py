@@ -232,13 +232,14 @@ def kernel_source_digest():
     return hsh.hexdigest()
 
 
-def recorded_traffic(precision, ordering):
-    """DRAM bytes per step-kernel launch from the committed ncu summary."""
+def recorded_traffic(precision, ordering, kernel):
+    """DRAM bytes per step of the step kernel from the committed ncu record."""
     tfile = os.path.join(ROOT, "profiles", "sem_step_kernel_traffic.json")
     try:
         with open(tfile) as fh:
             tj = json.load(fh)
         if (tj.get("workload") == WORKLOAD and tj.get("precision") == precision and tj.get("ordering") == ordering
+                and str(tj.get("kernel", "")).startswith(kernel + "<")
                 and tj.get("kernel_sha256") == kernel_source_digest()):
             return float(tj["dram_bytes_per_launch"]) / float(tj.get("steps_per_launch", 1))
     except (OSError, ValueError, KeyError, TypeError):
@@ -521,7 +522,8 @@ def main():
     # of the hot path times the node updates one launch makes
     algo = (ALGO_BYTES_HEUN if args.scheme == "heun" else ALGO_BYTES)[args.precision]
     achieved = algo * N * steps_per_launch / (launch_us * 1e-6) / 1e9
-    traffic_step = recorded_traffic(args.precision, args.ordering) if wname == WORKLOAD else None
+    kname = "sem_stream_kernel" if spl > 1 else "sem_step_kernel"
+    traffic_step = recorded_traffic(args.precision, args.ordering, kname) if wname == WORKLOAD else None
     traffic = None if traffic_step is None else traffic_step * steps_per_launch
     value = job_rate(world, N, K, el)
     line = {
@@ -535,7 +537,7 @@ def main():
                    "finite": finite},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "traffic_per_step": traffic_step,
-                     "kernel": "sem_stream_kernel" if spl > 1 else "sem_step_kernel", "peak_kind": peak_kind,
+                     "kernel": kname, "peak_kind": peak_kind,
                      "steps_per_launch": steps_per_launch, "launch_us": launch_us,
                      "step_kernel_us": blk_us, "open_kernel_us_per_run": 1e3 * oms / max(ol, 1),
                      "algorithmic_bytes_per_launch": algo * N * steps_per_launch,
