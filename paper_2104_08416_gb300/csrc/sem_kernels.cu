@@ -791,16 +791,15 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     // and packet are already on their way
     const DepWait w{&sa, b, sa.serial0 + (uint32_t)(i - 1), i > 0, &s_fail};
     step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend, w);
-    // every thread's stores of the unit precede the flag
+    // every thread's stores of the unit precede the flag: the barrier orders
+    // them before thread 0's release store (release at GPU scope covers what
+    // the barrier made it observe)
     __syncthreads();
     if (s_fail) {
         if (threadIdx.x == 0) atomicExch(sa.err, 1);
         return;
     }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
-    }
+    if (threadIdx.x == 0) st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
 }
 
 template <typename T, int MODE>
