@@ -996,7 +996,11 @@ sem_status sem_set_receivers(sem_mesh* m, const double* xy, int32_t nrec, int64_
     if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_receivers after the first step");
     ensure_node_xy(m);
     m->rec_nodes.assign((size_t)nrec, 0);
-    for (int32_t r = 0; r < nrec; ++r) m->rec_nodes[(size_t)r] = semhost::snap(m->node_xy, xy[2 * r], xy[2 * r + 1]);
+    {
+        std::vector<int64_t> got;
+        semhost::snap_many(m->node_xy, xy, xy + 1, nrec, 2, got);
+        for (int32_t r = 0; r < nrec; ++r) m->rec_nodes[(size_t)r] = got[(size_t)r];
+    }
     m->nrec = nrec;
     m->trace_cap = nrec > 0 ? max_steps : 0;
     return SEM_OK;

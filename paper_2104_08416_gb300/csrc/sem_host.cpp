@@ -14,6 +14,74 @@
 
 namespace semhost {
 
+namespace {
+// f(begin, end) over contiguous chunks of [0, n) on up to 16 host threads
+// (one thread when n is below `grain`); chunk t is [n t / T, n (t+1) / T).
+template <class F>
+void parallel_for(int64_t n, int64_t grain, F&& f) {
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int64_t T = std::max<int64_t>(1, std::min<int64_t>(hw, n / std::max<int64_t>(1, grain)));
+    if (T <= 1) {
+        f((int64_t)0, n, 0);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int64_t t = 1; t < T; ++t) pool.emplace_back([&, t]() { f(n * t / T, n * (t + 1) / T, (int)t); });
+    f((int64_t)0, n / T, 0);
+    for (auto& th : pool) th.join();
+}
+int parallel_chunks(int64_t n, int64_t grain) {
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(hw, n / std::max<int64_t>(1, grain)));
+}
+
+// Local edges (slot s = 4 e + le, from corner le to le+1) grouped by their
+// vertex pair without hashing: slots bucketed by the lower vertex in slot
+// order, then matched on the higher vertex inside each (small) bucket.
+// first[s] = the lowest slot holding the same edge; returns the largest
+// number of slots sharing one edge.
+int group_edges(const int32_t* quads, int64_t ne, int64_t nv, std::vector<int64_t>& first) {
+    const int64_t ns = ne * 4;
+    std::vector<int64_t> ptr((size_t)nv + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) {
+        const int32_t a = quads[s], b = quads[(s & ~int64_t(3)) + ((s + 1) & 3)];
+        ptr[(size_t)std::min(a, b) + 1]++;
+    }
+    for (size_t k = 1; k < ptr.size(); ++k) ptr[k] += ptr[k - 1];
+    std::vector<int64_t> bucket((size_t)ns);
+    {
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t s = 0; s < ns; ++s) {
+            const int32_t a = quads[s], b = quads[(s & ~int64_t(3)) + ((s + 1) & 3)];
+            bucket[(size_t)fill[(size_t)std::min(a, b)]++] = s;
+        }
+    }
+    first.assign((size_t)ns, -1);
+    std::vector<int> mult(parallel_chunks(nv, 1 << 15), 0);
+    parallel_for(nv, 1 << 15, [&](int64_t v0, int64_t v1, int t) {
+        int mx = 0;
+        for (int64_t v = v0; v < v1; ++v)
+            for (int64_t i = ptr[(size_t)v]; i < ptr[(size_t)v + 1]; ++i) {
+                const int64_t s = bucket[(size_t)i];
+                const int32_t hs = std::max(quads[s], quads[(s & ~int64_t(3)) + ((s + 1) & 3)]);
+                int64_t f = s;
+                int cnt = 0;
+                for (int64_t j = ptr[(size_t)v]; j < ptr[(size_t)v + 1]; ++j) {
+                    const int64_t r = bucket[(size_t)j];
+                    if (std::max(quads[r], quads[(r & ~int64_t(3)) + ((r + 1) & 3)]) == hs) {
+                        if (cnt == 0) f = r;  // the bucket is in slot order
+                        ++cnt;
+                    }
+                }
+                first[(size_t)s] = f;
+                mx = std::max(mx, cnt);
+            }
+        mult[(size_t)t] = mx;
+    });
+    return *std::max_element(mult.begin(), mult.end());
+}
+}  // namespace
+
 // ---------------------------------------------------------------- GLL rule
 static void legendre_eval(int p, double x, double& Pp, double& Pm1) {
     double a = 1.0, b = x;  // P_0, P_1
@@ -104,37 +172,41 @@ std::string validate(const double* coords, int64_t nv, const int32_t* quads, int
         if (!used[(size_t)v]) return "unreferenced vertex " + std::to_string(v);
     for (int64_t i = 0; i < nv * 2; ++i)
         if (!std::isfinite(coords[i])) return "non-finite coordinate";
-    std::unordered_map<uint64_t, int> ecount;
-    ecount.reserve((size_t)ne * 3);
     for (int64_t e = 0; e < ne; ++e) {
         const int32_t* q = quads + e * 4;
         for (int a = 0; a < 4; ++a)
             for (int b = a + 1; b < 4; ++b)
                 if (q[a] == q[b]) return "quad " + std::to_string(e) + " repeats a vertex";
-        for (int le = 0; le < 4; ++le) {
-            uint64_t lo = (uint64_t)std::min(q[le], q[(le + 1) & 3]);
-            uint64_t hi = (uint64_t)std::max(q[le], q[(le + 1) & 3]);
-            if (++ecount[lo * (uint64_t)nv + hi] > 2) return "edge shared by more than two quads";
-        }
+    }
+    {
+        std::vector<int64_t> first;
+        if (group_edges(quads, ne, nv, first) > 2) return "edge shared by more than two quads";
     }
     std::vector<double> x, w;
     gll_rule(p, x, w);
-    for (int64_t e = 0; e < ne; ++e) {
-        double X[8];
-        for (int c = 0; c < 4; ++c) {
-            X[c * 2 + 0] = coords[(size_t)quads[e * 4 + c] * 2 + 0];
-            X[c * 2 + 1] = coords[(size_t)quads[e * 4 + c] * 2 + 1];
-        }
-        for (int j = 0; j <= p; ++j)
-            for (int i = 0; i <= p; ++i) {
-                double J[4];
-                jac_at(X, x[i], x[j], J);
-                double det = J[0] * J[3] - J[1] * J[2];
-                if (!(det > 0.0))
-                    return "non-positive Jacobian in quad " + std::to_string(e) +
-                           " (clockwise or degenerate)";
+    // the first element (lowest id) with a non-positive Jacobian
+    std::vector<int64_t> bad(parallel_chunks(ne, 1 << 14), ne);
+    parallel_for(ne, 1 << 14, [&](int64_t e0, int64_t e1, int t) {
+        for (int64_t e = e0; e < e1; ++e) {
+            double X[8];
+            for (int c = 0; c < 4; ++c) {
+                X[c * 2 + 0] = coords[(size_t)quads[e * 4 + c] * 2 + 0];
+                X[c * 2 + 1] = coords[(size_t)quads[e * 4 + c] * 2 + 1];
             }
-    }
+            for (int j = 0; j <= p; ++j)
+                for (int i = 0; i <= p; ++i) {
+                    double J[4];
+                    jac_at(X, x[i], x[j], J);
+                    const double det = J[0] * J[3] - J[1] * J[2];
+                    if (!(det > 0.0)) {
+                        bad[(size_t)t] = e;
+                        return;
+                    }
+                }
+        }
+    });
+    const int64_t e_bad = *std::min_element(bad.begin(), bad.end());
+    if (e_bad < ne) return "non-positive Jacobian in quad " + std::to_string(e_bad) + " (clockwise or degenerate)";
     return "";
 }
 
@@ -147,34 +219,29 @@ void number_nodes(Mesh& m) {
     m.edge_lo.clear();
     m.edge_hi.clear();
     m.edge_first.clear();
-    std::unordered_map<uint64_t, int64_t> edge_id;
-    edge_id.reserve((size_t)m.ne * 3);
     const int corner[4] = {0, p, p * n + p, p * n};
     int64_t next = m.nv;
-    // pass 1: edges in order of first appearance
+    // pass 1: edges in order of first appearance (slot order)
     std::vector<int64_t> eid((size_t)m.ne * 4);
-    for (int64_t e = 0; e < m.ne; ++e) {
-        const int32_t* q = &m.quads[(size_t)e * 4];
-        for (int le = 0; le < 4; ++le) {
-            int64_t va = q[le], vb = q[(le + 1) & 3];
-            int64_t lo = std::min(va, vb), hi = std::max(va, vb);
-            uint64_t key = (uint64_t)lo * (uint64_t)m.nv + (uint64_t)hi;
-            auto it = edge_id.find(key);
-            int64_t id;
-            if (it == edge_id.end()) {
-                id = (int64_t)m.edge_lo.size();
-                edge_id.emplace(key, id);
-                m.edge_lo.push_back(lo);
-                m.edge_hi.push_back(hi);
+    {
+        std::vector<int64_t> first;
+        group_edges(m.quads.data(), m.ne, m.nv, first);
+        for (int64_t s = 0; s < m.ne * 4; ++s) {
+            if (first[(size_t)s] == s) {
+                const int64_t va = m.quads[(size_t)s], vb = m.quads[(size_t)((s & ~int64_t(3)) + ((s + 1) & 3))];
+                eid[(size_t)s] = (int64_t)m.edge_lo.size();
+                m.edge_lo.push_back(std::min(va, vb));
+                m.edge_hi.push_back(std::max(va, vb));
                 m.edge_first.push_back(next);
                 next += p - 1;
             } else {
-                id = it->second;
+                eid[(size_t)s] = eid[(size_t)first[(size_t)s]];
             }
-            eid[(size_t)e * 4 + le] = id;
         }
     }
-    for (int64_t e = 0; e < m.ne; ++e) {
+    const int64_t interior0 = next;
+    parallel_for(m.ne, 1 << 14, [&](int64_t e0, int64_t e1, int) {
+    for (int64_t e = e0; e < e1; ++e) {
         const int32_t* q = &m.quads[(size_t)e * 4];
         int32_t* c = &m.conn[(size_t)e * P];
         for (int k = 0; k < 4; ++k) c[corner[k]] = q[k];
@@ -192,13 +259,13 @@ void number_nodes(Mesh& m) {
                 c[li] = (int32_t)(m.edge_first[(size_t)id] + (k - 1));
             }
         }
-    }
-    for (int64_t e = 0; e < m.ne; ++e) {
-        int32_t* c = &m.conn[(size_t)e * P];
+        // element-interior nodes: elements ascending, i fastest
+        const int64_t base = interior0 + e * (int64_t)(p - 1) * (p - 1);
         for (int j = 1; j < p; ++j)
-            for (int i = 1; i < p; ++i) c[j * n + i] = (int32_t)(next++);
+            for (int i = 1; i < p; ++i) c[j * n + i] = (int32_t)(base + (j - 1) * (p - 1) + (i - 1));
     }
-    m.nn = next;
+    });
+    m.nn = interior0 + m.ne * (int64_t)(p - 1) * (p - 1);
 }
 
 void node_coordinates(const Mesh& m, std::vector<double>& xy) {
@@ -207,17 +274,20 @@ void node_coordinates(const Mesh& m, std::vector<double>& xy) {
     const int p = m.p, n = p + 1;
     xy.assign((size_t)m.nn * 2, 0.0);
     for (size_t i = 0; i < (size_t)m.nv * 2; ++i) xy[i] = m.coords[i];
-    for (size_t ed = 0; ed < m.edge_lo.size(); ++ed) {
-        const double* A = &m.coords[(size_t)m.edge_lo[ed] * 2];
-        const double* B = &m.coords[(size_t)m.edge_hi[ed] * 2];
+    parallel_for((int64_t)m.edge_lo.size(), 1 << 15, [&](int64_t d0, int64_t d1, int) {
+    for (int64_t ed = d0; ed < d1; ++ed) {
+        const double* A = &m.coords[(size_t)m.edge_lo[(size_t)ed] * 2];
+        const double* B = &m.coords[(size_t)m.edge_hi[(size_t)ed] * 2];
         for (int k = 1; k < p; ++k) {
             double s = x[k];
-            int64_t id = m.edge_first[ed] + k - 1;
+            int64_t id = m.edge_first[(size_t)ed] + k - 1;
             xy[(size_t)id * 2 + 0] = 0.5 * ((1.0 - s) * A[0] + (1.0 + s) * B[0]);
             xy[(size_t)id * 2 + 1] = 0.5 * ((1.0 - s) * A[1] + (1.0 + s) * B[1]);
         }
     }
-    for (int64_t e = 0; e < m.ne; ++e) {
+    });
+    parallel_for(m.ne, 1 << 14, [&](int64_t e0, int64_t e1, int) {
+    for (int64_t e = e0; e < e1; ++e) {
         const int32_t* q = &m.quads[(size_t)e * 4];
         const int32_t* c = &m.conn[(size_t)e * m.P];
         for (int j = 1; j < p; ++j)
@@ -233,6 +303,7 @@ void node_coordinates(const Mesh& m, std::vector<double>& xy) {
                 }
             }
     }
+    });
 }
 
 // ------------------------------------------------ generalized Hilbert curve
@@ -366,7 +437,7 @@ void node_degrees(const Mesh& m, std::vector<int32_t>& deg) {
     // set, so one evaluation per edge and per vertex suffices.
     const int P = m.P, p = m.p;
     deg.assign((size_t)m.nn, P - 1);
-    // vertex -> elements, edge -> elements
+    // vertex -> elements
     std::vector<int64_t> vptr((size_t)m.nv + 1, 0);
     for (int64_t i = 0; i < m.ne * 4; ++i) vptr[(size_t)m.quads[(size_t)i] + 1]++;
     for (size_t k = 1; k < vptr.size(); ++k) vptr[k] += vptr[k - 1];
@@ -376,42 +447,44 @@ void node_degrees(const Mesh& m, std::vector<int32_t>& deg) {
         for (int64_t e = 0; e < m.ne; ++e)
             for (int c = 0; c < 4; ++c) vel[(size_t)fill[(size_t)m.quads[(size_t)e * 4 + c]]++] = e;
     }
-    std::vector<int64_t> stamp((size_t)m.nn, -1);
-    int64_t tag = 0;
-    auto count_union = [&](const int64_t* els, int k) {
-        ++tag;
-        int32_t c = 0;
+    // distinct nodes of a few elements, minus one
+    auto count_union = [&](const int64_t* els, int k, std::vector<int32_t>& buf) {
+        buf.clear();
         for (int t = 0; t < k; ++t) {
             const int32_t* cc = &m.conn[(size_t)els[t] * P];
-            for (int q = 0; q < P; ++q)
-                if (stamp[(size_t)cc[q]] != tag) {
-                    stamp[(size_t)cc[q]] = tag;
-                    ++c;
-                }
+            buf.insert(buf.end(), cc, cc + P);
         }
-        return c - 1;
+        std::sort(buf.begin(), buf.end());
+        return (int32_t)(std::unique(buf.begin(), buf.end()) - buf.begin()) - 1;
     };
-    for (int64_t v = 0; v < m.nv; ++v)
-        deg[(size_t)v] = count_union(&vel[(size_t)vptr[(size_t)v]], (int)(vptr[(size_t)v + 1] - vptr[(size_t)v]));
+    parallel_for(m.nv, 1 << 14, [&](int64_t v0, int64_t v1, int) {
+        std::vector<int32_t> buf;
+        for (int64_t v = v0; v < v1; ++v)
+            deg[(size_t)v] =
+                count_union(&vel[(size_t)vptr[(size_t)v]], (int)(vptr[(size_t)v + 1] - vptr[(size_t)v]), buf);
+    });
     if (p >= 2) {
         // elements of an edge = elements holding both of its vertices
-        for (size_t ed = 0; ed < m.edge_lo.size(); ++ed) {
-            int64_t a = m.edge_lo[ed], b = m.edge_hi[ed];
-            int64_t els[8];
-            int k = 0;
-            for (int64_t t = vptr[(size_t)a]; t < vptr[(size_t)a + 1]; ++t) {
-                int64_t e = vel[(size_t)t];
-                const int32_t* q = &m.quads[(size_t)e * 4];
-                for (int c = 0; c < 4; ++c) {
-                    if (q[c] == b && (q[(c + 1) & 3] == a || q[(c + 3) & 3] == a)) {
-                        if (k < 8) els[k++] = e;
-                        break;
+        parallel_for((int64_t)m.edge_lo.size(), 1 << 14, [&](int64_t d0, int64_t d1, int) {
+            std::vector<int32_t> buf;
+            for (int64_t ed = d0; ed < d1; ++ed) {
+                const int64_t a = m.edge_lo[(size_t)ed], b = m.edge_hi[(size_t)ed];
+                int64_t els[8];
+                int k = 0;
+                for (int64_t t = vptr[(size_t)a]; t < vptr[(size_t)a + 1]; ++t) {
+                    const int64_t e = vel[(size_t)t];
+                    const int32_t* q = &m.quads[(size_t)e * 4];
+                    for (int c = 0; c < 4; ++c) {
+                        if (q[c] == b && (q[(c + 1) & 3] == a || q[(c + 3) & 3] == a)) {
+                            if (k < 8) els[k++] = e;
+                            break;
+                        }
                     }
                 }
+                const int32_t d = count_union(els, k, buf);
+                for (int t = 1; t < p; ++t) deg[(size_t)(m.edge_first[(size_t)ed] + t - 1)] = d;
             }
-            int32_t d = count_union(els, k);
-            for (int t = 1; t < p; ++t) deg[(size_t)(m.edge_first[ed] + t - 1)] = d;
-        }
+        });
     }
 }
 
@@ -583,27 +656,58 @@ std::string orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_
 }
 
 int64_t snap(const std::vector<double>& xy, double x, double y) {
-    int64_t best = 0;
-    double bd = std::numeric_limits<double>::infinity();
+    std::vector<int64_t> out;
+    snap_many(xy, &x, &y, 1, 1, out);
+    return out[0];
+}
+
+void snap_many(const std::vector<double>& xy, const double* qx, const double* qy, int64_t nq, int64_t stride,
+               std::vector<int64_t>& out) {
+    // every thread scans a contiguous node range for all points (a range
+    // stays in cache across the points); the ranges' minima are combined in
+    // range order with the same strict comparison, so a tie keeps the lowest id
     const int64_t n = (int64_t)(xy.size() / 2);
-    for (int64_t i = 0; i < n; ++i) {
-        double dx = xy[(size_t)i * 2] - x, dy = xy[(size_t)i * 2 + 1] - y;
-        double d = dx * dx + dy * dy;
-        if (d < bd) {
-            bd = d;
-            best = i;
+    const int T = parallel_chunks(n, 1 << 16);
+    std::vector<double> bd((size_t)T * nq, std::numeric_limits<double>::infinity());
+    std::vector<int64_t> bi((size_t)T * nq, 0);
+    parallel_for(n, 1 << 16, [&](int64_t i0, int64_t i1, int t) {
+        double* d = &bd[(size_t)t * nq];
+        int64_t* b = &bi[(size_t)t * nq];
+        for (int64_t c0 = i0; c0 < i1; c0 += 4096) {
+            const int64_t c1 = std::min(i1, c0 + 4096);
+            for (int64_t k = 0; k < nq; ++k) {
+                const double x = qx[k * stride], y = qy[k * stride];
+                for (int64_t i = c0; i < c1; ++i) {
+                    const double dx = xy[(size_t)i * 2] - x, dy = xy[(size_t)i * 2 + 1] - y;
+                    const double dd = dx * dx + dy * dy;
+                    if (dd < d[k]) {
+                        d[k] = dd;
+                        b[k] = i;
+                    }
+                }
+            }
         }
+    });
+    out.assign((size_t)nq, 0);
+    for (int64_t k = 0; k < nq; ++k) {
+        double best = std::numeric_limits<double>::infinity();
+        for (int t = 0; t < T; ++t)
+            if (bd[(size_t)t * nq + k] < best) {
+                best = bd[(size_t)t * nq + k];
+                out[(size_t)k] = bi[(size_t)t * nq + k];
+            }
     }
-    return best;
 }
 
 double cfl_dt(const Mesh& m, const double* vel) {
     std::vector<double> x, w;
     gll_rule(m.p, x, w);
     const int n = m.p + 1;
+    std::vector<double> part(parallel_chunks(m.ne, 1 << 14), std::numeric_limits<double>::infinity());
+    parallel_for(m.ne, 1 << 14, [&](int64_t e0, int64_t e1, int th) {
     double best = std::numeric_limits<double>::infinity();
     std::vector<double> pts((size_t)n * n * 2);
-    for (int64_t e = 0; e < m.ne; ++e) {
+    for (int64_t e = e0; e < e1; ++e) {
         const int32_t* q = &m.quads[(size_t)e * 4];
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
@@ -631,7 +735,9 @@ double cfl_dt(const Mesh& m, const double* vel) {
             }
         best = std::min(best, dmin / vel[e]);
     }
-    return best;
+    part[(size_t)th] = best;
+    });
+    return *std::min_element(part.begin(), part.end());
 }
 
 // ------------------------------------------------------------ block plan
@@ -794,17 +900,21 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
         {
             const int W = (neb + 63) / 64;
             std::vector<uint64_t> adj((size_t)neb * W, 0);
-            std::vector<std::vector<int>> touch((size_t)nent);
-            for (int el = 0; el < neb; ++el)
-                for (int q = 0; q < P; ++q) {
-                    auto& lst = touch[(size_t)slot_ent[(size_t)(el * P + q)]];
-                    if (lst.empty() || lst.back() != el) lst.push_back(el);
-                }
-            for (const auto& lst : touch)
-                for (size_t x = 0; x < lst.size(); ++x)
-                    for (size_t y = x + 1; y < lst.size(); ++y) {
-                        adj[(size_t)lst[x] * W + lst[y] / 64] |= 1ull << (lst[y] % 64);
-                        adj[(size_t)lst[y] * W + lst[x] / 64] |= 1ull << (lst[x] % 64);
+            // elements touching each entry (CSR, ascending element; an
+            // element's slots are distinct nodes, so no element repeats)
+            std::vector<int32_t> tptr((size_t)nent + 1, 0), tel((size_t)neb * P);
+            for (int t = 0; t < neb * P; ++t) tptr[(size_t)slot_ent[(size_t)t] + 1]++;
+            for (int64_t l = 0; l < nent; ++l) tptr[(size_t)l + 1] += tptr[(size_t)l];
+            {
+                std::vector<int32_t> fill(tptr.begin(), tptr.end() - 1);
+                for (int t = 0; t < neb * P; ++t) tel[(size_t)fill[(size_t)slot_ent[(size_t)t]]++] = t / P;
+            }
+            for (int64_t l = 0; l < nent; ++l)
+                for (int32_t x = tptr[(size_t)l]; x < tptr[(size_t)l + 1]; ++x)
+                    for (int32_t y = x + 1; y < tptr[(size_t)l + 1]; ++y) {
+                        const int ex = tel[(size_t)x], ey = tel[(size_t)y];
+                        adj[(size_t)ex * W + ey / 64] |= 1ull << (ey % 64);
+                        adj[(size_t)ey * W + ex / 64] |= 1ull << (ex % 64);
                     }
             std::vector<int> deg((size_t)neb, 0);
             for (int el = 0; el < neb; ++el)

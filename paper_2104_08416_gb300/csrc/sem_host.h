@@ -52,10 +52,13 @@ void random_order(int64_t n, uint64_t seed, std::vector<int64_t>& order);
 // 5 node distance (Section 6.1's strategies), 6 hilbert with the wide
 // bounding box of Section 4.3. Returns "" or why the ordering cannot be built.
 std::string orderings(const Mesh& m, int kind, uint64_t seed, std::vector<int64_t>& elem_order,
-               std::vector<int64_t>& node_order);
+                      std::vector<int64_t>& node_order);
 
 // Nearest global node (original id) to (x, y), ties to the lowest id.
 int64_t snap(const std::vector<double>& node_xy, double x, double y);
+// The same for nq points (qx[k * stride], qy[k * stride]) in one pass.
+void snap_many(const std::vector<double>& node_xy, const double* qx, const double* qy, int64_t nq, int64_t stride,
+               std::vector<int64_t>& out);
 
 // CFL step (see sem_cfl_dt in sem.h) for per-element speeds vel[ne].
 double cfl_dt(const Mesh& m, const double* vel);
