@@ -298,6 +298,16 @@ sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t
  * SEM_ERR_CUDA. Any time. */
 sem_status sem_set_stream(sem_mesh* m, int steps_per_launch);
 
+/* Test hook for the bounded waits of the streamed time loop: in the streamed
+ * launch that runs step `step`, the unit of element block `block` (in the
+ * plan's block order, 0 .. blocks-1) does its work but does not mark its
+ * block done, so the next step's units that share a node with that block wait
+ * until their wait limit (about a second), raise the error flag and stop the
+ * launch; the next read-back returns SEM_ERR_CUDA and clears the flag, and the
+ * wavefield is not meaningful until sem_set_state. Fires once; a negative
+ * step or block clears it. No effect on steps that run one launch each. */
+sem_status sem_stream_withhold(sem_mesh* m, int64_t step, int32_t block);
+
 /* Launch shape of the step kernel: elements per block (0 = default, about
  * 1600 element points per block; at most 256, one thread per element) and
  * threads per block (0 = one per element rounded up to whole warps; else a

@@ -39,7 +39,7 @@ EXPORTS = (
     "sem_set_receivers", "sem_cfl_dt", "sem_set_scheme", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
     "sem_read_wavefield", "sem_set_state", "sem_get_state", "sem_apply_stiffness", "sem_read_mass",
     "sem_get_permutation", "sem_get_sizes", "sem_node_coordinates", "sem_get_snapped",
-    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info", "sem_set_stream",
+    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info", "sem_set_stream", "sem_stream_withhold",
     "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
     "sem_apply_stiffness_dev_noalloc", "sem_misfit_gradient", "sem_batch_create", "sem_batch_step", "sem_batch_info",
@@ -99,6 +99,7 @@ def load(path: str | None = None):
                            C.c_int32, _I64, C.c_char_p, C.c_size_t),
         "sem_launch_info": (_P, _I64, _I64),
         "sem_set_stream": (_P, C.c_int),
+        "sem_stream_withhold": (_P, C.c_int64, C.c_int32),
         "sem_set_tuning": (_P, C.c_int, C.c_int),
         "sem_profile_enable": (_P, C.c_int),
         "sem_profile_read": (_P, _D, _I64, _D, _I64),
@@ -349,6 +350,9 @@ class SEM:
 
     def sem_set_stream(self, steps_per_launch: int):
         self._c(self._lib.sem_set_stream(self.h, int(steps_per_launch)))
+
+    def sem_stream_withhold(self, step: int, block: int):
+        self._c(self._lib.sem_stream_withhold(self.h, int(step), int(block)))
 
     def sem_profile_enable(self, enable: bool = True):
         self._c(self._lib.sem_profile_enable(self.h, 1 if enable else 0))

@@ -88,6 +88,8 @@ struct sem_mesh {
     unsigned long long* d_counter = nullptr;
     int32_t* d_err = nullptr;
     uint32_t serial = 1;              // serial of the next streamed step
+    int64_t hold_step = -1;           // test hook: (step, block) whose done flag is withheld
+    int32_t hold_block = -1;
     semdev::Basis<double> basis64{};
     semdev::Basis<float> basis32{};
     double* d_coords = nullptr;
@@ -310,13 +312,24 @@ sem_status build_host(sem_mesh* m) {
     std::vector<int32_t> conn_new((size_t)(M.ne * P));
     std::vector<int32_t> quads_new((size_t)M.ne * 4);
     std::vector<double> rho_new((size_t)M.ne), vel_new((size_t)M.ne);
-    for (int64_t en = 0; en < M.ne; ++en) {
-        int64_t eo = m->elem_order[(size_t)en];
-        for (int q = 0; q < P; ++q)
-            conn_new[(size_t)(en * P + q)] = (int32_t)m->node_new[(size_t)M.conn[(size_t)(eo * P + q)]];
-        for (int c = 0; c < 4; ++c) quads_new[(size_t)en * 4 + c] = M.quads[(size_t)eo * 4 + c];
-        rho_new[(size_t)en] = m->rho[(size_t)eo];
-        vel_new[(size_t)en] = m->vel[(size_t)eo];
+    {
+        // independent per element: split over host threads
+        const int64_t T = std::max<int64_t>(
+            1, std::min<int64_t>(std::min(16u, std::max(1u, std::thread::hardware_concurrency())), M.ne / 16384));
+        auto part = [&](int64_t t) {
+            for (int64_t en = M.ne * t / T; en < M.ne * (t + 1) / T; ++en) {
+                const int64_t eo = m->elem_order[(size_t)en];
+                for (int q = 0; q < P; ++q)
+                    conn_new[(size_t)(en * P + q)] = (int32_t)m->node_new[(size_t)M.conn[(size_t)(eo * P + q)]];
+                for (int c = 0; c < 4; ++c) quads_new[(size_t)en * 4 + c] = M.quads[(size_t)eo * 4 + c];
+                rho_new[(size_t)en] = m->rho[(size_t)eo];
+                vel_new[(size_t)en] = m->vel[(size_t)eo];
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int64_t t = 1; t < T; ++t) pool.emplace_back(part, t);
+        part(0);
+        for (auto& th : pool) th.join();
     }
     // receivers: new node ids; a second receiver on the same node copies the
     // first one's trace on the host
@@ -640,6 +653,11 @@ sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
     sa.nsteps = (int32_t)n;
     sa.pending0 = pending ? 1 : 0;
     sa.serial0 = m->serial;
+    sa.hold_unit = -1;
+    if (m->hold_step >= m->step && m->hold_step < m->step + n) {
+        sa.hold_unit = (m->hold_step - m->step) * m->plan.nblocks + m->hold_block;
+        m->hold_step = -1;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (m->profiling) {
         e0 = take_event(m);
@@ -688,13 +706,18 @@ sem_status launch_steps(sem_mesh* m, int64_t nsteps) {
     return SEM_OK;
 }
 
-// A wait of a streamed launch that gave up leaves the error flag raised.
+// A wait of a streamed launch that gave up leaves the error flag raised; it
+// is reported once and cleared (the state is then the caller's to reset).
 sem_status check_stream_error(sem_mesh* m) {
     if (!m->d_err) return SEM_OK;
     int32_t h = 0;
     SEM_CUDA(cudaMemcpyAsync(&h, m->d_err, 4, cudaMemcpyDeviceToHost, m->stream));
     SEM_CUDA(cudaStreamSynchronize(m->stream));
-    if (h != 0) return fail(m, SEM_ERR_CUDA, "a streamed step gave up waiting for a neighbouring block");
+    if (h != 0) {
+        SEM_CUDA(cudaMemsetAsync(m->d_err, 0, 4, m->stream));
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+        return fail(m, SEM_ERR_CUDA, "a streamed step gave up waiting for a neighbouring block; steps were skipped");
+    }
     return SEM_OK;
 }
 
@@ -1049,6 +1072,18 @@ sem_status sem_set_stream(sem_mesh* m, int steps_per_launch) {
     if (steps_per_launch < -1 || steps_per_launch > 65536)
         return fail(m, SEM_ERR_INVALID_ARG, "steps_per_launch must be in -1..65536");
     m->stream_steps = steps_per_launch;
+    return SEM_OK;
+}
+
+sem_status sem_stream_withhold(sem_mesh* m, int64_t step, int32_t block) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (step < 0 || block < 0) {
+        m->hold_step = -1;
+        m->hold_block = -1;
+        return SEM_OK;
+    }
+    m->hold_step = step;
+    m->hold_block = block;
     return SEM_OK;
 }
 

@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
         if (threadIdx.x == 0) atomicExch(sa.err, 1);
         return;
     }
-    if (threadIdx.x == 0) st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
+    if (threadIdx.x == 0 && u != sa.hold_unit) st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
 }
 
 template <typename T, int MODE>

@@ -137,6 +137,7 @@ struct StreamArgs {
     int32_t nsteps;               // steps in this launch
     int32_t pending0;             // open nodes pending before the first step
     uint32_t serial0;             // serial of the first step (done flags)
+    int64_t hold_unit;            // unit whose done flag is withheld (test hook), or -1
 };
 
 // Launchers; return cudaSuccess or the launch error.

@@ -110,3 +110,40 @@ def test_gather_plans_launch_per_step(order):
         assert spl == 1
     assert np.array_equal(u, u0)
     assert np.array_equal(tr, tr0)
+
+
+def test_withheld_done_flag_ends_in_an_error_not_a_hang():
+    """A unit that never marks its block done (the test hook withholds the
+    flag): the next step's units that wait on it give up after their bounded
+    wait, the launch stops, the next read-back reports SEM_ERR_CUDA, and both
+    the handle (after sem_set_state) and the GPU stay usable."""
+    import time
+
+    P = need_gpu()
+    m = gen.graded(40, seed=17)
+    h = _handle(P, m, 4, "fp32_kahan", "hilbert", 16, 256, 40)
+    assert h.sem_launch_info()[0] in (1, 256)
+    h.sem_step(1)   # builds the device data
+    u0 = h.sem_read_wavefield()
+    nblocks = -(-m["quads"].shape[0] // 16)
+    h.sem_stream_withhold(4, nblocks // 2)
+    t0 = time.perf_counter()
+    h.sem_step(12)
+    with pytest.raises(P.SemError) as ei:
+        h.sem_read_wavefield()
+    assert ei.value.status == 3   # SEM_ERR_CUDA
+    assert time.perf_counter() - t0 < 60.0
+    # the flag was cleared: a reset state steps normally, and bitwise like
+    # one launch per step from the same state
+    h.sem_set_state(u0, u0, 0)
+    h.sem_step(7)
+    u1 = h.sem_read_wavefield()
+    h.sem_destroy()
+    g = _handle(P, m, 4, "fp32_kahan", "hilbert", 16, 0, 40)
+    g.sem_step(1)
+    g.sem_set_state(u0, u0, 0)
+    g.sem_step(7)
+    u2 = g.sem_read_wavefield()
+    g.sem_destroy()
+    assert np.isfinite(u1).all()
+    assert np.array_equal(u1, u2)
