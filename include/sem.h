@@ -295,7 +295,7 @@ sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t
  * Waits are bounded: a wait that gives up (which no correct run does) raises
  * a device error flag, the remaining steps of the run are skipped, and the
  * next sem_read_wavefield, sem_get_state or sem_read_traces returns
- * SEM_ERR_CUDA. Any time. */
+ * SEM_ERR_TIMEOUT. Any time. */
 sem_status sem_set_stream(sem_mesh* m, int steps_per_launch);
 
 /* Test hook for the bounded waits of the streamed time loop: in the streamed
@@ -303,7 +303,7 @@ sem_status sem_set_stream(sem_mesh* m, int steps_per_launch);
  * plan's block order, 0 .. blocks-1) does its work but does not mark its
  * block done, so the next step's units that share a node with that block wait
  * until their wait limit (about a second), raise the error flag and stop the
- * launch; the next read-back returns SEM_ERR_CUDA and clears the flag, and the
+ * launch; the next read-back returns SEM_ERR_TIMEOUT and clears the flag, and the
  * wavefield is not meaningful until sem_set_state. Fires once; a negative
  * step or block clears it. No effect on steps that run one launch each. */
 sem_status sem_stream_withhold(sem_mesh* m, int64_t step, int32_t block);

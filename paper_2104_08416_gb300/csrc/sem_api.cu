@@ -716,7 +716,7 @@ sem_status check_stream_error(sem_mesh* m) {
     if (h != 0) {
         SEM_CUDA(cudaMemsetAsync(m->d_err, 0, 4, m->stream));
         SEM_CUDA(cudaStreamSynchronize(m->stream));
-        return fail(m, SEM_ERR_CUDA, "a streamed step gave up waiting for a neighbouring block; steps were skipped");
+        return fail(m, SEM_ERR_TIMEOUT, "a streamed step gave up waiting for a neighbouring block; steps were skipped");
     }
     return SEM_OK;
 }

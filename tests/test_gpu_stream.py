@@ -115,7 +115,7 @@ def test_gather_plans_launch_per_step(order):
 def test_withheld_done_flag_ends_in_an_error_not_a_hang():
     """A unit that never marks its block done (the test hook withholds the
     flag): the next step's units that wait on it give up after their bounded
-    wait, the launch stops, the next read-back reports SEM_ERR_CUDA, and both
+    wait, the launch stops, the next read-back reports SEM_ERR_TIMEOUT, and both
     the handle (after sem_set_state) and the GPU stay usable."""
     import time
 
@@ -131,7 +131,7 @@ def test_withheld_done_flag_ends_in_an_error_not_a_hang():
     h.sem_step(12)
     with pytest.raises(P.SemError) as ei:
         h.sem_read_wavefield()
-    assert ei.value.status == 3   # SEM_ERR_CUDA
+    assert ei.value.status == 5   # SEM_ERR_TIMEOUT
     assert time.perf_counter() - t0 < 60.0
     # the flag was cleared: a reset state steps normally, and bitwise like
     # one launch per step from the same state
