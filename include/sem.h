@@ -339,10 +339,11 @@ sem_status sem_traffic_model(const sem_mesh* m, double* block_bytes, double* ope
 sem_status sem_transfer_bytes(const sem_mesh* m, int64_t* h2d, int64_t* d2h);
 
 /* Stiffness application that allocates nothing, for callers that cannot
- * call cudaMalloc themselves or let a library do it: code running while a
- * CUDA graph is being captured, a real-time loop that must not hit the
- * allocator, or a host process whose memory budget was fixed up front. The
- * paper has no counterpart; it is a deployment aid.
+ * call cudaMalloc themselves or let a library do it: a real-time loop that
+ * must not reach the allocator (cudaMalloc and cudaFree can synchronise the
+ * device and take unbounded time), or a host process that hands all device
+ * memory out from its own pool sized up front, where an extra allocation
+ * fails. The paper has no counterpart; it is a deployment aid.
  *   dev_u   [N] device array, input; dev_Ku [N] device array, output. Both hold
  *           the handle's storage type (double for SEM_FP64, float otherwise)
  *           indexed by the library's storage order of the nodes

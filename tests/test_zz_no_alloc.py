@@ -1,8 +1,9 @@
 """The allocation-free stiffness entry point (sem_apply_stiffness_dev_noalloc).
 
 Some callers cannot allocate device memory at the moment they need the
-operator: code inside a CUDA graph capture, a real-time loop that must never
-reach the allocator, or a process whose memory was fixed up front. This entry
+operator: a real-time loop that must never reach the allocator (an allocation
+can synchronise the device and take unbounded time), or a process that hands
+all device memory out from its own pool sized up front. This entry
 point keeps its scratch (the partial sums of nodes shared between element
 blocks) in a fixed-size device array inside the library, so a call allocates
 nothing. Checked here through the C ABI against sem_apply_stiffness, on two
