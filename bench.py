@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scheme", default="leapfrog", choices=["leapfrog", "heun"],
                     help="leapfrog (default) or the paper's first-order system with Heun steps")
+    ap.add_argument("--band", type=int, default=-1,
+                    help="steps per band of the streamed wavefront order (-1 = library default, 0 = step order)")
+    ap.add_argument("--window", type=int, default=0, help="levels per wavefront tile (0 = automatic)")
     ap.add_argument("--eb", type=int, default=0, help="elements per block (0 = library default)")
     ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--stream", type=int, default=-1,
@@ -172,12 +175,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_handle(P, m, precision, ordering, nsteps_cap, eb=0, threads=0, scheme="leapfrog", stream=-1):
+def make_handle(P, m, precision, ordering, nsteps_cap, eb=0, threads=0, scheme="leapfrog", stream=-1,
+                tiling=(-1, 0)):
     h = P.SEM(m["coords"], m["quads"], 4, precision)
     if scheme != "leapfrog":
         h.sem_set_scheme(scheme)
     if stream >= 0:
         h.sem_set_stream(stream)
+    h.sem_set_stream_tiling(*tiling)
     h.sem_reorder(ordering)
     h.sem_set_model(m["vel"], m["rho"])
     if eb or threads:
@@ -232,15 +237,18 @@ def kernel_source_digest():
     return hsh.hexdigest()
 
 
-def recorded_traffic(precision, ordering, kernel):
-    """DRAM bytes per step of the step kernel from the committed ncu record."""
+def recorded_traffic(precision, ordering, kernel, stream_order="step"):
+    """DRAM bytes per step of the step kernel from the committed ncu record
+    (same workload, precision, ordering, kernel sources and order of the
+    streamed units)."""
     tfile = os.path.join(ROOT, "profiles", "sem_step_kernel_traffic.json")
     try:
         with open(tfile) as fh:
             tj = json.load(fh)
         if (tj.get("workload") == WORKLOAD and tj.get("precision") == precision and tj.get("ordering") == ordering
                 and str(tj.get("kernel", "")).startswith(kernel + "<")
-                and tj.get("kernel_sha256") == kernel_source_digest()):
+                and tj.get("kernel_sha256") == kernel_source_digest()
+                and tj.get("stream_order", "step") == stream_order):
             return float(tj["dram_bytes_per_launch"]) / float(tj.get("steps_per_launch", 1))
     except (OSError, ValueError, KeyError, TypeError):
         pass
@@ -448,7 +456,8 @@ def main():
     m = workload(args, rank)
     wname = "layered_4096x1024_p4" if args.workload == "layered" else (WORKLOAD if args.n == 512 else f"graded_{args.n}x{args.n}_p4")
     cap = W + 2 * K + 8
-    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads, args.scheme, args.stream)
+    h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads, args.scheme, args.stream,
+                    (args.band, args.window))
     N = h.n_nodes
     # warm-up (the first call builds the device data)
     h.sem_step(W)
@@ -467,6 +476,7 @@ def main():
     h.sem_profile_enable(False)
     block_bytes, open_bytes = h.sem_traffic_model()
     spl, nopen = h.sem_launch_info()
+    band, window = h.sem_stream_order()
     time.sleep(0.2)
     clocks = ClockSampler.summarize(sampler.stop()) if sampler else None
     u = h.sem_read_wavefield()
@@ -477,7 +487,8 @@ def main():
     # traces and wavefield back to the host, all inside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb, args.threads, args.scheme, args.stream)
+    h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb, args.threads, args.scheme, args.stream,
+                    (args.band, args.window))
     h2.sem_step(K)
     tr = h2.sem_read_traces()
     u2 = h2.sem_read_wavefield()
@@ -493,7 +504,8 @@ def main():
         orderings = {}
         kk = min(K, 500)
         for kind in ("hilbert", "rowmajor", "random", "none", "connectivity", "distance", "hilbert_wide"):
-            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb, args.threads, args.scheme, args.stream)
+            hh = make_handle(P, m, args.precision, kind, W + 2 * kk + 8, args.eb, args.threads, args.scheme, args.stream,
+                    (args.band, args.window))
             hh.sem_step(W)
             t_ord = time_steps(torch, hh, kk)
             hh.sem_profile_enable(True)
@@ -530,7 +542,8 @@ def main():
     algo = (ALGO_BYTES_HEUN if args.scheme == "heun" else ALGO_BYTES)[args.precision]
     achieved = algo * N * steps_per_launch / (launch_us * 1e-6) / 1e9
     kname = "sem_stream_kernel" if spl > 1 else "sem_step_kernel"
-    traffic_step = recorded_traffic(args.precision, args.ordering, kname) if wname == WORKLOAD else None
+    sorder = {"band_steps": band, "window_levels": window} if band > 0 else "step"
+    traffic_step = recorded_traffic(args.precision, args.ordering, kname, sorder) if wname == WORKLOAD else None
     traffic = None if traffic_step is None else traffic_step * steps_per_launch
     value = job_rate(world, N, K, el)
     line = {
@@ -540,6 +553,7 @@ def main():
         "config": {"workload": wname, "nodes": N, "elements": m["quads"].shape[0], "order": 4,
                    "precision": args.precision, "ordering": args.ordering, "scheme": args.scheme,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "stream_order": sorder,
                    "l2": f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
                    "finite": finite},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

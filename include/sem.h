@@ -252,7 +252,9 @@ sem_status sem_compute_ordering(const double* coords, int64_t nv, const int32_t*
  * that sums are exact, and compares with the direct per-slot sum; also
  * checks that every distinct receiver node (rec_xy[nrec][2], snapped like
  * sem_set_receivers) is recorded by exactly one block; checks that no two
- * elements of one colour in a block share a node. info[7] (may be NULL):
+ * elements of one colour in a block share a node; checks that the streamed
+ * loop's wavefront order (sem_set_stream_tiling; bands of 16 steps, windows
+ * of 1, 4 and 16 levels) over the plan's block graph is topological. info[7] (may be NULL):
  * blocks, DENSE layout (1/0), open nodes, largest entry count, largest
  * packet bytes, partial-sum slots, most colours in a block. msg (may be
  * NULL) receives the first violation. Returns SEM_OK when consistent, SEM_ERR_STATE on a
@@ -297,6 +299,43 @@ sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t
  * next sem_read_wavefield, sem_get_state or sem_read_traces returns
  * SEM_ERR_TIMEOUT. Any time. */
 sem_status sem_set_stream(sem_mesh* m, int steps_per_launch);
+
+/* Order of the units of a streamed launch. Section 4.3 orders elements so
+ * that data reused together is close in memory and in time; here the same
+ * argument is carried across time steps. In step order (band_steps = 0) a
+ * block's next step comes a whole step's data later (more than the L2 on the
+ * workloads this library streams). In the wavefront order (band_steps = T >=
+ * 1) each band of T consecutive steps of a launch runs as tiles over the
+ * block graph (blocks adjacent when they share a node): blocks get levels,
+ * their breadth-first distance from a pseudo-peripheral block; unit (step j
+ * of the band, block b) belongs to tile floor((level(b) + j) / W), and units
+ * run by tile, then step, then level, then block id. Every unit's
+ * dependencies come earlier (a topological order, checked on the host before
+ * upload), and a block's next step follows about W levels' worth of units
+ * later, so its element data and node state are mostly still in L2. Steps of
+ * a launch beyond its last whole band run in step order. window_levels = W >=
+ * 1, or 0 for the automatic window (about as many blocks per step of a tile as
+ * step CTAs are resident on the GPU at once). band_steps = -1 selects the
+ * default, the step order: the wavefront order trades the L2 reuse for units
+ * that wait on neighbours issued shortly before them, which on the meshes
+ * measured cost more than it saved. The results are bitwise the same in every
+ * order. Any time; takes effect at the next streamed launch. */
+sem_status sem_set_stream_tiling(sem_mesh* m, int band_steps, int window_levels);
+
+/* Band length and window of the wavefront order last uploaded for the
+ * handle's streamed launches (0, 0 before any). Either pointer may be NULL. */
+sem_status sem_stream_order(const sem_mesh* m, int32_t* band_steps, int32_t* window_levels);
+
+/* Host-only construction of the wavefront order above for a block graph in
+ * CSR form (dep[dep_ptr[b] .. dep_ptr[b+1]): the blocks adjacent to block b,
+ * b itself included; the graph must be symmetric). sched[band_steps *
+ * nblocks] receives the units as (j << 24) | b in run order; levels[nblocks]
+ * (may be NULL) the breadth-first levels. SEM_ERR_INVALID_ARG for a malformed
+ * graph or out-of-range sizes (band_steps 1..255, window_levels >= 1,
+ * nblocks < 2^24); SEM_ERR_STATE if the built order fails the library's own
+ * topological check. No device is needed. */
+sem_status sem_stream_schedule(const int32_t* dep_ptr, const int32_t* dep, int32_t nblocks, int band_steps,
+                               int window_levels, uint32_t* sched, int32_t* levels);
 
 /* Test hook for the bounded waits of the streamed time loop: in the streamed
  * launch that runs step `step`, the unit of element block `block` (in the

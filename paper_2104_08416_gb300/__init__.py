@@ -39,7 +39,8 @@ EXPORTS = (
     "sem_set_receivers", "sem_cfl_dt", "sem_set_scheme", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
     "sem_read_wavefield", "sem_set_state", "sem_get_state", "sem_apply_stiffness", "sem_read_mass",
     "sem_get_permutation", "sem_get_sizes", "sem_node_coordinates", "sem_get_snapped",
-    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info", "sem_set_stream", "sem_stream_withhold",
+    "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info", "sem_set_stream", "sem_set_stream_tiling",
+    "sem_stream_order", "sem_stream_schedule", "sem_stream_withhold",
     "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
     "sem_apply_stiffness_dev_noalloc", "sem_misfit_gradient", "sem_batch_create", "sem_batch_step", "sem_batch_info",
@@ -99,6 +100,9 @@ def load(path: str | None = None):
                            C.c_int32, _I64, C.c_char_p, C.c_size_t),
         "sem_launch_info": (_P, _I64, _I64),
         "sem_set_stream": (_P, C.c_int),
+        "sem_set_stream_tiling": (_P, C.c_int, C.c_int),
+        "sem_stream_order": (_P, _I32, _I32),
+        "sem_stream_schedule": (_I32, _I32, C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_uint32), _I32),
         "sem_stream_withhold": (_P, C.c_int64, C.c_int32),
         "sem_set_tuning": (_P, C.c_int, C.c_int),
         "sem_profile_enable": (_P, C.c_int),
@@ -201,6 +205,20 @@ def sem_hilbert_cells(W: int, H: int) -> np.ndarray:
     out = np.zeros((W * H, 2), dtype=np.int32)
     _check(lib.sem_hilbert_cells(int(W), int(H), _ptr(out, C.c_int32)))
     return out
+
+
+def sem_stream_schedule(dep_ptr, dep, band_steps: int, window_levels: int):
+    """Host-only wavefront order of a block graph (see sem.h): returns
+    (sched uint32[band_steps * nblocks], levels int32[nblocks])."""
+    lib = load()
+    dp = np.ascontiguousarray(dep_ptr, dtype=np.int32)
+    dd = np.ascontiguousarray(dep, dtype=np.int32)
+    nb = dp.shape[0] - 1
+    sched = np.zeros(max(0, band_steps * nb), dtype=np.uint32)
+    lev = np.zeros(max(0, nb), dtype=np.int32)
+    _check(lib.sem_stream_schedule(_ptr(dp, C.c_int32), _ptr(dd, C.c_int32), nb, int(band_steps),
+                                   int(window_levels), _ptr(sched, C.c_uint32), _ptr(lev, C.c_int32)))
+    return sched, lev
 
 
 def sem_plan_check(coords, quads, order: int, kind, eb: int, fp64: bool = False, receivers=None,
@@ -350,6 +368,15 @@ class SEM:
 
     def sem_set_stream(self, steps_per_launch: int):
         self._c(self._lib.sem_set_stream(self.h, int(steps_per_launch)))
+
+    def sem_set_stream_tiling(self, band_steps: int, window_levels: int = 0):
+        self._c(self._lib.sem_set_stream_tiling(self.h, int(band_steps), int(window_levels)))
+
+    def sem_stream_order(self):
+        """(band_steps, window_levels) of the wavefront order last uploaded."""
+        t, w = C.c_int32(), C.c_int32()
+        self._c(self._lib.sem_stream_order(self.h, C.byref(t), C.byref(w)))
+        return t.value, w.value
 
     def sem_stream_withhold(self, step: int, block: int):
         self._c(self._lib.sem_stream_withhold(self.h, int(step), int(block)))

@@ -90,6 +90,16 @@ struct sem_mesh {
     uint32_t serial = 1;              // serial of the next streamed step
     int64_t hold_step = -1;           // test hook: (step, block) whose done flag is withheld
     int32_t hold_block = -1;
+    // wavefront order of the streamed units (sem_set_stream_tiling):
+    // band_req steps per band (-1: default, 0: step order), window_req
+    // levels per tile (0: automatic); d_sched holds one band's order, built
+    // for (sched_T, sched_W)
+    int band_req = -1;
+    int window_req = 0;
+    uint32_t* d_sched = nullptr;
+    size_t sched_cap = 0;
+    int sched_T = 0, sched_W = 0;
+    int auto_window = 0;              // window of window_req = 0 (resident CTAs per step of a tile)
     semdev::Basis<double> basis64{};
     semdev::Basis<float> basis32{};
     double* d_coords = nullptr;
@@ -638,11 +648,57 @@ bool streamed(const sem_mesh* m) {
 }
 int64_t stream_len(const sem_mesh* m) { return m->stream_steps > 0 ? m->stream_steps : kAutoStreamSteps; }
 
+// Band length and window of the wavefront order (0 steps: step order, the
+// default: on the graded and layered meshes the wavefront order ran slower,
+// its units waiting on neighbours issued shortly before them).
+constexpr int kDefaultBandSteps = 0;
+int band_steps_of(const sem_mesh* m) {
+    const int T = m->band_req < 0 ? kDefaultBandSteps : m->band_req;
+    return m->plan.nblocks >= ((int64_t)1 << semhost::kSchedShift) ? 0 : T;
+}
+
+// One band's wavefront order on the device for the current band length and
+// window (built on the host, checked, uploaded once per setting).
+sem_status ensure_schedule(sem_mesh* m, int T) {
+    const auto& pl = m->plan;
+    if (m->auto_window <= 0)
+        m->auto_window = semhost::auto_window(semhost::block_levels(pl.dep_ptr.data(), pl.dep.data(), pl.nblocks),
+                                              std::max(1, m->resident_ctas));
+    const int W = m->window_req > 0 ? m->window_req : m->auto_window;
+    if (m->d_sched && m->sched_T == T && m->sched_W == W) return SEM_OK;
+    std::vector<uint32_t> sched;
+    std::string why = semhost::stream_schedule(pl.dep_ptr.data(), pl.dep.data(), pl.nblocks, T, W, sched, nullptr);
+    if (why.empty()) why = semhost::check_stream_schedule(pl.dep_ptr.data(), pl.dep.data(), pl.nblocks, T, sched);
+    if (!why.empty()) return fail(m, SEM_ERR_STATE, "wavefront order: " + why);
+    if (!m->d_sched || m->sched_cap < sched.size()) {
+        void* p = nullptr;
+        sem_status st = zeros(m, &p, sched.size() * 4);
+        if (st != SEM_OK) return st;
+        m->d_sched = (uint32_t*)p;
+        m->sched_cap = sched.size();
+    }
+    SEM_CUDA(cudaMemcpyAsync(m->d_sched, sched.data(), sched.size() * 4, cudaMemcpyHostToDevice, m->stream));
+    m->h2d += (int64_t)(sched.size() * 4);
+    SEM_CUDA(cudaStreamSynchronize(m->stream));
+    m->sched_T = T;
+    m->sched_W = W;
+    return SEM_OK;
+}
+
 // Steps k = m->step .. m->step + n - 1 as one streamed launch (pending: the
 // open nodes of step m->step - 1 are not finished yet), recorded with events
-// when profiling.
+// when profiling. Whole bands of the launch run in the wavefront order, the
+// rest step after step.
 sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
+    const int T = band_steps_of(m);
     semdev::StreamArgs sa{};
+    if (T > 0 && n >= T) {
+        sem_status st = ensure_schedule(m, T);
+        if (st != SEM_OK) return st;
+        sa.sched = m->d_sched;
+        sa.band_steps = T;
+        sa.tiled_units = (n / T) * T * m->plan.nblocks;
+    }
     sa.counter = m->d_counter;
     sa.base = 0;
     sa.done = m->d_done;
@@ -1075,6 +1131,53 @@ sem_status sem_set_stream(sem_mesh* m, int steps_per_launch) {
     return SEM_OK;
 }
 
+sem_status sem_set_stream_tiling(sem_mesh* m, int band_steps, int window_levels) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (band_steps < -1 || band_steps > semhost::kSchedMaxSteps)
+        return fail(m, SEM_ERR_INVALID_ARG, "band_steps must be in -1..255");
+    if (window_levels < 0) return fail(m, SEM_ERR_INVALID_ARG, "window_levels must be >= 0");
+    m->band_req = band_steps;
+    m->window_req = window_levels;
+    return SEM_OK;
+}
+
+sem_status sem_stream_order(const sem_mesh* m, int32_t* band_steps, int32_t* window_levels) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (band_steps) *band_steps = m->sched_T;
+    if (window_levels) *window_levels = m->sched_W;
+    return SEM_OK;
+}
+
+sem_status sem_stream_schedule(const int32_t* dep_ptr, const int32_t* dep, int32_t nblocks, int band_steps,
+                               int window_levels, uint32_t* sched, int32_t* levels) {
+    if (!dep_ptr || !dep || !sched || nblocks < 1 || band_steps < 1 || window_levels < 1) return SEM_ERR_INVALID_ARG;
+    if (dep_ptr[0] != 0) return SEM_ERR_INVALID_ARG;
+    for (int32_t b = 0; b < nblocks; ++b) {
+        if (dep_ptr[b + 1] < dep_ptr[b]) return SEM_ERR_INVALID_ARG;
+        bool self = false;
+        for (int32_t t = dep_ptr[b]; t < dep_ptr[b + 1]; ++t) {
+            if (dep[t] < 0 || dep[t] >= nblocks) return SEM_ERR_INVALID_ARG;
+            self = self || dep[t] == b;
+        }
+        if (!self) return SEM_ERR_INVALID_ARG;
+    }
+    // the graph must be symmetric (sharing a node is)
+    for (int32_t b = 0; b < nblocks; ++b)
+        for (int32_t t = dep_ptr[b]; t < dep_ptr[b + 1]; ++t) {
+            const int32_t c = dep[t];
+            if (std::find(dep + dep_ptr[c], dep + dep_ptr[c + 1], b) == dep + dep_ptr[c + 1]) return SEM_ERR_INVALID_ARG;
+        }
+    std::vector<uint32_t> sc;
+    std::vector<int32_t> lev;
+    std::string why = semhost::stream_schedule(dep_ptr, dep, nblocks, band_steps, window_levels, sc, &lev);
+    if (!why.empty()) return SEM_ERR_INVALID_ARG;
+    why = semhost::check_stream_schedule(dep_ptr, dep, nblocks, band_steps, sc);
+    if (!why.empty()) return SEM_ERR_STATE;
+    std::memcpy(sched, sc.data(), sc.size() * 4);
+    if (levels) std::memcpy(levels, lev.data(), lev.size() * 4);
+    return SEM_OK;
+}
+
 sem_status sem_stream_withhold(sem_mesh* m, int64_t step, int32_t block) {
     if (!m) return SEM_ERR_INVALID_ARG;
     if (step < 0 || block < 0) {
@@ -1343,6 +1446,16 @@ sem_status sem_plan_check(const double* coords, int64_t nv, const int32_t* quads
     if (!why.empty()) {
         say(why);
         return SEM_ERR_STATE;
+    }
+    // the streamed loop's wavefront order over this plan's block graph
+    for (int W : {1, 4, 16}) {
+        std::vector<uint32_t> sched;
+        why = semhost::stream_schedule(pl.dep_ptr.data(), pl.dep.data(), pl.nblocks, 16, W, sched, nullptr);
+        if (why.empty()) why = semhost::check_stream_schedule(pl.dep_ptr.data(), pl.dep.data(), pl.nblocks, 16, sched);
+        if (!why.empty()) {
+            say("wavefront order: " + why);
+            return SEM_ERR_STATE;
+        }
     }
     // receivers: every distinct receiver node is recorded exactly once
     std::vector<int> seen((size_t)nrec, 0);

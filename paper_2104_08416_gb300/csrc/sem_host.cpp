@@ -1245,4 +1245,95 @@ std::string check_block_plan(const BlockPlan& pl, const std::vector<int32_t>& co
     return "";
 }
 
+
+std::vector<int32_t> block_levels(const int32_t* dep_ptr, const int32_t* dep, int64_t nb) {
+    std::vector<int32_t> lev((size_t)nb, -1), first((size_t)nb, -1), queue;
+    queue.reserve((size_t)nb);
+    // breadth-first sweep from root over one connected part; returns the
+    // block reached last at the largest distance (the lowest id among those)
+    auto sweep = [&](int32_t root, std::vector<int32_t>& L) {
+        queue.clear();
+        queue.push_back(root);
+        L[(size_t)root] = 0;
+        int32_t far = root;
+        for (size_t h = 0; h < queue.size(); ++h) {
+            const int32_t x = queue[h];
+            if (L[(size_t)x] > L[(size_t)far] || (L[(size_t)x] == L[(size_t)far] && x < far)) far = x;
+            for (int32_t t = dep_ptr[x]; t < dep_ptr[x + 1]; ++t) {
+                const int32_t y = dep[t];
+                if (L[(size_t)y] < 0) {
+                    L[(size_t)y] = L[(size_t)x] + 1;
+                    queue.push_back(y);
+                }
+            }
+        }
+        return far;
+    };
+    for (int64_t r = 0; r < nb; ++r)
+        if (lev[(size_t)r] < 0) sweep(sweep((int32_t)r, first), lev);
+    return lev;
+}
+
+int auto_window(const std::vector<int32_t>& levels, int64_t target_units) {
+    int32_t top = 0;
+    for (int32_t l : levels) top = std::max(top, l);
+    const double per_level = (double)levels.size() / (double)(top + 1);
+    const double w = std::floor((double)target_units / std::max(1.0, per_level) + 0.5);
+    return (int)std::max(1.0, std::min(w, (double)(top + 1)));
+}
+
+std::string stream_schedule(const int32_t* dep_ptr, const int32_t* dep, int64_t nb, int T, int W,
+                            std::vector<uint32_t>& sched, std::vector<int32_t>* levels_out) {
+    if (T < 1 || T > kSchedMaxSteps) return "band of steps outside 1.." + std::to_string(kSchedMaxSteps);
+    if (W < 1) return "window below one level";
+    if (nb < 1 || nb >= ((int64_t)1 << kSchedShift)) return "block count outside the schedule's range";
+    const std::vector<int32_t> lev = block_levels(dep_ptr, dep, nb);
+    int32_t top = 0;
+    for (int32_t l : lev) top = std::max(top, l);
+    // blocks grouped by level, ascending id within a level
+    std::vector<int64_t> lptr((size_t)top + 2, 0);
+    for (int32_t l : lev) ++lptr[(size_t)l + 1];
+    for (int32_t l = 0; l <= top; ++l) lptr[(size_t)l + 1] += lptr[(size_t)l];
+    std::vector<int32_t> by_level((size_t)nb);
+    {
+        std::vector<int64_t> fill(lptr.begin(), lptr.end() - 1);
+        for (int64_t b = 0; b < nb; ++b) by_level[(size_t)fill[(size_t)lev[(size_t)b]]++] = (int32_t)b;
+    }
+    sched.clear();
+    sched.reserve((size_t)(T * nb));
+    const int64_t tiles = (int64_t)(top + T - 1) / W + 1;
+    for (int64_t t = 0; t < tiles; ++t)
+        for (int j = 0; j < T; ++j) {
+            // levels l with floor((l + j) / W) == t
+            const int64_t lo = std::max<int64_t>(0, t * W - j), hi = std::min<int64_t>(top, (t + 1) * W - j - 1);
+            for (int64_t l = lo; l <= hi; ++l)
+                for (int64_t k = lptr[(size_t)l]; k < lptr[(size_t)l + 1]; ++k)
+                    sched.push_back(((uint32_t)j << kSchedShift) | (uint32_t)by_level[(size_t)k]);
+        }
+    if ((int64_t)sched.size() != T * nb) return "schedule does not cover the band";
+    if (levels_out) *levels_out = lev;
+    return "";
+}
+
+std::string check_stream_schedule(const int32_t* dep_ptr, const int32_t* dep, int64_t nb, int T,
+                                  const std::vector<uint32_t>& sched) {
+    if ((int64_t)sched.size() != T * nb) return "schedule length differs from steps x blocks";
+    std::vector<int64_t> pos((size_t)(T * nb), -1);
+    const uint32_t mask = (1u << kSchedShift) - 1u;
+    for (size_t k = 0; k < sched.size(); ++k) {
+        const int64_t j = sched[k] >> kSchedShift, b = sched[k] & mask;
+        if (j >= T || b >= nb) return "entry " + std::to_string(k) + " outside the band";
+        int64_t& p = pos[(size_t)(j * nb + b)];
+        if (p >= 0) return "unit (" + std::to_string(j) + ", " + std::to_string(b) + ") listed twice";
+        p = (int64_t)k;
+    }
+    for (int64_t j = 1; j < T; ++j)
+        for (int64_t b = 0; b < nb; ++b)
+            for (int32_t t = dep_ptr[b]; t < dep_ptr[b + 1]; ++t)
+                if (pos[(size_t)((j - 1) * nb + dep[t])] > pos[(size_t)(j * nb + b)])
+                    return "unit (" + std::to_string(j) + ", " + std::to_string(b) + ") precedes step " +
+                           std::to_string(j - 1) + " of block " + std::to_string(dep[t]);
+    return "";
+}
+
 }  // namespace semhost

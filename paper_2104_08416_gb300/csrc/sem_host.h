@@ -109,4 +109,34 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
 // violation.
 std::string check_block_plan(const BlockPlan& plan, const std::vector<int32_t>& conn, int vec);
 
+// Order of the streamed time loop's units over a band of T consecutive steps
+// (unit (j, b): step j of the band at element block b). It carries Section
+// 4.3's locality argument across time steps: instead of every block of step j
+// before any block of step j+1 (which puts a whole step's data, more than the
+// L2, between a block's two visits), units follow a wavefront over the block
+// graph (blocks adjacent when they share a node). Each block gets a level, its
+// breadth-first distance from a pseudo-peripheral block of its connected part
+// (the far end of a first sweep), so that adjacent blocks' levels differ by at
+// most one. Units are emitted by tile t = floor((level + j) / W), then step j,
+// then level, then block id. A unit's dependencies, step j-1 at the block and
+// at its neighbours, have level + j - 1 <= level + 1 + j - 1, hence a tile no
+// later and an earlier step: the order is topological, which the streamed
+// loop needs for its waits to end. A block's next step follows after about W
+// levels' worth of units. Entry = (j << kSchedShift) | b.
+constexpr int kSchedShift = 24;
+constexpr int kSchedMaxSteps = 255;
+// levels[nb] as above.
+std::vector<int32_t> block_levels(const int32_t* dep_ptr, const int32_t* dep, int64_t nb);
+// Window W (levels per tile) giving about target_units units per step of a
+// tile: target_units over the mean number of blocks per level, at least 1.
+int auto_window(const std::vector<int32_t>& levels, int64_t target_units);
+// sched[T * nb]; "" on success, else why no schedule can be built.
+std::string stream_schedule(const int32_t* dep_ptr, const int32_t* dep, int64_t nb, int T, int W,
+                            std::vector<uint32_t>& sched, std::vector<int32_t>* levels_out);
+// Checks that sched holds every unit of the band once and that every unit
+// comes after step j-1 of each block in its neighbour list (itself
+// included). "" when valid, else the first violation.
+std::string check_stream_schedule(const int32_t* dep_ptr, const int32_t* dep, int64_t nb, int T,
+                                  const std::vector<uint32_t>& sched);
+
 }  // namespace semhost

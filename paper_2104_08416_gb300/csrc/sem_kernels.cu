@@ -751,8 +751,10 @@ struct DepWait {
 };
 
 // Several steps of one mesh in one launch of nsteps * nblocks CTAs. Each
-// CTA, once running, takes the next unit u = i * nblocks + b (step i of the
-// launch, block b) from a work counter, so units start in increasing order
+// CTA, once running, takes the next ticket from a work counter and runs its
+// unit (step i of the launch, block b): i * nblocks + b in step order, or the
+// band's wavefront order (StreamArgs::sched, a topological order of the
+// dependencies below built on the host), so units start in ticket order
 // whatever order the hardware runs CTAs in. Unit (i, b) first waits until
 // step i-1 has finished at b and at every block sharing a node with b: those
 // are exactly the blocks whose partial sums, open-node states and closed-node
@@ -770,19 +772,33 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     sem_stream_kernel(const ShotDesc<T> d, const StreamArgs sa, const Basis<T> bs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ StepArgs<T> s_a;
-    __shared__ long long s_unit;
+    __shared__ int s_i, s_b;
     __shared__ int s_fail;
     const int nb = d.pl.nblocks;
     const long long total = (long long)sa.nsteps * nb;
     if (threadIdx.x == 0) {
-        s_unit = ld_relaxed_gpu(sa.err) != 0 ? total : (long long)(atomicAdd(sa.counter, 1ull) - sa.base);
+        const long long u = ld_relaxed_gpu(sa.err) != 0 ? total : (long long)(atomicAdd(sa.counter, 1ull) - sa.base);
+        int ui = -1, ub = 0;
+        if (u >= 0 && u < total) {
+            if (u < sa.tiled_units) {
+                const long long band_units = (long long)sa.band_steps * nb;
+                const long long band = u / band_units;
+                const uint32_t en = __ldg(sa.sched + (u - band * band_units));
+                ui = (int)(band * sa.band_steps) + (int)(en >> 24);
+                ub = (int)(en & 0xFFFFFFu);
+            } else {
+                ui = (int)(u / nb);
+                ub = (int)(u - (long long)ui * nb);
+            }
+        }
+        s_i = ui;
+        s_b = ub;
         s_fail = 0;
     }
     __syncthreads();
-    const long long u = s_unit;
-    if (u < 0 || u >= total) return;
-    const int i = (int)(u / nb);
-    const int b = (int)(u - (long long)i * nb);
+    const int i = s_i;
+    const int b = s_b;
+    if (i < 0) return;
     const int64_t k = sa.step0 + i;
     const int pend = (i > 0 || sa.pending0) ? 1 : 0;
     if (threadIdx.x == 0) s_a = shot_step_args<T, MODE>(d, k, pend);
@@ -799,7 +815,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
         if (threadIdx.x == 0) atomicExch(sa.err, 1);
         return;
     }
-    if (threadIdx.x == 0 && u != sa.hold_unit) st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
+    if (threadIdx.x == 0 && (long long)i * nb + b != sa.hold_unit) st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
 }
 
 template <typename T, int MODE>

@@ -137,7 +137,14 @@ struct StreamArgs {
     int32_t nsteps;               // steps in this launch
     int32_t pending0;             // open nodes pending before the first step
     uint32_t serial0;             // serial of the first step (done flags)
-    int64_t hold_unit;            // unit whose done flag is withheld (test hook), or -1
+    int64_t hold_unit;            // step * nblocks + block of the unit whose done flag is withheld (test hook), or -1
+    // wavefront order: the first tiled_units tickets (whole bands of
+    // band_steps steps) map through sched, one band's entries
+    // (step-in-band << 24 | block), band after band; later tickets, and all
+    // when sched is null, run step after step
+    const uint32_t* sched;
+    int32_t band_steps;
+    int64_t tiled_units;
 };
 
 // Launchers; return cudaSuccess or the launch error.

@@ -4,7 +4,8 @@ waiting for the previous step at its block's neighbours. Its arithmetic per
 unit is the per-step kernel's, so wavefields and traces must be bitwise those
 of one launch per step, on meshes with few and with many blocks, at launch
 lengths that split runs at every possible point, in the three leapfrog
-storage precisions, and across sem_step calls that switch between the two.
+storage precisions, across sem_step calls that switch between the two, and
+in every order of the units (step order, wavefront orders).
 """
 import numpy as np
 import pytest
@@ -112,7 +113,52 @@ def test_gather_plans_launch_per_step(order):
     assert np.array_equal(tr, tr0)
 
 
-def test_withheld_done_flag_ends_in_an_error_not_a_hang():
+WAVEFRONT = [(0, 0), (1, 1), (16, 1), (16, 3), (5, 0), (16, 100), (7, 2), (255, 2)]
+
+
+@pytest.mark.parametrize("prec", ["fp32_kahan", "fp64", "fp32"])
+@pytest.mark.parametrize("band,window", WAVEFRONT)
+def test_wavefront_orders_bitwise_per_step(prec, band, window):
+    """Every wavefront order of the streamed units (sem_set_stream_tiling)
+    gives bitwise the result of one launch per step, across launches split
+    into whole bands and a step-ordered remainder, and across sem_step calls."""
+    P = need_gpu()
+    m = gen.graded(64, seed=5)
+    calls = [100, 37, 3]
+    u0, tr0, _ = _run(P, m, 4, prec, "hilbert", 32, 0, calls)
+    h = _handle(P, m, 4, prec, "hilbert", 32, 48, sum(calls))
+    h.sem_set_stream_tiling(band, window)
+    for n in calls:
+        h.sem_step(n)
+    u, tr = h.sem_read_wavefield(), h.sem_read_traces()
+    got_band, got_window = h.sem_stream_order()
+    h.sem_destroy()
+    assert np.array_equal(u, u0), rel_l2(u, u0)
+    assert np.array_equal(tr, tr0), rel_l2(tr, tr0)
+    if 0 < band <= 48:          # a launch of 48 steps holds whole bands
+        assert got_band == band
+        assert got_window == window or (window == 0 and got_window >= 1)
+    else:
+        assert got_band == 0
+
+
+def test_wavefront_order_on_many_blocks():
+    """A mesh of many small blocks (long wavefronts): bitwise per step."""
+    P = need_gpu()
+    m = gen.graded(96, seed=8)
+    u0, tr0, _ = _run(P, m, 4, "fp32_kahan", "hilbert", 16, 0, [70])
+    for band, window in ((16, 0), (32, 2)):
+        h = _handle(P, m, 4, "fp32_kahan", "hilbert", 16, 256, 70)
+        h.sem_set_stream_tiling(band, window)
+        h.sem_step(70)
+        u, tr = h.sem_read_wavefield(), h.sem_read_traces()
+        h.sem_destroy()
+        assert np.array_equal(u, u0)
+        assert np.array_equal(tr, tr0)
+
+
+@pytest.mark.parametrize("tiling", [(-1, 0), (4, 1)])
+def test_withheld_done_flag_ends_in_an_error_not_a_hang(tiling):
     """A unit that never marks its block done (the test hook withholds the
     flag): the next step's units that wait on it give up after their bounded
     wait, the launch stops, the next read-back reports SEM_ERR_TIMEOUT, and both
@@ -122,6 +168,7 @@ def test_withheld_done_flag_ends_in_an_error_not_a_hang():
     P = need_gpu()
     m = gen.graded(40, seed=17)
     h = _handle(P, m, 4, "fp32_kahan", "hilbert", 16, 256, 40)
+    h.sem_set_stream_tiling(*tiling)
     assert h.sem_launch_info()[0] in (1, 256)
     h.sem_step(1)   # builds the device data
     u0 = h.sem_read_wavefield()
