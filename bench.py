@@ -49,6 +49,14 @@ ALGO_BYTES = {"fp32": 41.0, "fp32_kahan": 53.0, "fp64": 76.0}
 # per slot (2 values) read/written 7 times, connectivity twice, node values
 # (U, U~, dU, s) read/written 9 times
 ALGO_BYTES_HEUN = {"fp32": 136.0, "fp64": 272.0}
+# FP64: GB300's double-precision rate is far below its FP32 rate, so the FP64
+# leapfrog is bound by arithmetic. Flops per node-update at p = 4: per element
+# 8 (p+1)^3 + 6 (p+1)^2 = 1150 (two derivative contractions of 2 (p+1)^3 each
+# way, 6 per point for the metric), times 262,144 / 4,198,401 elements per node,
+# plus 5 for the node update (f - Ku, 2u - u_prev, one FMA). Peak: the nominal 1.25 TFLOP/s, i.e. 152 SMs x
+# 2.07 GHz x 4 FP64 flop per SM-clock.
+FLOPS_FP64_LEAPFROG = 1150.0 * 262144 / 4198401 + 5.0
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 
 
 def parse():
@@ -574,6 +582,13 @@ def main():
         "clocks": clocks,
         "orderings": orderings,
     }
+    if args.precision == "fp64" and args.scheme == "leapfrog" and args.n == 512 and args.workload == "graded":
+        # FP64 arithmetic bound: the roofline is the FP64 ALU rate
+        fl = FLOPS_FP64_LEAPFROG * N * steps_per_launch / (launch_us * 1e-6) / 1e12
+        line["roofline"].update({"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": fl / FP64_PEAK_TFLOPS, "peak_kind": "derived (nominal FP64 rate)",
+                                 "flops_per_node_update": FLOPS_FP64_LEAPFROG,
+                                 "hbm_frac": achieved / peak})
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
