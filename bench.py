@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--ordering", default="hilbert",
                     choices=["hilbert", "rowmajor", "random", "none", "connectivity", "distance", "hilbert_wide"])
     ap.add_argument("--n", type=int, default=512, help="quads per side of the graded mesh")
-    ap.add_argument("--workload", default="graded", choices=["graded", "layered", "batched", "adjoint"],
+    ap.add_argument("--workload", default="graded", choices=["graded", "layered", "homogeneous", "batched", "adjoint"],
                     help="graded 512x512 (default), the layered 4096x1024 model (67M nodes), or batched shots")
     ap.add_argument("--batch-shots", type=int, default=64)
     ap.add_argument("--batch-nmin", type=int, default=64)
@@ -112,7 +112,12 @@ def dist_setup(args):
 
 
 def workload(args, rank=0):
-    m = gen.layered(4096, 1024) if args.workload == "layered" else gen.graded(args.n)
+    if args.workload == "layered":
+        m = gen.layered(4096, 1024)
+    elif args.workload == "homogeneous":
+        m = gen.unit_square(args.n)
+    else:
+        m = gen.graded(args.n)
     # replicas: each rank shoots from its own source position
     if rank:
         g = gen.SplitMix64(gen.DEFAULT_SEED + 100 + rank)
@@ -462,7 +467,12 @@ def main():
 
     K, W = args.steps, args.warmup
     m = workload(args, rank)
-    wname = "layered_4096x1024_p4" if args.workload == "layered" else (WORKLOAD if args.n == 512 else f"graded_{args.n}x{args.n}_p4")
+    if args.workload == "layered":
+        wname = "layered_4096x1024_p4"
+    elif args.workload == "homogeneous":
+        wname = f"homogeneous_{args.n}x{args.n}_p4"
+    else:
+        wname = WORKLOAD if args.n == 512 else f"graded_{args.n}x{args.n}_p4"
     cap = W + 2 * K + 8
     h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads, args.scheme, args.stream,
                     (args.band, args.window))
@@ -562,7 +572,9 @@ def main():
                    "precision": args.precision, "ordering": args.ordering, "scheme": args.scheme,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "stream_order": sorder,
-                   "l2": f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
+                   "l2": (f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush"
+                          if block_bytes > L2_BYTES else
+                          f"per-step working set {block_bytes / 1e6:.1f} MB fits in L2, no flush (small workload)"),
                    "finite": finite},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "traffic_per_step": traffic_step,
