@@ -62,6 +62,7 @@ struct sem_mesh {
     bool have_dt = false;
     double dt = 0;
     int eb_request = 0;
+    int sm_count = 0;           // SMs of the handle's device (0: unknown), for the default block size
     int scheme = 0;             // SEM_SCHEME_LEAPFROG or SEM_SCHEME_HEUN
     int threads_request = 0;
 
@@ -273,6 +274,19 @@ sem_status fill_source(sem_mesh* m, int64_t upto) {
     return SEM_OK;
 }
 
+// Smallest default block of a small mesh (elements).
+constexpr int kMinSmallMeshEb = 4;
+
+// SMs of the current device, or 0 when it cannot be queried.
+int device_sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;
+}
+
 int default_eb(int np) {
     // about 6400 element points per block, at most 256 elements (threads)
     const int P = np * np;
@@ -355,6 +369,10 @@ sem_status build_host(sem_mesh* m) {
         if (m->rec_row[(size_t)r] < 0) rec_gid[(size_t)r] = g;
     }
     int eb = m->eb_request > 0 ? m->eb_request : default_eb(M.np);
+    // small meshes (default size only): at least one block per SM, so that a
+    // step spreads over the whole GPU instead of a few SMs
+    if (m->eb_request <= 0 && m->sm_count > 0 && M.ne < (int64_t)eb * m->sm_count)
+        eb = (int)std::max<int64_t>(kMinSmallMeshEb, (M.ne + m->sm_count - 1) / m->sm_count);
     if ((int64_t)eb * P > 65535) eb = 65535 / P;
     if (eb > 256) eb = 256;
     // the default block size shrinks until the step kernel's shared memory
@@ -389,6 +407,7 @@ sem_status build_host(sem_mesh* m) {
 
 sem_status build(sem_mesh* m) {
     if (m->built) return SEM_OK;
+    if (!m->host_ready && m->sm_count == 0) m->sm_count = device_sm_count();
     sem_status st = build_host(m);
     if (st != SEM_OK) return st;
     const auto& M = m->mesh;
