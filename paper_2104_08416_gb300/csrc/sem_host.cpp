@@ -751,19 +751,21 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
     pl.P = P;
     pl.ne = ne;
     pl.nn = nn;
+    if (eb < 1 || (int64_t)eb * P > 65535) return "elements per block outside 1 .. 65535 / points per element";
     pl.nblocks = (ne + eb - 1) / eb;
     const int64_t nb = pl.nblocks;
-    if (eb < 1 || (int64_t)eb * P > 65535) return "elements per block x points per element above 65535";
     // blocks touching each node (blocks are visited in ascending order)
     std::vector<int32_t> nblk((size_t)nn, 0);
     {
-        std::vector<int64_t> last((size_t)nn, -1);
-        for (int64_t s = 0; s < ne * P; ++s) {
-            const int32_t g = conn[(size_t)s];
-            const int64_t b = s / P / eb;
-            if (last[(size_t)g] != b) {
-                last[(size_t)g] = b;
-                nblk[(size_t)g]++;
+        std::vector<int32_t> last((size_t)nn, -1);
+        for (int64_t b = 0; b < nb; ++b) {
+            const int64_t s1 = std::min(ne, (b + 1) * eb) * P;
+            for (int64_t s = b * eb * P; s < s1; ++s) {
+                const int32_t g = conn[(size_t)s];
+                if (last[(size_t)g] != (int32_t)b) {
+                    last[(size_t)g] = (int32_t)b;
+                    nblk[(size_t)g]++;
+                }
             }
         }
     }
@@ -791,6 +793,13 @@ std::string build_block_plan(const std::vector<int32_t>& conn, int64_t ne, int P
     pl.dense = dense;
     // partial-sum slots: a contiguous run per open node, ascending node id
     std::vector<int64_t> base((size_t)nn, -1);
+    {
+        int64_t nopen = 0;
+        for (int64_t g = 0; g < nn; ++g) nopen += nblk[(size_t)g] > 1;
+        pl.open_gid.reserve((size_t)nopen);
+        pl.open_base.reserve((size_t)nopen);
+        pl.open_cnt.reserve((size_t)nopen);
+    }
     for (int64_t g = 0; g < nn; ++g) {
         if (nblk[(size_t)g] > MAX_BLOCKS_PER_NODE) return "a node is touched by more than 255 element blocks";
         if (nblk[(size_t)g] > 1) {
