@@ -506,8 +506,14 @@ void renumber_nodes(const Mesh& m, const std::vector<int64_t>& elem_order, const
                 seen[(size_t)c[q]] = 1;
                 group.push_back(c[q]);
             }
-        std::stable_sort(group.begin(), group.end(),
-                         [&](int64_t a, int64_t b) { return deg[(size_t)a] < deg[(size_t)b]; });
+        // stable insertion sort by degree (at most P nodes; no allocation)
+        for (size_t i = 1; i < group.size(); ++i) {
+            const int64_t x = group[i];
+            const int32_t dx = deg[(size_t)x];
+            size_t j = i;
+            for (; j > 0 && deg[(size_t)group[j - 1]] > dx; --j) group[j] = group[j - 1];
+            group[j] = x;
+        }
         node_order.insert(node_order.end(), group.begin(), group.end());
     }
 }
