@@ -289,7 +289,7 @@ struct NoWait {
 template <int NP, typename T, int MODE, typename Ready = NoWait>
 __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a, const Basis<T>& bs, const int b,
                                            unsigned char* smem_raw, const int64_t step, const int pend,
-                                           const Ready& ready = Ready()) {
+                                           const Ready& ready = Ready(), const BlockHdr* hpre = nullptr) {
     constexpr int P = NP * NP;
     constexpr int UPH = (P + 1) / 2;
     constexpr bool HEUN = MODE == MODE_HEUN_P || MODE == MODE_HEUN_C;
@@ -309,7 +309,7 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     T* acc = sc + (KAHAN && !direct ? pl.slen_pad : 0);               // assembled K u at the positions
 
     const int tid = threadIdx.x, nt = blockDim.x;
-    const BlockHdr h = load_hdr(pl.hdr, b);
+    const BlockHdr h = hpre ? *hpre : load_hdr(pl.hdr, b);
     const int64_t e0 = (int64_t)b * pl.eb;
     const int neb = (int)min((int64_t)pl.eb, pl.ne - e0);
     const Offsets L = offsets(h.sulen, h.ulen, h.nopen, h.ncolors, h.nrc + h.nro);
@@ -728,14 +728,13 @@ constexpr int kWaitPolls = 1 << 21;
 // synchronises; a poll that gives up marks the unit failed.
 struct DepWait {
     const StreamArgs* sa;
-    int b;
+    int d0, d1;        // the block's neighbour list: sa->dep[d0 .. d1)
     uint32_t need;
     bool active;
     int* fail;
     __device__ __forceinline__ bool operator()() const {
         if (!active) return true;
-        const int d1 = sa->dep_ptr[b + 1];
-        for (int t = sa->dep_ptr[b] + (int)threadIdx.x; t < d1; t += (int)blockDim.x) {
+        for (int t = d0 + (int)threadIdx.x; t < d1; t += (int)blockDim.x) {
             const uint32_t* f = sa->done + sa->dep[t];
             for (int n = 0; (int32_t)(ld_acquire_gpu(f) - need) < 0; ++n) {
                 if (n >= kWaitPolls || ((n & 63) == 63 && ld_relaxed_gpu(sa->err) != 0)) {
@@ -772,12 +771,16 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     sem_stream_kernel(const ShotDesc<T> d, const StreamArgs sa, const Basis<T> bs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ StepArgs<T> s_a;
-    __shared__ int s_i, s_b;
+    __shared__ BlockHdr s_h;
+    __shared__ int s_i, s_b, s_d0, s_d1;
     __shared__ int s_fail;
     const int nb = d.pl.nblocks;
     const long long total = (long long)sa.nsteps * nb;
     if (threadIdx.x == 0) {
-        const long long u = ld_relaxed_gpu(sa.err) != 0 ? total : (long long)(atomicAdd(sa.counter, 1ull) - sa.base);
+        // the ticket and the error flag are fetched together (one round trip)
+        const unsigned long long t = atomicAdd(sa.counter, 1ull);
+        const int raised = ld_relaxed_gpu(sa.err);
+        const long long u = raised != 0 ? total : (long long)(t - sa.base);
         int ui = -1, ub = 0;
         if (u >= 0 && u < total) {
             if (u < sa.tiled_units) {
@@ -794,6 +797,13 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
         s_i = ui;
         s_b = ub;
         s_fail = 0;
+        if (ui >= 0) {
+            // the unit's step arguments and block header, for every thread
+            s_a = shot_step_args<T, MODE>(d, sa.step0 + ui, (ui > 0 || sa.pending0) ? 1 : 0);
+            s_h = load_hdr(d.pl.hdr, ub);
+            s_d0 = sa.dep_ptr[ub];
+            s_d1 = sa.dep_ptr[ub + 1];
+        }
     }
     __syncthreads();
     const int i = s_i;
@@ -801,12 +811,10 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     if (i < 0) return;
     const int64_t k = sa.step0 + i;
     const int pend = (i > 0 || sa.pending0) ? 1 : 0;
-    if (threadIdx.x == 0) s_a = shot_step_args<T, MODE>(d, k, pend);
-    __syncthreads();
     // the neighbours' previous step, awaited while the block's element data
     // and packet are already on their way
-    const DepWait w{&sa, b, sa.serial0 + (uint32_t)(i - 1), i > 0, &s_fail};
-    step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend, w);
+    const DepWait w{&sa, s_d0, s_d1, sa.serial0 + (uint32_t)(i - 1), i > 0, &s_fail};
+    step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend, w, &s_h);
     // every thread's stores of the unit precede the flag: the barrier orders
     // them before thread 0's release store (release at GPU scope covers what
     // the barrier made it observe)
