@@ -289,7 +289,8 @@ sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t
  * launch boundary or partly filled last wave separates them. The arithmetic
  * per unit is the per-step kernel's: the results are bitwise those of N = 0
  * (one launch per step). Used for DENSE block plans (the node numbering of
- * Section 4.3 along the element order) and the leapfrog scheme; other cases
+ * Section 4.3 along the element order) and the leapfrog scheme where no block
+ * shares nodes with more than 64 blocks (itself included); other cases
  * launch once per step. N = -1 (the default) streams 256 steps per launch
  * where a step has fewer element blocks than 8 times the step CTAs resident
  * on the GPU at once (there the partly filled last wave of a launch per step

@@ -83,8 +83,8 @@ struct sem_mesh {
     int stream_steps = -1;            // -1: automatic (see streamed())
     bool stream_ok = false;
     int resident_ctas = 0;            // step CTAs resident on the GPU at once
-    int32_t* d_dep_ptr = nullptr;
-    int32_t* d_dep = nullptr;
+    int32_t* d_dep = nullptr;         // [nblocks][dep_stride] padded neighbour lists
+    int32_t dep_stride = 0;
     uint32_t* d_done = nullptr;
     unsigned long long* d_counter = nullptr;
     int32_t* d_err = nullptr;
@@ -524,9 +524,19 @@ sem_status build(sem_mesh* m) {
     // streamed time loop: leapfrog on a DENSE plan
     m->stream_ok = false;
     const int md = mode_of(m);
-    if (pl.dense && m->scheme == SEM_SCHEME_LEAPFROG && (md == semdev::MODE_KAHAN || md == semdev::MODE_THREE_LEVEL)) {
-        if ((st = upload(m, &m->d_dep_ptr, pl.dep_ptr.data(), pl.dep_ptr.size())) != SEM_OK) return st;
-        if ((st = upload(m, &m->d_dep, pl.dep.data(), pl.dep.size())) != SEM_OK) return st;
+    if (pl.dense && m->scheme == SEM_SCHEME_LEAPFROG && (md == semdev::MODE_KAHAN || md == semdev::MODE_THREE_LEVEL) &&
+        pl.max_deps <= semdev::kMaxStreamDeps) {
+        // neighbour lists padded with the block itself to a common multiple
+        // of 4 entries (one 16-byte row load per unit)
+        const int stride = (pl.max_deps + 3) / 4 * 4;
+        std::vector<int32_t> pad((size_t)pl.nblocks * (size_t)stride);
+        for (int64_t b = 0; b < pl.nblocks; ++b)
+            for (int t = 0; t < stride; ++t) {
+                const int32_t k = pl.dep_ptr[(size_t)b] + t;
+                pad[(size_t)b * stride + t] = k < pl.dep_ptr[(size_t)b + 1] ? pl.dep[(size_t)k] : (int32_t)b;
+            }
+        m->dep_stride = stride;
+        if ((st = upload(m, &m->d_dep, pad.data(), pad.size())) != SEM_OK) return st;
         void *done = nullptr, *ctr = nullptr, *er = nullptr;
         if ((st = zeros(m, &done, (size_t)pl.nblocks * 4)) != SEM_OK) return st;
         if ((st = zeros(m, &ctr, 8)) != SEM_OK) return st;
@@ -721,8 +731,8 @@ sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
     sa.counter = m->d_counter;
     sa.base = 0;
     sa.done = m->d_done;
-    sa.dep_ptr = m->d_dep_ptr;
     sa.dep = m->d_dep;
+    sa.dep_stride = m->dep_stride;
     sa.err = m->d_err;
     sa.step0 = m->step;
     sa.nsteps = (int32_t)n;

@@ -109,6 +109,10 @@ __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
 }
+// Moves the 128-byte line holding p into L2 (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -360,6 +364,16 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 if (!direct) stage_range(ss, a.s, abase, h.ulen, pl.nn, vok, tid, nt);
                 stage_range(sx, a.x_k, abase, h.ulen, pl.nn, vok, tid, nt);
                 if (KAHAN && !direct) stage_range(sc, a.c_k, abase, h.ulen, pl.nn, vok, tid, nt);
+                if (direct) {
+                    // s and the compensation, read in phase C chunk by chunk:
+                    // into L2 now, so that phase C's first loads do not wait
+                    // on DRAM (32 values per 128-byte line)
+                    const int nline = (h.slen * (int)sizeof(T) + 127) / 128;
+                    for (int l = tid; l < nline; l += nt) {
+                        prefetch_l2(a.s + abase + (int64_t)l * (128 / sizeof(T)));
+                        if (KAHAN) prefetch_l2(a.c_k + abase + (int64_t)l * (128 / sizeof(T)));
+                    }
+                }
             }
         }
         cp_async_commit();
@@ -728,14 +742,14 @@ constexpr int kWaitPolls = 1 << 21;
 // synchronises; a poll that gives up marks the unit failed.
 struct DepWait {
     const StreamArgs* sa;
-    int d0, d1;        // the block's neighbour list: sa->dep[d0 .. d1)
+    const int32_t* dep;   // the block's padded neighbour list (shared memory)
     uint32_t need;
     bool active;
     int* fail;
     __device__ __forceinline__ bool operator()() const {
         if (!active) return true;
-        for (int t = d0 + (int)threadIdx.x; t < d1; t += (int)blockDim.x) {
-            const uint32_t* f = sa->done + sa->dep[t];
+        for (int t = (int)threadIdx.x; t < sa->dep_stride; t += (int)blockDim.x) {
+            const uint32_t* f = sa->done + dep[t];
             for (int n = 0; (int32_t)(ld_acquire_gpu(f) - need) < 0; ++n) {
                 if (n >= kWaitPolls || ((n & 63) == 63 && ld_relaxed_gpu(sa->err) != 0)) {
                     *fail = 1;
@@ -772,7 +786,8 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ StepArgs<T> s_a;
     __shared__ BlockHdr s_h;
-    __shared__ int s_i, s_b, s_d0, s_d1;
+    __shared__ int s_i, s_b;
+    __shared__ __align__(16) int32_t s_dep[kMaxStreamDeps];
     __shared__ int s_fail;
     const int nb = d.pl.nblocks;
     const long long total = (long long)sa.nsteps * nb;
@@ -801,8 +816,8 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
             // the unit's step arguments and block header, for every thread
             s_a = shot_step_args<T, MODE>(d, sa.step0 + ui, (ui > 0 || sa.pending0) ? 1 : 0);
             s_h = load_hdr(d.pl.hdr, ub);
-            s_d0 = sa.dep_ptr[ub];
-            s_d1 = sa.dep_ptr[ub + 1];
+            const int4* dr = reinterpret_cast<const int4*>(sa.dep + (int64_t)ub * sa.dep_stride);
+            for (int q = 0; q < sa.dep_stride / 4; ++q) reinterpret_cast<int4*>(s_dep)[q] = dr[q];
         }
     }
     __syncthreads();
@@ -813,7 +828,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     const int pend = (i > 0 || sa.pending0) ? 1 : 0;
     // the neighbours' previous step, awaited while the block's element data
     // and packet are already on their way
-    const DepWait w{&sa, s_d0, s_d1, sa.serial0 + (uint32_t)(i - 1), i > 0, &s_fail};
+    const DepWait w{&sa, s_dep, sa.serial0 + (uint32_t)(i - 1), i > 0, &s_fail};
     step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend, w, &s_h);
     // every thread's stores of the unit precede the flag: the barrier orders
     // them before thread 0's release store (release at GPU scope covers what

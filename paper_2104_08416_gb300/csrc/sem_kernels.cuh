@@ -126,12 +126,18 @@ struct BatchArgs {
 
 // A streamed launch: several steps of one mesh (the shot's plan and level
 // buffers) in one launch; see sem_stream_kernel.
+// Largest padded neighbour list of a streamed block.
+constexpr int kMaxStreamDeps = 64;
+
 struct StreamArgs {
     unsigned long long* counter;  // work counter
     unsigned long long base;      // its value when this launch starts
     uint32_t* done;               // per block: serial of its last finished step
-    const int32_t* dep_ptr;       // [nblocks + 1]
-    const int32_t* dep;           // blocks sharing a node with the block, itself included
+    // [nblocks][dep_stride]: the blocks sharing a node with the block, itself
+    // included, padded with the block itself to dep_stride (a multiple of 4,
+    // at most kMaxStreamDeps) entries
+    const int32_t* dep;
+    int32_t dep_stride;
     int32_t* err;                 // raised when a wait gave up
     int64_t step0;                // step number of the launch's first step
     int32_t nsteps;               // steps in this launch
