@@ -115,8 +115,6 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-// Waits for every committed group but the most recent one.
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Read-only streamed loads (each element datum is read once per step).
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
@@ -351,11 +349,11 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     {
         const uint8_t* gpk = pl.packet + (int64_t)h.start * 16;
         for (int o = tid * 16; o < L.bytes; o += nt * 16) cp_async16(spk + o, gpk + o);
-        cp_async_commit();   // group: the packet
         float4* az = reinterpret_cast<float4*>(acc);
         const int nz = (h.sulen * (int)sizeof(T) + 15) / 16;
         for (int k = tid; k < nz; k += nt) az[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!ready()) {
+            cp_async_commit();
             cp_async_wait_all();
             return;
         }
@@ -378,14 +376,8 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 }
             }
         }
-        cp_async_commit();   // group: the owned range (DENSE)
-        // DENSE: only the packet is needed before the open entries below;
-        // the owned range keeps landing meanwhile
-        if (pl.dense) {
-            cp_async_wait_prior();
-        } else {
-            cp_async_wait_all();
-        }
+        cp_async_commit();
+        cp_async_wait_all();
         __syncthreads();
     }
     const uint32_t* cmask = reinterpret_cast<const uint32_t*>(spk + L.cmask);
@@ -411,20 +403,17 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             }
     }
     const bool pending = STATE && pend;
-    // DENSE: the open entries' values wait in acc (zero again below) while
-    // the owned-range copies, which also cover open positions, may still land
-    T* oval = pl.dense ? acc : su;
     for (int o = tid; o < h.nopen; o += nt) {
         const int pos = opos[o];
         const int64_t g = pos < h.ulen ? abase + pos : (int64_t)egid[pos - h.ulen];
         if (!pending) {
-            oval[pos] = __ldcg(a.u_k + g);
+            su[pos] = __ldcg(a.u_k + g);
         } else {
             const T ku = sum_partials(a.part_rd, obase[o], ocnt[o]);
             const T f = (g == a.src_gid) ? f_prev : T(0);
             const Update<T, MODE> up = update_node<T, MODE>(__ldcg(a.u_km1 + g), __ldcg(a.x_km1 + g),
                                                              KAHAN ? __ldcg(a.c_km1 + g) : T(0), __ldcg(a.s + g), f, ku);
-            oval[pos] = up.u;
+            su[pos] = up.u;
             if (orank[o] == 0) {
                 __stcg(a.u_kw + g, up.u);
                 if (KAHAN) {
@@ -438,14 +427,6 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    if (pl.dense && h.nopen > 0) {
-        for (int o = tid; o < h.nopen; o += nt) {
-            const int pos = opos[o];
-            su[pos] = acc[pos];
-            acc[pos] = T(0);
-        }
-        __syncthreads();
-    }
     if (pending && h.nro > 0) {
         for (int k = tid; k < h.nro; k += nt) {
             const int pos = recs[2 * (h.nrc + k)], r = recs[2 * (h.nrc + k) + 1];
