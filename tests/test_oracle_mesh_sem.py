@@ -282,3 +282,29 @@ def test_heun_standing_mode_second_order():
         U, _, _ = S.run_heun(nsteps, h, U0=u0)
         errs.append(np.abs(U - u0 * np.cos(np.pi * np.sqrt(2) * T)).max())
     assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+def test_leapfrog_discrete_dispersion_on_eigenmodes():
+    """On an eigenvector v of the generalized problem K v = lambda M v (found
+    here by a dense library eigensolver, not by the oracle), the unforced
+    leapfrog started from u^0 = v, u^-1 = cos(theta) v must give exactly
+    u^n = cos(n theta) v with cos(theta) = 1 - dt^2 lambda / 2: the
+    three-level recurrence's discrete dispersion relation. A dropped factor 2,
+    a sign or dt power, or M where M^-1 belongs breaks it."""
+    import scipy.linalg
+
+    m = _tiny_graded(4, seed=5)
+    S = sem.SEM(m["coords"], m["quads"], 3, m["vel"], 1.0)
+    n = S.n_nodes
+    K = np.stack([S.apply_K(e) for e in np.eye(n)], axis=1)
+    lam, V = scipy.linalg.eigh(0.5 * (K + K.T), np.diag(S.M))
+    dt = 0.3 * S.cfl_dt()
+    nsteps = 60
+    for k in (1, 7, n // 2, n - 1):
+        v = V[:, k] / np.linalg.norm(V[:, k])
+        c = 1.0 - 0.5 * dt * dt * lam[k]
+        assert -1.0 < c <= 1.0           # stable at 0.3 of the CFL step
+        theta = math.acos(c)
+        u, up, _ = S.run(nsteps, dt, u0=v, u_prev=c * v)
+        assert np.allclose(u, math.cos(nsteps * theta) * v, rtol=0, atol=1e-9), k
+        assert np.allclose(up, math.cos((nsteps - 1) * theta) * v, rtol=0, atol=1e-9), k
