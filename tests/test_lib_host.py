@@ -162,3 +162,17 @@ def test_block_plan_hilbert_has_fewer_open_nodes(lib):
     opened = {k: lib.sem_plan_check(m["coords"], m["quads"], 4, k, 64)[1]["open_nodes"]
               for k in ("hilbert", "rowmajor", "random")}
     assert opened["hilbert"] < opened["rowmajor"] < opened["random"], opened
+
+
+def test_block_plan_replay_at_bench_size(lib):
+    """The plan of the benchmark configuration itself (graded 512 x 512,
+    order 4, Hilbert, 256-element blocks, FP32 storage, its 16 receivers),
+    replayed on the host with every index bounds-checked, with the streamed
+    loop's wavefront orders checked topological; the open-node count matches
+    what the bench reports for this workload."""
+    m = gen.graded(512)
+    st, info, msg = lib.sem_plan_check(m["coords"], m["quads"], 4, "hilbert", 256, False, m["receivers"])
+    assert st == lib.SEM_OK, msg
+    assert info["nblocks"] == 1024 and info["dense"] == 1
+    assert info["open_nodes"] == 195565
+    assert info["max_colors"] <= 6
