@@ -176,3 +176,19 @@ def test_block_plan_replay_at_bench_size(lib):
     assert info["nblocks"] == 1024 and info["dense"] == 1
     assert info["open_nodes"] == 195565
     assert info["max_colors"] <= 6
+
+
+def test_stream_tiling_arguments(lib):
+    """sem_set_stream_tiling validates its arguments on the host and nothing
+    is uploaded before the first streamed launch."""
+    m = gen.unit_square(4)
+    h = lib.SEM(m["coords"], m["quads"], 2, "fp32_kahan", stream=0)
+    assert h.sem_stream_order() == (0, 0)
+    for band, window in ((-2, 0), (256, 0), (16, -1)):
+        with pytest.raises(lib.SemError) as ei:
+            h.sem_set_stream_tiling(band, window)
+        assert ei.value.status == lib.SEM_ERR_INVALID_ARG
+    for band, window in ((-1, 0), (0, 0), (1, 1), (255, 1000)):
+        h.sem_set_stream_tiling(band, window)
+    assert h.sem_stream_order() == (0, 0)
+    h.sem_destroy()
