@@ -369,9 +369,12 @@ sem_status build_host(sem_mesh* m) {
         if (m->rec_row[(size_t)r] < 0) rec_gid[(size_t)r] = g;
     }
     int eb = m->eb_request > 0 ? m->eb_request : default_eb(M.np);
-    // small meshes (default size only): at least one block per SM, so that a
-    // step spreads over the whole GPU instead of a few SMs
-    if (m->eb_request <= 0 && m->sm_count > 0 && M.ne < (int64_t)eb * m->sm_count)
+    // small FP64 meshes (default size only): at least one block per SM, so
+    // that a step's double-precision arithmetic, slow per SM on this GPU,
+    // spreads over all of them (FP32 small meshes keep the larger blocks:
+    // there a step is bound by one unit's chain of round trips, and fewer
+    // blocks share fewer nodes)
+    if (m->eb_request <= 0 && fp64(m) && m->sm_count > 0 && M.ne < (int64_t)eb * m->sm_count)
         eb = (int)std::max<int64_t>(kMinSmallMeshEb, (M.ne + m->sm_count - 1) / m->sm_count);
     if ((int64_t)eb * P > 65535) eb = 65535 / P;
     if (eb > 256) eb = 256;
