@@ -16,8 +16,12 @@ Test infrastructure only (see the package docstring).
 * ``generalized_cells(W, H)``: a Hilbert-like Hamiltonian path over any W x H
   grid. Section 3 cites Cerveny (2020) for curves over rectangles of arbitrary
   side lengths and states that they coincide with the standard curve when the
-  sides are powers of two; the paper gives no algorithm, so the recursion
-  below is this project's own statement of one (the library implements the
+  sides are powers of two; the paper gives no algorithm. The recursion below
+  follows the construction of Cerveny's generalized Hilbert ("gilbert")
+  curve: a long block (2w > 3h) is cut in two along its length, otherwise it
+  is cut into a transposed lower-left part, the full-width upper part and a
+  reversed lower-right part. The parity rules for the cut positions and the
+  top-level orientation are written out here (the library implements the
   same statement independently):
 
   path(O, A, B): cells O + i a + j b for 0 <= i < w = |A|, 0 <= j < h = |B|

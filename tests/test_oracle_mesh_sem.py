@@ -308,3 +308,72 @@ def test_leapfrog_discrete_dispersion_on_eigenmodes():
         u, up, _ = S.run(nsteps, dt, u0=v, u_prev=c * v)
         assert np.allclose(u, math.cos(nsteps * theta) * v, rtol=0, atol=1e-9), k
         assert np.allclose(up, math.cos((nsteps - 1) * theta) * v, rtol=0, atol=1e-9), k
+
+
+@pytest.mark.parametrize("n,p", [(3, 2), (4, 3), (5, 4)])
+def test_lambda_max_matches_dense_generalized_eigensolver(n, p):
+    """The power iteration behind the stability pin against the largest
+    eigenvalue of K v = lambda M v from a dense library eigensolver (K built
+    column by column from apply_K, M the lumped mass). An unconverged
+    iteration or a wrong symmetrisation (M instead of sqrt(M) on one side)
+    gives a different value."""
+    import scipy.linalg
+
+    m = _tiny_graded(n, seed=11)
+    S = sem.SEM(m["coords"], m["quads"], p, m["vel"], 1.0)
+    K = np.stack([S.apply_K(e) for e in np.eye(S.n_nodes)], axis=1)
+    lam = scipy.linalg.eigh(0.5 * (K + K.T), np.diag(S.M), eigvals_only=True)
+    assert abs(S.lambda_max() - lam[-1]) <= 1e-10 * lam[-1]
+    # the stability pin then holds with the exact eigenvalue as well
+    assert 0.3 * S.cfl_dt() < 2.0 / math.sqrt(lam[-1])
+
+
+@pytest.mark.parametrize("p,gap", [(2, 0.5), (3, (1 - math.sqrt(1 / 5)) / 2), (4, (1 - math.sqrt(3 / 7)) / 2)])
+def test_cfl_dt_single_element_closed_form(p, gap):
+    """dt_CFL of one axis-aligned w x h element with speed c is the smallest
+    gap between neighbouring GLL points on [-1, 1] (end pair: 1 - x_1) scaled
+    by the shorter side over 2, divided by c. The GLL points are 0, +-1 at
+    p = 2; +-sqrt(1/5), +-1 at p = 3; 0, +-sqrt(3/7), +-1 at p = 4, so the
+    shortest gap in units of the element side is 0.5, (1 - sqrt(1/5))/2,
+    (1 - sqrt(3/7))/2."""
+    for w, h, c in ((1.0, 1.0, 2.0), (2.0, 0.5, 1.5), (0.25, 3.0, 4.0)):
+        coords = np.array([[0.0, 0.0], [w, 0.0], [w, h], [0.0, h]])
+        quads = np.array([[0, 1, 2, 3]])
+        S = sem.SEM(coords, quads, p, c, 1.0)
+        want = gap * min(w, h) / c
+        assert abs(S.cfl_dt() - want) <= 1e-15 * want, (w, h, c, S.cfl_dt(), want)
+
+
+def test_mesh_validate_accepts_and_rejects():
+    """mesh.validate passes the generators' meshes and refuses each kind of
+    broken input with its own message."""
+    for m in (gen.unit_square(3), _tiny_graded(4), gen.relabel(_tiny_graded(4), seed=2)):
+        mesh.validate(m["coords"], m["quads"], 4)
+    m = gen.unit_square(2)
+    coords, quads = m["coords"], m["quads"].copy()
+    bad = quads.copy()
+    bad[0, 0] = coords.shape[0]
+    with pytest.raises(ValueError, match="out of range"):
+        mesh.validate(coords, bad, 2)
+    bad = quads.copy()
+    bad[0, 0] = -1
+    with pytest.raises(ValueError, match="out of range"):
+        mesh.validate(coords, bad, 2)
+    with pytest.raises(ValueError, match="unreferenced"):
+        mesh.validate(np.vstack([coords, [[5.0, 5.0]]]), quads, 2)
+    # clockwise corners: negative Jacobian everywhere
+    with pytest.raises(ValueError, match="Jacobian"):
+        mesh.validate(coords, quads[:, ::-1].copy(), 2)
+    # a bow-tie (two corners swapped): the Jacobian changes sign inside
+    bt = quads.copy()
+    bt[0, [1, 2]] = bt[0, [2, 1]]
+    with pytest.raises(ValueError):
+        mesh.validate(coords, bt, 2)
+    # a third element on an existing edge
+    c3 = np.vstack([coords, [[0.25, -0.5], [0.75, -0.5]]])
+    nv = coords.shape[0]
+    e0 = quads[0]
+    extra = np.array([[nv, nv + 1, e0[1], e0[0]]])      # below element 0, sharing its bottom edge
+    dup = np.array([[nv, nv + 1, e0[1], e0[0]]])
+    with pytest.raises(ValueError, match="more than two"):
+        mesh.validate(c3, np.vstack([quads, extra, dup]), 2)
