@@ -28,6 +28,9 @@ spectral element method with Hilbert space-filling curves", 2021), in float64:
                    node renumbering by first touch sorted by degree
                    (Section 4.3, Cuthill-McKee-like procedure), and the
                    row-major / random baselines (Section 6.1, "No Strategy").
+* ``cpp``       -- the same mass, stiffness and leapfrog as ``sem`` in plain
+                   C loops with OpenMP (``sem_ref.c``): the multi-core CPU
+                   baseline that bench.py times, pinned to ``sem``.
 
 Readings of passages the paper leaves open are listed in the repository's
 design notes and repeated in the docstring of the function that takes them.
