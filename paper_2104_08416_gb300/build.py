@@ -27,8 +27,21 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _sources():
-    return [os.path.join(CSRC, f) for f in ("sem_host.cpp", "sem_kernels.cu", "sem_api.cu")]
+# sem_kernels.cu is compiled once per element order (SEM_KERNEL_NP = p + 1,
+# orders 1..8) for the kernels templated on the order, and once without it
+# for the dispatchers and the order-independent kernels: nine translation
+# units that compile in parallel.
+KERNEL_NP = tuple(range(2, 10))
+
+
+def _units():
+    """(source, object name, extra flags) of every translation unit."""
+    u = [(os.path.join(CSRC, "sem_host.cpp"), "sem_host.o", []),
+         (os.path.join(CSRC, "sem_api.cu"), "sem_api.o", []),
+         (os.path.join(CSRC, "sem_kernels.cu"), "sem_kernels.o", [])]
+    for n in KERNEL_NP:
+        u.append((os.path.join(CSRC, "sem_kernels.cu"), f"sem_kernels_np{n}.o", [f"-DSEM_KERNEL_NP={n}"]))
+    return u
 
 
 def _newest_input() -> float:
@@ -38,14 +51,15 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files if os.path.isfile(f))
 
 
-def _compile(src: str, nvcc: str) -> str:
-    obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+def _compile(unit, nvcc: str) -> str:
+    src, name, extra = unit
+    obj = os.path.join(OUT_DIR, name)
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if src.endswith(".cpp"):
         cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", *inc, "-c", src, "-o", obj]
     else:
         cmd = [nvcc, *ARCH, "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
-               *inc, "-c", src, "-o", obj]
+               *extra, *inc, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -58,8 +72,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    with ThreadPoolExecutor(max_workers=3) as ex:
-        objs = list(ex.map(lambda s: _compile(s, nvcc), _sources()))
+    units = _units()
+    with ThreadPoolExecutor(max_workers=max(1, min(len(units), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(lambda u: _compile(u, nvcc), units))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

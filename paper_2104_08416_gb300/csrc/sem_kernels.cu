@@ -737,6 +737,21 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int32_t* p) {
 // well over a second; a unit normally waits microseconds at most).
 constexpr int kWaitPolls = 1 << 21;
 
+// Unit (i, b) of a launch from its ticket offset u (0 <= u < total): step
+// order, or the band's wavefront order for the first tiled_units tickets.
+__device__ __forceinline__ void unit_of(const StreamArgs& sa, int nb, long long u, int& ui, int& ub) {
+    if (u < sa.tiled_units) {
+        const long long band_units = (long long)sa.band_steps * nb;
+        const long long band = u / band_units;
+        const uint32_t en = __ldg(sa.sched + (u - band * band_units));
+        ui = (int)(band * sa.band_steps) + (int)(en >> 24);
+        ub = (int)(en & 0xFFFFFFu);
+    } else {
+        ui = (int)(u / nb);
+        ub = (int)(u - (long long)ui * nb);
+    }
+}
+
 // Wait of unit (i, b) for step i-1 at b's neighbours (active when i > 0):
 // the threads poll one neighbour's done flag each (acquire), then the block
 // synchronises; a poll that gives up marks the unit failed.
@@ -797,18 +812,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
         const int raised = ld_relaxed_gpu(sa.err);
         const long long u = raised != 0 ? total : (long long)(t - sa.base);
         int ui = -1, ub = 0;
-        if (u >= 0 && u < total) {
-            if (u < sa.tiled_units) {
-                const long long band_units = (long long)sa.band_steps * nb;
-                const long long band = u / band_units;
-                const uint32_t en = __ldg(sa.sched + (u - band * band_units));
-                ui = (int)(band * sa.band_steps) + (int)(en >> 24);
-                ub = (int)(en & 0xFFFFFFu);
-            } else {
-                ui = (int)(u / nb);
-                ub = (int)(u - (long long)ui * nb);
-            }
-        }
+        if (u >= 0 && u < total) unit_of(sa, nb, u, ui, ub);
         s_i = ui;
         s_b = ub;
         s_fail = 0;
@@ -1032,6 +1036,32 @@ int grid_for(int64_t n, int threads) {
     return (int)g;
 }
 
+}  // namespace
+
+// ------------------------------------------------------ per-order launchers
+// The kernels templated on the order are instantiated one order per
+// translation unit: this file is compiled once per order with
+// SEM_KERNEL_NP = p + 1 (those units define the launchers below for their
+// order only) and once without it (the dispatchers and the order-independent
+// kernels), so that the orders compile in parallel.
+template <int NP>
+cudaError_t step_np(bool fp64, int mode, const Plan& pl, const void* args, const void* basis, int threads, int smem,
+                    cudaStream_t st);
+template <int NP>
+cudaError_t batch_np(bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas, const void* basis,
+                     int threads, int smem, cudaStream_t st);
+template <int NP>
+cudaError_t stream_np(bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis, int threads,
+                      int smem, int64_t ctas, cudaStream_t st);
+template <int NP>
+cudaError_t resident_np(bool fp64, int mode, int threads, int smem, int* out);
+template <int NP>
+cudaError_t mass_np(const Plan& pl, const double* mloc, double* partial, double* M, int threads, int smem,
+                    cudaStream_t st);
+
+#ifdef SEM_KERNEL_NP
+namespace {
+
 template <int NP, typename T, int MODE>
 cudaError_t launch_step_t(const Plan& pl, const void* args, const void* basis, int threads, int smem, cudaStream_t st) {
     auto kern = sem_step_kernel<NP, T, MODE>;
@@ -1046,77 +1076,14 @@ cudaError_t launch_step_t(const Plan& pl, const void* args, const void* basis, i
     return cudaGetLastError();
 }
 
-template <typename T, int MODE>
-cudaError_t dispatch_np(int np, const Plan& pl, const void* args, const void* basis, int threads, int smem,
-                        cudaStream_t st) {
-    switch (np) {
-        case 2: return launch_step_t<2, T, MODE>(pl, args, basis, threads, smem, st);
-        case 3: return launch_step_t<3, T, MODE>(pl, args, basis, threads, smem, st);
-        case 4: return launch_step_t<4, T, MODE>(pl, args, basis, threads, smem, st);
-        case 5: return launch_step_t<5, T, MODE>(pl, args, basis, threads, smem, st);
-        case 6: return launch_step_t<6, T, MODE>(pl, args, basis, threads, smem, st);
-        case 7: return launch_step_t<7, T, MODE>(pl, args, basis, threads, smem, st);
-        case 8: return launch_step_t<8, T, MODE>(pl, args, basis, threads, smem, st);
-        case 9: return launch_step_t<9, T, MODE>(pl, args, basis, threads, smem, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 template <int NP, typename T, int MODE>
-cudaError_t launch_batch_t(const BatchArgs& ba, int ctas, const void* basis, int threads, int smem, cudaStream_t st) {
+cudaError_t launch_batch_t(bool prepare_only, const BatchArgs& ba, int ctas, const void* basis, int threads, int smem,
+                           cudaStream_t st) {
     auto kern = sem_batch_step_kernel<NP, T, MODE>;
+    if (prepare_only) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     kern<<<ctas, threads, smem, st>>>(ba, *static_cast<const Basis<T>*>(basis));
     return cudaGetLastError();
 }
-
-template <int NP, typename T, int MODE>
-cudaError_t prepare_batch_t(int smem) {
-    return cudaFuncSetAttribute(sem_batch_step_kernel<NP, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-}
-
-template <typename T, int MODE>
-cudaError_t dispatch_batch(int np, bool prepare_only, const BatchArgs& ba, int ctas, const void* basis, int threads,
-                           int smem, cudaStream_t st) {
-    switch (np) {
-#define SEM_BATCH_CASE(N)                                                                            \
-    case N:                                                                                          \
-        return prepare_only ? prepare_batch_t<N, T, MODE>(smem)                                      \
-                            : launch_batch_t<N, T, MODE>(ba, ctas, basis, threads, smem, st);
-        SEM_BATCH_CASE(2)
-        SEM_BATCH_CASE(3)
-        SEM_BATCH_CASE(4)
-        SEM_BATCH_CASE(5)
-        SEM_BATCH_CASE(6)
-        SEM_BATCH_CASE(7)
-        SEM_BATCH_CASE(8)
-        SEM_BATCH_CASE(9)
-#undef SEM_BATCH_CASE
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-}  // namespace
-
-cudaError_t launch_batch_step(int np, bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas,
-                              const void* basis, int threads, int smem, cudaStream_t st) {
-    if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
-    if (fp64) {
-        if (mode == MODE_THREE_LEVEL)
-            return dispatch_batch<double, MODE_THREE_LEVEL>(np, prepare_only, ba, ctas, basis, threads, smem, st);
-        return cudaErrorInvalidValue;
-    }
-    if (mode == MODE_THREE_LEVEL)
-        return dispatch_batch<float, MODE_THREE_LEVEL>(np, prepare_only, ba, ctas, basis, threads, smem, st);
-    if (mode == MODE_KAHAN) return dispatch_batch<float, MODE_KAHAN>(np, prepare_only, ba, ctas, basis, threads, smem, st);
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cudaStream_t st) {
-    batch_advance_kernel<<<(nshots + 255) / 256, 256, 0, st>>>(step, pending, nshots);
-    return cudaGetLastError();
-}
-
-namespace {
 
 template <int NP, typename T, int MODE>
 cudaError_t stream_t(const void* shot, const StreamArgs& sa, const void* basis, int threads, int smem, int64_t ctas,
@@ -1146,68 +1113,126 @@ cudaError_t stream_resident_t(int threads, int smem, int* out) {
     return e;
 }
 
-template <typename T, int MODE>
-cudaError_t dispatch_resident(int np, int threads, int smem, int* out) {
-    switch (np) {
-#define SEM_RES_CASE(N) \
-    case N: return stream_resident_t<N, T, MODE>(threads, smem, out);
-        SEM_RES_CASE(2)
-        SEM_RES_CASE(3)
-        SEM_RES_CASE(4)
-        SEM_RES_CASE(5)
-        SEM_RES_CASE(6)
-        SEM_RES_CASE(7)
-        SEM_RES_CASE(8)
-        SEM_RES_CASE(9)
-#undef SEM_RES_CASE
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename T, int MODE>
-cudaError_t dispatch_stream(int np, const void* shot, const StreamArgs& sa, const void* basis, int threads, int smem,
-                            int64_t ctas, cudaStream_t st) {
-    switch (np) {
-#define SEM_STREAM_CASE(N) \
-    case N: return stream_t<N, T, MODE>(shot, sa, basis, threads, smem, ctas, st);
-        SEM_STREAM_CASE(2)
-        SEM_STREAM_CASE(3)
-        SEM_STREAM_CASE(4)
-        SEM_STREAM_CASE(5)
-        SEM_STREAM_CASE(6)
-        SEM_STREAM_CASE(7)
-        SEM_STREAM_CASE(8)
-        SEM_STREAM_CASE(9)
-#undef SEM_STREAM_CASE
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 }  // namespace
+
+template <int NP>
+cudaError_t step_np(bool fp64, int mode, const Plan& pl, const void* args, const void* basis, int threads, int smem,
+                    cudaStream_t st) {
+    if (fp64) {
+        switch (mode) {
+            case MODE_THREE_LEVEL: return launch_step_t<NP, double, MODE_THREE_LEVEL>(pl, args, basis, threads, smem, st);
+            case MODE_APPLY: return launch_step_t<NP, double, MODE_APPLY>(pl, args, basis, threads, smem, st);
+            case MODE_HEUN_P: return launch_step_t<NP, double, MODE_HEUN_P>(pl, args, basis, threads, smem, st);
+            case MODE_HEUN_C: return launch_step_t<NP, double, MODE_HEUN_C>(pl, args, basis, threads, smem, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (mode) {
+        case MODE_THREE_LEVEL: return launch_step_t<NP, float, MODE_THREE_LEVEL>(pl, args, basis, threads, smem, st);
+        case MODE_KAHAN: return launch_step_t<NP, float, MODE_KAHAN>(pl, args, basis, threads, smem, st);
+        case MODE_APPLY: return launch_step_t<NP, float, MODE_APPLY>(pl, args, basis, threads, smem, st);
+        case MODE_HEUN_P: return launch_step_t<NP, float, MODE_HEUN_P>(pl, args, basis, threads, smem, st);
+        case MODE_HEUN_C: return launch_step_t<NP, float, MODE_HEUN_C>(pl, args, basis, threads, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NP>
+cudaError_t batch_np(bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas, const void* basis,
+                     int threads, int smem, cudaStream_t st) {
+    if (fp64) {
+        if (mode == MODE_THREE_LEVEL)
+            return launch_batch_t<NP, double, MODE_THREE_LEVEL>(prepare_only, ba, ctas, basis, threads, smem, st);
+        return cudaErrorInvalidValue;
+    }
+    if (mode == MODE_THREE_LEVEL)
+        return launch_batch_t<NP, float, MODE_THREE_LEVEL>(prepare_only, ba, ctas, basis, threads, smem, st);
+    if (mode == MODE_KAHAN) return launch_batch_t<NP, float, MODE_KAHAN>(prepare_only, ba, ctas, basis, threads, smem, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int NP>
+cudaError_t stream_np(bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis, int threads,
+                      int smem, int64_t ctas, cudaStream_t st) {
+    if (fp64) {
+        if (mode == MODE_THREE_LEVEL) return stream_t<NP, double, MODE_THREE_LEVEL>(shot, sa, basis, threads, smem, ctas, st);
+        return cudaErrorInvalidValue;
+    }
+    if (mode == MODE_THREE_LEVEL) return stream_t<NP, float, MODE_THREE_LEVEL>(shot, sa, basis, threads, smem, ctas, st);
+    if (mode == MODE_KAHAN) return stream_t<NP, float, MODE_KAHAN>(shot, sa, basis, threads, smem, ctas, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int NP>
+cudaError_t resident_np(bool fp64, int mode, int threads, int smem, int* out) {
+    if (fp64) {
+        if (mode == MODE_THREE_LEVEL) return stream_resident_t<NP, double, MODE_THREE_LEVEL>(threads, smem, out);
+        return cudaErrorInvalidValue;
+    }
+    if (mode == MODE_THREE_LEVEL) return stream_resident_t<NP, float, MODE_THREE_LEVEL>(threads, smem, out);
+    if (mode == MODE_KAHAN) return stream_resident_t<NP, float, MODE_KAHAN>(threads, smem, out);
+    return cudaErrorInvalidValue;
+}
+
+template <int NP>
+cudaError_t mass_np(const Plan& pl, const double* mloc, double* partial, double* M, int threads, int smem,
+                    cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(mass_block_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    mass_block_kernel<NP><<<pl.nblocks, threads, smem, st>>>(pl, mloc, partial, M);
+    return cudaGetLastError();
+}
+
+template cudaError_t step_np<SEM_KERNEL_NP>(bool, int, const Plan&, const void*, const void*, int, int, cudaStream_t);
+template cudaError_t batch_np<SEM_KERNEL_NP>(bool, int, bool, const BatchArgs&, int, const void*, int, int,
+                                            cudaStream_t);
+template cudaError_t stream_np<SEM_KERNEL_NP>(bool, int, const void*, const StreamArgs&, const void*, int, int,
+                                             int64_t, cudaStream_t);
+template cudaError_t resident_np<SEM_KERNEL_NP>(bool, int, int, int, int*);
+template cudaError_t mass_np<SEM_KERNEL_NP>(const Plan&, const double*, double*, double*, int, int, cudaStream_t);
+
+#else  // the dispatchers and the order-independent kernels
+
+#define SEM_NP_SWITCH(np, CALL)        \
+    switch (np) {                      \
+        case 2: return CALL(2);        \
+        case 3: return CALL(3);        \
+        case 4: return CALL(4);        \
+        case 5: return CALL(5);        \
+        case 6: return CALL(6);        \
+        case 7: return CALL(7);        \
+        case 8: return CALL(8);        \
+        case 9: return CALL(9);        \
+        default: return cudaErrorInvalidValue; \
+    }
+
+cudaError_t launch_batch_step(int np, bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas,
+                              const void* basis, int threads, int smem, cudaStream_t st) {
+    if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
+#define SEM_CALL(N) batch_np<N>(fp64, mode, prepare_only, ba, ctas, basis, threads, smem, st)
+    SEM_NP_SWITCH(np, SEM_CALL)
+#undef SEM_CALL
+}
+
+cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cudaStream_t st) {
+    batch_advance_kernel<<<(nshots + 255) / 256, 256, 0, st>>>(step, pending, nshots);
+    return cudaGetLastError();
+}
 
 cudaError_t stream_resident_ctas(int np, bool fp64, int mode, int threads, int smem, int* out) {
     *out = 0;
-    if (fp64) {
-        if (mode == MODE_THREE_LEVEL) return dispatch_resident<double, MODE_THREE_LEVEL>(np, threads, smem, out);
-        return cudaErrorInvalidValue;
-    }
-    if (mode == MODE_THREE_LEVEL) return dispatch_resident<float, MODE_THREE_LEVEL>(np, threads, smem, out);
-    if (mode == MODE_KAHAN) return dispatch_resident<float, MODE_KAHAN>(np, threads, smem, out);
-    return cudaErrorInvalidValue;
+#define SEM_CALL(N) resident_np<N>(fp64, mode, threads, smem, out)
+    SEM_NP_SWITCH(np, SEM_CALL)
+#undef SEM_CALL
 }
 
 cudaError_t launch_stream(int np, bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis,
                           int threads, int smem, int nblocks, cudaStream_t st) {
     if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
     const int64_t ctas = (int64_t)sa.nsteps * (int64_t)nblocks;
-    if (fp64) {
-        if (mode == MODE_THREE_LEVEL)
-            return dispatch_stream<double, MODE_THREE_LEVEL>(np, shot, sa, basis, threads, smem, ctas, st);
-        return cudaErrorInvalidValue;
-    }
-    if (mode == MODE_THREE_LEVEL) return dispatch_stream<float, MODE_THREE_LEVEL>(np, shot, sa, basis, threads, smem, ctas, st);
-    if (mode == MODE_KAHAN) return dispatch_stream<float, MODE_KAHAN>(np, shot, sa, basis, threads, smem, ctas, st);
-    return cudaErrorInvalidValue;
+#define SEM_CALL(N) stream_np<N>(fp64, mode, shot, sa, basis, threads, smem, ctas, st)
+    SEM_NP_SWITCH(np, SEM_CALL)
+#undef SEM_CALL
 }
 
 int step_threads(int eb) {
@@ -1228,23 +1253,9 @@ int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, b
 cudaError_t launch_step(int np, bool fp64, int mode, const Plan& pl, const void* args, const void* basis,
                         int threads, int smem, cudaStream_t st) {
     if (threads < 1 || threads > kMaxStepThreads || threads < pl.eb) return cudaErrorInvalidValue;
-    if (fp64) {
-        switch (mode) {
-            case MODE_THREE_LEVEL: return dispatch_np<double, MODE_THREE_LEVEL>(np, pl, args, basis, threads, smem, st);
-            case MODE_APPLY: return dispatch_np<double, MODE_APPLY>(np, pl, args, basis, threads, smem, st);
-            case MODE_HEUN_P: return dispatch_np<double, MODE_HEUN_P>(np, pl, args, basis, threads, smem, st);
-            case MODE_HEUN_C: return dispatch_np<double, MODE_HEUN_C>(np, pl, args, basis, threads, smem, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (mode) {
-        case MODE_THREE_LEVEL: return dispatch_np<float, MODE_THREE_LEVEL>(np, pl, args, basis, threads, smem, st);
-        case MODE_KAHAN: return dispatch_np<float, MODE_KAHAN>(np, pl, args, basis, threads, smem, st);
-        case MODE_APPLY: return dispatch_np<float, MODE_APPLY>(np, pl, args, basis, threads, smem, st);
-        case MODE_HEUN_P: return dispatch_np<float, MODE_HEUN_P>(np, pl, args, basis, threads, smem, st);
-        case MODE_HEUN_C: return dispatch_np<float, MODE_HEUN_C>(np, pl, args, basis, threads, smem, st);
-        default: return cudaErrorInvalidValue;
-    }
+#define SEM_CALL(N) step_np<N>(fp64, mode, pl, args, basis, threads, smem, st)
+    SEM_NP_SWITCH(np, SEM_CALL)
+#undef SEM_CALL
 }
 
 cudaError_t launch_open_finish(bool fp64, int mode, const Plan& pl, const void* args, cudaStream_t st) {
@@ -1326,11 +1337,8 @@ cudaError_t launch_mass(const Plan& pl, int np, const double* mloc, double* part
     const int smem = pl.sulen_pad * 8;
     cudaError_t e = cudaSuccess;
     switch (np) {
-#define SEM_MASS_CASE(N)                                                                                     \
-    case N:                                                                                                  \
-        e = cudaFuncSetAttribute(mass_block_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);   \
-        if (e == cudaSuccess) mass_block_kernel<N><<<pl.nblocks, threads, smem, st>>>(pl, mloc, partial, M); \
-        break;
+#define SEM_MASS_CASE(N) \
+    case N: e = mass_np<N>(pl, mloc, partial, M, threads, smem, st); break;
         SEM_MASS_CASE(2)
         SEM_MASS_CASE(3)
         SEM_MASS_CASE(4)
@@ -1343,8 +1351,6 @@ cudaError_t launch_mass(const Plan& pl, int np, const double* mloc, double* part
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     if (pl.nopen_nodes > 0) mass_open_kernel<<<grid_for(pl.nopen_nodes, kThreads), kThreads, 0, st>>>(pl, partial, M);
     return cudaGetLastError();
 }
@@ -1353,5 +1359,7 @@ cudaError_t launch_scale(const double* M, int64_t nn, double num, double* s64, f
     scale_kernel<<<grid_for(nn, kThreads), kThreads, 0, st>>>(M, nn, num, s64, s32);
     return cudaGetLastError();
 }
+
+#endif  // SEM_KERNEL_NP
 
 }  // namespace semdev
