@@ -190,11 +190,15 @@ sem_status sem_set_dt(sem_mesh* m, double dt);
  * host-to-device copies). Needs the model and dt. */
 sem_status sem_step(sem_mesh* m, int64_t nsteps);
 
-/* Number of steps taken so far. */
+/* Number of steps taken so far, n in t_n = n dt (the step counter of the
+ * time loop, Eq. u_change's time index; no passage of its own: an accessor). */
 sem_status sem_get_step(const sem_mesh* m, int64_t* step);
 
 /* Copy traces to out[nrec][cap]: out[r*cap + k] = u at receiver r after step
- * k+1, for k < min(cap, steps taken). Synchronises the stream. */
+ * k+1, for k < min(cap, steps taken). Synchronises the stream. Receiver
+ * records are the seismograms of the multilayer model of Section 6.2 (the
+ * paper records the wavefield at surface receivers; it gives no interface
+ * for reading them, so this call is an accessor). */
 sem_status sem_read_traces(sem_mesh* m, double* out, int64_t cap);
 
 /* u^n at every global node, original node order, as FP64. Synchronises. */
@@ -222,11 +226,14 @@ sem_status sem_apply_stiffness(sem_mesh* m, const double* u, double* Ku);
 sem_status sem_read_mass(sem_mesh* m, double* mass);
 
 /* Permutations chosen by sem_reorder: elem_new_of_old[ne] and
- * node_new_of_old[N] (either may be NULL). */
+ * node_new_of_old[N] (either may be NULL). These are the element order of
+ * Section 4.3 (the curve order L) and the node renumbering of the same
+ * section, read back; no passage of their own: an accessor. */
 sem_status sem_get_permutation(const sem_mesh* m, int64_t* elem_new_of_old,
                                int64_t* node_new_of_old);
 
-/* Global node count N and element count E. */
+/* Global node count N and element count E (the counts of Section 4.2's
+ * global node set and element set; no passage of their own: an accessor). */
 sem_status sem_get_sizes(const sem_mesh* m, int64_t* n_nodes, int64_t* n_elems);
 
 /* Positions of the global nodes, original order, out[N][2]. */

@@ -307,7 +307,9 @@ void node_coordinates(const Mesh& m, std::vector<double>& xy) {
 }
 
 // ------------------------------------------------ generalized Hilbert curve
-// Recursive split of a w x h block spanned by the integer vectors A (length w
+// The construction of Cerveny's generalized Hilbert ("gilbert") curve, which
+// Section 3 cites for rectangles of any side lengths, with this library's own
+// parity rules and top-level orientation. Recursive split of a w x h block spanned by the integer vectors A (length w
 // along the curve's main direction) and B (length h), starting at origin O
 // and ending at O + (w-1) a. Long blocks (2w > 3h) are cut in two along A
 // (first part even when h is even); otherwise the block is cut into a
