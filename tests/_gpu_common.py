@@ -20,6 +20,36 @@ def need_gpu():
     return P
 
 
+# unit roundoff of FP32 (round to nearest)
+U32 = 2.0 ** -24
+
+
+def fp32_apply_bound(S, u):
+    """Relative L2 bound for K u computed in FP32 by the sum-factorised path.
+
+    Forward error analysis: every output (K u)_nu is a chain of sums and
+    products of the FP32-rounded input u, the GLL derivative entries and the
+    per-point metric G_q (formed in FP32 from the element's bilinear map).
+    Each floating-point operation contributes at most one unit roundoff U32
+    relative to the absolute value of what it combines, so
+        |fl(K u) - K u| <= gamma * a,   a = sum_e |B|^T |G_q| |B| |u_e|
+    elementwise (a is K u with every term taken in absolute value, in the
+    factorisation the kernels evaluate: gradient, metric, transposed
+    gradient), with gamma = (2 (p+1) + 24) U32: p+1 terms in each of the two
+    contractions, the input rounding, the metric's own error (a few ulps from
+    the bilinear coefficients, the determinant and the division) and the
+    assembly of at most four element contributions, with a margin. Returned
+    as gamma ||a|| / ||K u||: for white noise ||a|| / ||K u|| is 2 to 3, for
+    smooth fields it grows like 1/h^2 (K u is small where u is nearly in
+    the kernel of K), which is the cancellation any FP32 evaluation of the
+    operator meets, whatever the implementation."""
+    ae = np.einsum("qda,eqdk,qkb,eb->ea", np.abs(S.B), np.abs(S.G), np.abs(S.B), np.abs(u[S.conn]),
+                   optimize=True)
+    a = np.bincount(S.conn.ravel(), weights=ae.ravel(), minlength=S.n_nodes)
+    gamma = (2 * (S.p + 1) + 24) * U32
+    return float(gamma * np.linalg.norm(a) / np.linalg.norm(S.apply_K(u)))
+
+
 def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)

@@ -18,7 +18,7 @@ import pytest
 
 import gen
 from oracle import sem as osem
-from tests._gpu_common import FP32_TOL, FP64_TOL, need_gpu, rel_l2
+from tests._gpu_common import FP32_TOL, FP64_TOL, fp32_apply_bound, need_gpu, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -51,10 +51,12 @@ def test_graded_stiffness_whole_field(P, graded):
     rng = np.random.default_rng(11)
     u = rng.standard_normal(S.n_nodes)
     ref = S.apply_K(u)
-    for prec, tol in (("fp64", FP64_TOL), ("fp32_kahan", 20 * FP32_TOL)):
+    # FP32: the benchmark spec's 1e-5, or the FP32 forward error bound if tighter
+    for prec, tol in (("fp64", FP64_TOL), ("fp32_kahan", min(FP32_TOL, fp32_apply_bound(S, u)))):
         h = _handle(P, m, prec)
         ku = h.sem_apply_stiffness(u)
         h.sem_destroy()
+        print(f"graded 512 stiffness {prec}: rel L2 {rel_l2(ku, ref):.2e} (bound {tol:.2e})")
         assert rel_l2(ku, ref) < tol, (prec, rel_l2(ku, ref))
 
 

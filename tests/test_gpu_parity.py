@@ -7,7 +7,7 @@ import pytest
 
 import gen
 from oracle import mesh, ordering, sem as osem
-from tests._gpu_common import FP32_TOL, FP64_TOL, gpu_run, need_gpu, oracle_run, rel_l2
+from tests._gpu_common import FP32_TOL, FP64_TOL, fp32_apply_bound, gpu_run, need_gpu, oracle_run, rel_l2
 
 pytestmark = pytest.mark.gpu
 ORDERINGS = ["none", "rowmajor", "random", "hilbert", "connectivity", "distance", "hilbert_wide"]
@@ -46,20 +46,29 @@ def test_stiffness_apply(P, p, prec):
     S = osem.SEM(m["coords"], m["quads"], p, m["vel"], rho)
     xy = S.node_xy
     fields = [rng.standard_normal(S.n_nodes), np.sin(3 * xy[:, 0]) * np.cos(2 * xy[:, 1])]
-    tol = FP64_TOL if prec == "fp64" else FP32_TOL
+    refs = [S.apply_K(u) for u in fields]
+    # FP64: the stated 1e-12. FP32: the forward error bound of the FP32
+    # evaluation (fp32_apply_bound), and the benchmark spec's 1e-5 on white noise,
+    # where the operator is well conditioned
+    tols = ([FP64_TOL, FP64_TOL] if prec == "fp64" else
+            [min(FP32_TOL, fp32_apply_bound(S, fields[0])), fp32_apply_bound(S, fields[1])])
+    worst = [0.0, 0.0]
     for kind in ORDERINGS:
         h = P.SEM(m["coords"], m["quads"], p, prec)
         h.sem_reorder(kind, 99)
         h.sem_set_model(m["vel"], rho)
         h.sem_set_tuning(7)          # several blocks, ragged tail (121 elements)
-        for u in fields:
+        for f, (u, ref) in enumerate(zip(fields, refs)):
             ku = h.sem_apply_stiffness(u)
-            ref = S.apply_K(u)
-            assert rel_l2(ku, ref) < (tol if prec == "fp64" else 20 * tol), (kind, rel_l2(ku, ref))
+            err = rel_l2(ku, ref)
+            worst[f] = max(worst[f], err)
+            assert err < tols[f], (kind, f, err, tols[f])
         # constants are in the kernel of K
         k1 = h.sem_apply_stiffness(np.ones(S.n_nodes))
-        assert np.abs(k1).max() < (1e-12 if prec == "fp64" else 1e-4) * np.abs(S.apply_K(fields[0])).max()
+        assert np.abs(k1).max() < (1e-12 if prec == "fp64" else 1e-4) * np.abs(refs[0]).max()
         h.sem_destroy()
+    print(f"stiffness p={p} {prec}: worst rel L2 white noise {worst[0]:.2e} (bound {tols[0]:.2e}), "
+          f"smooth {worst[1]:.2e} (bound {tols[1]:.2e})")
 
 
 @pytest.mark.parametrize("kind", ORDERINGS)
