@@ -111,6 +111,14 @@ class SEMC:
             raise ValueError("oracle C set-up failed (allocation or non-positive Jacobian)")
         self.M = np.empty(self.n_nodes)
         lib.osem_mass(self._h, _dp(self.M))
+        self._snapped = {}
+
+    def _snap(self, x, y) -> int:
+        """sem.snap, remembered per position (a search over all nodes)."""
+        key = (float(x), float(y))
+        if key not in self._snapped:
+            self._snapped[key] = _sem.snap(self.node_xy, x, y)
+        return self._snapped[key]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -136,12 +144,12 @@ class SEMC:
         f = np.zeros(max(nsteps, 1))
         if src is not None:
             sx, sy, f0, t0, amp = src
-            s_node = _sem.snap(self.node_xy, sx, sy)
+            s_node = self._snap(sx, sy)
             f = np.ascontiguousarray(_sem.ricker((step0 + np.arange(max(nsteps, 1))) * dt, f0, t0, amp),
                                      dtype=np.float64)
         rec = np.zeros(0, dtype=np.int64)
         if receivers is not None and len(receivers):
-            rec = np.array([_sem.snap(self.node_xy, x, y) for x, y in np.asarray(receivers)], dtype=np.int64)
+            rec = np.array([self._snap(x, y) for x, y in np.asarray(receivers)], dtype=np.int64)
         traces = np.zeros((rec.size, max(nsteps, 1)))
         _load().osem_run(self._h, int(nsteps), float(dt), int(s_node), _dp(f), _ip(rec), int(rec.size), _dp(u),
                          _dp(up), _dp(traces))

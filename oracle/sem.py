@@ -70,6 +70,25 @@ def snap(node_xy: np.ndarray, x: float, y: float) -> int:
     return int(np.argmin(dx * dx + dy * dy))
 
 
+def cfl_dt(coords, quads, p: int, vel) -> float:
+    """dt_CFL = min over elements of (shortest distance between GLL points
+    adjacent along a local grid line) / c_e. Section 6.2 only says the step
+    meets the CFL condition; this is the reading used throughout."""
+    coords = np.asarray(coords, dtype=np.float64)
+    quads = np.asarray(quads, dtype=np.int64)
+    vel = np.broadcast_to(np.asarray(vel, dtype=np.float64), (quads.shape[0],))
+    n = p + 1
+    s = _gll.gll_nodes(p)
+    corners = coords[quads]
+    pts = np.zeros((quads.shape[0], n, n, 2))      # [e, j, i]
+    for j in range(n):
+        for i in range(n):
+            pts[:, j, i] = _mesh.bilinear(corners, s[i], s[j])
+    d1 = np.linalg.norm(pts[:, :, 1:] - pts[:, :, :-1], axis=-1).min(axis=(1, 2))
+    d2 = np.linalg.norm(pts[:, 1:, :] - pts[:, :-1, :], axis=-1).min(axis=(1, 2))
+    return float(np.min(np.minimum(d1, d2) / vel))
+
+
 class SEM:
     """Discrete operators of one mesh + model, in the original numbering."""
 
@@ -132,19 +151,8 @@ class SEM:
         return out
 
     def cfl_dt(self) -> float:
-        """dt_CFL = min over elements of (shortest distance between GLL points
-        adjacent along a local grid line) / c_e. Section 6.2 only says the step
-        meets the CFL condition; this is the reading used throughout."""
-        n = self.p + 1
-        s = _gll.gll_nodes(self.p)
-        corners = self.coords[self.quads]
-        pts = np.zeros((self.quads.shape[0], n, n, 2))      # [e, j, i]
-        for j in range(n):
-            for i in range(n):
-                pts[:, j, i] = _mesh.bilinear(corners, s[i], s[j])
-        d1 = np.linalg.norm(pts[:, :, 1:] - pts[:, :, :-1], axis=-1).min(axis=(1, 2))
-        d2 = np.linalg.norm(pts[:, 1:, :] - pts[:, :-1, :], axis=-1).min(axis=(1, 2))
-        return float(np.min(np.minimum(d1, d2) / self.vel))
+        """dt_CFL of this mesh and model (see the module function cfl_dt)."""
+        return cfl_dt(self.coords, self.quads, self.p, self.vel)
 
     def lambda_max(self, iters: int = 300, seed: int = 7) -> float:
         """Largest eigenvalue of M^-1 K by power iteration (symmetrised form)."""
