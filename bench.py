@@ -15,7 +15,16 @@ Metric: GLL node-updates/s = nodes x steps / time (higher is better).
 
 Under torchrun each rank runs an independent replica (its own shot; weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
-`--impl reference` times the FP64 CPU oracle on the host cores instead.
+`--impl reference` times the FP64 CPU oracle (the C/OpenMP restatement, all
+host cores) on the same workload instead.
+
+Besides the headline (FP32 bulk + Kahan, Hilbert order) the line carries the
+rest of the metric "FP32 vs FP64 at stated error": the FP64 and plain FP32
+rates on the same mesh (`precisions`), the errors of FP32+Kahan against FP64
+on the GPU over the workload's 2000 steps and of both precisions against the
+CPU oracle over the first steps (`error`), and the multilayered
+4096 x 1024 model (67M nodes), the largest single-GPU workload
+(`workloads`).
 """
 from __future__ import annotations
 
@@ -218,25 +227,34 @@ def time_steps(torch, h, k):
     return e0.elapsed_time(e1) / 1e3
 
 
-def cpu_baseline(n, budget_s=12.0):
-    """Oracle (FP64 NumPy, as it stands) on the same graded mesh: a bounded
-    number of leapfrog steps after its set-up."""
-    from oracle import sem as osem
-    m = gen.graded(n)
-    S = osem.SEM(m["coords"], m["quads"], 4, m["vel"], m["rho"], validate=False)
-    _ = S.Ke
-    dt = 0.3 * S.cfl_dt()
+def oracle_c(m):
+    """The C/OpenMP FP64 oracle on a workload mesh (all host cores)."""
+    from oracle import cpp
+    return cpp.SEMC(m["coords"], m["quads"], 4, m["vel"], m["rho"], validate=False)
+
+
+def cpu_baseline(m, dt, budget_s=12.0, S=None):
+    """The FP64 CPU oracle (the C/OpenMP restatement, as it stands) on the
+    same mesh: leapfrog steps with source and receivers after 2 warm-up
+    steps, as many as fit in about budget_s seconds, on all host cores; then
+    2 steps on one thread. Returns (node-updates/s all cores, steps, busy
+    threads, node-updates/s one thread)."""
+    from oracle import cpp
+    S = S or oracle_c(m)
     src = (m["src_xy"][0], m["src_xy"][1], m["f0"], m["t0"], m["amp"])
-    S.run(1, dt, src=src)
-    k = 1
-    while True:
-        t, c = time.perf_counter(), time.process_time()
-        S.run(k, dt, src=src, receivers=m["receivers"])
-        el, cpu = time.perf_counter() - t, time.process_time() - c
-        if el > budget_s / 4 or k >= 64:
-            break
-        k *= 2
-    return S.n_nodes * k / el, k, S.n_nodes, cores_busy(cpu, el)
+    t = time.perf_counter()
+    u, up, _ = S.run(2, dt, src=src, receivers=m["receivers"])
+    per = max((time.perf_counter() - t) / 2, 1e-6)
+    k = int(max(2, min(2000, budget_s / per)))
+    t, c = time.perf_counter(), time.process_time()
+    S.run(k, dt, src=src, receivers=m["receivers"], u0=u, u_prev=up, step0=2)
+    el, cpu = time.perf_counter() - t, time.process_time() - c
+    S1 = cpp.SEMC(m["coords"], m["quads"], 4, m["vel"], m["rho"], threads=1, validate=False)
+    t = time.perf_counter()
+    S1.run(2, dt, src=src)
+    el1 = time.perf_counter() - t
+    S1.close()
+    return S.n_nodes * k / el, k, cores_busy(cpu, el), S.n_nodes * 2 / el1
 
 
 def kernel_source_digest():
@@ -250,21 +268,25 @@ def kernel_source_digest():
     return hsh.hexdigest()
 
 
-def recorded_traffic(precision, ordering, kernel, stream_order="step"):
-    """DRAM bytes per step of the step kernel from the committed ncu record
+def recorded_traffic(precision, ordering, kernel, stream_order="step", workload=WORKLOAD):
+    """DRAM bytes per step of the step kernel from the committed ncu records
     (same workload, precision, ordering, kernel sources and order of the
-    streamed units)."""
+    streamed units); None when no record matches."""
     tfile = os.path.join(ROOT, "profiles", "sem_step_kernel_traffic.json")
     try:
         with open(tfile) as fh:
             tj = json.load(fh)
-        if (tj.get("workload") == WORKLOAD and tj.get("precision") == precision and tj.get("ordering") == ordering
-                and str(tj.get("kernel", "")).startswith(kernel + "<")
-                and tj.get("kernel_sha256") == kernel_source_digest()
-                and tj.get("stream_order", "step") == stream_order):
-            return float(tj["dram_bytes_per_launch"]) / float(tj.get("steps_per_launch", 1))
-    except (OSError, ValueError, KeyError, TypeError):
-        pass
+    except (OSError, ValueError):
+        return None
+    digest = kernel_source_digest()
+    for r in (tj.get("records", []) if isinstance(tj, dict) else []):
+        try:
+            if (r.get("workload") == workload and r.get("precision") == precision and r.get("ordering") == ordering
+                    and str(r.get("kernel", "")).startswith(kernel + "<") and r.get("kernel_sha256") == digest
+                    and r.get("stream_order", "step") == stream_order):
+                return float(r["dram_bytes_per_launch"]) / float(r.get("steps_per_launch", 1))
+        except (ValueError, KeyError, TypeError):
+            continue
     return None
 
 
@@ -282,33 +304,33 @@ def threads_used():
 
 
 def run_reference(args, world, rank):
-    """--impl reference: the FP64 CPU oracle timed on the host cores; each of
-    the K steps is one leapfrog step of the oracle on a graded mesh of the
-    same family sized so that the whole run ends within a few minutes."""
+    """--impl reference: the FP64 CPU oracle (the C/OpenMP restatement, as it
+    stands, on all host cores) on the same workload as the GPU line: W
+    untimed leapfrog steps, then K timed steps with source and receivers."""
     if rank != 0:
         return
+    if args.workload == "layered":
+        m, wname = gen.layered(4096, 1024), "layered_4096x1024_p4"
+    elif args.workload == "homogeneous":
+        m, wname = gen.unit_square(args.n), f"homogeneous_{args.n}x{args.n}_p4"
+    else:
+        m, wname = gen.graded(args.n), (WORKLOAD if args.n == 512 else f"graded_{args.n}x{args.n}_p4")
     from oracle import sem as osem
-    budget = 120.0
-    per_step = budget / max(1, args.steps + args.warmup)
-    # oracle speed on this host is roughly 6e6 node-updates/s; pick the side
-    nodes = max(2000.0, per_step * 6e6)
-    n = int(max(8, min(args.n, (nodes ** 0.5 - 1) / 4)))
-    m = gen.graded(n)
-    S = osem.SEM(m["coords"], m["quads"], 4, m["vel"], m["rho"], validate=False)
-    _ = S.Ke
-    dt = 0.3 * S.cfl_dt()
+    S = oracle_c(m)
+    dt = 0.3 * osem.cfl_dt(m["coords"], m["quads"], 4, m["vel"])
     src = (m["src_xy"][0], m["src_xy"][1], m["f0"], m["t0"], m["amp"])
-    S.run(args.warmup, dt, src=src)
+    u, up, _ = S.run(args.warmup, dt, src=src, receivers=m["receivers"])
     t, c = time.perf_counter(), time.process_time()
-    S.run(args.steps, dt, src=src, receivers=m["receivers"])
+    S.run(args.steps, dt, src=src, receivers=m["receivers"], u0=u, u_prev=up, step0=args.warmup)
     el, cpu = time.perf_counter() - t, time.process_time() - c
     v = S.n_nodes * args.steps / el
-    sample = f"graded_{n}x{n}_p4 ({S.n_nodes} nodes), {args.steps} leapfrog steps of the FP64 NumPy oracle"
+    sample = (f"{wname} ({S.n_nodes} nodes), {args.steps} leapfrog steps of the FP64 C/OpenMP oracle "
+              f"(dense element matrices) after {args.warmup} untimed")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "data": "synthetic", "config": {"workload": wname, "sample": sample},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores_busy(cpu, el), "host_threads": threads_used(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -438,6 +460,131 @@ def run_adjoint(args, P, torch):
     print(json.dumps(line))
 
 
+def step_rate(P, torch, m, precision, k, w, ordering="hilbert"):
+    """node-updates/s and the step kernel's time per step of one precision on
+    a workload mesh: w untimed steps, k timed, k more with per-launch events."""
+    h = make_handle(P, m, precision, ordering, w + 2 * k + 8)
+    h.sem_step(w)
+    torch.cuda.synchronize()
+    el = time_steps(torch, h, k)
+    h.sem_profile_enable(True)
+    time_steps(torch, h, k)
+    bms, bl, oms, ol = h.sem_profile_read()
+    h.sem_profile_enable(False)
+    spl, nopen = h.sem_launch_info()
+    block_bytes, _ = h.sem_traffic_model()
+    N = h.n_nodes
+    h.sem_destroy()
+    return {"node_updates_per_s": N * k / el, "ms_per_step": 1e3 * el / k, "steps": k,
+            "step_kernel_us": 1e3 * bms / k, "launches": int(bl), "steps_per_launch": k / max(bl, 1),
+            "kernel": "sem_stream_kernel" if spl > 1 else "sem_step_kernel",
+            "compulsory_bytes_per_step": block_bytes, "nodes": N}
+
+
+def hbm_roofline(r, precision, peak, peak_kind, workload, ordering="hilbert"):
+    """Roofline of the step kernel from a step_rate() result: algorithmic
+    bytes per node-update times the node updates of one launch over the
+    launch's mean event time, and, where an ncu record of the same kernel
+    sources exists, the DRAM traffic per step and its fraction of the peak."""
+    N, spl = r["nodes"], r["steps_per_launch"]
+    launch_us = r["step_kernel_us"] * spl
+    algo = ALGO_BYTES[precision]
+    achieved = algo * N * spl / (launch_us * 1e-6) / 1e9
+    tps = recorded_traffic(precision, ordering, r["kernel"], "step", workload)
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "peak_kind": peak_kind, "kernel": r["kernel"], "launch_us": launch_us, "steps_per_launch": spl,
+           "algorithmic_bytes_per_node_update": algo, "traffic": None if tps is None else tps * spl,
+           "traffic_per_step": tps, "dram_frac": None,
+           "compulsory_bytes_per_step": r["compulsory_bytes_per_step"],
+           "compulsory_frac": r["compulsory_bytes_per_step"] / (r["step_kernel_us"] * 1e-6) / 1e9 / peak}
+    if tps is not None:
+        out["dram_gbs"] = tps / (r["step_kernel_us"] * 1e-6) / 1e9
+        out["dram_frac"] = out["dram_gbs"] / peak
+    return out
+
+
+def fp64_roofline(r):
+    """The FP64 leapfrog is bound by GB300's FP64 arithmetic rate."""
+    fl = FLOPS_FP64_LEAPFROG * r["nodes"] / (r["step_kernel_us"] * 1e-6) / 1e12
+    return {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": fl / FP64_PEAK_TFLOPS, "peak_kind": "derived (nominal FP64 rate)",
+            "flops_per_node_update": FLOPS_FP64_LEAPFROG, "kernel": r["kernel"]}
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def error_block(P, torch, m, nsteps=2000, S=None):
+    """The stated error of the FP32 path: (1) FP32+Kahan against FP64, both
+    on the GPU, after the workload's nsteps steps from rest (wavefield and
+    receiver traces); (2) both precisions against the FP64 C oracle over the
+    first 10 steps from a smooth field cos(3 pi x) cos(2 pi y) that puts signal
+    on every node (u^-1 from the oracle's K and M), with the source on."""
+    out = {}
+    res = {}
+    for prec in ("fp64", "fp32_kahan"):
+        h = make_handle(P, m, prec, "hilbert", nsteps)
+        h.sem_step(nsteps)
+        res[prec] = (h.sem_read_wavefield(), h.sem_read_traces())
+        h.sem_destroy()
+    tr32, tr64 = res["fp32_kahan"][1], res["fp64"][1]
+    reached = bool(np.abs(tr64).max() > 0)
+    out["fp32_kahan_vs_fp64_gpu"] = {"steps": nsteps, "wavefield_rel_l2": rel_l2(res["fp32_kahan"][0], res["fp64"][0]),
+                                     # None while the wavefront has not reached the receivers
+                                     "traces_rel_l2": rel_l2(tr32, tr64) if reached else None,
+                                     "tolerance": 1e-5}
+    if S is not None:
+        n = 10
+        h = make_handle(P, m, "fp64", "hilbert", n)
+        dt = 0.3 * h.sem_cfl_dt()
+        xy = h.sem_node_coordinates()
+        h.sem_destroy()
+        u0 = np.cos(3.0 * np.pi * xy[:, 0]) * np.cos(2.0 * np.pi * xy[:, 1])
+        um1 = u0 - 0.5 * dt * dt * S.apply_K(u0) / S.M
+        src = (m["src_xy"][0], m["src_xy"][1], m["f0"], m["t0"], m["amp"])
+        u_ref, _, tr_ref = S.run(n, dt, src=src, receivers=m["receivers"], u0=u0, u_prev=um1)
+        vs = {"steps": n, "start": "cos(3 pi x) cos(2 pi y)"}
+        for prec, tol in (("fp64", 1e-12), ("fp32_kahan", 1e-5)):
+            h = make_handle(P, m, prec, "hilbert", n)
+            h.sem_set_dt(dt)
+            h.sem_set_state(u0, um1, 0)
+            h.sem_step(n)
+            vs[prec] = {"wavefield_rel_l2": rel_l2(h.sem_read_wavefield(), u_ref),
+                        "traces_rel_l2": rel_l2(h.sem_read_traces(), tr_ref), "tolerance": tol}
+            h.sem_destroy()
+        out["vs_cpu_oracle"] = vs
+    return out
+
+
+def layered_line(P, torch, K, peak, peak_kind):
+    """The multilayered 4096 x 1024 model (67,129,345 nodes; the largest
+    single-GPU workload) in FP32+Kahan, Hilbert order: rate, roofline, and the
+    error against FP64 after 300 steps on every 16th node and on the traces."""
+    m = gen.layered(4096, 1024)
+    k = max(K, 100)
+    r = step_rate(P, torch, m, "fp32_kahan", k, 3)
+    line = {"workload": "layered_4096x1024_p4", "nodes": r["nodes"], "elements": int(m["quads"].shape[0]),
+            "value": r["node_updates_per_s"], "unit": UNIT, "ms_per_step": r["ms_per_step"], "steps": k,
+            "roofline": hbm_roofline(r, "fp32_kahan", peak, peak_kind, "layered_4096x1024_p4")}
+    n = 300
+    res = {}
+    for prec in ("fp64", "fp32_kahan"):
+        h = make_handle(P, m, prec, "hilbert", n)
+        h.sem_step(n)
+        res[prec] = (h.sem_read_wavefield()[::16], h.sem_read_traces())
+        h.sem_destroy()
+    line["error"] = {"fp32_kahan_vs_fp64_gpu": {
+        "steps": n, "wavefield_rel_l2_every_16th_node": rel_l2(res["fp32_kahan"][0], res["fp64"][0]),
+        "traces_max_abs_over_field_max": float(np.abs(res["fp32_kahan"][1] - res["fp64"][1]).max()
+                                               / max(np.abs(res["fp64"][0]).max(), 1e-300)),
+        "tolerance": 1e-5}}
+    return line
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -542,14 +689,37 @@ def main():
             dist.destroy_process_group()
         return
 
-    cpu = None
-    if not args.no_cpu_baseline and world == 1 and args.workload == "graded":
-        v, k, nn, busy = cpu_baseline(args.n)
-        cpu = {"value": v, "unit": UNIT, "cores": busy, "host_threads": threads_used(), "kind": "oracle",
-               "sample": f"{k} leapfrog steps of the FP64 NumPy oracle on the full {WORKLOAD} mesh ({nn} nodes), "
-                         "set-up excluded"}
-
     peak, peak_kind = read_peaks()
+    full = args.workload == "graded" and args.n == 512 and args.scheme == "leapfrog" and world == 1
+    cpu = None
+    S_c = None
+    if not args.no_cpu_baseline and world == 1 and args.workload == "graded":
+        from oracle import sem as osem
+        S_c = oracle_c(m)
+        dt_w = 0.3 * osem.cfl_dt(m["coords"], m["quads"], 4, m["vel"])
+        v, k, busy, v1 = cpu_baseline(m, dt_w, S=S_c)
+        cpu = {"value": v, "unit": UNIT, "cores": busy, "host_threads": threads_used(), "kind": "oracle",
+               "one_core": v1,
+               "sample": f"{k} leapfrog steps (after 2 untimed) of the FP64 C/OpenMP oracle on the full {wname} "
+                         f"mesh ({N} nodes) on all host threads, set-up excluded; one_core: 2 steps on one thread"}
+    extra = {}
+    if full and args.precision == "fp32_kahan" and args.ordering == "hilbert":
+        kk = max(K, 200)
+        precs = {}
+        for prec in ("fp64", "fp32"):
+            r = step_rate(P, torch, m, prec, kk, 3)
+            precs[prec] = {"value": r["node_updates_per_s"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                           "steps": kk,
+                           "roofline": fp64_roofline(r) if prec == "fp64" else
+                           hbm_roofline(r, prec, peak, peak_kind, WORKLOAD)}
+            if prec == "fp64":
+                precs[prec]["roofline"]["hbm_frac"] = hbm_roofline(r, prec, peak, peak_kind, WORKLOAD)["frac"]
+        extra["precisions"] = precs
+        extra["error"] = error_block(P, torch, m, 2000, S_c)
+        extra["workloads"] = {"layered_4096x1024_p4": layered_line(P, torch, K, peak, peak_kind)}
+    if S_c is not None:
+        S_c.close()
+
     # the profiled pass covers K steps in bl step-kernel launches (one step
     # each, or several when the time loop is streamed)
     blk_us = 1e3 * bms / K
@@ -561,8 +731,9 @@ def main():
     achieved = algo * N * steps_per_launch / (launch_us * 1e-6) / 1e9
     kname = "sem_stream_kernel" if spl > 1 else "sem_step_kernel"
     sorder = {"band_steps": band, "window_levels": window} if band > 0 else "step"
-    traffic_step = recorded_traffic(args.precision, args.ordering, kname, sorder) if wname == WORKLOAD else None
+    traffic_step = recorded_traffic(args.precision, args.ordering, kname, sorder, wname)
     traffic = None if traffic_step is None else traffic_step * steps_per_launch
+    dram_gbs = None if traffic_step is None else traffic_step / (blk_us * 1e-6) / 1e9
     value = job_rate(world, N, K, el)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -578,6 +749,7 @@ def main():
                    "finite": finite},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "traffic_per_step": traffic_step,
+                     "dram_gbs": dram_gbs, "dram_frac": None if dram_gbs is None else dram_gbs / peak,
                      "kernel": kname, "peak_kind": peak_kind,
                      "steps_per_launch": steps_per_launch, "launch_us": launch_us,
                      "step_kernel_us": blk_us, "open_kernel_us_per_run": 1e3 * oms / max(ol, 1),
@@ -594,6 +766,7 @@ def main():
         "clocks": clocks,
         "orderings": orderings,
     }
+    line.update(extra)
     if args.precision == "fp64" and args.scheme == "leapfrog" and args.n == 512 and args.workload == "graded":
         # FP64 arithmetic bound: the roofline is the FP64 ALU rate
         fl = FLOPS_FP64_LEAPFROG * N * steps_per_launch / (launch_us * 1e-6) / 1e12
