@@ -302,7 +302,9 @@ sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t
  * where a step has fewer element blocks than 8 times the step CTAs resident
  * on the GPU at once (there the partly filled last wave of a launch per step
  * costs more than the units' waits) and launches once per step otherwise.
- * Waits are bounded: a wait that gives up (which no correct run does) raises
+ * Waits are bounded: a wait gives up after 1 s of the GPU's global timer
+ * (checked every 64 polls of 128 ns back-off each; in any case after 2^26
+ * polls); one that gives up (which no correct run does) raises
  * a device error flag, the remaining steps of the run are skipped, and the
  * next sem_read_wavefield, sem_get_state or sem_read_traces returns
  * SEM_ERR_TIMEOUT. Any time. */
@@ -349,7 +351,7 @@ sem_status sem_stream_schedule(const int32_t* dep_ptr, const int32_t* dep, int32
  * launch that runs step `step`, the unit of element block `block` (in the
  * plan's block order, 0 .. blocks-1) does its work but does not mark its
  * block done, so the next step's units that share a node with that block wait
- * until their wait limit (about a second), raise the error flag and stop the
+ * until their wait limit (1 s of global timer), raise the error flag and stop the
  * launch; the next read-back returns SEM_ERR_TIMEOUT and clears the flag, and the
  * wavefield is not meaningful until sem_set_state. Fires once; a negative
  * step or block clears it. No effect on steps that run one launch each. */

@@ -281,6 +281,17 @@ __device__ __forceinline__ void heun_element(const Plan& pl, const StepArgs<T>& 
     }
 }
 
+// The loaded inputs of one open entry whose node is finished in this unit
+// (position, node, partial sums, previous-level state).
+template <typename T>
+struct OpenIn {
+    T p[4];
+    T u, x, c, s;
+    int64_t g;
+    int pos, pb, cnt;
+    bool own;
+};
+
 // One block of one mesh, one CTA (the body of the step kernels).
 // Called by every thread of a block after the loads that do not depend on
 // the previous step (element data, packet) are issued and before the node
@@ -403,25 +414,53 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             }
     }
     const bool pending = STATE && pend;
-    for (int o = tid; o < h.nopen; o += nt) {
-        const int pos = opos[o];
-        const int64_t g = pos < h.ulen ? abase + pos : (int64_t)egid[pos - h.ulen];
-        if (!pending) {
+    if (!pending) {
+        for (int o = tid; o < h.nopen; o += nt) {
+            const int pos = opos[o];
+            const int64_t g = pos < h.ulen ? abase + pos : (int64_t)egid[pos - h.ulen];
             su[pos] = __ldcg(a.u_k + g);
-        } else {
-            const T ku = sum_partials(a.part_rd, obase[o], ocnt[o]);
-            const T f = (g == a.src_gid) ? f_prev : T(0);
-            const Update<T, MODE> up = update_node<T, MODE>(__ldcg(a.u_km1 + g), __ldcg(a.x_km1 + g),
-                                                             KAHAN ? __ldcg(a.c_km1 + g) : T(0), __ldcg(a.s + g), f, ku);
-            su[pos] = up.u;
-            if (orank[o] == 0) {
-                __stcg(a.u_kw + g, up.u);
+        }
+    } else {
+        // two open entries per pass, every load of both issued before either
+        // is used: one round trip per pass
+        auto fetch = [&](int o, OpenIn<T>& in) {
+            in.pos = opos[o];
+            in.g = in.pos < h.ulen ? abase + in.pos : (int64_t)egid[in.pos - h.ulen];
+            in.pb = obase[o];
+            in.cnt = ocnt[o];
+            in.own = orank[o] == 0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) in.p[t] = (t < in.cnt) ? __ldcg(a.part_rd + in.pb + t) : T(0);
+            in.u = __ldcg(a.u_km1 + in.g);
+            in.x = __ldcg(a.x_km1 + in.g);
+            in.c = KAHAN ? __ldcg(a.c_km1 + in.g) : T(0);
+            in.s = __ldcg(a.s + in.g);
+        };
+        auto finish = [&](const OpenIn<T>& in) {
+            // partial sums in ascending block order, as sum_partials adds them
+            T ku = add_rn(in.p[0], in.p[1]);
+            if (in.cnt > 2) ku = add_rn(ku, in.p[2]);
+            if (in.cnt > 3) ku = add_rn(ku, in.p[3]);
+            for (int t = 4; t < in.cnt; ++t) ku = add_rn(ku, __ldcg(a.part_rd + in.pb + t));
+            const T f = (in.g == a.src_gid) ? f_prev : T(0);
+            const Update<T, MODE> up = update_node<T, MODE>(in.u, in.x, in.c, in.s, f, ku);
+            su[in.pos] = up.u;
+            if (in.own) {
+                __stcg(a.u_kw + in.g, up.u);
                 if (KAHAN) {
-                    __stcg(a.x_kw + g, up.x);
-                    __stcg(a.c_kw + g, up.c);
-                    if (!direct) sc[pos] = up.c;  // for a receiver record (the owner's entries are staged)
+                    __stcg(a.x_kw + in.g, up.x);
+                    __stcg(a.c_kw + in.g, up.c);
+                    if (!direct) sc[in.pos] = up.c;  // for a receiver record (the owner's entries are staged)
                 }
             }
+        };
+        for (int o0 = tid; o0 < h.nopen; o0 += 2 * nt) {
+            const int o1 = o0 + nt;
+            OpenIn<T> in0, in1;
+            fetch(o0, in0);
+            if (o1 < h.nopen) fetch(o1, in1);
+            finish(in0);
+            if (o1 < h.nopen) finish(in1);
         }
     }
     cp_async_commit();
@@ -707,6 +746,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     step_block<NP, T, MODE>(s_pl, s_a, bs, ba.cta_block[blockIdx.x], smem_raw, s_a.step, s_a.pending);
 }
 
+#ifndef SEM_KERNEL_NP
 // After a batch step: every shot's step number advances and its open nodes
 // are pending from now on.
 __global__ void batch_advance_kernel(int64_t* step, int32_t* pending, int nshots) {
@@ -716,6 +756,7 @@ __global__ void batch_advance_kernel(int64_t* step, int32_t* pending, int nshots
         pending[i] = 1;
     }
 }
+#endif
 
 // ------------------------------------------------------- streamed time loop
 
@@ -733,9 +774,17 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int32_t* p) {
     return v;
 }
 
-// Polls of one done flag before a wait gives up (with the back-off below,
-// well over a second; a unit normally waits microseconds at most).
-constexpr int kWaitPolls = 1 << 21;
+// A wait gives up once it has lasted kWaitNs of the GPU's global timer
+// (read every 64 polls; a unit normally waits microseconds at most), or,
+// whatever the timer says, after kWaitPolls polls (each followed by a
+// 128 ns back-off, so at least 8.6 s of nominal sleep).
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr int kWaitPolls = 1 << 26;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
 
 // Unit (i, b) of a launch from its ticket offset u (0 <= u < total): step
 // order, or the band's wavefront order for the first tiled_units tickets.
@@ -752,30 +801,27 @@ __device__ __forceinline__ void unit_of(const StreamArgs& sa, int nb, long long 
     }
 }
 
-// Wait of unit (i, b) for step i-1 at b's neighbours (active when i > 0):
-// the threads poll one neighbour's done flag each (acquire), then the block
-// synchronises; a poll that gives up marks the unit failed.
-struct DepWait {
-    const StreamArgs* sa;
-    const int32_t* dep;   // the block's padded neighbour list (shared memory)
-    uint32_t need;
-    bool active;
-    int* fail;
-    __device__ __forceinline__ bool operator()() const {
-        if (!active) return true;
-        for (int t = (int)threadIdx.x; t < sa->dep_stride; t += (int)blockDim.x) {
-            const uint32_t* f = sa->done + dep[t];
-            for (int n = 0; (int32_t)(ld_acquire_gpu(f) - need) < 0; ++n) {
-                if (n >= kWaitPolls || ((n & 63) == 63 && ld_relaxed_gpu(sa->err) != 0)) {
-                    *fail = 1;
-                    break;
-                }
-                __nanosleep(128);
-            }
+// Bounded wait for one done flag: true once it reaches `need` (acquire,
+// GPU scope), false when the wait gave up or another unit raised the error
+// flag.
+__device__ __forceinline__ bool wait_flag(const uint32_t* f, uint32_t need, const int32_t* err) {
+    unsigned long long t0 = 0;
+    for (int n = 0; (int32_t)(ld_acquire_gpu(f) - need) < 0; ++n) {
+        if ((n & 63) == 63) {
+            const unsigned long long now = global_ns();
+            if (n == 63) t0 = now;
+            if (now - t0 > kWaitNs || n >= kWaitPolls || ld_relaxed_gpu(err) != 0) return false;
         }
-        __syncthreads();
-        return *fail == 0;
+        __nanosleep(128);
     }
+    return true;
+}
+
+// step_block's "ready" hook of a streamed unit: the neighbours were awaited
+// in the unit's prologue; a unit whose wait gave up stops here.
+struct PrologueWaited {
+    const int* fail;
+    __device__ __forceinline__ bool operator()() const { return *fail == 0; }
 };
 
 // Several steps of one mesh in one launch of nsteps * nblocks CTAs. Each
@@ -824,15 +870,25 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
             for (int q = 0; q < sa.dep_stride / 4; ++q) reinterpret_cast<int4*>(s_dep)[q] = dr[q];
         }
     }
+    // the neighbours' previous step, awaited by warp 0 (one flag per lane)
+    // before the unit issues any other load. Measured on the graded 512 x 512
+    // mesh: polling with the element data and packet loads already in flight
+    // took 5.6k cycles per unit against 1.1k here, so the early poll shortens
+    // the unit although the element loads now start one round trip later.
+    __syncwarp();
+    if (threadIdx.x < 32 && s_i > 0) {
+        const uint32_t need = sa.serial0 + (uint32_t)(s_i - 1);
+        bool ok = true;
+        for (int t = (int)threadIdx.x; t < sa.dep_stride; t += 32) ok = ok && wait_flag(sa.done + s_dep[t], need, sa.err);
+        if (!ok) s_fail = 1;
+    }
     __syncthreads();
     const int i = s_i;
     const int b = s_b;
     if (i < 0) return;
     const int64_t k = sa.step0 + i;
     const int pend = (i > 0 || sa.pending0) ? 1 : 0;
-    // the neighbours' previous step, awaited while the block's element data
-    // and packet are already on their way
-    const DepWait w{&sa, s_dep, sa.serial0 + (uint32_t)(i - 1), i > 0, &s_fail};
+    const PrologueWaited w{&s_fail};
     step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend, w, &s_h);
     // every thread's stores of the unit precede the flag: the barrier orders
     // them before thread 0's release store (release at GPU scope covers what
@@ -878,6 +934,7 @@ __global__ void __launch_bounds__(kThreads) sem_open_finish_kernel(const Plan pl
     }
 }
 
+#ifndef SEM_KERNEL_NP
 // ------------------------------------------------------------ precompute
 __global__ void geometry_kernel(int np, int64_t ne, const double* __restrict__ coords,
                                 const int32_t* __restrict__ quads, const double* __restrict__ rho,
@@ -926,6 +983,7 @@ __global__ void geometry_kernel(int np, int64_t ne, const double* __restrict__ c
         if (mloc != nullptr) mloc[t] = wq * det * rinv / (vel[e] * vel[e]);
     }
 }
+#endif
 
 // Lumped mass through the block plan: the same colour-ordered scatter as the
 // step kernel, in FP64, of w_q |J_q| / (rho c^2) per slot (mloc, device
@@ -968,6 +1026,7 @@ __global__ void __launch_bounds__(kMaxStepThreads) mass_block_kernel(const Plan 
     for (int o = tid; o < h.nopen; o += nt) partial[obase[o] + orank[o]] = acc[opos[o]];
 }
 
+#ifndef SEM_KERNEL_NP
 __global__ void mass_open_kernel(const Plan pl, const double* __restrict__ partial, double* M) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pl.nopen_nodes; k += gridDim.x * blockDim.x) {
         double acc = 0.0;
@@ -1035,6 +1094,7 @@ int grid_for(int64_t n, int threads) {
     if (g > 152 * 64) g = 152 * 64;
     return (int)g;
 }
+#endif
 
 }  // namespace
 
