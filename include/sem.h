@@ -100,6 +100,19 @@ typedef enum {
 
 typedef enum { SEM_SRC_RICKER = 0 } sem_source_kind;
 
+/* Where the FP32 kernels take the per-point geometric factors G_q of Eq.
+ * deriv_u from (SEM_FP64 always streams its FP64 copy). Both start from the
+ * FP64 precompute of Section 4.2's "precalculate" step: */
+typedef enum {
+    SEM_METRIC_BILINEAR = 0, /* the default: the FP64-derived bilinear map of
+                                each element (b, c, d and 1/rho, 32 B per element),
+                                rounded to FP32 once; G_q is formed from it in FP32
+                                at every point of every step                      */
+    SEM_METRIC_STORED = 1    /* G_q computed in FP64 and rounded to FP32 once,
+                                stored [3P][ne] and streamed every step (12 B per
+                                GLL point)                                        */
+} sem_metric;
+
 typedef enum {
     SEM_SCHEME_LEAPFROG = 0, /* second-order form M u_tt = f e_s - K u, leapfrog
                                 (the default; see sem_precision)                 */
@@ -179,6 +192,24 @@ sem_status sem_cfl_dt(const sem_mesh* m, double* dt_cfl);
  * zeros), sem_set_state sets U and V = 0 (u_prev is ignored); the batched and
  * adjoint calls are leapfrog-only (SEM_ERR_STATE / SEM_ERR_UNSUPPORTED). */
 sem_status sem_set_scheme(sem_mesh* m, int scheme);
+
+/* Metric source of the FP32 kernels (sem_metric), before the device data is
+ * built. SEM_METRIC_STORED on an SEM_FP64 handle is a no-op (FP64 always
+ * stores); with SEM_SCHEME_HEUN it returns SEM_ERR_UNSUPPORTED, and so does
+ * sem_set_scheme(SEM_SCHEME_HEUN) after it; handles with a stored FP32 metric
+ * cannot join a batch (sem_batch_create returns SEM_ERR_UNSUPPORTED). After
+ * the build: SEM_ERR_STATE. (The paper precalculates its geometric factors,
+ * Section 4.2; this call chooses the FP32 copy the step streams.) */
+sem_status sem_set_metric(sem_mesh* m, int metric);
+
+/* The geometric factors G_q = w_q |J_q| / rho_e J_q^-1 J_q^-T (Eq. deriv_u,
+ * with the quadrature weight of Eq. numerical_integ) exactly as the step
+ * kernels use them: G[e][q][3] = (gxx, gxy, gyy) for every element e
+ * (original order) and GLL point q = j (p+1) + i, in FP64. SEM_FP64 and
+ * SEM_METRIC_STORED: the stored values; SEM_METRIC_BILINEAR: the FP32 values
+ * the kernels form from the bilinear map, by the same device code. Builds the
+ * device data if needed (needs the model); synchronises. */
+sem_status sem_read_metric(sem_mesh* m, double* G);
 
 /* Time step dt > 0 (values above sem_cfl_dt are accepted; stability is the
  * caller's business). Before the first step only. */
@@ -426,31 +457,49 @@ sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void*
  *                   be destroyed before any of them.
  *   autotune_steps  0: keep each handle's block size. > 0: for each order, the
  *                   not yet built handle whose element count is closest to
- *                   65,536 is timed for this many steps with each candidate
- *                   elements-per-block (48..256), and every
+ *                   65,536 is timed for this many steps (20 or more give
+ *                   stable choices) with each candidate elements-per-block
+ *                   (48..256; the threads of a block follow: one per element,
+ *                   whole warps), as one streamed launch where the handle can
+ *                   stream (the way a streamed batch runs it), and every
  *                   not yet built handle of that order without its own
  *                   sem_set_tuning uses the fastest (the timed handle is then
  *                   rebuilt from its initial state).
  * Returns SEM_ERR_STATE if a handle lacks model or dt or the precisions or
- * streams differ. */
+ * streams differ, SEM_ERR_UNSUPPORTED for a handle with a stored FP32 metric
+ * (sem_set_metric). */
 typedef struct sem_batch sem_batch;
 sem_status sem_batch_create(sem_mesh* const* shots, int32_t nshots, int32_t autotune_steps, sem_batch** out);
 
-/* Advance every shot nsteps leapfrog steps. Each step is one launch per
- * polynomial order present (CTAs over the element blocks of all shots of
- * that order) plus a step-counter update; a block of 16 steps is captured
- * once as a CUDA graph and replayed, the remainder launched directly; after
+/* Advance every shot nsteps leapfrog steps. Streamed batch (every shot on a
+ * DENSE plan with at most 16 neighbour blocks per block, as Hilbert and
+ * row-major orderings give): per polynomial order present, one launch runs a
+ * block of 64 steps over the element blocks of all shots of that order, one
+ * CTA per (step, block) unit taken from a work counter, each unit waiting
+ * (bounded) for the previous step at the blocks of its own shot that share a
+ * node with it (as sem_set_stream does for one mesh); the launches of all
+ * orders and the clock update after them are captured once as a CUDA graph
+ * and replayed, the remainder launched directly. Otherwise each step is one
+ * launch per order plus a step-counter update, with a 16-step graph. After
  * the last step each shot's open nodes are completed as by sem_step. The
  * first call builds the shots' device data. Results equal those of sem_step
- * on each handle with the same block size, bit for bit. Asynchronous on the
- * stream. */
+ * on each handle with the same block size, bit for bit. A streamed wait that
+ * gives up (which no correct run does) makes the call return
+ * SEM_ERR_TIMEOUT. Synchronises the stream at the start (state upload) and
+ * at the end of a streamed call (its error flag). */
 sem_status sem_batch_step(sem_batch* b, int64_t nsteps);
 
 /* After the first sem_batch_step: number of order classes, and per class its
- * polynomial order, elements per block (the largest in the class) and CTAs
- * per step launch (any output may be NULL; arrays hold nclasses entries). */
+ * polynomial order, elements per block (the largest in the class) and element
+ * blocks per step (the CTAs of one step; any output may be NULL; arrays hold
+ * nclasses entries). */
 sem_status sem_batch_info(const sem_batch* b, int32_t* nclasses, int32_t* orders, int32_t* elems_per_block,
                           int32_t* ctas);
+
+/* After the first sem_batch_step: streamed = 1 when the batch runs streamed
+ * launches (see sem_batch_step), else 0; steps_per_launch = the steps of one
+ * streamed launch (1 otherwise). Either output may be NULL. */
+sem_status sem_batch_mode(const sem_batch* b, int32_t* streamed, int32_t* steps_per_launch);
 
 /* Message of the last failing batch call ("" if none). Never NULL. */
 const char* sem_batch_last_error(const sem_batch* b);

@@ -27,6 +27,8 @@ SEM_ORDER_CONNECTIVITY, SEM_ORDER_DISTANCE, SEM_ORDER_HILBERT_WIDE = 4, 5, 6
 SEM_SRC_RICKER = 0
 SEM_SCHEME_LEAPFROG, SEM_SCHEME_HEUN = 0, 1
 SCHEMES = {"leapfrog": SEM_SCHEME_LEAPFROG, "heun": SEM_SCHEME_HEUN}
+SEM_METRIC_BILINEAR, SEM_METRIC_STORED = 0, 1
+METRICS = {"bilinear": SEM_METRIC_BILINEAR, "stored": SEM_METRIC_STORED}
 PRECISIONS = {"fp64": SEM_FP64, "fp32_kahan": SEM_FP32_KAHAN, "fp32": SEM_FP32}
 ORDERINGS = {"none": SEM_ORDER_NONE, "rowmajor": SEM_ORDER_ROWMAJOR, "random": SEM_ORDER_RANDOM,
              "hilbert": SEM_ORDER_HILBERT, "connectivity": SEM_ORDER_CONNECTIVITY, "distance": SEM_ORDER_DISTANCE,
@@ -36,7 +38,7 @@ DEFAULT_SEED = 2104084160
 # every symbol include/sem.h declares
 EXPORTS = (
     "sem_set_allocator", "sem_mesh_create", "sem_reorder", "sem_set_model", "sem_set_source",
-    "sem_set_receivers", "sem_cfl_dt", "sem_set_scheme", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
+    "sem_set_receivers", "sem_cfl_dt", "sem_set_scheme", "sem_set_metric", "sem_read_metric", "sem_set_dt", "sem_step", "sem_get_step", "sem_read_traces",
     "sem_read_wavefield", "sem_set_state", "sem_get_state", "sem_apply_stiffness", "sem_read_mass",
     "sem_get_permutation", "sem_get_sizes", "sem_node_coordinates", "sem_get_snapped",
     "sem_compute_ordering", "sem_count_nodes", "sem_hilbert_cells", "sem_plan_check", "sem_launch_info", "sem_set_stream", "sem_set_stream_tiling",
@@ -44,7 +46,7 @@ EXPORTS = (
     "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
     "sem_apply_stiffness_dev_noalloc", "sem_misfit_gradient", "sem_batch_create", "sem_batch_step", "sem_batch_info",
-    "sem_batch_last_error", "sem_batch_destroy", "sem_last_error", "sem_destroy",
+    "sem_batch_mode", "sem_batch_last_error", "sem_batch_destroy", "sem_last_error", "sem_destroy",
 )
 
 _lib = None
@@ -81,6 +83,8 @@ def load(path: str | None = None):
         "sem_cfl_dt": (_P, _D),
         "sem_set_dt": (_P, C.c_double),
         "sem_set_scheme": (_P, C.c_int),
+        "sem_set_metric": (_P, C.c_int),
+        "sem_read_metric": (_P, _D),
         "sem_step": (_P, C.c_int64),
         "sem_get_step": (_P, _I64),
         "sem_read_traces": (_P, _D, C.c_int64),
@@ -114,6 +118,7 @@ def load(path: str | None = None):
         "sem_batch_create": (C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(_P)),
         "sem_batch_step": (_P, C.c_int64),
         "sem_batch_info": (_P, _I32, _I32, _I32, _I32),
+        "sem_batch_mode": (_P, _I32, _I32),
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -296,6 +301,19 @@ class SEM:
         scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self._c(self._lib.sem_set_scheme(self.h, scheme))
 
+    def sem_set_metric(self, metric):
+        """'bilinear' (FP32 metric formed per point from the bilinear map) or
+        'stored' (FP64-computed metric rounded once to FP32 and streamed)."""
+        metric = METRICS[metric] if isinstance(metric, str) else int(metric)
+        self._c(self._lib.sem_set_metric(self.h, metric))
+
+    def sem_read_metric(self) -> np.ndarray:
+        """(E, P, 3) array of (gxx, gxy, gyy) per element (original order) and
+        GLL point, as the step kernels use them."""
+        out = np.zeros((self.n_elems, (self.order + 1) ** 2, 3))
+        self._c(self._lib.sem_read_metric(self.h, _ptr(out, C.c_double)))
+        return out
+
     def sem_set_dt(self, dt: float):
         self._c(self._lib.sem_set_dt(self.h, float(dt)))
 
@@ -458,6 +476,11 @@ class SEMBatch:
 
     def sem_batch_step(self, nsteps: int):
         self._c(self._lib.sem_batch_step(self.h, int(nsteps)))
+
+    def sem_batch_mode(self):
+        st, spl = C.c_int32(), C.c_int32()
+        self._c(self._lib.sem_batch_mode(self.h, C.byref(st), C.byref(spl)))
+        return {"streamed": bool(st.value), "steps_per_launch": spl.value}
 
     def sem_batch_info(self):
         n = C.c_int32()

@@ -109,6 +109,9 @@ struct sem_mesh {
     double* d_vel = nullptr;
     uint8_t* d_packet = nullptr;
     double* d_G64 = nullptr;
+    float* d_G32 = nullptr;       // stored FP32 metric (SEM_METRIC_STORED)
+    double* d_metric_out = nullptr;   // sem_read_metric's output buffer
+    int metric = SEM_METRIC_BILINEAR;
     double* d_coef64 = nullptr;   // FP64 bilinear map (first-order system, FP64)
     void* d_v[2] = {nullptr, nullptr};   // first-order system: V, V~ ([2P][ne])
     void* d_vd1 = nullptr;               // predictor rate of V
@@ -138,6 +141,8 @@ struct sem_mesh {
     int32_t* d_conn_dev = nullptr;
     int32_t* d_rec_node = nullptr;
     int32_t* d_rec_row = nullptr;
+    int32_t* d_rec_order = nullptr;   // receivers sorted by (node, index)
+    int32_t* d_rec_first = nullptr;   // [nn]: first of a node's receivers in d_rec_order, or -1
     std::vector<void*> d_chk;   // per checkpoint: u^{n0}, u^{n0-1}
     std::vector<void*> d_seg;   // recomputed states of one segment
     // measurement
@@ -446,6 +451,7 @@ sem_status build(sem_mesh* m) {
     dp.epos = epos;
     dp.coef = nullptr;
     dp.G = nullptr;
+    dp.G32 = nullptr;
     dp.open_gid = open_gid;
     dp.open_base = open_base;
     dp.open_cnt = open_cnt;
@@ -486,6 +492,11 @@ sem_status build(sem_mesh* m) {
         coef = (float4*)dev_alloc(m, (size_t)M.ne * 2 * sizeof(float4));
         if (!coef) return fail(m, SEM_ERR_OOM, "device allocation failed");
         dp.coef = coef;
+        if (m->metric == SEM_METRIC_STORED) {
+            m->d_G32 = (float*)dev_alloc(m, nslot * 3 * 4);
+            if (!m->d_G32) return fail(m, SEM_ERR_OOM, "device allocation failed");
+            dp.G32 = m->d_G32;
+        }
     }
     if (m->scheme == SEM_SCHEME_HEUN && fp64(m)) {
         m->d_coef64 = (double*)dev_alloc(m, (size_t)M.ne * 8 * 8);
@@ -493,7 +504,7 @@ sem_status build(sem_mesh* m) {
         dp.coef64 = m->d_coef64;
     }
     SEM_CUDA(semdev::launch_geometry(M.np, M.ne, m->d_coords, m->d_quads, m->d_rho, m->d_vel, m->basis64, coef,
-                                     m->d_G64, m->d_mloc, m->d_coef64, m->stream));
+                                     m->d_G64, m->d_mloc, m->d_coef64, m->d_G32, m->stream));
     SEM_CUDA(semdev::launch_mass(dp, M.np, m->d_mloc, (double*)m->d_part[0], m->d_M, m->stream));
 
     // time-stepping state
@@ -549,7 +560,7 @@ sem_status build(sem_mesh* m) {
         m->d_err = (int32_t*)er;
         m->serial = 1;
         int res = 0;
-        SEM_CUDA(semdev::stream_resident_ctas(M.np, fp64(m), md, m->threads, m->smem, &res));
+        SEM_CUDA(semdev::stream_resident_ctas(M.np, fp64(m), md, m->d_G32 != nullptr, m->threads, m->smem, &res));
         m->resident_ctas = res;
         m->stream_ok = res > 0;
     }
@@ -584,7 +595,8 @@ sem_status refresh_model(sem_mesh* m) {
     SEM_CUDA(cudaMemcpyAsync(m->d_vel, vd.data(), vd.size() * 8, cudaMemcpyHostToDevice, m->stream));
     m->h2d += (int64_t)(rd.size() + vd.size()) * 8;
     SEM_CUDA(semdev::launch_geometry(m->mesh.np, m->mesh.ne, m->d_coords, m->d_quads, m->d_rho, m->d_vel, m->basis64,
-                                     const_cast<float4*>(m->dplan.coef), m->d_G64, m->d_mloc, m->d_coef64, m->stream));
+                                     const_cast<float4*>(m->dplan.coef), m->d_G64, m->d_mloc, m->d_coef64, m->d_G32,
+                                     m->stream));
     SEM_CUDA(semdev::launch_mass(m->dplan, m->mesh.np, m->d_mloc, (double*)m->d_part[0], m->d_M, m->stream));
     if (m->have_dt)
         SEM_CUDA(semdev::launch_scale(m->d_M, m->mesh.nn, scale_numerator(m), fp64(m) ? (double*)m->d_s : nullptr,
@@ -1130,7 +1142,66 @@ sem_status sem_set_scheme(sem_mesh* m, int scheme) {
     if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_scheme after the device data was built");
     if (scheme == SEM_SCHEME_HEUN && m->prec == SEM_FP32_KAHAN)
         return fail(m, SEM_ERR_UNSUPPORTED, "the first-order scheme runs on SEM_FP64 or SEM_FP32");
+    if (scheme == SEM_SCHEME_HEUN && m->metric == SEM_METRIC_STORED && !fp64(m))
+        return fail(m, SEM_ERR_UNSUPPORTED, "the first-order scheme forms its FP32 metric from the bilinear map");
     m->scheme = scheme;
+    return SEM_OK;
+}
+
+sem_status sem_set_metric(sem_mesh* m, int metric) {
+    if (!m) return SEM_ERR_INVALID_ARG;
+    if (metric != SEM_METRIC_BILINEAR && metric != SEM_METRIC_STORED)
+        return fail(m, SEM_ERR_INVALID_ARG, "unknown metric source");
+    if (!before_first_step(m)) return fail(m, SEM_ERR_STATE, "sem_set_metric after the device data was built");
+    if (fp64(m)) return SEM_OK;
+    if (metric == SEM_METRIC_STORED && m->scheme == SEM_SCHEME_HEUN)
+        return fail(m, SEM_ERR_UNSUPPORTED, "the first-order scheme forms its FP32 metric from the bilinear map");
+    m->metric = metric;
+    return SEM_OK;
+}
+
+sem_status sem_read_metric(sem_mesh* m, double* G) {
+    if (!m || !G) return SEM_ERR_INVALID_ARG;
+    if (!m->have_model) return fail(m, SEM_ERR_STATE, "sem_set_model must come first");
+    sem_status st = build(m);
+    if (st != SEM_OK) return st;
+    const int64_t ne = m->mesh.ne;
+    const int P = m->mesh.P;
+    const size_t nslot = (size_t)ne * (size_t)P;
+    std::vector<double> g(nslot * 3);   // [dev element][q][3]
+    if (fp64(m) || m->d_G32) {
+        // stored [3P][ne], element-fastest
+        std::vector<double> raw(nslot * 3);
+        if (fp64(m)) {
+            SEM_CUDA(cudaMemcpyAsync(raw.data(), m->d_G64, raw.size() * 8, cudaMemcpyDeviceToHost, m->stream));
+            m->d2h += (int64_t)(raw.size() * 8);
+        } else {
+            std::vector<float> r32(nslot * 3);
+            SEM_CUDA(cudaMemcpyAsync(r32.data(), m->d_G32, r32.size() * 4, cudaMemcpyDeviceToHost, m->stream));
+            m->d2h += (int64_t)(r32.size() * 4);
+            SEM_CUDA(cudaStreamSynchronize(m->stream));
+            for (size_t k = 0; k < raw.size(); ++k) raw[k] = (double)r32[k];
+        }
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+        for (int64_t e = 0; e < ne; ++e)
+            for (int q = 0; q < P; ++q)
+                for (int c = 0; c < 3; ++c)
+                    g[((size_t)e * P + q) * 3 + c] = raw[((size_t)c * P + q) * (size_t)ne + (size_t)e];
+    } else {
+        if (!m->d_metric_out) {
+            m->d_metric_out = (double*)dev_alloc(m, nslot * 3 * 8);
+            if (!m->d_metric_out) return fail(m, SEM_ERR_OOM, "device allocation failed");
+        }
+        SEM_CUDA(semdev::launch_metric_fp32(m->mesh.np, m->dplan, m->basis32, m->d_metric_out, m->stream));
+        SEM_CUDA(cudaMemcpyAsync(g.data(), m->d_metric_out, g.size() * 8, cudaMemcpyDeviceToHost, m->stream));
+        m->d2h += (int64_t)(g.size() * 8);
+        SEM_CUDA(cudaStreamSynchronize(m->stream));
+    }
+    // device element i is original element elem_order[dev_order[i]]
+    for (int64_t i = 0; i < ne; ++i) {
+        const int64_t eo = m->elem_order[(size_t)m->plan.dev_order[(size_t)i]];
+        std::copy(g.begin() + (size_t)i * P * 3, g.begin() + (size_t)(i + 1) * P * 3, G + (size_t)eo * P * 3);
+    }
     return SEM_OK;
 }
 
@@ -1687,6 +1758,15 @@ sem_status adjoint_alloc(sem_mesh* m, int64_t nsteps, int64_t kc) {
         }
         SEM_CUDA(cudaMemcpyAsync(m->d_rec_node, rn.data(), rn.size() * 4, cudaMemcpyHostToDevice, m->stream));
         SEM_CUDA(cudaMemcpyAsync(m->d_rec_row, rr.data(), rr.size() * 4, cudaMemcpyHostToDevice, m->stream));
+        // receivers sorted by (node, index), and per node the first of them
+        std::vector<int32_t> order((size_t)m->nrec), first((size_t)m->mesh.nn, -1);
+        for (int32_t r = 0; r < m->nrec; ++r) order[(size_t)r] = r;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return rn[(size_t)a] < rn[(size_t)b]; });
+        for (int32_t k = m->nrec - 1; k >= 0; --k) first[(size_t)rn[(size_t)order[(size_t)k]]] = k;
+        if (order.empty()) order.push_back(0);   // never read (no receivers), keeps the upload non-empty
+        if ((st = upload(m, &m->d_rec_order, order.data(), order.size())) != SEM_OK) return st;
+        if ((st = upload(m, &m->d_rec_first, first.data(), first.size())) != SEM_OK) return st;
         SEM_CUDA(cudaStreamSynchronize(m->stream));
     }
     if (nsteps > m->adj_steps || kc != m->adj_kc) {
@@ -1790,15 +1870,14 @@ sem_status sem_misfit_gradient(sem_mesh* m, const double* d_obs, int64_t nsteps,
         auto u_at = [&](int64_t k) -> const void* {
             return k >= n0 ? m->d_seg[(size_t)(k - n0)] : m->d_chk[(size_t)(2 * c + 1)];
         };
+        // per backward step: K lambda (step kernel in apply mode and the
+        // open-node kernel), then one fused node pass
         for (int64_t mm = n1; mm > n0; --mm) {
             if ((st = launch_apply(m, lam(mm + 1), m->d_klam, m->d_part[0])) != SEM_OK) return st;
-            SEM_CUDA(semdev::launch_adjoint_update(f64, m->mesh.nn, lam(mm), lam(mm + 1), lam(mm + 2), m->d_s, m->d_klam,
-                                                   m->stream));
-            SEM_CUDA(semdev::launch_adjoint_receivers(f64, m->nrec, lam(mm), m->d_s, m->d_rec_node, m->d_rec_row,
-                                                      m->d_trace, m->trace_cap, m->d_obs, nsteps, mm, inv_dt,
-                                                      m->stream));
-            SEM_CUDA(semdev::launch_correlate(f64, m->mesh.nn, m->d_C, lam(mm), u_at(mm), u_at(mm - 1), u_at(mm - 2),
-                                              m->stream));
+            SEM_CUDA(semdev::launch_adjoint_node(f64, m->mesh.nn, lam(mm), lam(mm + 1), lam(mm + 2), m->d_s, m->d_klam,
+                                                 m->d_rec_first, m->d_rec_order, m->nrec, m->d_rec_node, m->d_rec_row,
+                                                 m->d_trace, m->trace_cap, m->d_obs, nsteps, mm, inv_dt, m->d_C,
+                                                 u_at(mm), u_at(mm - 1), u_at(mm - 2), m->stream));
         }
     }
     SEM_CUDA(semdev::launch_gradient(m->mesh.ne, m->mesh.P, m->d_conn_dev, m->d_mloc, m->d_C, m->d_vel, m->d_grad,
@@ -1877,8 +1956,21 @@ struct sem_batch {
         int eb = 0;
         int32_t* d_cta_shot = nullptr;
         int32_t* d_cta_block = nullptr;
+        // streamed batch: one record per block of the class's shots, and
+        // the class launch's work counter
+        semdev::BatchUnit* d_units = nullptr;
+        unsigned long long* d_counter = nullptr;
     };
     std::vector<Class> classes;
+    // streamed batch (every shot streamable): each order class runs a block
+    // of steps as one launch over the blocks of all its shots
+    bool streamed = false;
+    int stream_steps = 64;                 // steps per streamed launch (one graph replay)
+    semdev::ShotClock* d_clock = nullptr;  // [nshots]
+    uint32_t** d_done = nullptr;           // [nshots]: each shot's done flags
+    uint32_t* d_serial = nullptr;          // serial of the next launch's first step
+    int32_t* d_err = nullptr;
+    uint32_t serial = 1;
     void* d_desc = nullptr;
     size_t desc_bytes = 0;
     int64_t* d_step = nullptr;
@@ -1887,6 +1979,7 @@ struct sem_batch {
     bool ready = false;
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t sgraph = nullptr;      // one streamed block of stream_steps steps
 };
 
 namespace {
@@ -1910,6 +2003,20 @@ void* balloc(sem_batch* b, size_t bytes) {
 // autotuner); the handle's settings stay.
 void unbuild(sem_mesh* m) {
     dev_free_all(m);
+    m->d_G32 = nullptr;
+    m->d_metric_out = nullptr;
+    // adjoint buffers went with the rest: the next sem_misfit_gradient
+    // allocates them again
+    m->adj_steps = m->adj_kc = 0;
+    for (auto& l : m->d_lam) l = nullptr;
+    m->d_klam = nullptr;
+    m->d_C = nullptr;
+    m->d_obs = nullptr;
+    m->d_grad = nullptr;
+    m->d_conn_dev = nullptr;
+    m->d_rec_node = m->d_rec_row = m->d_rec_order = m->d_rec_first = nullptr;
+    m->d_chk.clear();
+    m->d_seg.clear();
     m->built = false;
     m->step = 0;
     m->d_src = nullptr;
@@ -1950,13 +2057,20 @@ sem_status upload_desc(sem_batch* b) {
     return SEM_OK;
 }
 
-// Time per step of one handle (after two warm-up steps), in ms.
+// Time per step of one handle (after two warm-up steps), in ms: one
+// streamed launch of `steps` steps where the handle can stream (the way a
+// streamed batch runs it), else one launch per step.
 sem_status time_handle(sem_mesh* m, int steps, double* ms) {
     sem_status st;
     if ((st = build(m)) != SEM_OK) return st;
     if ((st = fill_source(m, steps + 2)) != SEM_OK) return st;
-    for (int k = 0; k < 2; ++k)
-        if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+    const bool stream = m->stream_ok && m->dep_stride <= 16;
+    if (stream) {
+        if ((st = launch_stream_steps(m, 2, false)) != SEM_OK) return st;
+    } else {
+        for (int k = 0; k < 2; ++k)
+            if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return fail(m, SEM_ERR_CUDA, "event");
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1964,8 +2078,12 @@ sem_status time_handle(sem_mesh* m, int steps, double* ms) {
         return fail(m, SEM_ERR_CUDA, "event");
     }
     cudaEventRecord(e0, m->stream);
-    for (int k = 0; k < steps; ++k)
-        if ((st = launch_one_step(m, true)) != SEM_OK) break;
+    if (stream) {
+        st = launch_stream_steps(m, steps, true);
+    } else {
+        for (int k = 0; k < steps; ++k)
+            if ((st = launch_one_step(m, true)) != SEM_OK) break;
+    }
     cudaEventRecord(e1, m->stream);
     float t = 0.f;
     if (st == SEM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
@@ -1995,6 +2113,92 @@ sem_status batch_launch_step(sem_batch* b) {
     cudaError_t e = semdev::launch_batch_advance(b->d_step, b->d_pending, (int)b->shots.size(), b->run);
     if (e != cudaSuccess) return bfail(b, SEM_ERR_CUDA, std::string("batch advance: ") + cudaGetErrorString(e));
     return SEM_OK;
+}
+
+// Streamed launches of n steps: every order class as one launch over the
+// blocks of its shots, then the shots' clocks and the batch serial advance.
+sem_status batch_launch_stream(sem_batch* b, int n) {
+    const bool f64 = b->prec == SEM_FP64;
+    const int mode = b->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
+    for (auto& c : b->classes) {
+        semdev::BatchStreamArgs sa{};
+        sa.shots = b->d_desc;
+        sa.units = c.d_units;
+        sa.clock = b->d_clock;
+        sa.done = b->d_done;
+        sa.serial0 = b->d_serial;
+        sa.counter = c.d_counter;
+        sa.err = b->d_err;
+        sa.nblk = c.ctas;
+        sa.nsteps = n;
+        const sem_mesh* m0 = nullptr;
+        for (auto* m : b->shots)
+            if (m->mesh.np == c.np) {
+                m0 = m;
+                break;
+            }
+        const void* basis = f64 ? (const void*)&m0->basis64 : (const void*)&m0->basis32;
+        if (cudaMemsetAsync(c.d_counter, 0, 8, b->run) != cudaSuccess)
+            return bfail(b, SEM_ERR_CUDA, "work counter reset failed");
+        cudaError_t e = semdev::launch_batch_stream(c.np, f64, mode, false, sa, basis, c.threads, c.smem, b->run);
+        if (e != cudaSuccess)
+            return bfail(b, SEM_ERR_CUDA, std::string("streamed batch launch: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = semdev::launch_batch_clock_advance(b->d_clock, (int)b->shots.size(), b->d_serial, n, b->run);
+    if (e != cudaSuccess) return bfail(b, SEM_ERR_CUDA, std::string("batch clock advance: ") + cudaGetErrorString(e));
+    return SEM_OK;
+}
+
+// Device records of a streamed batch (after the shots are built): per class
+// one BatchUnit per block of its shots, the clocks, done-flag table, serial
+// and error flag. Falls back to one launch per class and step (returns
+// false) when a shot cannot stream.
+bool batch_prepare_stream(sem_batch* b) {
+    for (auto* m : b->shots)
+        if (!m->stream_ok || m->dep_stride > 16) return false;
+    const bool f64 = b->prec == SEM_FP64;
+    const int mode = b->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
+    for (auto& c : b->classes) {
+        std::vector<semdev::BatchUnit> units;
+        for (size_t i = 0; i < b->shots.size(); ++i) {
+            const sem_mesh* m = b->shots[i];
+            if (m->mesh.np != c.np) continue;
+            const auto& pl = m->plan;
+            for (int64_t k = 0; k < pl.nblocks; ++k) {
+                semdev::BatchUnit u{};
+                for (int f = 0; f < 12; ++f) u.hdr[f] = pl.hdr[(size_t)k * 12 + f];
+                u.shot = (int32_t)i;
+                u.block = (int32_t)k;
+                u.dep_stride = m->dep_stride;
+                for (int t = 0; t < 16; ++t) {
+                    const int32_t q = pl.dep_ptr[(size_t)k] + t;
+                    u.dep[t] = (t < m->dep_stride && q < pl.dep_ptr[(size_t)k + 1]) ? pl.dep[(size_t)q] : (int32_t)k;
+                }
+                units.push_back(u);
+            }
+        }
+        c.d_units = (semdev::BatchUnit*)balloc(b, units.size() * sizeof(semdev::BatchUnit));
+        c.d_counter = (unsigned long long*)balloc(b, 8);
+        if (!c.d_units || !c.d_counter) return false;
+        if (cudaMemcpy(c.d_units, units.data(), units.size() * sizeof(semdev::BatchUnit), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return false;
+        semdev::BatchStreamArgs none{};
+        if (semdev::launch_batch_stream(c.np, f64, mode, true, none, nullptr, c.threads, c.smem, b->run) != cudaSuccess)
+            return false;
+    }
+    const size_t n = b->shots.size();
+    b->d_clock = (semdev::ShotClock*)balloc(b, n * sizeof(semdev::ShotClock));
+    b->d_done = (uint32_t**)balloc(b, n * sizeof(uint32_t*));
+    b->d_serial = (uint32_t*)balloc(b, 4);
+    b->d_err = (int32_t*)balloc(b, 4);
+    if (!b->d_clock || !b->d_done || !b->d_serial || !b->d_err) return false;
+    std::vector<uint32_t*> done(n);
+    for (size_t i = 0; i < n; ++i) done[i] = b->shots[i]->d_done;
+    if (cudaMemcpy(b->d_done, done.data(), n * sizeof(uint32_t*), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_err, 0, 4) != cudaSuccess)
+        return false;
+    return true;
 }
 
 sem_status batch_prepare(sem_batch* b) {
@@ -2055,11 +2259,80 @@ sem_status batch_prepare(sem_batch* b) {
     b->d_step = (int64_t*)balloc(b, b->shots.size() * 8);
     b->d_pending = (int32_t*)balloc(b, b->shots.size() * 4);
     if (!b->d_step || !b->d_pending) return bfail(b, SEM_ERR_OOM, "device allocation failed");
+    b->streamed = batch_prepare_stream(b);
+    cudaGetLastError();
     b->ready = true;
     return SEM_OK;
 }
 
 }  // namespace
+
+// sem_batch_step of a streamed batch: each shot's done flags restart from
+// zero and the batch serial from 1, the clocks start at the shots' steps;
+// blocks of stream_steps steps replay one captured graph (per class: reset
+// of the work counter, one streamed launch; then the clock advance), the
+// remainder is launched directly; then the open nodes of every shot.
+sem_status batch_step_streamed(sem_batch* b, int64_t nsteps) {
+    sem_status st;
+    const size_t n = b->shots.size();
+    std::vector<semdev::ShotClock> clk(n);
+    for (size_t i = 0; i < n; ++i) {
+        sem_mesh* m = b->shots[i];
+        clk[i].step0 = m->step;
+        clk[i].pending0 = 0;
+        if (cudaMemsetAsync(m->d_done, 0, (size_t)m->plan.nblocks * 4, b->run) != cudaSuccess)
+            return bfail(b, SEM_ERR_CUDA, "done flags reset failed");
+    }
+    b->serial = 1;
+    if (cudaMemcpyAsync(b->d_clock, clk.data(), n * sizeof(semdev::ShotClock), cudaMemcpyHostToDevice, b->run) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->d_serial, &b->serial, 4, cudaMemcpyHostToDevice, b->run) != cudaSuccess ||
+        cudaStreamSynchronize(b->run) != cudaSuccess)
+        return bfail(b, SEM_ERR_CUDA, "batch clock upload failed");
+    const int G = b->stream_steps;
+    int64_t done = 0;
+    if (nsteps >= G) {
+        if (!b->sgraph) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(b->run, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return bfail(b, SEM_ERR_CUDA, "graph capture begin failed");
+            const sem_status cst = batch_launch_stream(b, G);
+            const cudaError_t ce = cudaStreamEndCapture(b->run, &g);
+            if (cst != SEM_OK) {
+                if (g) cudaGraphDestroy(g);
+                return cst;
+            }
+            if (ce != cudaSuccess) return bfail(b, SEM_ERR_CUDA, "graph capture failed");
+            const cudaError_t ie = cudaGraphInstantiate(&b->sgraph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                b->sgraph = nullptr;
+                return bfail(b, SEM_ERR_CUDA, "graph instantiation failed");
+            }
+        }
+        for (; done + G <= nsteps; done += G)
+            if (cudaGraphLaunch(b->sgraph, b->run) != cudaSuccess) return bfail(b, SEM_ERR_CUDA, "graph launch failed");
+    }
+    if (done < nsteps && (st = batch_launch_stream(b, (int)(nsteps - done))) != SEM_OK) return st;
+    // a bounded wait that gave up: reported once, flag cleared
+    int32_t raised = 0;
+    if (cudaMemcpyAsync(&raised, b->d_err, 4, cudaMemcpyDeviceToHost, b->run) != cudaSuccess ||
+        cudaStreamSynchronize(b->run) != cudaSuccess)
+        return bfail(b, SEM_ERR_CUDA, "batch error flag read failed");
+    b->serial = (uint32_t)(1 + nsteps);
+    for (auto* m : b->shots) {
+        m->step += nsteps;
+        m->serial = b->serial;
+        if ((st = launch_flush(m)) != SEM_OK) return bfail(b, st, m->err);
+        m->stepped_calls++;
+    }
+    if (raised) {
+        cudaMemsetAsync(b->d_err, 0, 4, b->run);
+        cudaStreamSynchronize(b->run);
+        return bfail(b, SEM_ERR_TIMEOUT, "a streamed batch step gave up waiting for a neighbouring block");
+    }
+    return SEM_OK;
+}
 
 extern "C" {
 
@@ -2089,6 +2362,10 @@ sem_status sem_batch_create(sem_mesh* const* shots, int32_t nshots, int32_t auto
             m->scheme != SEM_SCHEME_LEAPFROG) {
             delete b;
             return SEM_ERR_STATE;
+        }
+        if (m->metric == SEM_METRIC_STORED) {
+            delete b;
+            return SEM_ERR_UNSUPPORTED;
         }
     }
     // autotuner: per order, the not yet built shot whose element count is
@@ -2137,6 +2414,7 @@ sem_status sem_batch_step(sem_batch* b, int64_t nsteps) {
     }
     if ((st = upload_desc(b)) != SEM_OK) return st;
     const size_t n = b->shots.size();
+    if (b->streamed) return batch_step_streamed(b, nsteps);
     std::vector<int64_t> steps(n);
     for (size_t i = 0; i < n; ++i) steps[i] = b->shots[i]->step;
     if (cudaMemcpyAsync(b->d_step, steps.data(), n * 8, cudaMemcpyHostToDevice, b->run) != cudaSuccess ||
@@ -2195,6 +2473,14 @@ sem_status sem_batch_info(const sem_batch* b, int32_t* nclasses, int32_t* orders
     return SEM_OK;
 }
 
+sem_status sem_batch_mode(const sem_batch* b, int32_t* streamed, int32_t* steps_per_launch) {
+    if (!b) return SEM_ERR_INVALID_ARG;
+    if (!b->ready) return SEM_ERR_STATE;
+    if (streamed) *streamed = b->streamed ? 1 : 0;
+    if (steps_per_launch) *steps_per_launch = b->streamed ? b->stream_steps : 1;
+    return SEM_OK;
+}
+
 const char* sem_batch_last_error(const sem_batch* b) {
     if (!b) return "NULL batch";
     return b->err.c_str();
@@ -2204,6 +2490,7 @@ void sem_batch_destroy(sem_batch* b) {
     if (!b) return;
     cudaStreamSynchronize(b->run);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->sgraph) cudaGraphExecDestroy(b->sgraph);
     for (void* p : b->allocs) cudaFree(p);
     delete b;
 }

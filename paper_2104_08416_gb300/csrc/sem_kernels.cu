@@ -23,6 +23,9 @@
 // run. No floating-point atomics are used, so results are bitwise reproducible.
 #include "sem_kernels.cuh"
 
+#include <map>
+#include <mutex>
+
 namespace semdev {
 
 namespace {
@@ -120,6 +123,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 
 // 16-byte shared-memory vector of VEC values.
 template <typename T, int VEC>
@@ -281,6 +285,44 @@ __device__ __forceinline__ void heun_element(const Plan& pl, const StepArgs<T>& 
     }
 }
 
+// The FP32 metric of Eq. deriv_u, G_q = w_q |J_q| / rho_e J_q^-1 J_q^-T =
+// w_q / (rho_e |J_q|) adj(J_q) adj(J_q)^T, formed at a GLL point from the
+// element's bilinear map x = a + b xi + c eta + d xi eta (coefficients b, c,
+// d and 1/rho in cf0 = (bx, by, cx, cy), cf1 = (dx, dy, 1/rho, -)):
+// J = [j00 j01; j10 j11] with j00, j10 depending on eta only (one row of
+// points) and j01, j11 on xi only (one column). Every operation is an
+// explicitly rounded intrinsic, so the step kernels and sem_read_metric's
+// kernel form bitwise the same values.
+struct BilCol {
+    float j01, j11, cB;   // cB = j11^2 + j01^2
+};
+struct BilRow {
+    float j00, j10, cA;   // cA = j10^2 + j00^2
+};
+__device__ __forceinline__ BilCol bil_col(const float4& cf0, const float4& cf1, float xi) {
+    BilCol c;
+    c.j01 = __fmaf_rn(cf1.x, xi, cf0.z);
+    c.j11 = __fmaf_rn(cf1.y, xi, cf0.w);
+    c.cB = __fmaf_rn(c.j11, c.j11, __fmul_rn(c.j01, c.j01));
+    return c;
+}
+__device__ __forceinline__ BilRow bil_row(const float4& cf0, const float4& cf1, float eta) {
+    BilRow r;
+    r.j00 = __fmaf_rn(cf1.x, eta, cf0.x);
+    r.j10 = __fmaf_rn(cf1.y, eta, cf0.y);
+    r.cA = __fmaf_rn(r.j10, r.j10, __fmul_rn(r.j00, r.j00));
+    return r;
+}
+// wr = w_q / rho_e
+__device__ __forceinline__ void bil_metric(const BilRow& r, const BilCol& c, float wr, float& gxx, float& gxy,
+                                           float& gyy) {
+    const float det = __fmaf_rn(r.j00, c.j11, -__fmul_rn(c.j01, r.j10));
+    const float kk = __fdividef(wr, det);
+    gxx = __fmul_rn(kk, c.cB);
+    gyy = __fmul_rn(kk, r.cA);
+    gxy = -__fmul_rn(kk, __fmaf_rn(r.j10, c.j11, __fmul_rn(r.j00, c.j01)));
+}
+
 // The loaded inputs of one open entry whose node is finished in this unit
 // (position, node, partial sums, previous-level state).
 template <typename T>
@@ -301,7 +343,9 @@ struct NoWait {
     __device__ __forceinline__ bool operator()() const { return true; }
 };
 
-template <int NP, typename T, int MODE, typename Ready = NoWait>
+// SG: FP32 kernels stream the stored metric (pl.G32, computed in FP64 and
+// rounded once) instead of forming it from the bilinear map.
+template <int NP, typename T, int MODE, bool SG = false, typename Ready = NoWait>
 __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a, const Basis<T>& bs, const int b,
                                            unsigned char* smem_raw, const int64_t step, const int pend,
                                            const Ready& ready = Ready(), const BlockHdr* hpre = nullptr) {
@@ -310,7 +354,8 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     constexpr bool HEUN = MODE == MODE_HEUN_P || MODE == MODE_HEUN_C;
     constexpr bool STATE = MODE == MODE_THREE_LEVEL || MODE == MODE_KAHAN;   // leapfrog state staged
     constexpr bool KAHAN = MODE == MODE_KAHAN;
-    constexpr bool BIL = sizeof(T) == 4;  // FP32: metric from the bilinear map; FP64: stored metric
+    // FP32: metric from the bilinear map (or stored, SG); FP64: stored metric
+    constexpr bool BIL = sizeof(T) == 4 && !SG;
     constexpr int VEC = 16 / sizeof(T);
     uint8_t* spk = smem_raw;
     T* su = reinterpret_cast<T*>(smem_raw + pl.max_packet);   // node values at the positions
@@ -486,27 +531,16 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             u[q] = su[(pw[q / 2] >> (16 * (q & 1))) & 0xFFFFu];
             r[q] = T(0);
         }
-        // per-column (xi = x_i) parts of the Jacobian: J = [j00 j01; j10 j11],
-        // j00, j10 vary with eta only, j01, j11 with xi only
-        float j01[NP], j11[NP], cB[NP];
+        // per-column (xi = x_i) parts of the Jacobian, hoisted out of the rows
+        BilCol col[NP];
         if constexpr (BIL) {
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                const float xi = (float)bs.x[i];
-                j01[i] = cf0.z + cf1.x * xi;
-                j11[i] = cf0.w + cf1.y * xi;
-                cB[i] = j11[i] * j11[i] + j01[i] * j01[i];
-            }
+            for (int i = 0; i < NP; ++i) col[i] = bil_col(cf0, cf1, (float)bs.x[i]);
         }
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            float j00 = 0.f, j10 = 0.f, cA = 0.f;
-            if constexpr (BIL) {
-                const float eta = (float)bs.x[j];
-                j00 = cf0.x + cf1.x * eta;
-                j10 = cf0.y + cf1.y * eta;
-                cA = j10 * j10 + j00 * j00;
-            }
+            BilRow row{};
+            if constexpr (BIL) row = bil_row(cf0, cf1, (float)bs.x[j]);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const int q = j * NP + i;
@@ -518,12 +552,15 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 }
                 T gxx, gxy, gyy;
                 if constexpr (BIL) {
-                    // w |J| / rho J^-1 J^-T = w / (rho |J|) adj(J) adj(J)^T
-                    const float det = j00 * j11[i] - j01[i] * j10;
-                    const float kk = __fdividef((float)bs.W[q] * cf1.z, det);
-                    gxx = kk * cB[i];
-                    gyy = kk * cA;
-                    gxy = -kk * (j10 * j11[i] + j00 * j01[i]);
+                    float fx, fxy, fy;
+                    bil_metric(row, col[i], __fmul_rn((float)bs.W[q], cf1.z), fx, fxy, fy);
+                    gxx = fx;
+                    gxy = fxy;
+                    gyy = fy;
+                } else if constexpr (SG) {
+                    gxx = ld_stream(pl.G32 + (int64_t)q * nes + e);
+                    gxy = ld_stream(pl.G32 + (int64_t)(P + q) * nes + e);
+                    gyy = ld_stream(pl.G32 + (int64_t)(2 * P + q) * nes + e);
                 } else {
                     gxx = ld_stream(pl.G + (int64_t)q * nes + e);
                     gxy = ld_stream(pl.G + (int64_t)(P + q) * nes + e);
@@ -672,11 +709,11 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
 }
 
 // One step of one mesh: CTA b handles block b.
-template <int NP, typename T, int MODE>
+template <int NP, typename T, int MODE, bool SG = false>
 __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     sem_step_kernel(const Plan pl, const StepArgs<T> a, const Basis<T> bs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_block<NP, T, MODE>(pl, a, bs, blockIdx.x, smem_raw, a.step, a.pending);
+    step_block<NP, T, MODE, SG>(pl, a, bs, blockIdx.x, smem_raw, a.step, a.pending);
 }
 
 // Arguments of launch k of a shot, from its level buffers (the same
@@ -841,7 +878,7 @@ struct PrologueWaited {
 // bitwise that of one launch per step. DENSE plans only: the gathers of
 // GATHER plans stage through L1, which is not coherent with the other CTAs'
 // writes within a launch.
-template <int NP, typename T, int MODE>
+template <int NP, typename T, int MODE, bool SG = false>
 __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     sem_stream_kernel(const ShotDesc<T> d, const StreamArgs sa, const Basis<T> bs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -889,7 +926,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     const int64_t k = sa.step0 + i;
     const int pend = (i > 0 || sa.pending0) ? 1 : 0;
     const PrologueWaited w{&s_fail};
-    step_block<NP, T, MODE>(d.pl, s_a, bs, b, smem_raw, k, pend, w, &s_h);
+    step_block<NP, T, MODE, SG>(d.pl, s_a, bs, b, smem_raw, k, pend, w, &s_h);
     // every thread's stores of the unit precede the flag: the barrier orders
     // them before thread 0's release store (release at GPU scope covers what
     // the barrier made it observe)
@@ -900,6 +937,97 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     }
     if (threadIdx.x == 0 && (long long)i * nb + b != sa.hold_unit) st_release_gpu(sa.done + b, sa.serial0 + (uint32_t)i);
 }
+
+// Several steps of every shot of one order in one launch of
+// nsteps * nblk CTAs (batched shots streamed like sem_stream_kernel): each
+// CTA takes the next ticket from the launch's work counter; ticket u is
+// unit (i = u / nblk, g = u % nblk): step i of the launch at block g of the
+// order's blocks, i.e. block units[g].block of shot units[g].shot. The unit
+// waits until step i-1 has finished at that block and at every block of the
+// same shot sharing a node with it (the record's neighbour list, the shot's
+// done flags, one serial sequence for the whole batch), runs step_block on
+// the shot's plan and level buffers at the shot's own step number, and
+// releases its block's done flag. As in sem_stream_kernel a unit waits only
+// on units taken earlier, every wait is bounded, and the arithmetic is
+// step_block's: bitwise the result of one launch per shot and step.
+template <int NP, typename T, int MODE>
+__global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
+    sem_batch_stream_kernel(const BatchStreamArgs ba, const Basis<T> bs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Plan s_pl;
+    __shared__ StepArgs<T> s_a;
+    __shared__ BlockHdr s_h;
+    __shared__ __align__(16) int32_t s_dep[16];
+    __shared__ int s_i, s_b, s_shot, s_stride, s_fail;
+    __shared__ uint32_t s_serial0;
+    const long long total = (long long)ba.nsteps * ba.nblk;
+    if (threadIdx.x == 0) {
+        const unsigned long long t = atomicAdd(ba.counter, 1ull);
+        const int raised = ld_relaxed_gpu(ba.err);
+        const uint32_t serial0 = __ldcg(ba.serial0);
+        const long long u = raised != 0 ? total : (long long)t;
+        int ui = -1;
+        s_fail = 0;
+        if (u < total) {
+            ui = (int)(u / ba.nblk);
+            const BatchUnit* rec = ba.units + (u - (long long)ui * ba.nblk);
+            const int4* r4 = reinterpret_cast<const int4*>(rec);
+            const int4 h0 = r4[0], h1 = r4[1], h2 = r4[2], meta = r4[3];
+            BlockHdr h;
+            h.start = h0.x; h.nent = h0.y; h.nown = h0.z; h.own_start = h0.w;
+            h.nopen = h1.x; h.ulen = h1.y; h.slen = h1.z; h.sulen = h1.w;
+            h.ncolors = h2.x; h.nrc = h2.y; h.nro = h2.z;
+            s_h = h;
+            s_shot = meta.x;
+            s_b = meta.y;
+            s_stride = meta.z;
+            for (int q = 0; q < meta.z / 4; ++q) reinterpret_cast<int4*>(s_dep)[q] = r4[4 + q];
+        }
+        s_i = ui;
+        s_serial0 = serial0;
+    }
+    // warp 0 only (its lanes see thread 0's writes after __syncwarp): lanes
+    // 0..15 await the neighbours' previous step (at most 16, one flag each)
+    // before any other load, as in sem_stream_kernel; lane 16 meanwhile
+    // fetches the shot's descriptor and clock
+    __syncwarp();
+    if (threadIdx.x < 32) {
+        const int lane = (int)threadIdx.x, ui = s_i;
+        if (lane < 16) {
+            if (ui > 0 && lane < s_stride &&
+                !wait_flag(ba.done[s_shot] + s_dep[lane], s_serial0 + (uint32_t)(ui - 1), ba.err))
+                s_fail = 1;
+        } else if (lane == 16 && ui >= 0) {
+            const ShotDesc<T>& d = static_cast<const ShotDesc<T>*>(ba.shots)[s_shot];
+            const ShotClock c = ba.clock[s_shot];
+            s_pl = d.pl;
+            s_a = shot_step_args<T, MODE>(d, c.step0 + ui, (ui > 0 || c.pending0) ? 1 : 0);
+        }
+    }
+    __syncthreads();
+    if (s_i < 0) return;
+    const PrologueWaited w{&s_fail};
+    step_block<NP, T, MODE>(s_pl, s_a, bs, s_b, smem_raw, s_a.step, s_a.pending, w, &s_h);
+    __syncthreads();
+    if (s_fail) {
+        if (threadIdx.x == 0) atomicExch(ba.err, 1);
+        return;
+    }
+    if (threadIdx.x == 0) st_release_gpu(ba.done[s_shot] + s_b, s_serial0 + (uint32_t)s_i);
+}
+
+// After a streamed batch launch of n steps: every shot's clock and the
+// batch serial advance by n, and the open nodes are pending from now on.
+#ifndef SEM_KERNEL_NP
+__global__ void batch_clock_advance_kernel(ShotClock* clock, int nshots, uint32_t* serial, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nshots) {
+        clock[i].step0 += n;
+        clock[i].pending0 = 1;
+    }
+    if (i == 0) *serial += (uint32_t)n;
+}
+#endif
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) sem_open_finish_kernel(const Plan pl, const StepArgs<T> a) {
@@ -939,7 +1067,7 @@ __global__ void __launch_bounds__(kThreads) sem_open_finish_kernel(const Plan pl
 __global__ void geometry_kernel(int np, int64_t ne, const double* __restrict__ coords,
                                 const int32_t* __restrict__ quads, const double* __restrict__ rho,
                                 const double* __restrict__ vel, const Basis<double> bs, float4* coef, double* G64,
-                                double* mloc, double* coef64) {
+                                double* mloc, double* coef64, float* G32) {
     const int P = np * np;
     const int64_t total = ne * P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -975,10 +1103,18 @@ __global__ void geometry_kernel(int np, int64_t ne, const double* __restrict__ c
         const double det = j00 * j11 - j01 * j10;
         const double wq = bs.w[i] * bs.w[j];
         const double k = wq * rinv / det;
+        const double gxx = k * (j11 * j11 + j01 * j01);
+        const double gxy = -k * (j10 * j11 + j00 * j01);
+        const double gyy = k * (j10 * j10 + j00 * j00);
         if (G64 != nullptr) {
-            G64[(int64_t)q * ne + e] = k * (j11 * j11 + j01 * j01);
-            G64[(int64_t)(P + q) * ne + e] = -k * (j10 * j11 + j00 * j01);
-            G64[(int64_t)(2 * P + q) * ne + e] = k * (j10 * j10 + j00 * j00);
+            G64[(int64_t)q * ne + e] = gxx;
+            G64[(int64_t)(P + q) * ne + e] = gxy;
+            G64[(int64_t)(2 * P + q) * ne + e] = gyy;
+        }
+        if (G32 != nullptr) {   // the same FP64 values, rounded once
+            G32[(int64_t)q * ne + e] = (float)gxx;
+            G32[(int64_t)(P + q) * ne + e] = (float)gxy;
+            G32[(int64_t)(2 * P + q) * ne + e] = (float)gyy;
         }
         if (mloc != nullptr) mloc[t] = wq * det * rinv / (vel[e] * vel[e]);
     }
@@ -1026,6 +1162,27 @@ __global__ void __launch_bounds__(kMaxStepThreads) mass_block_kernel(const Plan 
     for (int o = tid; o < h.nopen; o += nt) partial[obase[o] + orank[o]] = acc[opos[o]];
 }
 
+// The FP32 metric as the step kernels form it, written out in FP64 (one
+// thread per element, device element order): sem_read_metric's kernel.
+template <int NP>
+__global__ void __launch_bounds__(kThreads) metric_fp32_kernel(const Plan pl, const Basis<float> bs, double* out) {
+    constexpr int P = NP * NP;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pl.ne; e += (int64_t)gridDim.x * blockDim.x) {
+        const float4 cf0 = pl.coef[e], cf1 = pl.coef[pl.ne + e];
+        for (int j = 0; j < NP; ++j) {
+            const BilRow row = bil_row(cf0, cf1, bs.x[j]);
+            for (int i = 0; i < NP; ++i) {
+                const int q = j * NP + i;
+                float gxx, gxy, gyy;
+                bil_metric(row, bil_col(cf0, cf1, bs.x[i]), __fmul_rn(bs.W[q], cf1.z), gxx, gxy, gyy);
+                out[(e * P + q) * 3 + 0] = gxx;
+                out[(e * P + q) * 3 + 1] = gxy;
+                out[(e * P + q) * 3 + 2] = gyy;
+            }
+        }
+    }
+}
+
 #ifndef SEM_KERNEL_NP
 __global__ void mass_open_kernel(const Plan pl, const double* __restrict__ partial, double* M) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pl.nopen_nodes; k += gridDim.x * blockDim.x) {
@@ -1064,6 +1221,38 @@ __global__ void adjoint_receivers_kernel(int nrec, T* lam, const T* __restrict__
         const int32_t g = rec_node[r];
         const double res = trace[(int64_t)rec_row[r] * trace_cap + m - 1] - obs[(int64_t)r * obs_cap + m - 1];
         lam[g] = (T)((double)lam[g] - (double)s[g] * res * inv_dt);
+    }
+}
+
+// One backward step at every node, fused: lambda^m = 2 lambda^{m+1} -
+// lambda^{m+2} - s (K lambda^{m+1}); then the receiver residuals of step m
+// at receiver nodes, lambda^m -= s (trace_r^{m-1} - obs_r^{m-1}) / dt for the
+// node's receivers in ascending order (rec_first[g]: the first of them in
+// rec_order, the receivers sorted by (node, index), or -1); then
+// C += lambda^m (u^m - 2 u^{m-1} + u^{m-2}) in FP64. The same operations in
+// the same order as the three separate kernels below, so bitwise the same.
+template <typename T>
+__global__ void adjoint_node_kernel(int64_t nn, T* lam, const T* __restrict__ lam1, const T* __restrict__ lam2,
+                                    const T* __restrict__ s, const T* __restrict__ klam1,
+                                    const int32_t* __restrict__ rec_first, const int32_t* __restrict__ rec_order,
+                                    int nrec, const int32_t* __restrict__ rec_node, const int32_t* __restrict__ rec_row,
+                                    const double* __restrict__ trace, int64_t trace_cap, const double* __restrict__ obs,
+                                    int64_t obs_cap, int64_t m, double inv_dt, double* C, const T* __restrict__ um,
+                                    const T* __restrict__ um1, const T* __restrict__ um2) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        const T sg = s[g];
+        T l = fma_rn(-sg, klam1[g], sub_rn(add_rn(lam1[g], lam1[g]), lam2[g]));
+        const int k0 = rec_first[g];
+        if (k0 >= 0) {
+            for (int k = k0; k < nrec && rec_node[rec_order[k]] == (int32_t)g; ++k) {
+                const int r = rec_order[k];
+                const double res = trace[(int64_t)rec_row[r] * trace_cap + m - 1] - obs[(int64_t)r * obs_cap + m - 1];
+                l = (T)((double)l - (double)sg * res * inv_dt);
+            }
+        }
+        lam[g] = l;
+        const double a = ((double)um[g] - 2.0 * (double)um1[g]) + (double)um2[g];
+        C[g] = fma((double)l, a, C[g]);
     }
 }
 
@@ -1108,13 +1297,20 @@ template <int NP>
 cudaError_t step_np(bool fp64, int mode, const Plan& pl, const void* args, const void* basis, int threads, int smem,
                     cudaStream_t st);
 template <int NP>
+cudaError_t metric_np(const Plan& pl, const Basis<float>& basis, double* out, cudaStream_t st);
+template <int NP>
 cudaError_t batch_np(bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas, const void* basis,
                      int threads, int smem, cudaStream_t st);
 template <int NP>
 cudaError_t stream_np(bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis, int threads,
                       int smem, int64_t ctas, cudaStream_t st);
 template <int NP>
-cudaError_t resident_np(bool fp64, int mode, int threads, int smem, int* out);
+cudaError_t resident_np(bool fp64, int mode, bool sg, int threads, int smem, int* out);
+template <int NP>
+cudaError_t bstream_np(bool fp64, int mode, bool prepare_only, const BatchStreamArgs& ba, const void* basis,
+                       int threads, int smem, cudaStream_t st);
+template <int NP>
+cudaError_t bresident_np(bool fp64, int mode, int threads, int smem, int* out);
 template <int NP>
 cudaError_t mass_np(const Plan& pl, const double* mloc, double* partial, double* M, int threads, int smem,
                     cudaStream_t st);
@@ -1122,15 +1318,28 @@ cudaError_t mass_np(const Plan& pl, const double* mloc, double* partial, double*
 #ifdef SEM_KERNEL_NP
 namespace {
 
-template <int NP, typename T, int MODE>
+// Raises the dynamic shared-memory limit of a kernel to at least `smem` and
+// never lowers it: handles with different block sizes share one kernel, and
+// a limit set for a smaller block would make a later launch of a larger one
+// fail. One table per translation unit (each kernel lives in one unit).
+std::mutex g_smem_mu;
+std::map<const void*, int> g_smem_limit;
+template <typename K>
+cudaError_t raise_smem(K kern, int smem) {
+    const void* f = reinterpret_cast<const void*>(kern);
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    int& lim = g_smem_limit[f];
+    if (smem <= lim) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) lim = smem;
+    return e;
+}
+
+template <int NP, typename T, int MODE, bool SG = false>
 cudaError_t launch_step_t(const Plan& pl, const void* args, const void* basis, int threads, int smem, cudaStream_t st) {
-    auto kern = sem_step_kernel<NP, T, MODE>;
-    static int configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    auto kern = sem_step_kernel<NP, T, MODE, SG>;
+    const cudaError_t e = raise_smem(kern, smem);
+    if (e != cudaSuccess) return e;
     kern<<<pl.nblocks, threads, smem, st>>>(pl, *static_cast<const StepArgs<T>*>(args),
                                             *static_cast<const Basis<T>*>(basis));
     return cudaGetLastError();
@@ -1140,20 +1349,18 @@ template <int NP, typename T, int MODE>
 cudaError_t launch_batch_t(bool prepare_only, const BatchArgs& ba, int ctas, const void* basis, int threads, int smem,
                            cudaStream_t st) {
     auto kern = sem_batch_step_kernel<NP, T, MODE>;
-    if (prepare_only) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (prepare_only) return raise_smem(kern, smem);
     kern<<<ctas, threads, smem, st>>>(ba, *static_cast<const Basis<T>*>(basis));
     return cudaGetLastError();
 }
 
-template <int NP, typename T, int MODE>
+template <int NP, typename T, int MODE, bool SG = false>
 cudaError_t stream_t(const void* shot, const StreamArgs& sa, const void* basis, int threads, int smem, int64_t ctas,
                      cudaStream_t st) {
-    auto kern = sem_stream_kernel<NP, T, MODE>;
-    static int configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = sem_stream_kernel<NP, T, MODE, SG>;
+    {
+        const cudaError_t e = raise_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     if (ctas < 1 || ctas > 2147483647LL) return cudaErrorInvalidValue;
     kern<<<(unsigned)ctas, threads, smem, st>>>(*static_cast<const ShotDesc<T>*>(shot), sa,
@@ -1161,10 +1368,33 @@ cudaError_t stream_t(const void* shot, const StreamArgs& sa, const void* basis, 
     return cudaGetLastError();
 }
 
-template <int NP, typename T, int MODE>
+template <int NP, typename T, int MODE, bool SG = false>
 cudaError_t stream_resident_t(int threads, int smem, int* out) {
-    auto kern = sem_stream_kernel<NP, T, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = sem_stream_kernel<NP, T, MODE, SG>;
+    cudaError_t e = raise_smem(kern, smem);
+    int per_sm = 0, dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) *out = per_sm * sms;
+    return e;
+}
+
+template <int NP, typename T, int MODE>
+cudaError_t bstream_t(bool prepare_only, const BatchStreamArgs& ba, const void* basis, int threads, int smem,
+                      cudaStream_t st) {
+    auto kern = sem_batch_stream_kernel<NP, T, MODE>;
+    if (prepare_only) return raise_smem(kern, smem);
+    const long long ctas = (long long)ba.nsteps * ba.nblk;
+    if (ctas < 1 || ctas > 2147483647LL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)ctas, threads, smem, st>>>(ba, *static_cast<const Basis<T>*>(basis));
+    return cudaGetLastError();
+}
+
+template <int NP, typename T, int MODE>
+cudaError_t bresident_t(int threads, int smem, int* out) {
+    auto kern = sem_batch_stream_kernel<NP, T, MODE>;
+    cudaError_t e = raise_smem(kern, smem);
     int per_sm = 0, dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -1176,6 +1406,30 @@ cudaError_t stream_resident_t(int threads, int smem, int* out) {
 }  // namespace
 
 template <int NP>
+cudaError_t bstream_np(bool fp64, int mode, bool prepare_only, const BatchStreamArgs& ba, const void* basis,
+                       int threads, int smem, cudaStream_t st) {
+    if (fp64) {
+        if (mode == MODE_THREE_LEVEL)
+            return bstream_t<NP, double, MODE_THREE_LEVEL>(prepare_only, ba, basis, threads, smem, st);
+        return cudaErrorInvalidValue;
+    }
+    if (mode == MODE_THREE_LEVEL) return bstream_t<NP, float, MODE_THREE_LEVEL>(prepare_only, ba, basis, threads, smem, st);
+    if (mode == MODE_KAHAN) return bstream_t<NP, float, MODE_KAHAN>(prepare_only, ba, basis, threads, smem, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int NP>
+cudaError_t bresident_np(bool fp64, int mode, int threads, int smem, int* out) {
+    if (fp64) {
+        if (mode == MODE_THREE_LEVEL) return bresident_t<NP, double, MODE_THREE_LEVEL>(threads, smem, out);
+        return cudaErrorInvalidValue;
+    }
+    if (mode == MODE_THREE_LEVEL) return bresident_t<NP, float, MODE_THREE_LEVEL>(threads, smem, out);
+    if (mode == MODE_KAHAN) return bresident_t<NP, float, MODE_KAHAN>(threads, smem, out);
+    return cudaErrorInvalidValue;
+}
+
+template <int NP>
 cudaError_t step_np(bool fp64, int mode, const Plan& pl, const void* args, const void* basis, int threads, int smem,
                     cudaStream_t st) {
     if (fp64) {
@@ -1184,6 +1438,15 @@ cudaError_t step_np(bool fp64, int mode, const Plan& pl, const void* args, const
             case MODE_APPLY: return launch_step_t<NP, double, MODE_APPLY>(pl, args, basis, threads, smem, st);
             case MODE_HEUN_P: return launch_step_t<NP, double, MODE_HEUN_P>(pl, args, basis, threads, smem, st);
             case MODE_HEUN_C: return launch_step_t<NP, double, MODE_HEUN_C>(pl, args, basis, threads, smem, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (pl.G32) {
+        switch (mode) {
+            case MODE_THREE_LEVEL:
+                return launch_step_t<NP, float, MODE_THREE_LEVEL, true>(pl, args, basis, threads, smem, st);
+            case MODE_KAHAN: return launch_step_t<NP, float, MODE_KAHAN, true>(pl, args, basis, threads, smem, st);
+            case MODE_APPLY: return launch_step_t<NP, float, MODE_APPLY, true>(pl, args, basis, threads, smem, st);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -1218,15 +1481,26 @@ cudaError_t stream_np(bool fp64, int mode, const void* shot, const StreamArgs& s
         if (mode == MODE_THREE_LEVEL) return stream_t<NP, double, MODE_THREE_LEVEL>(shot, sa, basis, threads, smem, ctas, st);
         return cudaErrorInvalidValue;
     }
+    if (static_cast<const ShotDesc<float>*>(shot)->pl.G32) {
+        if (mode == MODE_THREE_LEVEL)
+            return stream_t<NP, float, MODE_THREE_LEVEL, true>(shot, sa, basis, threads, smem, ctas, st);
+        if (mode == MODE_KAHAN) return stream_t<NP, float, MODE_KAHAN, true>(shot, sa, basis, threads, smem, ctas, st);
+        return cudaErrorInvalidValue;
+    }
     if (mode == MODE_THREE_LEVEL) return stream_t<NP, float, MODE_THREE_LEVEL>(shot, sa, basis, threads, smem, ctas, st);
     if (mode == MODE_KAHAN) return stream_t<NP, float, MODE_KAHAN>(shot, sa, basis, threads, smem, ctas, st);
     return cudaErrorInvalidValue;
 }
 
 template <int NP>
-cudaError_t resident_np(bool fp64, int mode, int threads, int smem, int* out) {
+cudaError_t resident_np(bool fp64, int mode, bool sg, int threads, int smem, int* out) {
     if (fp64) {
         if (mode == MODE_THREE_LEVEL) return stream_resident_t<NP, double, MODE_THREE_LEVEL>(threads, smem, out);
+        return cudaErrorInvalidValue;
+    }
+    if (sg) {
+        if (mode == MODE_THREE_LEVEL) return stream_resident_t<NP, float, MODE_THREE_LEVEL, true>(threads, smem, out);
+        if (mode == MODE_KAHAN) return stream_resident_t<NP, float, MODE_KAHAN, true>(threads, smem, out);
         return cudaErrorInvalidValue;
     }
     if (mode == MODE_THREE_LEVEL) return stream_resident_t<NP, float, MODE_THREE_LEVEL>(threads, smem, out);
@@ -1237,18 +1511,31 @@ cudaError_t resident_np(bool fp64, int mode, int threads, int smem, int* out) {
 template <int NP>
 cudaError_t mass_np(const Plan& pl, const double* mloc, double* partial, double* M, int threads, int smem,
                     cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(mass_block_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = raise_smem(mass_block_kernel<NP>, smem);
     if (e != cudaSuccess) return e;
     mass_block_kernel<NP><<<pl.nblocks, threads, smem, st>>>(pl, mloc, partial, M);
     return cudaGetLastError();
 }
 
+template <int NP>
+cudaError_t metric_np(const Plan& pl, const Basis<float>& basis, double* out, cudaStream_t st) {
+    int64_t g = (pl.ne + kThreads - 1) / kThreads;
+    if (g < 1) g = 1;
+    if (g > 152 * 64) g = 152 * 64;
+    metric_fp32_kernel<NP><<<(int)g, kThreads, 0, st>>>(pl, basis, out);
+    return cudaGetLastError();
+}
+
 template cudaError_t step_np<SEM_KERNEL_NP>(bool, int, const Plan&, const void*, const void*, int, int, cudaStream_t);
+template cudaError_t metric_np<SEM_KERNEL_NP>(const Plan&, const Basis<float>&, double*, cudaStream_t);
 template cudaError_t batch_np<SEM_KERNEL_NP>(bool, int, bool, const BatchArgs&, int, const void*, int, int,
                                             cudaStream_t);
 template cudaError_t stream_np<SEM_KERNEL_NP>(bool, int, const void*, const StreamArgs&, const void*, int, int,
                                              int64_t, cudaStream_t);
-template cudaError_t resident_np<SEM_KERNEL_NP>(bool, int, int, int, int*);
+template cudaError_t resident_np<SEM_KERNEL_NP>(bool, int, bool, int, int, int*);
+template cudaError_t bstream_np<SEM_KERNEL_NP>(bool, int, bool, const BatchStreamArgs&, const void*, int, int,
+                                              cudaStream_t);
+template cudaError_t bresident_np<SEM_KERNEL_NP>(bool, int, int, int, int*);
 template cudaError_t mass_np<SEM_KERNEL_NP>(const Plan&, const double*, double*, double*, int, int, cudaStream_t);
 
 #else  // the dispatchers and the order-independent kernels
@@ -1279,9 +1566,29 @@ cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cu
     return cudaGetLastError();
 }
 
-cudaError_t stream_resident_ctas(int np, bool fp64, int mode, int threads, int smem, int* out) {
+cudaError_t launch_batch_stream(int np, bool fp64, int mode, bool prepare_only, const BatchStreamArgs& sa,
+                                const void* basis, int threads, int smem, cudaStream_t st) {
+    if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
+#define SEM_CALL(N) bstream_np<N>(fp64, mode, prepare_only, sa, basis, threads, smem, st)
+    SEM_NP_SWITCH(np, SEM_CALL)
+#undef SEM_CALL
+}
+
+cudaError_t launch_batch_clock_advance(ShotClock* clock, int nshots, uint32_t* serial, int nsteps, cudaStream_t st) {
+    batch_clock_advance_kernel<<<(nshots + 255) / 256, 256, 0, st>>>(clock, nshots, serial, nsteps);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_stream_resident_ctas(int np, bool fp64, int mode, int threads, int smem, int* out) {
     *out = 0;
-#define SEM_CALL(N) resident_np<N>(fp64, mode, threads, smem, out)
+#define SEM_CALL(N) bresident_np<N>(fp64, mode, threads, smem, out)
+    SEM_NP_SWITCH(np, SEM_CALL)
+#undef SEM_CALL
+}
+
+cudaError_t stream_resident_ctas(int np, bool fp64, int mode, bool sg, int threads, int smem, int* out) {
+    *out = 0;
+#define SEM_CALL(N) resident_np<N>(fp64, mode, sg, threads, smem, out)
     SEM_NP_SWITCH(np, SEM_CALL)
 #undef SEM_CALL
 }
@@ -1291,6 +1598,13 @@ cudaError_t launch_stream(int np, bool fp64, int mode, const void* shot, const S
     if (threads < 1 || threads > kMaxStepThreads) return cudaErrorInvalidValue;
     const int64_t ctas = (int64_t)sa.nsteps * (int64_t)nblocks;
 #define SEM_CALL(N) stream_np<N>(fp64, mode, shot, sa, basis, threads, smem, ctas, st)
+    SEM_NP_SWITCH(np, SEM_CALL)
+#undef SEM_CALL
+}
+
+cudaError_t launch_metric_fp32(int np, const Plan& pl, const Basis<float>& basis, double* out, cudaStream_t st) {
+    if (!pl.coef) return cudaErrorInvalidValue;
+#define SEM_CALL(N) metric_np<N>(pl, basis, out, st)
     SEM_NP_SWITCH(np, SEM_CALL)
 #undef SEM_CALL
 }
@@ -1366,6 +1680,25 @@ cudaError_t launch_adjoint_receivers(bool fp64, int nrec, void* lam, const void*
     return cudaGetLastError();
 }
 
+cudaError_t launch_adjoint_node(bool fp64, int64_t nn, void* lam, const void* lam1, const void* lam2, const void* s,
+                                const void* klam1, const int32_t* rec_first, const int32_t* rec_order, int nrec,
+                                const int32_t* rec_node, const int32_t* rec_row, const double* trace,
+                                int64_t trace_cap, const double* obs, int64_t obs_cap, int64_t m, double inv_dt,
+                                double* C, const void* um, const void* um1, const void* um2, cudaStream_t st) {
+    const int grid = grid_for(nn, kThreads);
+    if (fp64)
+        adjoint_node_kernel<double><<<grid, kThreads, 0, st>>>(
+            nn, (double*)lam, (const double*)lam1, (const double*)lam2, (const double*)s, (const double*)klam1,
+            rec_first, rec_order, nrec, rec_node, rec_row, trace, trace_cap, obs, obs_cap, m, inv_dt, C,
+            (const double*)um, (const double*)um1, (const double*)um2);
+    else
+        adjoint_node_kernel<float><<<grid, kThreads, 0, st>>>(
+            nn, (float*)lam, (const float*)lam1, (const float*)lam2, (const float*)s, (const float*)klam1, rec_first,
+            rec_order, nrec, rec_node, rec_row, trace, trace_cap, obs, obs_cap, m, inv_dt, C, (const float*)um,
+            (const float*)um1, (const float*)um2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_correlate(bool fp64, int64_t nn, double* C, const void* lam, const void* um, const void* um1,
                              const void* um2, cudaStream_t st) {
     const int grid = grid_for(nn, kThreads);
@@ -1386,9 +1719,9 @@ cudaError_t launch_gradient(int64_t ne, int P, const int32_t* conn, const double
 
 cudaError_t launch_geometry(int np, int64_t ne, const double* coords, const int32_t* quads_new, const double* rho,
                             const double* vel, const Basis<double>& basis, float4* coef, double* G64, double* mloc,
-                            double* coef64, cudaStream_t st) {
+                            double* coef64, float* G32, cudaStream_t st) {
     geometry_kernel<<<grid_for(ne * np * np, kThreads), kThreads, 0, st>>>(np, ne, coords, quads_new, rho, vel, basis,
-                                                                          coef, G64, mloc, coef64);
+                                                                          coef, G64, mloc, coef64, G32);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ struct Plan {
     const uint32_t* epos;      // [(P+1)/2][ne]
     const float4* coef;        // [2][ne] bilinear map (FP32 kernels)
     const double* G;           // [3P][ne] stored metric (FP64 kernels)
+    const float* G32;          // [3P][ne] stored metric rounded to FP32 (FP32 kernels, or null: from coef)
     const double* coef64;      // [8][ne] FP64 bilinear map, 1/rho (FP64 first-order kernels)
     const int32_t* open_gid;   // open nodes, ascending
     const int32_t* open_base;
@@ -124,6 +125,36 @@ struct BatchArgs {
     const int32_t* pending;
 };
 
+// A streamed batch launch: several steps of every shot of one order in one
+// launch of nsteps * nblk CTAs, one (step, block) unit each, the units of a
+// step running over the blocks of all the shots (see sem_batch_stream_kernel).
+// Per block g of the order's shots, one 128-byte record: the block header,
+// its shot, its block index in the shot and its padded neighbour list.
+struct BatchUnit {
+    int32_t hdr[12];
+    int32_t shot, block, dep_stride, pad;
+    int32_t dep[16];
+};
+// Per shot, advanced on the device after every launch (so that a captured
+// launch sequence can be replayed): the step number of the launch's first
+// step and whether the shot's open nodes are pending before it.
+struct ShotClock {
+    int64_t step0;
+    int32_t pending0;
+    int32_t pad;
+};
+struct BatchStreamArgs {
+    const void* shots;          // ShotDesc<T>[nshots]
+    const BatchUnit* units;     // [nblk]
+    ShotClock* clock;           // [nshots]
+    uint32_t* const* done;      // [nshots]: each shot's done flags
+    const uint32_t* serial0;    // serial of the launch's first step (one for the whole batch)
+    unsigned long long* counter;
+    int32_t* err;
+    int32_t nblk;               // blocks per step, all shots of the order
+    int32_t nsteps;             // steps in this launch
+};
+
 // A streamed launch: several steps of one mesh (the shot's plan and level
 // buffers) in one launch; see sem_stream_kernel.
 // Largest padded neighbour list of a streamed block.
@@ -165,7 +196,11 @@ cudaError_t launch_open_finish(bool fp64, int mode, const Plan& plan, const void
 // metric (G64 non-null) and w_q |J_q| / (rho c^2) per slot (mloc).
 cudaError_t launch_geometry(int np, int64_t ne, const double* coords, const int32_t* quads_new, const double* rho,
                             const double* vel, const Basis<double>& basis, float4* coef, double* G64, double* mloc,
-                            double* coef64, cudaStream_t st);
+                            double* coef64, float* G32, cudaStream_t st);
+// The FP32 metric the step kernels form from the bilinear map (plan.coef),
+// for every GLL point of every element (device element order):
+// out[(e * P + q) * 3 + (0, 1, 2)] = (gxx, gxy, gyy), in FP64.
+cudaError_t launch_metric_fp32(int np, const Plan& plan, const Basis<float>& basis, double* out, cudaStream_t st);
 // Lumped mass through the block plan (deterministic), M[nn] in FP64; mloc
 // per slot in the device element order.
 cudaError_t launch_mass(const Plan& plan, int np, const double* mloc, double* partial, double* M, cudaStream_t st);
@@ -184,6 +219,15 @@ cudaError_t launch_adjoint_receivers(bool fp64, int nrec, void* lam, const void*
                                      int64_t obs_cap, int64_t m, double inv_dt, cudaStream_t st);
 cudaError_t launch_correlate(bool fp64, int64_t nn, double* C, const void* lam, const void* um, const void* um1,
                              const void* um2, cudaStream_t st);
+// The three above in one pass over the nodes (backward update, receiver
+// residuals of step m, correlation): rec_first[nn] is the first index in
+// rec_order (receivers sorted by node, then index) of the node's receivers,
+// or -1.
+cudaError_t launch_adjoint_node(bool fp64, int64_t nn, void* lam, const void* lam1, const void* lam2, const void* s,
+                                const void* klam1, const int32_t* rec_first, const int32_t* rec_order, int nrec,
+                                const int32_t* rec_node, const int32_t* rec_row, const double* trace,
+                                int64_t trace_cap, const double* obs, int64_t obs_cap, int64_t m, double inv_dt,
+                                double* C, const void* um, const void* um1, const void* um2, cudaStream_t st);
 cudaError_t launch_gradient(int64_t ne, int P, const int32_t* conn, const double* mloc, const double* C,
                             const double* vel, double* grad, cudaStream_t st);
 
@@ -199,6 +243,14 @@ int smem_bytes_for(int P, int eb, int max_packet, int sulen_pad, int slen_pad, b
 cudaError_t launch_batch_step(int np, bool fp64, int mode, bool prepare_only, const BatchArgs& ba, int ctas,
                               const void* basis, int threads, int smem, cudaStream_t st);
 cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cudaStream_t st);
+// Streamed batch launch of sa.nsteps steps of the order-np shots
+// (prepare_only: set the kernel's shared-memory limit, launch nothing), the
+// advance of every shot's clock and of the batch serial by nsteps after it,
+// and the CTAs of that launch shape resident at once.
+cudaError_t launch_batch_stream(int np, bool fp64, int mode, bool prepare_only, const BatchStreamArgs& sa,
+                                const void* basis, int threads, int smem, cudaStream_t st);
+cudaError_t launch_batch_clock_advance(ShotClock* clock, int nshots, uint32_t* serial, int nsteps, cudaStream_t st);
+cudaError_t batch_stream_resident_ctas(int np, bool fp64, int mode, int threads, int smem, int* out);
 
 // Streamed steps (leapfrog modes of DENSE plans): sa.nsteps steps of the
 // shot (a host ShotDesc<T> whose plan has nblocks blocks) in one launch of
@@ -206,6 +258,7 @@ cudaError_t launch_batch_advance(int64_t* step, int32_t* pending, int nshots, cu
 cudaError_t launch_stream(int np, bool fp64, int mode, const void* shot, const StreamArgs& sa, const void* basis,
                           int threads, int smem, int nblocks, cudaStream_t st);
 // CTAs of that launch shape resident on the whole GPU at once.
-cudaError_t stream_resident_ctas(int np, bool fp64, int mode, int threads, int smem, int* out);
+// (sg: the kernel that streams the stored FP32 metric, plan.G32)
+cudaError_t stream_resident_ctas(int np, bool fp64, int mode, bool sg, int threads, int smem, int* out);
 
 }  // namespace semdev

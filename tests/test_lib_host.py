@@ -192,3 +192,27 @@ def test_stream_tiling_arguments(lib):
         h.sem_set_stream_tiling(band, window)
     assert h.sem_stream_order() == (0, 0)
     h.sem_destroy()
+
+
+def test_metric_source_arguments_before_device(lib):
+    """sem_set_metric validates on the host: unknown source, the first-order
+    scheme with a stored FP32 metric (either call order), FP64 accepts it as
+    a no-op; nothing touches the device."""
+    m = gen.unit_square(2)
+    h = lib.SEM(m["coords"], m["quads"], 2, "fp32", stream=0)
+    with pytest.raises(lib.SemError) as ei:
+        h.sem_set_metric(7)
+    assert ei.value.status == lib.SEM_ERR_INVALID_ARG
+    h.sem_set_metric("stored")
+    with pytest.raises(lib.SemError) as ei:
+        h.sem_set_scheme("heun")
+    assert ei.value.status == lib.SEM_ERR_UNSUPPORTED
+    h.sem_set_metric("bilinear")
+    h.sem_set_scheme("heun")
+    with pytest.raises(lib.SemError) as ei:
+        h.sem_set_metric("stored")
+    assert ei.value.status == lib.SEM_ERR_UNSUPPORTED
+    h.sem_destroy()
+    g = lib.SEM(m["coords"], m["quads"], 2, "fp64", stream=0)
+    g.sem_set_metric("stored")
+    g.sem_destroy()
