@@ -69,12 +69,71 @@ def test_batch_equals_individual_runs(P, prec):
         h.sem_destroy()
 
 
+def _streamable_shots():
+    # DENSE plans only (Hilbert and row-major), orders 3..7, three shots of
+    # order 4 of uneven sizes
+    return [
+        (gen.graded(10, seed=1), 3, "hilbert"),
+        (gen.graded(16, seed=2), 4, "hilbert"),
+        (gen.unit_square(12), 5, "rowmajor"),
+        (gen.graded(7, seed=3), 7, "hilbert"),
+        (gen.graded(21, seed=4), 4, "hilbert"),
+        (gen.relabel(gen.graded(9, seed=5), seed=6), 6, "hilbert"),
+        (gen.graded(5, seed=9), 4, "rowmajor"),
+    ]
+
+
+@pytest.mark.parametrize("prec", ["fp32_kahan", "fp64"])
+def test_streamed_batch_equals_individual_runs(P, prec):
+    """Every shot streamable: each order runs as one launch per block of 64
+    steps over the blocks of all its shots (graph replays, a single step, a
+    remainder, a second call); shot by shot bitwise the results of sem_step
+    on each handle alone."""
+    shots = _streamable_shots()
+    nmax = 160
+    chunks = (70, 1, 64, 5)
+    batch_h = [_handle(P, m, p, k, prec, nmax, eb=11) for m, p, k in shots]
+    solo_h = [_handle(P, m, p, k, prec, nmax, eb=11) for m, p, k in shots]
+    b = P.SEMBatch(batch_h)
+    for c in chunks:
+        b.sem_batch_step(c)
+    assert b.sem_batch_mode() == {"streamed": True, "steps_per_launch": 64}
+    for h in solo_h:
+        for c in chunks:
+            h.sem_step(c)
+    for hb, hs in zip(batch_h, solo_h):
+        assert hb.sem_get_step() == hs.sem_get_step() == sum(chunks)
+        ub, us = hb.sem_read_wavefield(), hs.sem_read_wavefield()
+        assert np.linalg.norm(us) > 0
+        assert np.array_equal(ub, us)
+        assert np.array_equal(hb.sem_read_traces(), hs.sem_read_traces())
+    # the shots stay usable on their own after the batch
+    for hb, hs in zip(batch_h, solo_h):
+        hb.sem_step(9)
+        hs.sem_step(9)
+        assert np.array_equal(hb.sem_read_wavefield(), hs.sem_read_wavefield())
+    b.sem_batch_destroy()
+    for h in batch_h + solo_h:
+        h.sem_destroy()
+
+
+def test_batch_with_a_gather_plan_runs_one_launch_per_step(P):
+    shots = _shots()
+    hs = [_handle(P, m, p, k, "fp32_kahan", 8, eb=11) for m, p, k in shots]
+    b = P.SEMBatch(hs)
+    b.sem_batch_step(3)
+    assert b.sem_batch_mode() == {"streamed": False, "steps_per_launch": 1}
+    b.sem_batch_destroy()
+    for h in hs:
+        h.sem_destroy()
+
+
 def test_batch_autotuned_matches_oracle(P):
     shots = [(gen.graded(24, seed=7), 4, "hilbert"), (gen.graded(12, seed=8), 4, "hilbert"),
              (gen.graded(14, seed=9), 3, "hilbert")]
     n = 80
     hs = [_handle(P, m, p, k, "fp32_kahan", n) for m, p, k in shots]
-    b = P.SEMBatch(hs, autotune_steps=3)
+    b = P.SEMBatch(hs, autotune_steps=20)
     b.sem_batch_step(n)
     info = b.sem_batch_info()
     assert all(e > 0 for e in info["elems_per_block"])
