@@ -99,10 +99,10 @@ def test_set_model_after_build_matches_fresh_handle(P):
 
 def test_adjoint_case_central_differences_and_autograd(P):
     """256 x 256 quads, order 4, layered true model vs the smoothed start
-    model, 3000 steps, one shot: the adjoint gradient against central finite
-    differences of the misfit on 20 seeded random elements (among those whose
-    gradient is at least 1 % of the largest), and the torch.autograd wrapper
-    against sem_misfit_gradient."""
+    model, 3000 steps, all 8 shots: the summed adjoint gradient against
+    central finite differences of the summed misfit on 20 seeded random
+    elements (among those whose gradient is at least 1 % of the largest), and
+    the torch.autograd wrapper against sem_misfit_gradient."""
     import torch
     from paper_2104_08416_gb300.autograd import Survey, trace_misfit
     c = gen.adjoint_case()
@@ -113,7 +113,8 @@ def test_adjoint_case_central_differences_and_autograd(P):
     h.sem_set_model(c["vel_true"], m["rho"])
     dt = 0.3 * h.sem_cfl_dt()
     h.sem_destroy()
-    sources = c["sources"][3:4]
+    sources = c["sources"]
+    assert len(sources) == 8
     d_obs = []
     for sx, sy in sources:
         t = P.SEM(m["coords"], m["quads"], 4, "fp64")
