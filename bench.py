@@ -85,6 +85,11 @@ def parse():
     ap.add_argument("--batch-nmax", type=int, default=1024)
     ap.add_argument("--no-compare", action="store_true", help="skip the per-ordering comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline only: skip the other precisions, the error block and the layered model")
+    ap.add_argument("--metric", default="bilinear", choices=["bilinear", "stored"],
+                    help="FP32 geometric factors formed per point from the bilinear map (default) or "
+                         "computed in FP64, rounded once and streamed")
     ap.add_argument("--scheme", default="leapfrog", choices=["leapfrog", "heun"],
                     help="leapfrog (default) or the paper's first-order system with Heun steps")
     ap.add_argument("--band", type=int, default=-1,
@@ -198,10 +203,12 @@ class ClockSampler:
 
 
 def make_handle(P, m, precision, ordering, nsteps_cap, eb=0, threads=0, scheme="leapfrog", stream=-1,
-                tiling=(-1, 0)):
+                tiling=(-1, 0), metric="bilinear"):
     h = P.SEM(m["coords"], m["quads"], 4, precision)
     if scheme != "leapfrog":
         h.sem_set_scheme(scheme)
+    if metric != "bilinear":
+        h.sem_set_metric(metric)
     if stream >= 0:
         h.sem_set_stream(stream)
     h.sem_set_stream_tiling(*tiling)
@@ -338,52 +345,66 @@ def run_reference(args, world, rank):
 
 
 def run_batched(args, P, torch):
-    """Batched shots: independent layered models of n x n quads (n uniform in
-    [nmin, nmax]) and orders 3..7 advanced by sem_batch_step (one launch per
-    order per step, CUDA graph replay, autotuned block sizes), against the same
-    handles stepped one at a time with sem_step."""
+    """Batched shots (C4): 64 independent layered models of n x n quads (n
+    uniform in [nmin, nmax]), orders 3..7, one Ricker source each, advanced by
+    sem_batch_step (streamed: per order one launch per 64-step block over the
+    blocks of all its shots, captured in a CUDA graph; block sizes autotuned
+    on 24-step streamed trials). Reported against the same shots in FP64 on
+    the GPU (batched likewise: the plain FP64 GPU path), with the error of
+    the batched run against that FP64 run after the same steps, and against
+    the batched handles stepped one shot at a time with sem_step."""
     shots = gen.batched(args.batch_shots, args.batch_nmin, args.batch_nmax)
-    K, W = args.steps, args.warmup
-    cap = 2 * (W + K) + 8
-    t0 = time.perf_counter()
-    hs = []
-    for m in shots:
-        h = P.SEM(m["coords"], m["quads"], m["order"], args.precision)
-        h.sem_reorder(args.ordering)
-        h.sem_set_model(m["vel"], m["rho"])
-        h.sem_set_source(m["f0"], m["t0"], m["amp"], *m["src_xy"])
-        h.sem_set_receivers(m["receivers"], cap)
-        h.sem_set_dt(0.3 * h.sem_cfl_dt())
-        hs.append(h)
-    b = P.SEMBatch(hs, autotune_steps=5)
-    b.sem_batch_step(W)
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
+    K = args.steps if args.steps != 2000 else 1000
+    W = args.warmup
+    cap = W + K + 8
+
+    def build_all(prec):
+        t0 = time.perf_counter()
+        hs = []
+        for m in shots:
+            h = P.SEM(m["coords"], m["quads"], m["order"], prec)
+            h.sem_reorder(args.ordering)
+            h.sem_set_model(m["vel"], m["rho"])
+            h.sem_set_source(m["f0"], m["t0"], m["amp"], *m["src_xy"])
+            h.sem_set_receivers(m["receivers"], cap + K)
+            h.sem_set_dt(0.3 * h.sem_cfl_dt())
+            hs.append(h)
+        b = P.SEMBatch(hs, autotune_steps=24)
+        b.sem_batch_step(W)
+        torch.cuda.synchronize()
+        return hs, b, time.perf_counter() - t0
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    hs, b, setup_s = build_all(args.precision)
     nodes = sum(h.n_nodes for h in hs)
     elems = sum(m["quads"].shape[0] for m in shots)
     sampler = ClockSampler(0)
     time.sleep(0.2)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    b.sem_batch_step(K)
-    e1.record()
-    torch.cuda.synchronize()
-    el = e0.elapsed_time(e1) / 1e3
-    # the same handles, one sem_step call (one launch per step) per shot
-    torch.cuda.synchronize()
-    e0.record()
-    for h in hs:
-        h.sem_step(K)
-    e1.record()
-    torch.cuda.synchronize()
-    el_solo = e0.elapsed_time(e1) / 1e3
+    el = timed(lambda: b.sem_batch_step(K))
     clocks = ClockSampler.summarize(sampler.stop())
-    finite = all(bool(np.isfinite(h.sem_read_wavefield()).all()) for h in hs[:4])
     info = b.sem_batch_info()
+    mode = b.sem_batch_mode()
+    u32 = [h.sem_read_wavefield() for h in hs]
+    # the same handles one shot at a time (each streams on its own)
+    el_solo = timed(lambda: [h.sem_step(K) for h in hs])
     b.sem_batch_destroy()
     for h in hs:
+        h.sem_destroy()
+    # the plain FP64 GPU path on the same shots and steps
+    h64, b64, setup64 = build_all("fp64")
+    el64 = timed(lambda: b64.sem_batch_step(K))
+    errs = [rel_l2(u, h.sem_read_wavefield()) for u, h in zip(u32, h64)]
+    b64.sem_batch_destroy()
+    for h in h64:
         h.sem_destroy()
     line = {
         "metric": "GLL node-updates/s (batched shots, orders 3-7)", "value": nodes * K / el, "unit": UNIT,
@@ -392,9 +413,13 @@ def run_batched(args, P, torch):
         "dtype": {"fp32_kahan": "f32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": f"batched_{args.batch_shots}_shots_{args.batch_nmin}-{args.batch_nmax}_p3-7",
                    "shots": len(hs), "nodes": nodes, "elements": elems, "precision": args.precision,
-                   "ordering": args.ordering, "autotuned": info, "setup_s": setup_s, "finite": finite},
-        "one_launch_per_shot": {"value": nodes * K / el_solo, "unit": UNIT, "ms_per_step": 1e3 * el_solo / K},
-        "gpu_launches": int(K * (len(info["orders"]) + 1) + len(hs)),
+                   "ordering": args.ordering, "autotuned": info, "mode": mode, "setup_s": setup_s},
+        "one_shot_at_a_time": {"value": nodes * K / el_solo, "unit": UNIT, "ms_per_step": 1e3 * el_solo / K},
+        "fp64_gpu": {"value": nodes * K / el64, "unit": UNIT, "ms_per_step": 1e3 * el64 / K, "setup_s": setup64},
+        "error_vs_fp64_gpu": {"steps": W + K, "max_rel_l2_over_shots": max(errs),
+                              "median_rel_l2_over_shots": float(np.median(errs)), "tolerance": 1e-5},
+        "gpu_launches": int((K // mode["steps_per_launch"] + 1) * (len(info["orders"]) + 1) + len(hs))
+        if mode["streamed"] else int(K * (len(info["orders"]) + 1) + len(hs)),
         "clocks": clocks,
     }
     print(json.dumps(line))
@@ -460,10 +485,10 @@ def run_adjoint(args, P, torch):
     print(json.dumps(line))
 
 
-def step_rate(P, torch, m, precision, k, w, ordering="hilbert"):
+def step_rate(P, torch, m, precision, k, w, ordering="hilbert", metric="bilinear"):
     """node-updates/s and the step kernel's time per step of one precision on
     a workload mesh: w untimed steps, k timed, k more with per-launch events."""
-    h = make_handle(P, m, precision, ordering, w + 2 * k + 8)
+    h = make_handle(P, m, precision, ordering, w + 2 * k + 8, metric=metric)
     h.sem_step(w)
     torch.cuda.synchronize()
     el = time_steps(torch, h, k)
@@ -526,17 +551,20 @@ def error_block(P, torch, m, nsteps=2000, S=None):
     on every node (u^-1 from the oracle's K and M), with the source on."""
     out = {}
     res = {}
-    for prec in ("fp64", "fp32_kahan"):
-        h = make_handle(P, m, prec, "hilbert", nsteps)
+    variants = (("fp64", "fp64", "bilinear"), ("fp32_kahan", "fp32_kahan", "bilinear"),
+                ("fp32_kahan_stored_metric", "fp32_kahan", "stored"))
+    for name, prec, metric in variants:
+        h = make_handle(P, m, prec, "hilbert", nsteps, metric=metric)
         h.sem_step(nsteps)
-        res[prec] = (h.sem_read_wavefield(), h.sem_read_traces())
+        res[name] = (h.sem_read_wavefield(), h.sem_read_traces())
         h.sem_destroy()
-    tr32, tr64 = res["fp32_kahan"][1], res["fp64"][1]
+    tr64 = res["fp64"][1]
     reached = bool(np.abs(tr64).max() > 0)
-    out["fp32_kahan_vs_fp64_gpu"] = {"steps": nsteps, "wavefield_rel_l2": rel_l2(res["fp32_kahan"][0], res["fp64"][0]),
-                                     # None while the wavefront has not reached the receivers
-                                     "traces_rel_l2": rel_l2(tr32, tr64) if reached else None,
-                                     "tolerance": 1e-5}
+    for name in ("fp32_kahan", "fp32_kahan_stored_metric"):
+        out[f"{name}_vs_fp64_gpu"] = {"steps": nsteps, "wavefield_rel_l2": rel_l2(res[name][0], res["fp64"][0]),
+                                      # None while the wavefront has not reached the receivers
+                                      "traces_rel_l2": rel_l2(res[name][1], tr64) if reached else None,
+                                      "tolerance": 1e-5}
     if S is not None:
         n = 10
         h = make_handle(P, m, "fp64", "hilbert", n)
@@ -548,12 +576,14 @@ def error_block(P, torch, m, nsteps=2000, S=None):
         src = (m["src_xy"][0], m["src_xy"][1], m["f0"], m["t0"], m["amp"])
         u_ref, _, tr_ref = S.run(n, dt, src=src, receivers=m["receivers"], u0=u0, u_prev=um1)
         vs = {"steps": n, "start": "cos(3 pi x) cos(2 pi y)"}
-        for prec, tol in (("fp64", 1e-12), ("fp32_kahan", 1e-5)):
-            h = make_handle(P, m, prec, "hilbert", n)
+        for name, prec, metric, tol in (("fp64", "fp64", "bilinear", 1e-12),
+                                        ("fp32_kahan", "fp32_kahan", "bilinear", 1e-5),
+                                        ("fp32_kahan_stored_metric", "fp32_kahan", "stored", 1e-5)):
+            h = make_handle(P, m, prec, "hilbert", n, metric=metric)
             h.sem_set_dt(dt)
             h.sem_set_state(u0, um1, 0)
             h.sem_step(n)
-            vs[prec] = {"wavefield_rel_l2": rel_l2(h.sem_read_wavefield(), u_ref),
+            vs[name] = {"wavefield_rel_l2": rel_l2(h.sem_read_wavefield(), u_ref),
                         "traces_rel_l2": rel_l2(h.sem_read_traces(), tr_ref), "tolerance": tol}
             h.sem_destroy()
         out["vs_cpu_oracle"] = vs
@@ -622,7 +652,7 @@ def main():
         wname = WORKLOAD if args.n == 512 else f"graded_{args.n}x{args.n}_p4"
     cap = W + 2 * K + 8
     h = make_handle(P, m, args.precision, args.ordering, cap, args.eb, args.threads, args.scheme, args.stream,
-                    (args.band, args.window))
+                    (args.band, args.window), args.metric)
     N = h.n_nodes
     # warm-up (the first call builds the device data)
     h.sem_step(W)
@@ -653,7 +683,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2 = make_handle(P, m, args.precision, args.ordering, K, args.eb, args.threads, args.scheme, args.stream,
-                    (args.band, args.window))
+                     (args.band, args.window), args.metric)
     h2.sem_step(K)
     tr = h2.sem_read_traces()
     u2 = h2.sem_read_wavefield()
@@ -703,10 +733,17 @@ def main():
                "sample": f"{k} leapfrog steps (after 2 untimed) of the FP64 C/OpenMP oracle on the full {wname} "
                          f"mesh ({N} nodes) on all host threads, set-up excluded; one_core: 2 steps on one thread"}
     extra = {}
-    if full and args.precision == "fp32_kahan" and args.ordering == "hilbert":
+    if full and args.precision == "fp32_kahan" and args.ordering == "hilbert" and not args.no_extra:
         kk = max(K, 200)
         precs = {}
-        for prec in ("fp64", "fp32"):
+        for prec in ("fp64", "fp32", "fp32_kahan_stored_metric"):
+            if prec == "fp32_kahan_stored_metric":
+                r = step_rate(P, torch, m, "fp32_kahan", kk, 3, metric="stored")
+                precs[prec] = {"value": r["node_updates_per_s"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                               "steps": kk, "note": "FP32+Kahan streaming G_q computed in FP64 and rounded once "
+                                                    "(12 B per GLL point) instead of forming it from the bilinear map",
+                               "roofline": hbm_roofline(r, "fp32_kahan", peak, peak_kind, WORKLOAD)}
+                continue
             r = step_rate(P, torch, m, prec, kk, 3)
             precs[prec] = {"value": r["node_updates_per_s"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
                            "steps": kk,
@@ -741,6 +778,7 @@ def main():
         "dtype": {"fp32_kahan": "f32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": wname, "nodes": N, "elements": m["quads"].shape[0], "order": 4,
                    "precision": args.precision, "ordering": args.ordering, "scheme": args.scheme,
+                   "metric": args.metric,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "stream_order": sorder,
                    "l2": (f"per-step working set {block_bytes / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush"
