@@ -471,16 +471,19 @@ sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void*
 typedef struct sem_batch sem_batch;
 sem_status sem_batch_create(sem_mesh* const* shots, int32_t nshots, int32_t autotune_steps, sem_batch** out);
 
-/* Advance every shot nsteps leapfrog steps. Streamed batch (every shot on a
- * DENSE plan with at most 16 neighbour blocks per block, as Hilbert and
- * row-major orderings give): per polynomial order present, one launch runs a
- * block of 64 steps over the element blocks of all shots of that order, one
- * CTA per (step, block) unit taken from a work counter, each unit waiting
- * (bounded) for the previous step at the blocks of its own shot that share a
- * node with it (as sem_set_stream does for one mesh); the launches of all
- * orders and the clock update after them are captured once as a CUDA graph
- * and replayed, the remainder launched directly. Otherwise each step is one
- * launch per order plus a step-counter update, with a 16-step graph. After
+/* Advance every shot nsteps leapfrog steps. Clock-driven batch (every shot on
+ * a DENSE plan with at most 16 neighbour blocks per block, as Hilbert and
+ * row-major orderings give, and at least one order class streaming; see
+ * sem_batch_set_stream): per polynomial order present, a streamed class runs a
+ * block of 64 steps as one launch over the element blocks of all shots of
+ * that order, one CTA per (step, block) unit taken from a work counter, each
+ * unit waiting (bounded) for the previous step at the blocks of its own shot
+ * that share a node with it (as sem_set_stream does for one mesh); a class
+ * that does not stream runs 64 launches of one step each; the launches of
+ * all orders and the update of the shots' clocks after them are captured
+ * once as a CUDA graph and replayed, the remainder launched directly.
+ * Otherwise each step is one launch per order plus a step-counter update,
+ * with a 16-step graph. After
  * the last step each shot's open nodes are completed as by sem_step. The
  * first call builds the shots' device data. Results equal those of sem_step
  * on each handle with the same block size, bit for bit. A streamed wait that
@@ -496,9 +499,21 @@ sem_status sem_batch_step(sem_batch* b, int64_t nsteps);
 sem_status sem_batch_info(const sem_batch* b, int32_t* nclasses, int32_t* orders, int32_t* elems_per_block,
                           int32_t* ctas);
 
-/* After the first sem_batch_step: streamed = 1 when the batch runs streamed
- * launches (see sem_batch_step), else 0; steps_per_launch = the steps of one
- * streamed launch (1 otherwise). Either output may be NULL. */
+/* Which order classes stream, before the first sem_batch_step: -1 (the
+ * default) streams a class where one step of it has fewer element blocks than
+ * 8 times the CTAs resident at once (the rule sem_set_stream(-1) applies to
+ * one mesh) and runs the others one launch per step inside the same captured
+ * block; 1 streams every class; 2 streams none but keeps the captured
+ * 64-step blocks with steps taken from the shots' clocks; 0 none (one launch
+ * per class and step with step counters, 16-step graphs: the scheme for
+ * GATHER plans). SEM_ERR_STATE after the first step. */
+sem_status sem_batch_set_stream(sem_batch* b, int mode);
+
+/* After the first sem_batch_step: streamed = the number of order classes
+ * running streamed launches (see sem_batch_step); steps_per_launch = the
+ * steps of one captured block of the clock-driven path (64), 1 when the
+ * batch runs one launch per class and step with step counters. Either
+ * output may be NULL. */
 sem_status sem_batch_mode(const sem_batch* b, int32_t* streamed, int32_t* steps_per_launch);
 
 /* Message of the last failing batch call ("" if none). Never NULL. */

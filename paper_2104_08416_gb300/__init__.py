@@ -46,7 +46,7 @@ EXPORTS = (
     "sem_set_tuning",
     "sem_profile_enable", "sem_profile_read", "sem_traffic_model", "sem_transfer_bytes",
     "sem_apply_stiffness_dev_noalloc", "sem_misfit_gradient", "sem_batch_create", "sem_batch_step", "sem_batch_info",
-    "sem_batch_mode", "sem_batch_last_error", "sem_batch_destroy", "sem_last_error", "sem_destroy",
+    "sem_batch_set_stream", "sem_batch_mode", "sem_batch_last_error", "sem_batch_destroy", "sem_last_error", "sem_destroy",
 )
 
 _lib = None
@@ -119,6 +119,7 @@ def load(path: str | None = None):
         "sem_batch_step": (_P, C.c_int64),
         "sem_batch_info": (_P, _I32, _I32, _I32, _I32),
         "sem_batch_mode": (_P, _I32, _I32),
+        "sem_batch_set_stream": (_P, C.c_int),
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -477,10 +478,15 @@ class SEMBatch:
     def sem_batch_step(self, nsteps: int):
         self._c(self._lib.sem_batch_step(self.h, int(nsteps)))
 
+    def sem_batch_set_stream(self, mode: int):
+        """-1 automatic (default), 1 stream every order class, 2 none but in
+        clock-driven 64-step blocks, 0 none (one launch per class and step)."""
+        self._c(self._lib.sem_batch_set_stream(self.h, int(mode)))
+
     def sem_batch_mode(self):
         st, spl = C.c_int32(), C.c_int32()
         self._c(self._lib.sem_batch_mode(self.h, C.byref(st), C.byref(spl)))
-        return {"streamed": bool(st.value), "steps_per_launch": spl.value}
+        return {"streamed_classes": st.value, "steps_per_launch": spl.value}
 
     def sem_batch_info(self):
         n = C.c_int32()

@@ -1960,11 +1960,13 @@ struct sem_batch {
         // the class launch's work counter
         semdev::BatchUnit* d_units = nullptr;
         unsigned long long* d_counter = nullptr;
+        bool streamed = false;   // streamed launches; else one launch per step (clock path)
     };
     std::vector<Class> classes;
     // streamed batch (every shot streamable): each order class runs a block
     // of steps as one launch over the blocks of all its shots
-    bool streamed = false;
+    bool streamed = false;                 // the clock-driven path (some class streams)
+    int stream_mode = -1;                  // sem_batch_set_stream: -1 automatic, 0 never, 1 every class, 2 clock path, no class
     int stream_steps = 64;                 // steps per streamed launch (one graph replay)
     semdev::ShotClock* d_clock = nullptr;  // [nshots]
     uint32_t** d_done = nullptr;           // [nshots]: each shot's done flags
@@ -2121,6 +2123,24 @@ sem_status batch_launch_stream(sem_batch* b, int n) {
     const bool f64 = b->prec == SEM_FP64;
     const int mode = b->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
     for (auto& c : b->classes) {
+        const sem_mesh* m0 = nullptr;
+        for (auto* m : b->shots)
+            if (m->mesh.np == c.np) {
+                m0 = m;
+                break;
+            }
+        const void* basis = f64 ? (const void*)&m0->basis64 : (const void*)&m0->basis32;
+        if (!c.streamed) {
+            // one launch per step over the class's blocks, steps from the clocks
+            for (int o = 0; o < n; ++o) {
+                semdev::BatchArgs ba{b->d_desc, c.d_cta_shot, c.d_cta_block, nullptr, nullptr, b->d_clock, o};
+                cudaError_t e = semdev::launch_batch_step(c.np, f64, mode, false, ba, c.ctas, basis, c.threads, c.smem,
+                                                          b->run);
+                if (e != cudaSuccess)
+                    return bfail(b, SEM_ERR_CUDA, std::string("batch step launch: ") + cudaGetErrorString(e));
+            }
+            continue;
+        }
         semdev::BatchStreamArgs sa{};
         sa.shots = b->d_desc;
         sa.units = c.d_units;
@@ -2131,13 +2151,6 @@ sem_status batch_launch_stream(sem_batch* b, int n) {
         sa.err = b->d_err;
         sa.nblk = c.ctas;
         sa.nsteps = n;
-        const sem_mesh* m0 = nullptr;
-        for (auto* m : b->shots)
-            if (m->mesh.np == c.np) {
-                m0 = m;
-                break;
-            }
-        const void* basis = f64 ? (const void*)&m0->basis64 : (const void*)&m0->basis32;
         if (cudaMemsetAsync(c.d_counter, 0, 8, b->run) != cudaSuccess)
             return bfail(b, SEM_ERR_CUDA, "work counter reset failed");
         cudaError_t e = semdev::launch_batch_stream(c.np, f64, mode, false, sa, basis, c.threads, c.smem, b->run);
@@ -2151,14 +2164,29 @@ sem_status batch_launch_stream(sem_batch* b, int n) {
 
 // Device records of a streamed batch (after the shots are built): per class
 // one BatchUnit per block of its shots, the clocks, done-flag table, serial
-// and error flag. Falls back to one launch per class and step (returns
-// false) when a shot cannot stream.
+// and error flag. A class streams where a step of it has fewer than
+// kAutoStreamWaves waves of resident CTAs (the rule sem_step applies to one
+// mesh: with more, the per-unit ticket, waits and release cost more than a
+// launch per step loses at its last wave); the other classes run one launch
+// per step inside the same captured block, their steps taken from the
+// shots' clocks. Returns false (the batch keeps one launch per class and
+// step, with step counters) when a shot cannot stream or no class would.
 bool batch_prepare_stream(sem_batch* b) {
+    if (b->stream_mode == 0) return false;
     for (auto* m : b->shots)
         if (!m->stream_ok || m->dep_stride > 16) return false;
     const bool f64 = b->prec == SEM_FP64;
     const int mode = b->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
+    int nstream = 0;
     for (auto& c : b->classes) {
+        int res = 0;
+        if (semdev::batch_stream_resident_ctas(c.np, f64, mode, c.threads, c.smem, &res) != cudaSuccess) return false;
+        c.streamed = b->stream_mode == 1 || (b->stream_mode == -1 && (int64_t)c.ctas < (int64_t)kAutoStreamWaves * res);
+        nstream += c.streamed ? 1 : 0;
+    }
+    if (nstream == 0 && b->stream_mode != 2) return false;
+    for (auto& c : b->classes) {
+        if (!c.streamed) continue;
         std::vector<semdev::BatchUnit> units;
         for (size_t i = 0; i < b->shots.size(); ++i) {
             const sem_mesh* m = b->shots[i];
@@ -2473,10 +2501,20 @@ sem_status sem_batch_info(const sem_batch* b, int32_t* nclasses, int32_t* orders
     return SEM_OK;
 }
 
+sem_status sem_batch_set_stream(sem_batch* b, int mode) {
+    if (!b || mode < -1 || mode > 2) return SEM_ERR_INVALID_ARG;
+    if (b->ready) return bfail(b, SEM_ERR_STATE, "sem_batch_set_stream after the first sem_batch_step");
+    b->stream_mode = mode;
+    return SEM_OK;
+}
+
 sem_status sem_batch_mode(const sem_batch* b, int32_t* streamed, int32_t* steps_per_launch) {
     if (!b) return SEM_ERR_INVALID_ARG;
     if (!b->ready) return SEM_ERR_STATE;
-    if (streamed) *streamed = b->streamed ? 1 : 0;
+    int32_t n = 0;
+    if (b->streamed)
+        for (const auto& c : b->classes) n += c.streamed ? 1 : 0;
+    if (streamed) *streamed = n;
     if (steps_per_launch) *steps_per_launch = b->streamed ? b->stream_steps : 1;
     return SEM_OK;
 }

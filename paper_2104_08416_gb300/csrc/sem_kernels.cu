@@ -778,7 +778,12 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     if (threadIdx.x == 0) {
         const ShotDesc<T>& d = static_cast<const ShotDesc<T>*>(ba.shots)[shot];
         s_pl = d.pl;
-        s_a = shot_step_args<T, MODE>(d, ba.step[shot], ba.pending[shot]);
+        if (ba.clock) {
+            const ShotClock c = ba.clock[shot];
+            s_a = shot_step_args<T, MODE>(d, c.step0 + ba.offset, (ba.offset > 0 || c.pending0) ? 1 : 0);
+        } else {
+            s_a = shot_step_args<T, MODE>(d, ba.step[shot], ba.pending[shot]);
+        }
     }
     __syncthreads();
     step_block<NP, T, MODE>(s_pl, s_a, bs, ba.cta_block[blockIdx.x], smem_raw, s_a.step, s_a.pending);

@@ -115,14 +115,27 @@ struct ShotDesc {
     int32_t src_gid;
 };
 
+// Per shot, advanced on the device after every launch (so that a captured
+// launch sequence can be replayed): the step number of the launch's first
+// step and whether the shot's open nodes are pending before it.
+struct ShotClock {
+    int64_t step0;
+    int32_t pending0;
+    int32_t pad;
+};
+
 // One batch launch: CTA i handles block cta_block[i] of shot cta_shot[i];
-// step[] and pending[] hold each shot's step number and pending flag.
+// step[] and pending[] hold each shot's step number and pending flag, or,
+// when clock is set, the shot's step is clock[shot].step0 + offset and its
+// open nodes are pending when offset > 0 or clock[shot].pending0.
 struct BatchArgs {
     const void* shots;         // ShotDesc<T>[nshots]
     const int32_t* cta_shot;
     const int32_t* cta_block;
     const int64_t* step;
     const int32_t* pending;
+    const ShotClock* clock;
+    int32_t offset;
 };
 
 // A streamed batch launch: several steps of every shot of one order in one
@@ -134,14 +147,6 @@ struct BatchUnit {
     int32_t hdr[12];
     int32_t shot, block, dep_stride, pad;
     int32_t dep[16];
-};
-// Per shot, advanced on the device after every launch (so that a captured
-// launch sequence can be replayed): the step number of the launch's first
-// step and whether the shot's open nodes are pending before it.
-struct ShotClock {
-    int64_t step0;
-    int32_t pending0;
-    int32_t pad;
 };
 struct BatchStreamArgs {
     const void* shots;          // ShotDesc<T>[nshots]

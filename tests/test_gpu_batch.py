@@ -83,21 +83,27 @@ def _streamable_shots():
     ]
 
 
-@pytest.mark.parametrize("prec", ["fp32_kahan", "fp64"])
-def test_streamed_batch_equals_individual_runs(P, prec):
-    """Every shot streamable: each order runs as one launch per block of 64
-    steps over the blocks of all its shots (graph replays, a single step, a
-    remainder, a second call); shot by shot bitwise the results of sem_step
-    on each handle alone."""
+@pytest.mark.parametrize("prec,mode", [("fp32_kahan", -1), ("fp64", -1), ("fp32_kahan", 2), ("fp64", 1)])
+def test_streamed_batch_equals_individual_runs(P, prec, mode):
+    """Every shot streamable: in clock-driven 64-step blocks each order runs
+    as one streamed launch over the blocks of all its shots (mode -1: the
+    automatic choice streams these small classes; 1: every class) or as one
+    launch per step (mode 2), across graph replays, a single step, a
+    remainder and a second call; shot by shot bitwise the results of
+    sem_step on each handle alone."""
     shots = _streamable_shots()
     nmax = 160
     chunks = (70, 1, 64, 5)
     batch_h = [_handle(P, m, p, k, prec, nmax, eb=11) for m, p, k in shots]
     solo_h = [_handle(P, m, p, k, prec, nmax, eb=11) for m, p, k in shots]
     b = P.SEMBatch(batch_h)
+    b.sem_batch_set_stream(mode)
     for c in chunks:
         b.sem_batch_step(c)
-    assert b.sem_batch_mode() == {"streamed": True, "steps_per_launch": 64}
+    assert b.sem_batch_mode() == {"streamed_classes": 0 if mode == 2 else 5, "steps_per_launch": 64}
+    with pytest.raises(P.SemError) as ei:
+        b.sem_batch_set_stream(0)
+    assert ei.value.status == P.SEM_ERR_STATE
     for h in solo_h:
         for c in chunks:
             h.sem_step(c)
@@ -122,7 +128,7 @@ def test_batch_with_a_gather_plan_runs_one_launch_per_step(P):
     hs = [_handle(P, m, p, k, "fp32_kahan", 8, eb=11) for m, p, k in shots]
     b = P.SEMBatch(hs)
     b.sem_batch_step(3)
-    assert b.sem_batch_mode() == {"streamed": False, "steps_per_launch": 1}
+    assert b.sem_batch_mode() == {"streamed_classes": 0, "steps_per_launch": 1}
     b.sem_batch_destroy()
     for h in hs:
         h.sem_destroy()
