@@ -389,8 +389,9 @@ sem_status sem_stream_schedule(const int32_t* dep_ptr, const int32_t* dep, int32
 sem_status sem_stream_withhold(sem_mesh* m, int64_t step, int32_t block);
 
 /* Launch shape of the step kernel: elements per block (0 = default, about
- * 6400 element points per block, at most 256, one thread per element; in
- * FP64 on a mesh with fewer elements than that times the device's SM count,
+ * 6400 element points per block in FP32 and 3200 in FP64, at most 256, one
+ * thread per element; in FP64 on a mesh with fewer elements than that times
+ * the device's SM count,
  * the elements over the SM count, at least 4, so that a step's
  * double-precision arithmetic spreads over every SM) and
  * threads per block (0 = one per element rounded up to whole warps; else a

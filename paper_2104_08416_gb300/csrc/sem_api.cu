@@ -292,10 +292,16 @@ int device_sm_count() {
     return sms;
 }
 
-int default_eb(int np) {
-    // about 6400 element points per block, at most 256 elements (threads)
+int default_eb(int np, bool f64) {
+    // about 6400 element points per block (FP32), at most 256 elements
+    // (threads). FP64 blocks hold half as many (128 elements at order 4):
+    // the FP64 kernels use about 254 registers per thread, so a 256-thread
+    // block is alone on its SM and its memory phases leave the FP64 units
+    // idle; two half-size blocks per SM overlap one's memory phases with the
+    // other's arithmetic (graded 512 x 512, order 4: 10.6 against 9.8 G
+    // node-updates/s; layered 4096 x 1024: 11.1 against 10.2 G)
     const int P = np * np;
-    int eb = (6400 + P / 2) / P;
+    int eb = ((f64 ? 3200 : 6400) + P / 2) / P;
     if (eb > 256) eb = 256;
     if (eb < 1) eb = 1;
     return eb;
@@ -373,7 +379,7 @@ sem_status build_host(sem_mesh* m) {
             }
         if (m->rec_row[(size_t)r] < 0) rec_gid[(size_t)r] = g;
     }
-    int eb = m->eb_request > 0 ? m->eb_request : default_eb(M.np);
+    int eb = m->eb_request > 0 ? m->eb_request : default_eb(M.np, fp64(m));
     // small FP64 meshes (default size only): at least one block per SM, so
     // that a step's double-precision arithmetic, slow per SM on this GPU,
     // spreads over all of them (FP32 small meshes keep the larger blocks:
