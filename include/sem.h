@@ -248,7 +248,13 @@ sem_status sem_get_state(sem_mesh* m, double* u, double* u_prev, int64_t* step);
 /* Matrix-free stiffness application Ku = K u (Eq. u_change_r_effic in the
  * second-order form) with the handle's precision, on host arrays in original
  * node order (u[N] in, Ku[N] out). Does not change the time-stepping state.
- * Synchronises. Needs the model. */
+ * Synchronises. Needs the model. On DENSE block plans every step and apply
+ * launch copies each block's packet and owned node range into shared memory
+ * with bulk copies whose completion barrier is waited on with the same
+ * bound as the streamed waits (sem_set_stream); a wait that gave up raises
+ * the device error flag, and this call (or, after a step or a device-array
+ * apply, the next sem_read_wavefield, sem_get_state or sem_read_traces)
+ * returns SEM_ERR_TIMEOUT. */
 sem_status sem_apply_stiffness(sem_mesh* m, const double* u, double* Ku);
 
 /* Lumped diagonal mass M_nu = sum over (e, q) with mu(q, e) = nu of
@@ -444,7 +450,9 @@ sem_status sem_transfer_bytes(const sem_mesh* m, int64_t* h2d, int64_t* d2h);
  * first call before any stream capture. All calls share the one scratch
  * array: calls that may overlap on the GPU (different streams, handles or
  * threads) race on it. Every scratch value a call reads was written earlier
- * in the same call, so nothing needs clearing between calls. */
+ * in the same call, so nothing needs clearing between calls. A bounded wait
+ * that gave up is reported as for sem_apply_stiffness, at the next call that
+ * reads back. */
 #define SEM_NOALLOC_SCRATCH_BYTES (16u << 20)
 sem_status sem_apply_stiffness_dev_noalloc(sem_mesh* m, const void* dev_u, void* dev_Ku);
 

@@ -541,6 +541,13 @@ sem_status build(sem_mesh* m) {
         if ((st = zeros(m, &tr, (size_t)m->nrec * (size_t)m->trace_cap * 8)) != SEM_OK) return st;
         m->d_trace = (double*)tr;
     }
+    // error word: raised on the device by a bounded wait that gave up (a
+    // streamed unit's neighbour flags, a bulk copy's barrier)
+    {
+        void* er = nullptr;
+        if ((st = zeros(m, &er, 4)) != SEM_OK) return st;
+        m->d_err = (int32_t*)er;
+    }
     // streamed time loop: leapfrog on a DENSE plan
     m->stream_ok = false;
     const int md = mode_of(m);
@@ -557,13 +564,11 @@ sem_status build(sem_mesh* m) {
             }
         m->dep_stride = stride;
         if ((st = upload(m, &m->d_dep, pad.data(), pad.size())) != SEM_OK) return st;
-        void *done = nullptr, *ctr = nullptr, *er = nullptr;
+        void *done = nullptr, *ctr = nullptr;
         if ((st = zeros(m, &done, (size_t)pl.nblocks * 4)) != SEM_OK) return st;
         if ((st = zeros(m, &ctr, 8)) != SEM_OK) return st;
-        if ((st = zeros(m, &er, 4)) != SEM_OK) return st;
         m->d_done = (uint32_t*)done;
         m->d_counter = (unsigned long long*)ctr;
-        m->d_err = (int32_t*)er;
         m->serial = 1;
         int res = 0;
         SEM_CUDA(semdev::stream_resident_ctas(M.np, fp64(m), md, m->d_G32 != nullptr, m->threads, m->smem, &res));
@@ -647,6 +652,7 @@ semdev::StepArgs<T> step_args(sem_mesh* m, int64_t k, bool pending) {
     a.trace_cap = m->trace_cap;
     a.pending = pending ? 1 : 0;
     a.vec_ok = 1;
+    a.err = m->d_err;
     return a;
 }
 
@@ -682,6 +688,7 @@ semdev::ShotDesc<T> shot_desc(const sem_mesh* m) {
     d.trace = m->d_trace;
     d.trace_cap = m->trace_cap;
     d.src_gid = m->have_src ? (int32_t)m->node_new[(size_t)m->src_node] : -1;
+    d.err = m->d_err;
     return d;
 }
 
@@ -822,7 +829,9 @@ sem_status check_stream_error(sem_mesh* m) {
     if (h != 0) {
         SEM_CUDA(cudaMemsetAsync(m->d_err, 0, 4, m->stream));
         SEM_CUDA(cudaStreamSynchronize(m->stream));
-        return fail(m, SEM_ERR_TIMEOUT, "a streamed step gave up waiting for a neighbouring block; steps were skipped");
+        return fail(m, SEM_ERR_TIMEOUT,
+                    "a step gave up waiting (a streamed unit for a neighbouring block, or a block for its bulk copy); "
+                    "steps were skipped");
     }
     return SEM_OK;
 }
@@ -896,6 +905,7 @@ sem_status heun_launches(sem_mesh* m) {
     a.trace = m->d_trace;
     a.trace_cap = m->trace_cap;
     a.vec_ok = 1;
+    a.err = m->d_err;
     a.h = m->dt;
     a.u_d1 = (T*)m->d_ud1;
     a.v_d1 = (T*)m->d_vd1;
@@ -946,6 +956,7 @@ sem_status launch_apply(sem_mesh* m, const void* dev_in, void* dev_out, void* pa
         a.part_rd = (const double*)partial;
         a.vec_ok = vok;
         a.src_gid = -1;
+        a.err = m->d_err;
         e = semdev::launch_step(m->mesh.np, true, semdev::MODE_APPLY, m->dplan, &a, basis_of(m), m->threads, m->smem,
                                 m->stream);
         if (e == cudaSuccess) e = semdev::launch_open_finish(true, semdev::MODE_APPLY, m->dplan, &a, m->stream);
@@ -957,6 +968,7 @@ sem_status launch_apply(sem_mesh* m, const void* dev_in, void* dev_out, void* pa
         a.part_rd = (const float*)partial;
         a.vec_ok = vok;
         a.src_gid = -1;
+        a.err = m->d_err;
         e = semdev::launch_step(m->mesh.np, false, semdev::MODE_APPLY, m->dplan, &a, basis_of(m), m->threads,
                                 m->smem, m->stream);
         if (e == cudaSuccess) e = semdev::launch_open_finish(false, semdev::MODE_APPLY, m->dplan, &a, m->stream);
@@ -1437,6 +1449,7 @@ sem_status sem_apply_stiffness(sem_mesh* m, const double* u, double* Ku) {
     if ((st = launch_apply(m, m->d_apply_in, m->d_apply_out, m->d_part[m->step & 1])) != SEM_OK) return st;
     std::vector<double> out;
     if ((st = read_nodes(m, m->d_apply_out, fp64(m), out)) != SEM_OK) return st;
+    if ((st = check_stream_error(m)) != SEM_OK) return st;
     to_original(m, out, Ku);
     return SEM_OK;
 }
@@ -1896,6 +1909,7 @@ sem_status sem_misfit_gradient(sem_mesh* m, const double* d_obs, int64_t nsteps,
     if ((st = copy_dev(m, level_x(m, nsteps), fin_x)) != SEM_OK) return st;
     SEM_CUDA(cudaStreamSynchronize(m->stream));
     m->step = nsteps;
+    if ((st = check_stream_error(m)) != SEM_OK) return st;
     for (int64_t i = 0; i < m->mesh.ne; ++i) grad_vel[(size_t)m->elem_order[(size_t)m->plan.dev_order[(size_t)i]]] = g[(size_t)i];
     return SEM_OK;
 }
@@ -2023,6 +2037,11 @@ void unbuild(sem_mesh* m) {
     m->d_grad = nullptr;
     m->d_conn_dev = nullptr;
     m->d_rec_node = m->d_rec_row = m->d_rec_order = m->d_rec_first = nullptr;
+    m->d_err = nullptr;
+    m->d_done = nullptr;
+    m->d_counter = nullptr;
+    m->d_dep = nullptr;
+    m->stream_ok = false;
     m->d_chk.clear();
     m->d_seg.clear();
     m->built = false;
@@ -2047,11 +2066,17 @@ sem_status upload_desc(sem_batch* b) {
     std::vector<uint8_t> host;
     if (b->prec == SEM_FP64) {
         std::vector<semdev::ShotDesc<double>> v(n);
-        for (size_t i = 0; i < n; ++i) v[i] = shot_desc<double>(b->shots[i]);
+        for (size_t i = 0; i < n; ++i) {
+            v[i] = shot_desc<double>(b->shots[i]);
+            if (b->d_err) v[i].err = b->d_err;
+        }
         host.assign(reinterpret_cast<uint8_t*>(v.data()), reinterpret_cast<uint8_t*>(v.data() + n));
     } else {
         std::vector<semdev::ShotDesc<float>> v(n);
-        for (size_t i = 0; i < n; ++i) v[i] = shot_desc<float>(b->shots[i]);
+        for (size_t i = 0; i < n; ++i) {
+            v[i] = shot_desc<float>(b->shots[i]);
+            if (b->d_err) v[i].err = b->d_err;
+        }
         host.assign(reinterpret_cast<uint8_t*>(v.data()), reinterpret_cast<uint8_t*>(v.data() + n));
     }
     if (!b->d_desc) {

@@ -116,6 +116,64 @@ __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
 }
+// A wait gives up once it has lasted kWaitNs of the GPU's global timer
+// (read every 64 polls; a unit normally waits microseconds at most), or,
+// whatever the timer says, after kWaitPolls polls (each followed by a
+// 128 ns back-off, so at least 8.6 s of nominal sleep, for a flag; a bulk
+// copy's barrier is polled with the hardware's own suspend hint instead).
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr int kWaitPolls = 1 << 26;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// 1-D bulk copies (the TMA engine) into shared memory, completing on an
+// mbarrier of the CTA: one thread issues them, every thread waits on the
+// barrier's phase. Source and destination 16-byte aligned, size a multiple
+// of 16 bytes. The barrier is initialised once per unit (arrival count 1:
+// the issuing thread's arrive with the expected byte count).
+__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned bytes, unsigned mb) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(sa), "l"(gmem), "r"(bytes), "r"(mb) : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned mb) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+    // the initialisation, and this thread's earlier shared-memory accesses,
+    // ordered before the copies the async proxy performs
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned mb, unsigned bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cluster.shared::cta.b64 [%0], %1;\n" ::"r"(mb), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(unsigned mb, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned mb, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for phase 0 of the barrier; false if it gave up (kWaitNs of the
+// global timer, or kWaitPolls polls).
+__device__ __forceinline__ bool mbar_wait(unsigned mb) {
+    unsigned long long t0 = 0;
+    for (int n = 0; !mbar_try(mb, 0); ++n) {
+        if ((n & 63) == 63) {
+            const unsigned long long now = global_ns();
+            if (n == 63) t0 = now;
+            if (now - t0 > kWaitNs || n >= kWaitPolls) return false;
+        }
+    }
+    return true;
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -404,41 +462,80 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
         }
     }
 
-    // A1. packet, owned node range, zeroed accumulators
+    // A1. packet, owned node range, zeroed accumulators. DENSE plans with
+    // 16-byte aligned node arrays copy the packet and the owned range of u
+    // with 1-D bulk copies issued by thread 0 (one instruction per range,
+    // completion on an mbarrier), the others with 16-byte cp.async per thread
     {
         const uint8_t* gpk = pl.packet + (int64_t)h.start * 16;
-        for (int o = tid * 16; o < L.bytes; o += nt * 16) cp_async16(spk + o, gpk + o);
+        __shared__ __align__(8) unsigned long long s_mbar;
+        const unsigned mb = (unsigned)__cvta_generic_to_shared(&s_mbar);
+        const bool bulk = pl.dense && a.vec_ok != 0;
+        if (bulk) {
+            if (tid == 0) {
+                mbar_init(mb);
+                mbar_expect(mb, (unsigned)L.bytes);
+                bulk_g2s(spk, gpk, (unsigned)L.bytes, mb);
+            }
+        } else {
+            for (int o = tid * 16; o < L.bytes; o += nt * 16) cp_async16(spk + o, gpk + o);
+        }
         float4* az = reinterpret_cast<float4*>(acc);
         const int nz = (h.sulen * (int)sizeof(T) + 15) / 16;
         for (int k = tid; k < nz; k += nt) az[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!ready()) {
+            // the packet copy in flight completes before the CTA leaves
+            if (bulk) {
+                if (tid == 0) mbar_arrive_expect(mb, 0u);
+                __syncthreads();
+                mbar_wait(mb);
+            }
             cp_async_commit();
             cp_async_wait_all();
             return;
         }
         if (pl.dense) {
-            const bool vok = a.vec_ok != 0;
-            stage_range(su, a.u_k, abase, h.ulen, pl.nn, vok, tid, nt);
+            if (bulk) {
+                // the chunks wholly inside the array by one copy; the last
+                // block's tail, if the array ends inside a chunk, by loads
+                const int nchunk = h.ulen / VEC;
+                const int64_t room = (pl.nn - abase) / VEC;
+                const int nfull = (int)max((int64_t)0, min((int64_t)nchunk, room));
+                if (tid == 0) {
+                    const unsigned ub = (unsigned)nfull * 16u;
+                    mbar_arrive_expect(mb, ub);
+                    if (ub) bulk_g2s(su, a.u_k + abase, ub, mb);
+                }
+                for (int ch = nfull + tid; ch < nchunk; ch += nt) {
+                    const int64_t g = abase + (int64_t)ch * VEC;
+#pragma unroll
+                    for (int t = 0; t < VEC; ++t)
+                        if (g + t < pl.nn) su[ch * VEC + t] = __ldcg(a.u_k + g + t);
+                }
+            } else {
+                stage_range(su, a.u_k, abase, h.ulen, pl.nn, false, tid, nt);
+            }
             if (STATE) {
-                if (!direct) stage_range(ss, a.s, abase, h.ulen, pl.nn, vok, tid, nt);
-                if (KAHAN && !direct) stage_range(sc, a.c_k, abase, h.ulen, pl.nn, vok, tid, nt);
-                if (direct) {
-                    // s, u^{k-1} or delta and the compensation, read in
-                    // phase C chunk by chunk:
-                    // into L2 now, so that phase C's first loads do not wait
-                    // on DRAM (32 values per 128-byte line)
-                    const int nline = (h.slen * (int)sizeof(T) + 127) / 128;
-                    for (int l = tid; l < nline; l += nt) {
-                        prefetch_l2(a.s + abase + (int64_t)l * (128 / sizeof(T)));
-                        prefetch_l2(a.x_k + abase + (int64_t)l * (128 / sizeof(T)));
-                        if (KAHAN) prefetch_l2(a.c_k + abase + (int64_t)l * (128 / sizeof(T)));
-                    }
+                // s, u^{k-1} or delta and the compensation, read in phase C
+                // chunk by chunk: into L2 now, so that phase C's first loads
+                // do not wait on DRAM (32 values per 128-byte line)
+                const int nline = (h.slen * (int)sizeof(T) + 127) / 128;
+                for (int l = tid; l < nline; l += nt) {
+                    prefetch_l2(a.s + abase + (int64_t)l * (128 / sizeof(T)));
+                    prefetch_l2(a.x_k + abase + (int64_t)l * (128 / sizeof(T)));
+                    if (KAHAN) prefetch_l2(a.c_k + abase + (int64_t)l * (128 / sizeof(T)));
                 }
             }
         }
         cp_async_commit();
         cp_async_wait_all();
-        __syncthreads();
+        __syncthreads();   // every thread is past the barrier's initialisation
+        if (bulk && __syncthreads_or(!mbar_wait(mb))) {
+            // a copy that never completed (the wait is bounded): the unit
+            // is abandoned and the error word raised
+            if (tid == 0 && a.err) atomicExch(a.err, 1);
+            return;
+        }
     }
     const uint32_t* cmask = reinterpret_cast<const uint32_t*>(spk + L.cmask);
     const int32_t* egid = reinterpret_cast<const int32_t*>(spk + L.egid);
@@ -630,10 +727,14 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 T ui[VEC], ku[VEC], out[VEC];
                 load_vec<T, VEC>(ui, su + p0);
                 load_vec<T, VEC>(ku, acc + p0);
+                // closed positions only: the predictor also stores the rate
+                // dU at the node, and the chunk's other positions are open
+                // nodes (finished by the open-node kernel) or, at the ends of
+                // the owned range, nodes of the neighbouring blocks
 #pragma unroll
                 for (int t = 0; t < VEC; ++t) {
                     const T f = (g0 + t == a.src_gid) ? f_now : T(0);
-                    out[t] = heun_node<T, MODE>(a, g0 + t, ui[t], ku[t], f);
+                    out[t] = ((bits >> t) & 1u) ? heun_node<T, MODE>(a, g0 + t, ui[t], ku[t], f) : T(0);
                 }
                 store_masked<T, VEC>(a.u_kp1 + g0, out, bits);
                 if (MODE == MODE_HEUN_C && h.nrc > 0) {
@@ -767,6 +868,7 @@ __device__ __forceinline__ StepArgs<T> shot_step_args(const ShotDesc<T>& d, int6
     a.trace_cap = d.trace_cap;
     a.pending = pending;
     a.vec_ok = 1;
+    a.err = d.err;
     return a;
 }
 
@@ -823,17 +925,6 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int32_t* p) {
     return v;
 }
 
-// A wait gives up once it has lasted kWaitNs of the GPU's global timer
-// (read every 64 polls; a unit normally waits microseconds at most), or,
-// whatever the timer says, after kWaitPolls polls (each followed by a
-// 128 ns back-off, so at least 8.6 s of nominal sleep).
-constexpr unsigned long long kWaitNs = 1000000000ull;
-constexpr int kWaitPolls = 1 << 26;
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
-    return t;
-}
 
 // Unit (i, b) of a launch from its ticket offset u (0 <= u < total): step
 // order, or the band's wavefront order for the first tiled_units tickets.

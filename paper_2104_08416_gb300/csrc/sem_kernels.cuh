@@ -82,6 +82,7 @@ struct StepArgs {
     int64_t trace_cap;
     int pending;
     int vec_ok;           // node arrays 16-byte aligned (vector copies allowed)
+    int32_t* err;         // error word raised by a wait that gave up (may be null)
     // first-order system (Section 4.1-4.2: pressure U at global nodes,
     // velocity V at every element's local nodes, layout [2P][ne]) advanced by
     // Heun's method: the predictor reads U (u_k) and V (v_in), writes
@@ -113,6 +114,7 @@ struct ShotDesc {
     double* trace;
     int64_t trace_cap;
     int32_t src_gid;
+    int32_t* err;     // error word of the handle or batch running the shot
 };
 
 // Per shot, advanced on the device after every launch (so that a captured

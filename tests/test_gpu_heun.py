@@ -81,6 +81,19 @@ def test_heun_split_runs_bitwise(P):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+def test_heun_repeated_runs_bitwise(P):
+    # small blocks: many owned ranges whose 16-byte-aligned ends reach into a
+    # neighbouring block's nodes; every run must give the same bits (the
+    # predictor stores its rate only at the block's own closed nodes)
+    m = gen.graded(16, seed=5)
+    S = osem.SEM(m["coords"], m["quads"], 4, m["vel"], m["rho"])
+    dt = 0.1 * S.cfl_dt()
+    rec = np.array([[0.3, 0.7]])
+    runs = [_run(P, m, 4, "fp32", "hilbert", 120, dt, rec, eb=5) for _ in range(3)]
+    for u, tr in runs[1:]:
+        assert np.array_equal(u, runs[0][0]) and np.array_equal(tr, runs[0][1])
+
+
 def test_heun_rejects_kahan_and_adjoint(P):
     m = gen.unit_square(3)
     h = P.SEM(m["coords"], m["quads"], 3, "fp32_kahan")
