@@ -146,9 +146,6 @@ __device__ __forceinline__ void mbar_init(unsigned mb) {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
-__device__ __forceinline__ void mbar_expect(unsigned mb, unsigned bytes) {
-    asm volatile("mbarrier.expect_tx.relaxed.cluster.shared::cta.b64 [%0], %1;\n" ::"r"(mb), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive_expect(unsigned mb, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(bytes) : "memory");
 }
@@ -407,7 +404,8 @@ struct NoWait {
 template <int NP, typename T, int MODE, bool SG = false, typename Ready = NoWait>
 __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a, const Basis<T>& bs, const int b,
                                            unsigned char* smem_raw, const int64_t step, const int pend,
-                                           const Ready& ready = Ready(), const BlockHdr* hpre = nullptr) {
+                                           const Ready& ready = Ready(), const BlockHdr* hpre = nullptr,
+                                           unsigned long long* mbar_pre = nullptr) {
     constexpr int P = NP * NP;
     constexpr int UPH = (P + 1) / 2;
     constexpr bool HEUN = MODE == MODE_HEUN_P || MODE == MODE_HEUN_C;
@@ -464,18 +462,25 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
 
     // A1. packet, owned node range, zeroed accumulators. DENSE plans with
     // 16-byte aligned node arrays copy the packet and the owned range of u
-    // with 1-D bulk copies issued by thread 0 (one instruction per range,
-    // completion on an mbarrier), the others with 16-byte cp.async per thread
+    // with 1-D bulk copies issued by thread 0 (one instruction per range),
+    // completing on two mbarriers (packet, u), so that the open entries'
+    // loads can go out as soon as the packet is in, while u is still landing;
+    // a caller may have issued the packet copy already (mbar_pre: the
+    // streamed kernel does it while its neighbour wait is under way). Other
+    // plans copy with 16-byte cp.async per thread.
+    const bool bulk = pl.dense && a.vec_ok != 0;
+    __shared__ __align__(8) unsigned long long s_mbar_own[2];
+    unsigned long long* mbp = mbar_pre ? mbar_pre : s_mbar_own;
+    const unsigned mbk = (unsigned)__cvta_generic_to_shared(mbp);
+    const unsigned mbu = (unsigned)__cvta_generic_to_shared(mbp + 1);
     {
         const uint8_t* gpk = pl.packet + (int64_t)h.start * 16;
-        __shared__ __align__(8) unsigned long long s_mbar;
-        const unsigned mb = (unsigned)__cvta_generic_to_shared(&s_mbar);
-        const bool bulk = pl.dense && a.vec_ok != 0;
         if (bulk) {
-            if (tid == 0) {
-                mbar_init(mb);
-                mbar_expect(mb, (unsigned)L.bytes);
-                bulk_g2s(spk, gpk, (unsigned)L.bytes, mb);
+            if (!mbar_pre && tid == 0) {
+                mbar_init(mbk);
+                mbar_init(mbu);
+                mbar_arrive_expect(mbk, (unsigned)L.bytes);
+                bulk_g2s(spk, gpk, (unsigned)L.bytes, mbk);
             }
         } else {
             for (int o = tid * 16; o < L.bytes; o += nt * 16) cp_async16(spk + o, gpk + o);
@@ -486,9 +491,8 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
         if (!ready()) {
             // the packet copy in flight completes before the CTA leaves
             if (bulk) {
-                if (tid == 0) mbar_arrive_expect(mb, 0u);
                 __syncthreads();
-                mbar_wait(mb);
+                mbar_wait(mbk);
             }
             cp_async_commit();
             cp_async_wait_all();
@@ -503,8 +507,8 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 const int nfull = (int)max((int64_t)0, min((int64_t)nchunk, room));
                 if (tid == 0) {
                     const unsigned ub = (unsigned)nfull * 16u;
-                    mbar_arrive_expect(mb, ub);
-                    if (ub) bulk_g2s(su, a.u_k + abase, ub, mb);
+                    mbar_arrive_expect(mbu, ub);
+                    if (ub) bulk_g2s(su, a.u_k + abase, ub, mbu);
                 }
                 for (int ch = nfull + tid; ch < nchunk; ch += nt) {
                     const int64_t g = abase + (int64_t)ch * VEC;
@@ -527,14 +531,19 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 }
             }
         }
-        cp_async_commit();
-        cp_async_wait_all();
-        __syncthreads();   // every thread is past the barrier's initialisation
-        if (bulk && __syncthreads_or(!mbar_wait(mb))) {
-            // a copy that never completed (the wait is bounded): the unit
-            // is abandoned and the error word raised
-            if (tid == 0 && a.err) atomicExch(a.err, 1);
-            return;
+        if (bulk) {
+            // the barriers' initialisation seen by every thread (when this
+            // block did it), then the packet; a copy that never completes
+            // (the wait is bounded) abandons the unit and raises the error word
+            if (!mbar_pre) __syncthreads();
+            if (__syncthreads_or(!mbar_wait(mbk))) {
+                if (tid == 0 && a.err) atomicExch(a.err, 1);
+                return;
+            }
+        } else {
+            cp_async_commit();
+            cp_async_wait_all();
+            __syncthreads();
         }
     }
     const uint32_t* cmask = reinterpret_cast<const uint32_t*>(spk + L.cmask);
@@ -560,15 +569,21 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             }
     }
     const bool pending = STATE && pend;
+    bool staged_ok = true;
     if (!pending) {
+        // level k stored whole: u^k at the open entries outside the staged
+        // range (those inside it are staged)
         for (int o = tid; o < h.nopen; o += nt) {
             const int pos = opos[o];
-            const int64_t g = pos < h.ulen ? abase + pos : (int64_t)egid[pos - h.ulen];
-            su[pos] = __ldcg(a.u_k + g);
+            if (pos < h.ulen) continue;
+            su[pos] = __ldcg(a.u_k + egid[pos - h.ulen]);
         }
+        if (bulk) staged_ok = mbar_wait(mbu);
     } else {
         // two open entries per pass, every load of both issued before either
-        // is used: one round trip per pass
+        // is used: one round trip per pass; the first pass's loads go out
+        // before the wait for the staged u, which the finished values
+        // overwrite
         auto fetch = [&](int o, OpenIn<T>& in) {
             in.pos = opos[o];
             in.g = in.pos < h.ulen ? abase + in.pos : (int64_t)egid[in.pos - h.ulen];
@@ -600,18 +615,29 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 }
             }
         };
-        for (int o0 = tid; o0 < h.nopen; o0 += 2 * nt) {
-            const int o1 = o0 + nt;
-            OpenIn<T> in0, in1;
-            fetch(o0, in0);
-            if (o1 < h.nopen) fetch(o1, in1);
-            finish(in0);
+        const int o0 = tid, o1 = tid + nt;
+        OpenIn<T> in0, in1;
+        if (o0 < h.nopen) fetch(o0, in0);
+        if (o1 < h.nopen) fetch(o1, in1);
+        if (bulk) staged_ok = mbar_wait(mbu);
+        if (staged_ok) {
+            if (o0 < h.nopen) finish(in0);
             if (o1 < h.nopen) finish(in1);
+            for (int q0 = tid + 2 * nt; q0 < h.nopen; q0 += 2 * nt) {
+                const int q1 = q0 + nt;
+                fetch(q0, in0);
+                if (q1 < h.nopen) fetch(q1, in1);
+                finish(in0);
+                if (q1 < h.nopen) finish(in1);
+            }
         }
     }
     cp_async_commit();
     cp_async_wait_all();
-    __syncthreads();
+    if (__syncthreads_or(!staged_ok)) {
+        if (tid == 0 && a.err) atomicExch(a.err, 1);
+        return;
+    }
     if (pending && h.nro > 0) {
         for (int k = tid; k < h.nro; k += nt) {
             const int pos = recs[2 * (h.nrc + k)], r = recs[2 * (h.nrc + k) + 1];
@@ -990,6 +1016,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     __shared__ int s_i, s_b;
     __shared__ __align__(16) int32_t s_dep[kMaxStreamDeps];
     __shared__ int s_fail;
+    __shared__ __align__(8) unsigned long long s_mb[2];
     const int nb = d.pl.nblocks;
     const long long total = (long long)sa.nsteps * nb;
     if (threadIdx.x == 0) {
@@ -1005,9 +1032,20 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
         if (ui >= 0) {
             // the unit's step arguments and block header, for every thread
             s_a = shot_step_args<T, MODE>(d, sa.step0 + ui, (ui > 0 || sa.pending0) ? 1 : 0);
-            s_h = load_hdr(d.pl.hdr, ub);
+            const BlockHdr hh = load_hdr(d.pl.hdr, ub);
+            s_h = hh;
             const int4* dr = reinterpret_cast<const int4*>(sa.dep + (int64_t)ub * sa.dep_stride);
             for (int q = 0; q < sa.dep_stride / 4; ++q) reinterpret_cast<int4*>(s_dep)[q] = dr[q];
+            if (d.pl.dense) {
+                // the block's packet (static) is copied while the neighbour
+                // wait below is under way; step_block waits for it
+                const unsigned m0 = (unsigned)__cvta_generic_to_shared(&s_mb[0]);
+                mbar_init(m0);
+                mbar_init((unsigned)__cvta_generic_to_shared(&s_mb[1]));
+                const Offsets L = offsets(hh.sulen, hh.ulen, hh.nopen, hh.ncolors, hh.nrc + hh.nro);
+                mbar_arrive_expect(m0, (unsigned)L.bytes);
+                bulk_g2s(smem_raw, d.pl.packet + (int64_t)hh.start * 16, (unsigned)L.bytes, m0);
+            }
         }
     }
     // the neighbours' previous step, awaited by warp 0 (one flag per lane)
@@ -1029,7 +1067,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
     const int64_t k = sa.step0 + i;
     const int pend = (i > 0 || sa.pending0) ? 1 : 0;
     const PrologueWaited w{&s_fail};
-    step_block<NP, T, MODE, SG>(d.pl, s_a, bs, b, smem_raw, k, pend, w, &s_h);
+    step_block<NP, T, MODE, SG>(d.pl, s_a, bs, b, smem_raw, k, pend, w, &s_h, d.pl.dense ? s_mb : nullptr);
     // every thread's stores of the unit precede the flag: the barrier orders
     // them before thread 0's release store (release at GPU scope covers what
     // the barrier made it observe)
