@@ -507,6 +507,10 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
                 const int nfull = (int)max((int64_t)0, min((int64_t)nchunk, room));
                 if (tid == 0) {
                     const unsigned ub = (unsigned)nfull * 16u;
+                    // u as other blocks' stores left it (made visible to this
+                    // CTA by the neighbour wait or the launch boundary), ordered
+                    // before the copy engine's reads
+                    asm volatile("fence.proxy.async.global;\n" ::: "memory");
                     mbar_arrive_expect(mbu, ub);
                     if (ub) bulk_g2s(su, a.u_k + abase, ub, mbu);
                 }
@@ -1049,10 +1053,12 @@ __global__ void __launch_bounds__(kMaxStepThreads, (step_min_blocks<NP, T>()))
         }
     }
     // the neighbours' previous step, awaited by warp 0 (one flag per lane)
-    // before the unit issues any other load. Measured on the graded 512 x 512
-    // mesh: polling with the element data and packet loads already in flight
-    // took 5.6k cycles per unit against 1.1k here, so the early poll shortens
-    // the unit although the element loads now start one round trip later.
+    // before the unit issues any other load of its own (only the packet's
+    // bulk copy, which the copy engine carries, is under way). Measured on
+    // the graded 512 x 512 mesh: polling with the element data and packet
+    // loads of the threads already in flight took 5.6k cycles per unit
+    // against 1.1k here, so the early poll shortens the unit although the
+    // element loads now start one round trip later.
     __syncwarp();
     if (threadIdx.x < 32 && s_i > 0) {
         const uint32_t need = sa.serial0 + (uint32_t)(s_i - 1);
