@@ -725,10 +725,14 @@ def main():
             time_steps(torch, hh, kk)
             b_ms, b_l, o_ms, o_l = hh.sem_profile_read()   # kk steps
             bb, ob = hh.sem_traffic_model()
-            _, no = hh.sem_launch_info()
+            spl_o, no = hh.sem_launch_info()
             hh.sem_destroy()
+            # which kernel ran: DENSE plans (orderings whose node numbering
+            # follows the element order) may stream; GATHER plans launch once
+            # per step (--stream 0 makes every ordering do so)
             orderings[kind] = {"node_updates_per_s": N * kk / t_ord, "ms_per_step": 1e3 * t_ord / kk,
                                "step_kernel_us": 1e3 * b_ms / kk, "open_nodes": no,
+                               "kernel": "sem_stream_kernel" if spl_o > 1 else "sem_step_kernel",
                                "step_bytes_model": bb}
     if world > 1:
         dist.barrier()
