@@ -336,9 +336,11 @@ sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t
  * Section 4.3 along the element order) and the leapfrog scheme where no block
  * shares nodes with more than 64 blocks (itself included); other cases
  * launch once per step. N = -1 (the default) streams 256 steps per launch
- * where a step has fewer element blocks than 8 times the step CTAs resident
- * on the GPU at once (there the partly filled last wave of a launch per step
- * costs more than the units' waits) and launches once per step otherwise.
+ * where a step has at least as many element blocks as step CTAs resident on
+ * the GPU at once and fewer than 8 times as many (there the partly filled
+ * last wave of a launch per step costs more than the units' waits; with
+ * less than one wave streaming only adds the units' waits) and launches
+ * once per step otherwise.
  * Waits are bounded: a wait gives up after 1 s of the GPU's global timer
  * (checked every 64 polls of 128 ns back-off each; in any case after 2^26
  * polls); one that gives up (which no correct run does) raises
