@@ -512,8 +512,10 @@ sem_status sem_batch_info(const sem_batch* b, int32_t* nclasses, int32_t* orders
 
 /* Which order classes stream, before the first sem_batch_step: -1 (the
  * default) streams a class where one step of it has fewer element blocks than
- * 8 times the CTAs resident at once (the rule sem_set_stream(-1) applies to
- * one mesh) and runs the others one launch per step inside the same captured
+ * 8 times the CTAs resident at once (the upper bound of the rule
+ * sem_set_stream(-1) applies to one mesh; a class with less than one wave
+ * streams too, since its shots share the launch) and runs the others one
+ * launch per step inside the same captured
  * block; 1 streams every class; 2 streams none but keeps the captured
  * 64-step blocks with steps taken from the shots' clocks; 0 none (one launch
  * per class and step with step counters, 16-step graphs: the scheme for
