@@ -218,7 +218,14 @@ sem_status sem_set_dt(sem_mesh* m, double dt);
 /* Advance nsteps >= 0 leapfrog steps from the current state (u^0 = u^-1 = 0
  * unless sem_set_state was called; Eq. initial_cond). Asynchronous on the
  * handle's stream. The first call builds the device data (allocation and
- * host-to-device copies). Needs the model and dt. */
+ * host-to-device copies). Needs the model and dt. The nodes shared between
+ * element blocks are finished from per-block partial sums by the next
+ * step's blocks; after a call's last step they stay partial until the next
+ * sem_step call finishes them the same way, or until a call that reads or
+ * replaces the state (sem_get_state, sem_read_wavefield, sem_read_traces,
+ * sem_set_model, a batch step, the gradient) runs one open-node launch
+ * first: what the API returns is the same, bit for bit, however the steps
+ * were split into calls. */
 sem_status sem_step(sem_mesh* m, int64_t nsteps);
 
 /* Number of steps taken so far, n in t_n = n dt (the step counter of the
@@ -319,10 +326,10 @@ sem_status sem_hilbert_cells(int32_t W, int32_t H, int32_t* cells);
 
 /* Launch accounting of the time loop: steps per step-kernel launch (1, or
  * the streamed launch length of sem_set_stream when the time loop is
- * streamed; each sem_step call adds one open-node launch after its last
- * step) and the number of open nodes, i.e. nodes whose elements span more
- * than one element block (-1 before the device data is built). Either
- * pointer may be NULL. */
+ * streamed; a read of the state after a sem_step call adds one open-node
+ * launch, see sem_step) and the number of open nodes, i.e. nodes whose
+ * elements span more than one element block (-1 before the device data is
+ * built). Either pointer may be NULL. */
 sem_status sem_launch_info(const sem_mesh* m, int64_t* steps_per_launch, int64_t* open_nodes);
 
 /* Streamed time loop. With steps_per_launch = N >= 1 sem_step runs up to N

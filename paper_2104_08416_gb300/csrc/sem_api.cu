@@ -73,6 +73,10 @@ struct sem_mesh {
     std::vector<double> host_rho, host_vel;
     int64_t step = 0;
     int64_t stepped_calls = 0;
+    // the open nodes of the last leapfrog step still stand as partial sums:
+    // the next step finishes them as any step does, and a call that reads or
+    // replaces the state first runs the open-node kernel (flush_pending)
+    bool open_pending = false;
     semhost::BlockPlan plan;
     semdev::Plan dplan{};
     int smem = 0;
@@ -810,17 +814,19 @@ sem_status launch_one_step(sem_mesh* m, bool pending);
 // else one launch per step.
 sem_status launch_steps(sem_mesh* m, int64_t nsteps) {
     sem_status st;
+    const bool p0 = m->open_pending;
     for (int64_t k = 0; k < nsteps;) {
         if (streamed(m)) {
             // at most 2^31 - 1 CTAs per launch
             const int64_t cap = std::max<int64_t>(1, 2147483647LL / std::max<int64_t>(1, m->plan.nblocks));
             const int64_t n = std::min<int64_t>(std::min<int64_t>(nsteps - k, stream_len(m)), cap);
-            if ((st = launch_stream_steps(m, n, k > 0)) != SEM_OK) return st;
+            if ((st = launch_stream_steps(m, n, k > 0 || p0)) != SEM_OK) return st;
             k += n;
         } else {
-            if ((st = launch_one_step(m, k > 0)) != SEM_OK) return st;
+            if ((st = launch_one_step(m, k > 0 || p0)) != SEM_OK) return st;
             k += 1;
         }
+        m->open_pending = true;
     }
     return SEM_OK;
 }
@@ -868,6 +874,15 @@ sem_status launch_one_step(sem_mesh* m, bool pending) {
     if (m->profiling) m->ev_block.push_back({e0, e1});
     m->step++;
     return SEM_OK;
+}
+
+sem_status launch_flush(sem_mesh* m);
+// The open nodes of the last step finished (the open-node kernel), if they
+// are still partial sums.
+sem_status flush_pending(sem_mesh* m) {
+    if (!m->open_pending) return SEM_OK;
+    m->open_pending = false;
+    return launch_flush(m);
 }
 
 // After the last launch k of a run: finish the open nodes to level k+1.
@@ -1112,7 +1127,11 @@ sem_status sem_set_model(sem_mesh* m, const double* vel, const double* rho) {
     if (rho) m->rho.assign(rho, rho + ne);
     else m->rho.assign((size_t)ne, 1.0);
     m->have_model = true;
-    if (m->built) return refresh_model(m);
+    if (m->built) {
+        // the pending open nodes belong to the old model's step
+        if (sem_status sf = flush_pending(m)) return sf;
+        return refresh_model(m);
+    }
     return SEM_OK;
 }
 
@@ -1333,11 +1352,11 @@ sem_status sem_step(sem_mesh* m, int64_t nsteps) {
         m->stepped_calls++;
         return SEM_OK;
     }
-    // the first launch reads a fully stored level; later ones finish the
-    // open nodes of the previous launch themselves; the flush completes the
-    // open nodes after the last launch
+    // every launch but the first of a stored level finishes the open nodes
+    // of the previous step itself; those of the last step stay pending until
+    // the next sem_step finishes them the same way, or a read of the state
+    // runs the open-node kernel
     if ((st = launch_steps(m, nsteps)) != SEM_OK) return st;
-    if ((st = launch_flush(m)) != SEM_OK) return st;
     m->stepped_calls++;
     return SEM_OK;
 }
@@ -1355,8 +1374,9 @@ sem_status sem_read_traces(sem_mesh* m, double* out, int64_t cap) {
         std::fill(out, out + (size_t)m->nrec * (size_t)cap, 0.0);
         return SEM_OK;
     }
-    sem_status st = check_stream_error(m);
+    sem_status st = flush_pending(m);
     if (st != SEM_OK) return st;
+    if ((st = check_stream_error(m)) != SEM_OK) return st;
     const int64_t n = std::min(cap, m->step);
     std::fill(out, out + (size_t)m->nrec * (size_t)cap, 0.0);
     if (n > 0) {
@@ -1381,6 +1401,7 @@ sem_status sem_set_state(sem_mesh* m, const double* u, const double* u_prev, int
     if (st != SEM_OK) return st;
     if (m->nrec > 0 && step > m->trace_cap) return fail(m, SEM_ERR_INVALID_ARG, "step beyond max_steps");
     m->step = step;
+    m->open_pending = false;   // the state is replaced whole
     if (m->scheme == SEM_SCHEME_HEUN) {
         if ((st = write_nodes(m, m->d_u[0], u)) != SEM_OK) return st;
         const size_t vb = (size_t)m->mesh.ne * (size_t)m->mesh.P * 2 * tsize(m);
@@ -1410,6 +1431,7 @@ sem_status sem_get_state(sem_mesh* m, double* u, double* u_prev, int64_t* step) 
         if (u_prev) std::fill(u_prev, u_prev + nn, 0.0);
         return SEM_OK;
     }
+    if (sem_status sf = flush_pending(m)) return sf;
     if (sem_status se = check_stream_error(m)) return se;
     std::vector<double> un, tmp;
     if (m->scheme == SEM_SCHEME_HEUN) {
@@ -1820,7 +1842,7 @@ sem_status copy_dev(sem_mesh* m, void* dst, const void* src) {
 sem_status run_steps(sem_mesh* m, int64_t n) {
     sem_status st;
     if ((st = launch_steps(m, n)) != SEM_OK) return st;
-    return n > 0 ? launch_flush(m) : SEM_OK;
+    return flush_pending(m);
 }
 
 }  // namespace
@@ -1849,6 +1871,7 @@ sem_status sem_misfit_gradient(sem_mesh* m, const double* d_obs, int64_t nsteps,
     for (auto* u : m->d_u) SEM_CUDA(cudaMemsetAsync(u, 0, nb, m->stream));
     SEM_CUDA(cudaMemsetAsync(m->d_trace, 0, (size_t)m->nrec * (size_t)m->trace_cap * 8, m->stream));
     m->step = 0;
+    m->open_pending = false;   // the state restarts from rest
     for (int64_t c = 0; c < nchk; ++c) {
         const int64_t n0 = c * kc;
         if ((st = copy_dev(m, m->d_chk[(size_t)(2 * c)], level_u(m, n0))) != SEM_OK) return st;
@@ -2051,6 +2074,7 @@ void unbuild(sem_mesh* m) {
     m->d_chk.clear();
     m->d_seg.clear();
     m->built = false;
+    m->open_pending = false;
     m->step = 0;
     m->d_src = nullptr;
     m->src_cap = 0;
@@ -2474,6 +2498,16 @@ sem_status sem_batch_step(sem_batch* b, int64_t nsteps) {
     sem_status st = batch_prepare(b);
     if (st != SEM_OK) return st;
     if (nsteps == 0) return SEM_OK;
+    // a shot stepped on its own since the last batch step: its open nodes
+    // finished first (the batch starts from stored levels)
+    bool flushed = false;
+    for (auto* m : b->shots) {
+        if (!m->open_pending) continue;
+        flushed = true;
+        if ((st = flush_pending(m)) != SEM_OK) return bfail(b, st, m->err);
+    }
+    if (flushed && cudaStreamSynchronize(b->shots[0]->stream) != cudaSuccess)
+        return bfail(b, SEM_ERR_CUDA, "open-node launch failed");
     for (auto* m : b->shots) {
         if (m->nrec > 0 && m->step + nsteps > m->trace_cap)
             return bfail(b, SEM_ERR_INVALID_ARG, "steps beyond a shot's receiver max_steps");

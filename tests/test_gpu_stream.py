@@ -65,6 +65,31 @@ def test_streamed_bitwise_per_step(n, p, prec, eb, calls):
         assert np.array_equal(tr, tr0), (stream, rel_l2(tr, tr0))
 
 
+@pytest.mark.parametrize("prec,stream", [("fp32_kahan", 0), ("fp32_kahan", 256), ("fp64", 0), ("fp32", 3)])
+def test_calls_and_reads_bitwise(prec, stream):
+    """The open nodes of a call's last step stay partial sums until the next
+    call or a read: one call, split calls, and split calls with a state read
+    between them (which finishes the open nodes first) give the same bits,
+    and the read in the middle equals a run that stops there."""
+    P = need_gpu()
+    m = gen.graded(40, seed=17)
+    one = _run(P, m, 4, prec, "hilbert", 16, stream, [41])
+    split = _run(P, m, 4, prec, "hilbert", 16, stream, [17, 1, 23])
+    h = _handle(P, m, 4, prec, "hilbert", 16, stream, 41)
+    h.sem_step(17)
+    mid = h.sem_read_wavefield()
+    mid_u, mid_prev, mid_step = h.sem_get_state()
+    h.sem_step(1)
+    h.sem_read_traces()
+    h.sem_step(23)
+    read_between = (h.sem_read_wavefield(), h.sem_read_traces())
+    h.sem_destroy()
+    stop = _run(P, m, 4, prec, "hilbert", 16, stream, [17])
+    for got in (split, read_between):
+        assert np.array_equal(got[0], one[0]) and np.array_equal(got[1], one[1])
+    assert mid_step == 17 and np.array_equal(mid, stop[0]) and np.array_equal(mid_u, stop[0])
+
+
 def test_streamed_against_oracle():
     P = need_gpu()
     m = gen.graded(36, seed=9)
