@@ -2162,7 +2162,8 @@ sem_status batch_launch_step(sem_batch* b) {
     const bool f64 = b->prec == SEM_FP64;
     const int mode = b->prec == SEM_FP32_KAHAN ? semdev::MODE_KAHAN : semdev::MODE_THREE_LEVEL;
     for (auto& c : b->classes) {
-        semdev::BatchArgs ba{b->d_desc, c.d_cta_shot, c.d_cta_block, b->d_step, b->d_pending};
+        // step counters, no clocks (clock = nullptr, offset = 0)
+        semdev::BatchArgs ba{b->d_desc, c.d_cta_shot, c.d_cta_block, b->d_step, b->d_pending, nullptr, 0};
         const sem_mesh* m0 = nullptr;
         for (auto* m : b->shots)
             if (m->mesh.np == c.np) {
