@@ -51,7 +51,7 @@ def test_graded_stiffness_whole_field(P, graded):
     rng = np.random.default_rng(11)
     u = rng.standard_normal(S.n_nodes)
     ref = S.apply_K(u)
-    # FP32: the benchmark spec's 1e-5, or the FP32 forward error bound if tighter
+    # FP32: the stated 1e-5, or the FP32 forward error bound if tighter
     for prec, tol in (("fp64", FP64_TOL), ("fp32_kahan", min(FP32_TOL, fp32_apply_bound(S, u)))):
         h = _handle(P, m, prec)
         ku = h.sem_apply_stiffness(u)

@@ -48,7 +48,7 @@ def test_stiffness_apply(P, p, prec):
     fields = [rng.standard_normal(S.n_nodes), np.sin(3 * xy[:, 0]) * np.cos(2 * xy[:, 1])]
     refs = [S.apply_K(u) for u in fields]
     # FP64: the stated 1e-12. FP32: the forward error bound of the FP32
-    # evaluation (fp32_apply_bound), and the benchmark spec's 1e-5 on white noise,
+    # evaluation (fp32_apply_bound), and the stated 1e-5 on white noise,
     # where the operator is well conditioned
     tols = ([FP64_TOL, FP64_TOL] if prec == "fp64" else
             [min(FP32_TOL, fp32_apply_bound(S, fields[0])), fp32_apply_bound(S, fields[1])])
