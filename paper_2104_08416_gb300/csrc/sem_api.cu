@@ -91,6 +91,10 @@ struct sem_mesh {
     int32_t dep_stride = 0;
     uint32_t* d_done = nullptr;
     unsigned long long* d_counter = nullptr;
+    // the counter's value when the next streamed launch starts: every CTA of
+    // a launch takes exactly one ticket, so it grows by the launch's units
+    // and needs no reset between launches
+    unsigned long long ticket_base = 0;
     int32_t* d_err = nullptr;
     uint32_t serial = 1;              // serial of the next streamed step
     int64_t hold_step = -1;           // test hook: (step, block) whose done flag is withheld
@@ -573,6 +577,7 @@ sem_status build(sem_mesh* m) {
         if ((st = zeros(m, &ctr, 8)) != SEM_OK) return st;
         m->d_done = (uint32_t*)done;
         m->d_counter = (unsigned long long*)ctr;
+        m->ticket_base = 0;
         m->serial = 1;
         int res = 0;
         SEM_CUDA(semdev::stream_resident_ctas(M.np, fp64(m), md, m->d_G32 != nullptr, m->threads, m->smem, &res));
@@ -767,7 +772,7 @@ sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
         sa.tiled_units = (n / T) * T * m->plan.nblocks;
     }
     sa.counter = m->d_counter;
-    sa.base = 0;
+    sa.base = m->ticket_base;
     sa.done = m->d_done;
     sa.dep = m->d_dep;
     sa.dep_stride = m->dep_stride;
@@ -788,7 +793,6 @@ sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
         if (!e0 || !e1) return fail(m, SEM_ERR_CUDA, "cudaEventCreate failed");
     }
     cudaError_t e = e0 ? cudaEventRecord(e0, m->stream) : cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_counter, 0, 8, m->stream);
     if (e == cudaSuccess) {
         if (fp64(m)) {
             auto d = shot_desc<double>(m);
@@ -804,6 +808,7 @@ sem_status launch_stream_steps(sem_mesh* m, int64_t n, bool pending) {
     if (e != cudaSuccess) return cuda_fail(m, e, "streamed step launch");
     if (m->profiling) m->ev_block.push_back({e0, e1});
     m->serial += (uint32_t)n;
+    m->ticket_base += (unsigned long long)n * (unsigned long long)m->plan.nblocks;
     m->step += n;
     return SEM_OK;
 }
