@@ -542,6 +542,7 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
             if (!mbar_pre) __syncthreads();
             if (__syncthreads_or(!mbar_wait(mbk))) {
                 if (tid == 0 && a.err) atomicExch(a.err, 1);
+                if (pl.dense) mbar_wait(mbu);   // the copy of u in flight, bounded too
                 return;
             }
         } else {
@@ -640,6 +641,7 @@ __device__ __forceinline__ void step_block(const Plan& pl, const StepArgs<T>& a,
     cp_async_wait_all();
     if (__syncthreads_or(!staged_ok)) {
         if (tid == 0 && a.err) atomicExch(a.err, 1);
+        if (bulk) mbar_wait(mbu);   // once more (bounded) for the copy of u in flight
         return;
     }
     if (pending && h.nro > 0) {
